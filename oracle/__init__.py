@@ -1,0 +1,232 @@
+"""Python face of the FP64 CPU oracle (``oracle/tvc_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+the CPU-baseline leg of ``bench.py`` may import this package.  It shares no
+code with the CUDA library and never imports it.
+
+The C file is compiled with gcc on first use (or by ``build()``) into
+``oracle/_build/liboracle.so``.  Every function takes and returns numpy
+arrays; vectors are FP64.
+
+Parity is pinned for every function here (see tests/test_oracle_pins.py):
+closed forms, brute-force unfolding, library routines (numpy einsum, SVD,
+torch dtype conversions), Eq. 3's touched-memory model, Algorithm 1's
+contraction count and the paper's Table 1.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+__all__ = [
+    "F64", "F32", "BF16", "E4M3", "build", "tvc", "tvc_grad_x", "tvc_grad_A",
+    "hopm", "hopm3", "quantise", "decode_bf16", "decode_e4m3",
+    "bf16_from_f32", "e4m3_from_f32", "dequantise", "OracleError",
+]
+
+F64, F32, BF16, E4M3 = 0, 1, 2, 3
+_DTYPE_OF = {np.dtype(np.float64): F64, np.dtype(np.float32): F32,
+             np.dtype(np.uint16): BF16, np.dtype(np.uint8): E4M3}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "tvc_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+class OracleError(RuntimeError):
+    """Non-zero status from an oracle routine (1 = bad argument,
+    5 = zero norm, 6 = non-finite value)."""
+
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: oracle status {status}")
+        self.status = status
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (IEEE semantics: no FMA contraction)."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-shared", "-fPIC",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            P, I, D, L = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64
+            lib.oracle_tvc.argtypes = [I, P, P, I, P, I, P, P, D, D]
+            lib.oracle_tvc_grad_x.argtypes = [I, P, P, I, P, I, P, P]
+            lib.oracle_tvc_grad_A.argtypes = [I, P, I, P, P, P]
+            for f in (lib.oracle_hopm, lib.oracle_hopm3):
+                f.argtypes = [I, P, P, I, P, P, I, D, P, P, P, P, P]
+            lib.oracle_quantise.argtypes = [I, P, I, P, P, P, I]
+            lib.oracle_decode_bf16.argtypes = [ctypes.c_uint16]
+            lib.oracle_decode_bf16.restype = D
+            lib.oracle_decode_e4m3.argtypes = [ctypes.c_uint8]
+            lib.oracle_decode_e4m3.restype = D
+            lib.oracle_bf16_from_f32.argtypes = [ctypes.c_float, I]
+            lib.oracle_bf16_from_f32.restype = ctypes.c_uint16
+            lib.oracle_e4m3_from_f32.argtypes = [ctypes.c_float]
+            lib.oracle_e4m3_from_f32.restype = ctypes.c_uint8
+            _lib = lib
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _dims(dims):
+    return np.ascontiguousarray(np.asarray(dims, dtype=np.int64))
+
+
+def _tensor(A, dims):
+    A = np.ascontiguousarray(A)
+    if A.dtype not in _DTYPE_OF:
+        raise TypeError(f"unsupported tensor dtype {A.dtype}")
+    dims = A.shape if dims is None else dims
+    d = _dims(dims)
+    if int(np.prod(d)) != A.size:
+        raise ValueError("dims do not match the tensor size")
+    return A, d, _DTYPE_OF[A.dtype]
+
+
+def _scales(dt, scales, n0):
+    if dt in (BF16, E4M3):
+        if scales is None:
+            raise ValueError("narrow storage needs per-slab scales")
+        s = np.ascontiguousarray(np.asarray(scales, dtype=np.float32))
+        if s.size != n0:
+            raise ValueError("one scale per slab A[i0] is required")
+        return s
+    return None
+
+
+def tvc(A, mode: int, x, *, dims=None, scales=None, y=None, alpha=1.0, beta=0.0) -> np.ndarray:
+    """Y = alpha * (A x_mode x) + beta * Y in FP64 (shape: dims without mode)."""
+    A, d, dt = _tensor(A, dims)
+    s = _scales(dt, scales, int(d[0]))
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+    if not 0 <= mode < d.size or x.size != d[mode]:
+        raise ValueError("bad mode or vector length")
+    out_shape = tuple(int(n) for i, n in enumerate(d) if i != mode)
+    out = (np.zeros(out_shape) if y is None else
+           np.ascontiguousarray(np.asarray(y, dtype=np.float64)).reshape(out_shape).copy())
+    st = _load().oracle_tvc(dt, _p(A), _p(s), int(d.size), _p(d), int(mode), _p(x), _p(out),
+                            float(alpha), float(beta))
+    if st:
+        raise OracleError(st, "tvc")
+    return out
+
+
+def tvc_grad_x(A, mode: int, gy, *, dims=None, scales=None) -> np.ndarray:
+    """gx[j] = sum_{i,l} A[i][j][l] gy[i][l] (adjoint of the contraction in x)."""
+    A, d, dt = _tensor(A, dims)
+    s = _scales(dt, scales, int(d[0]))
+    gy = np.ascontiguousarray(np.asarray(gy, dtype=np.float64)).ravel()
+    gx = np.zeros(int(d[mode]))
+    st = _load().oracle_tvc_grad_x(dt, _p(A), _p(s), int(d.size), _p(d), int(mode), _p(gy), _p(gx))
+    if st:
+        raise OracleError(st, "tvc_grad_x")
+    return gx
+
+
+def tvc_grad_A(dims, mode: int, x, gy) -> np.ndarray:
+    """gA[i][j][l] = gy[i][l] x[j] (adjoint of the contraction in A)."""
+    d = _dims(dims)
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+    gy = np.ascontiguousarray(np.asarray(gy, dtype=np.float64)).ravel()
+    gA = np.zeros(tuple(int(n) for n in d))
+    st = _load().oracle_tvc_grad_A(int(d.size), _p(d), int(mode), _p(x), _p(gy), _p(gA))
+    if st:
+        raise OracleError(st, "tvc_grad_A")
+    return gA
+
+
+def _hopm(fn, A, xs, iters, tol, dims, scales):
+    A, d, dt = _tensor(A, dims)
+    s = _scales(dt, scales, int(d[0]))
+    if len(xs) != d.size:
+        raise ValueError("one start vector per mode")
+    x = np.ascontiguousarray(np.concatenate([np.asarray(v, dtype=np.float64).ravel() for v in xs]))
+    if x.size != int(d.sum()):
+        raise ValueError("start vector lengths do not match dims")
+    lam = np.zeros(1)
+    sweeps = np.zeros(1, dtype=np.int32)
+    hist = np.zeros(max(iters, 1))
+    touched = np.zeros(max(iters, 1), dtype=np.int64)
+    tvcs = np.zeros(1, dtype=np.int64)
+    st = fn(dt, _p(A), _p(s), int(d.size), _p(d), _p(x), int(iters), float(tol), _p(lam),
+            _p(sweeps), _p(hist), _p(touched), _p(tvcs))
+    offs = np.concatenate([[0], np.cumsum(d)])
+    out_x = [x[offs[m]:offs[m + 1]].copy() for m in range(d.size)]
+    n = int(sweeps[0])
+    return dict(status=int(st), x=out_x, lam=float(lam[0]), sweeps=n, lam_hist=hist[:n].copy(),
+                touched=touched[:n].copy(), tvcs=int(tvcs[0]))
+
+
+def hopm(A, xs, iters: int, tol: float = 0.0, *, dims=None, scales=None) -> dict:
+    """Canonical Gauss-Seidel HOPM (Section 3).  Returns a dict with x (list),
+    lam, sweeps, lam_hist, touched (Eq. 3 element counts per sweep), tvcs and
+    status (0, or 5 zero norm / 6 non-finite: x keeps its last valid state)."""
+    return _hopm(_load().oracle_hopm, A, xs, iters, tol, dims, scales)
+
+
+def hopm3(A, xs, iters: int, tol: float = 0.0, *, dims=None, scales=None) -> dict:
+    """Three-buffer HOPM of Algorithm 1 (p = 1); same outputs as :func:`hopm`."""
+    return _hopm(_load().oracle_hopm3, A, xs, iters, tol, dims, scales)
+
+
+def quantise(src, fmt: int, *, truncate: bool = False):
+    """Per-slab quantisation of an FP32 tensor: returns (codes, scales)."""
+    src = np.ascontiguousarray(np.asarray(src, dtype=np.float32))
+    d = _dims(src.shape)
+    codes = np.zeros(src.shape, dtype=np.uint8 if fmt == E4M3 else np.uint16)
+    scales = np.zeros(int(d[0]), dtype=np.float32)
+    st = _load().oracle_quantise(int(fmt), _p(src), int(d.size), _p(d), _p(codes), _p(scales),
+                                 int(bool(truncate)))
+    if st:
+        raise OracleError(st, "quantise")
+    return codes, scales
+
+
+def decode_bf16(code: int) -> float:
+    return _load().oracle_decode_bf16(int(code))
+
+
+def decode_e4m3(code: int) -> float:
+    return _load().oracle_decode_e4m3(int(code))
+
+
+def bf16_from_f32(f: float, truncate: bool = False) -> int:
+    return int(_load().oracle_bf16_from_f32(float(f), int(bool(truncate))))
+
+
+def e4m3_from_f32(f: float) -> int:
+    return int(_load().oracle_e4m3_from_f32(float(f)))
+
+
+def dequantise(codes, scales) -> np.ndarray:
+    """FP64 values scale[i0] * decode(code) of a narrow tensor (via the
+    oracle's own decoders, one code at a time through a 256/65536 table)."""
+    codes = np.asarray(codes)
+    if codes.dtype == np.uint8:
+        table = np.array([decode_e4m3(c) for c in range(256)])
+    elif codes.dtype == np.uint16:
+        table = np.array([decode_bf16(c) for c in range(65536)])
+    else:
+        raise TypeError("codes must be uint8 (E4M3) or uint16 (BF16)")
+    vals = table[codes]
+    s = np.asarray(scales, dtype=np.float64).reshape((-1,) + (1,) * (codes.ndim - 1))
+    return vals * s

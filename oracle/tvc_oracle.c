@@ -1,0 +1,442 @@
+/*
+ * Oracle for the tensor-vector contraction (TVC) and the higher-order power
+ * method (HOPM).  TEST INFRASTRUCTURE ONLY: nothing in the library's product
+ * path may call, link or load this file.  It is plain, slow and written to be
+ * checked against the paper by eye: FP64 loop nests, no blocking, no fusion,
+ * no reordering beyond what each definition states.  It shares no code with
+ * the CUDA path.
+ *
+ * Paper: Martinez-Ferrer, Yzelman, Beltran, "Distributed and heterogeneous
+ * tensor-vector contraction algorithms for high performance computing"
+ * (arXiv 2501.03121).
+ *
+ * Storage (Section 3): dense tensors in last-order ("C row-major") layout,
+ * zero-based indices, N = prod(n_i) elements.  The mode-k contraction
+ * Y = A x_k x keeps the other d-1 modes; viewed through u = prod_{i<k} n_i
+ * and v = prod_{i>k} n_i the tensor is a u x n_k x v array and
+ *     Y[i][l] = sum_{j<n_k} A[i][j][l] x[j].
+ *
+ * Element types of A: FP64, FP32, BF16 (upper half of binary32) and
+ * FP8 E4M3 (OCP 8-bit floating point, bias 7, max 448, no infinities).  The
+ * two narrow types carry one FP32 scale per slab A[i_0, ...]; an element's
+ * value is scale[i_0] * decode(code), promoted to FP64 before any arithmetic
+ * (the storage-only use of low precision of Section 5.5).
+ *
+ * Build: gcc -O2 -ffp-contract=off -fopenmp -shared -fPIC (IEEE semantics,
+ * no fused multiply-add, no reassociation).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_F64 0
+#define OR_F32 1
+#define OR_BF16 2
+#define OR_E4M3 3
+
+#define OR_OK 0
+#define OR_ERR_ARG 1
+#define OR_ERR_ZERO_NORM 5
+#define OR_ERR_NONFINITE 6
+
+#define OR_MAXD 16
+
+/* ---------------------------------------------------------------- decoding */
+
+/* BF16: the code is the upper 16 bits of a binary32 (Section 5.5). */
+double oracle_decode_bf16(uint16_t code) {
+  uint32_t bits = ((uint32_t)code) << 16;
+  float f;
+  memcpy(&f, &bits, 4);
+  return (double)f;
+}
+
+/* E4M3 per the OCP FP8 definition: s.eeee.mmm, bias 7; e = 0 is subnormal
+ * (m/8 * 2^-6); s.1111.111 is NaN; everything else (1 + m/8) * 2^(e-7). */
+double oracle_decode_e4m3(uint8_t code) {
+  int s = (code >> 7) & 1;
+  int e = (code >> 3) & 15;
+  int m = code & 7;
+  double mag;
+  if (e == 15 && m == 7) return NAN;
+  if (e == 0)
+    mag = ldexp((double)m / 8.0, -6);
+  else
+    mag = ldexp(1.0 + (double)m / 8.0, e - 7);
+  return s ? -mag : mag;
+}
+
+/* Value of element f of A, promoted to FP64.  slab = N / n_0. */
+static double elem(int dtype, const void* A, const float* scales, int64_t slab, int64_t f) {
+  switch (dtype) {
+    case OR_F64: return ((const double*)A)[f];
+    case OR_F32: return (double)((const float*)A)[f];
+    case OR_BF16: return (double)scales[f / slab] * oracle_decode_bf16(((const uint16_t*)A)[f]);
+    case OR_E4M3: return (double)scales[f / slab] * oracle_decode_e4m3(((const uint8_t*)A)[f]);
+  }
+  return NAN;
+}
+
+static int valid_shape(int order, const int64_t* dims) {
+  if (order < 1 || order > OR_MAXD) return 0;
+  for (int i = 0; i < order; i++)
+    if (dims[i] < 1) return 0;
+  return 1;
+}
+
+static int64_t prod(const int64_t* dims, int lo, int hi) {
+  int64_t p = 1;
+  for (int i = lo; i < hi; i++) p *= dims[i];
+  return p;
+}
+
+/* -------------------------------------------------------------------- TVC */
+
+/* Y := alpha * (A x_k x) + beta * Y (Section 3 definition, with the BLAS-like
+ * scalars of Eq. 1 for p = 1).  beta == 0 means Y is not read.  x has n_k
+ * entries, Y has u*v entries in row-major order of the remaining modes. */
+int oracle_tvc(int dtype, const void* A, const float* scales, int order, const int64_t* dims,
+               int mode, const double* x, double* y, double alpha, double beta) {
+  if (!valid_shape(order, dims) || mode < 0 || mode >= order) return OR_ERR_ARG;
+  int64_t u = prod(dims, 0, mode), nk = dims[mode], v = prod(dims, mode + 1, order);
+  int64_t slab = prod(dims, 1, order);
+  int64_t nout = u * v;
+#pragma omp parallel for schedule(static)
+  for (int64_t o = 0; o < nout; o++) {
+    int64_t i = o / v, l = o % v;
+    double s = 0.0;
+    for (int64_t j = 0; j < nk; j++) s += elem(dtype, A, scales, slab, (i * nk + j) * v + l) * x[j];
+    y[o] = (beta != 0.0) ? alpha * s + beta * y[o] : alpha * s;
+  }
+  return OR_OK;
+}
+
+/* ---------------------------------------------------------- TVC gradients */
+
+/* Gradient of L(Y) with Y = A x_k x, with respect to x:
+ *     gx[j] = sum_{i,l} A[i][j][l] * gy[i][l]. */
+int oracle_tvc_grad_x(int dtype, const void* A, const float* scales, int order, const int64_t* dims,
+                      int mode, const double* gy, double* gx) {
+  if (!valid_shape(order, dims) || mode < 0 || mode >= order) return OR_ERR_ARG;
+  int64_t u = prod(dims, 0, mode), nk = dims[mode], v = prod(dims, mode + 1, order);
+  int64_t slab = prod(dims, 1, order);
+#pragma omp parallel for schedule(static)
+  for (int64_t j = 0; j < nk; j++) {
+    double s = 0.0;
+    for (int64_t i = 0; i < u; i++)
+      for (int64_t l = 0; l < v; l++) s += elem(dtype, A, scales, slab, (i * nk + j) * v + l) * gy[i * v + l];
+    gx[j] = s;
+  }
+  return OR_OK;
+}
+
+/* Gradient with respect to A: gA[i][j][l] = gy[i][l] * x[j] (rank-1). */
+int oracle_tvc_grad_A(int order, const int64_t* dims, int mode, const double* x, const double* gy,
+                      double* gA) {
+  if (!valid_shape(order, dims) || mode < 0 || mode >= order) return OR_ERR_ARG;
+  int64_t u = prod(dims, 0, mode), nk = dims[mode], v = prod(dims, mode + 1, order);
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < u; i++)
+    for (int64_t j = 0; j < nk; j++)
+      for (int64_t l = 0; l < v; l++) gA[(i * nk + j) * v + l] = gy[i * v + l] * x[j];
+  return OR_OK;
+}
+
+/* ------------------------------------------------------------------ HOPM */
+
+/* A working tensor of the power method: its data (FP64, or the typed input
+ * tensor when `typed` is set), the original mode ids it still carries, and
+ * their sizes.  Contracted modes are dropped (they would be of size one). */
+typedef struct {
+  int typed;
+  int dtype;
+  const void* A;
+  const float* scales;
+  int64_t slab;
+  double* data;
+  int nd;
+  int modes[OR_MAXD];
+  int64_t dims[OR_MAXD];
+} otensor;
+
+static int64_t osize(const otensor* t) { return prod(t->dims, 0, t->nd); }
+
+/* out = t x_m x_m (m is an ORIGINAL mode id that t still carries).
+ * Counts touched elements: the whole input, the whole output, the vector. */
+static int ocontract(const otensor* t, int m, const double* xm, otensor* out, int64_t* touched) {
+  int p = -1;
+  for (int q = 0; q < t->nd; q++)
+    if (t->modes[q] == m) p = q;
+  if (p < 0) return OR_ERR_ARG;
+  int64_t u = prod(t->dims, 0, p), nk = t->dims[p], v = prod(t->dims, p + 1, t->nd);
+  out->typed = 0;
+  out->nd = t->nd - 1;
+  for (int q = 0, r = 0; q < t->nd; q++)
+    if (q != p) {
+      out->modes[r] = t->modes[q];
+      out->dims[r] = t->dims[q];
+      r++;
+    }
+  out->data = (double*)malloc(sizeof(double) * (size_t)(u * v));
+  if (!out->data) return OR_ERR_ARG;
+  if (t->typed) {
+    oracle_tvc(t->dtype, t->A, t->scales, t->nd, t->dims, p, xm, out->data, 1.0, 0.0);
+  } else {
+    oracle_tvc(OR_F64, t->data, NULL, t->nd, t->dims, p, xm, out->data, 1.0, 0.0);
+  }
+  if (touched) *touched += osize(t) + u * v + nk;
+  return OR_OK;
+}
+
+static void ofree(otensor* t) {
+  if (!t->typed && t->data) free(t->data);
+  t->data = NULL;
+}
+
+/* Normalisation x_j <- T / ||T||_2 (FP64).  Reads T twice and writes x_j:
+ * the 3 n term of Eq. 3.  Returns the norm through *sigma. */
+static int onormalise(const double* T, int64_t n, double* xj, double* sigma, int64_t* touched) {
+  double ss = 0.0;
+  for (int64_t i = 0; i < n; i++) ss += T[i] * T[i];
+  double s = sqrt(ss);
+  if (touched) *touched += 3 * n;
+  *sigma = s;
+  if (!isfinite(s)) return OR_ERR_NONFINITE;
+  if (s == 0.0) return OR_ERR_ZERO_NORM;
+  for (int64_t i = 0; i < n; i++) xj[i] = T[i] / s;
+  return OR_OK;
+}
+
+static void base_tensor(otensor* t, int dtype, const void* A, const float* scales, int order,
+                        const int64_t* dims) {
+  t->typed = 1;
+  t->dtype = dtype;
+  t->A = A;
+  t->scales = scales;
+  t->slab = prod(dims, 1, order);
+  t->data = NULL;
+  t->nd = order;
+  for (int q = 0; q < order; q++) {
+    t->modes[q] = q;
+    t->dims[q] = dims[q];
+  }
+}
+
+/* Stopping rule (the paper states none): after sweep t >= 2 stop when
+ * tol > 0 and |lambda_t - lambda_{t-1}| <= tol * lambda_t. */
+static int converged(double lam, double prev, int t, double tol) {
+  if (t < 2 || !(tol > 0.0)) return 0;
+  double scale = lam > 1e-300 ? lam : 1e-300;
+  return fabs(lam - prev) <= tol * scale;
+}
+
+/* Canonical (two-buffer) Gauss-Seidel HOPM, Section 3: in each sweep, for
+ * every external mode j = 0..d-1 in ascending order, contract A with every
+ * other x_m in ascending m, normalise the resulting n_j-vector into x_j.
+ * lambda_t = the norm of the last update (j = d-1) of sweep t.
+ * x holds x_0..x_{d-1} back to back (in/out).  x_0's input value is unused.
+ * touched (nullable) accumulates Eq. 3's streamed-element count per sweep:
+ * entry t-1 gets sweep t's count.  tvcs (nullable) counts contractions. */
+int oracle_hopm(int dtype, const void* A, const float* scales, int order, const int64_t* dims,
+                double* x, int iters, double tol, double* lambda_out, int* sweeps_out,
+                double* lambda_hist, int64_t* touched, int64_t* tvcs) {
+  if (!valid_shape(order, dims) || order < 2 || iters < 0) return OR_ERR_ARG;
+  int64_t off[OR_MAXD + 1];
+  off[0] = 0;
+  for (int m = 0; m < order; m++) off[m + 1] = off[m] + dims[m];
+  double lam = 0.0, prev = 0.0;
+  int status = OR_OK, t;
+  for (t = 1; t <= iters; t++) {
+    int64_t tc = 0;
+    for (int j = 0; j < order && status == OR_OK; j++) {
+      otensor cur;
+      base_tensor(&cur, dtype, A, scales, order, dims);
+      for (int m = 0; m < order; m++) {
+        if (m == j) continue;
+        otensor nxt;
+        status = ocontract(&cur, m, x + off[m], &nxt, &tc);
+        ofree(&cur);
+        cur = nxt;
+        if (tvcs) (*tvcs)++;
+        if (status != OR_OK) break;
+      }
+      if (status != OR_OK) {
+        ofree(&cur);
+        break;
+      }
+      double sigma;
+      status = onormalise(cur.data, dims[j], x + off[j], &sigma, &tc);
+      ofree(&cur);
+      if (j == order - 1 && status == OR_OK) lam = sigma;
+    }
+    if (touched) touched[t - 1] = tc;
+    if (status != OR_OK) break;
+    if (lambda_hist) lambda_hist[t - 1] = lam;
+    if (converged(lam, prev, t, tol)) {
+      prev = lam;
+      break;
+    }
+    prev = lam;
+  }
+  if (lambda_out) *lambda_out = lam;
+  if (sweeps_out) *sweeps_out = (t > iters) ? iters : t;
+  return status;
+}
+
+/* Three-buffer HOPM of Algorithm 1 for one process (p = 1): the external
+ * iteration j reuses the prefix W_{j-1} = A x_0 x_0 ... x_{j-2} x_{j-2}
+ * (ORIGINAL mode ids throughout).  Per iteration j, with
+ *     a = (j > 0 ? 0 : 1),  mu = max(a, j),  nu = (j < d-1 ? d-1 : d-2):
+ *   j < 2 :  Y_a := W_j <- A x_a x_a
+ *   j >= 2:  Y_{mu-1} := W_j <- W_{j-1} x_{mu-1} x_{mu-1}
+ *   Y_{mu+1} <- Y_{mu+a-1} x_{mu+1} x_{mu+1}     (skipped when mu+1 > d-1)
+ *   Y_k <- Y_{k-1} x_k x_k for k = mu+2 .. nu
+ *   x_j <- Y_nu / ||Y_nu||.
+ * The skip of the second step when mu+1 > d-1 is the reading under which the
+ * algorithm saves (d-1)(d-2)/2 contractions per sweep.  Same stopping rule,
+ * outputs and counters as oracle_hopm. */
+int oracle_hopm3(int dtype, const void* A, const float* scales, int order, const int64_t* dims,
+                 double* x, int iters, double tol, double* lambda_out, int* sweeps_out,
+                 double* lambda_hist, int64_t* touched, int64_t* tvcs) {
+  if (!valid_shape(order, dims) || order < 2 || iters < 0) return OR_ERR_ARG;
+  int d = order;
+  int64_t off[OR_MAXD + 1];
+  off[0] = 0;
+  for (int m = 0; m < d; m++) off[m + 1] = off[m] + dims[m];
+  double lam = 0.0, prev = 0.0;
+  int status = OR_OK, t;
+  otensor Abase;
+  base_tensor(&Abase, dtype, A, scales, order, dims);
+  for (t = 1; t <= iters; t++) {
+    int64_t tc = 0;
+    otensor W;  /* W_{j-1}, carried from iteration j-1 */
+    W.typed = 0;
+    W.data = NULL;
+    for (int j = 0; j < d && status == OR_OK; j++) {
+      int a = (j > 0) ? 0 : 1;
+      int mu = (a > j) ? a : j;
+      int nu = (j < d - 1) ? d - 1 : d - 2;
+      otensor Y[OR_MAXD + 1];
+      int have[OR_MAXD + 1];
+      memset(have, 0, sizeof(have));
+      otensor Wj;
+      if (j < 2) {
+        status = ocontract(&Abase, a, x + off[a], &Wj, &tc);
+      } else {
+        status = ocontract(&W, mu - 1, x + off[mu - 1], &Wj, &tc);
+      }
+      if (tvcs) (*tvcs)++;
+      if (status != OR_OK) break;
+      int widx = (j < 2) ? a : mu - 1;
+      Y[widx] = Wj; /* aliases W_j: not freed through Y */
+      have[widx] = 2;
+      if (mu + 1 <= d - 1) {
+        int src = mu + a - 1;
+        status = ocontract(&Y[src], mu + 1, x + off[mu + 1], &Y[mu + 1], &tc);
+        if (tvcs) (*tvcs)++;
+        if (status == OR_OK) have[mu + 1] = 1;
+      }
+      for (int k = mu + 2; k <= nu && status == OR_OK; k++) {
+        status = ocontract(&Y[k - 1], k, x + off[k], &Y[k], &tc);
+        if (tvcs) (*tvcs)++;
+        if (status == OR_OK) have[k] = 1;
+      }
+      double sigma = 0.0;
+      if (status == OR_OK) status = onormalise(Y[nu].data, dims[j], x + off[j], &sigma, &tc);
+      if (j == d - 1 && status == OR_OK) lam = sigma;
+      for (int k = 0; k <= d; k++)
+        if (have[k] == 1) ofree(&Y[k]);
+      ofree(&W);
+      W = Wj;
+    }
+    ofree(&W);
+    if (touched) touched[t - 1] = tc;
+    if (status != OR_OK) break;
+    if (lambda_hist) lambda_hist[t - 1] = lam;
+    if (converged(lam, prev, t, tol)) {
+      prev = lam;
+      break;
+    }
+    prev = lam;
+  }
+  if (lambda_out) *lambda_out = lam;
+  if (sweeps_out) *sweeps_out = (t > iters) ? iters : t;
+  return status;
+}
+
+/* --------------------------------------------------------------- storage */
+
+/* Round-to-nearest-even of a binary32 to BF16 (upper 16 bits).  With
+ * truncate != 0 the lower half is simply dropped, the paper's "brain"
+ * conversion (Section 5.5).  NaN maps to 0x7FC0 with the input's sign. */
+uint16_t oracle_bf16_from_f32(float f, int truncate) {
+  uint32_t b;
+  memcpy(&b, &f, 4);
+  if (isnan(f)) return (uint16_t)(((b >> 16) & 0x8000u) | 0x7FC0u);
+  if (truncate) return (uint16_t)(b >> 16);
+  uint32_t lsb = (b >> 16) & 1u;
+  b += 0x7FFFu + lsb;
+  return (uint16_t)(b >> 16);
+}
+
+/* Round a binary32 to E4M3 to nearest, ties to even, saturating to +-448
+ * (OCP "satfinite" conversion); NaN -> 0x7F.  The E4M3 magnitudes in code
+ * order form a grid whose spacing is 2^-9 below 2^-6 and 2^(e-3) in the
+ * binade [2^e, 2^(e+1)); the code of a magnitude is its grid index. */
+uint8_t oracle_e4m3_from_f32(float f) {
+  if (isnan(f)) return 0x7F;
+  uint8_t s = signbit(f) ? 0x80 : 0x00;
+  double a = fabs((double)f);
+  if (a >= 448.0) return s | 0x7E;
+  double r;
+  int code;
+  if (a < ldexp(1.0, -6)) {
+    r = nearbyint(a / ldexp(1.0, -9)); /* 0..8, exact quotient */
+    code = (int)r;
+  } else {
+    int e2;
+    frexp(a, &e2); /* a = f * 2^e2, f in [0.5, 1): binade exponent e = e2-1 */
+    int e = e2 - 1;
+    r = nearbyint(a / ldexp(1.0, e - 3)); /* 8..16 */
+    if (r >= 16.0) {
+      e += 1;
+      r = 8.0;
+    }
+    code = ((e + 7) << 3) | ((int)r - 8);
+    if (code > 0x7E) code = 0x7E;
+  }
+  return (uint8_t)(s | code);
+}
+
+/* Per-slab quantisation of an FP32 tensor (slab = A[i_0, ...], N/n_0
+ * elements).  E4M3: scale = amax(slab) / 448 in FP32 (1 when the slab is all
+ * zero), code = E4M3(value / scale) with the FP32 quotient.  BF16: scale = 1,
+ * code = BF16(value) (RNE, or truncation when truncate != 0). */
+int oracle_quantise(int dtype, const float* src, int order, const int64_t* dims, void* codes,
+                    float* scales, int truncate) {
+  if (!valid_shape(order, dims)) return OR_ERR_ARG;
+  if (dtype != OR_BF16 && dtype != OR_E4M3) return OR_ERR_ARG;
+  int64_t n0 = dims[0], slab = prod(dims, 1, order);
+  for (int64_t i = 0; i < n0; i++) {
+    const float* p = src + i * slab;
+    float sc = 1.0f;
+    if (dtype == OR_E4M3) {
+      float amax = 0.0f;
+      for (int64_t f = 0; f < slab; f++) {
+        float a = fabsf(p[f]);
+        if (!(a <= amax)) amax = a; /* NaN propagates */
+      }
+      if (!isfinite(amax)) return OR_ERR_NONFINITE;
+      if (amax > 0.0f) sc = amax / 448.0f;
+    }
+    scales[i] = sc;
+    for (int64_t f = 0; f < slab; f++) {
+      if (dtype == OR_E4M3)
+        ((uint8_t*)codes)[i * slab + f] = oracle_e4m3_from_f32(p[f] / sc);
+      else
+        ((uint16_t*)codes)[i * slab + f] = oracle_bf16_from_f32(p[f], truncate);
+    }
+  }
+  return OR_OK;
+}

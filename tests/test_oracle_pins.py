@@ -1,0 +1,352 @@
+"""Pins of the FP64 oracle against things other than itself: closed forms,
+brute-force unfolding, library routines (numpy einsum / SVD, torch dtype
+conversions), invariances, Eq. 3's touched-memory model, the contraction
+count of Algorithm 1 and the paper's Table 1.  CPU only."""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.conftest import golden
+
+RNG_SEED = 0
+
+
+def rand_tensor(dims, sid=0, seed=RNG_SEED):
+    return synth.tensor("u64", seed, dims, sid)
+
+
+SHAPES = [(7,), (5, 3), (1, 4), (4, 1), (3, 1, 5), (2, 3, 4), (6, 5, 4, 3), (2, 1, 3, 1, 2),
+          (3, 2, 2, 3, 2, 2), (2, 2, 2, 2, 2, 2, 2, 3)]
+
+
+# ------------------------------------------------------------------ TVC ----
+
+@pytest.mark.parametrize("dims", SHAPES)
+def test_tvc_matches_einsum_every_mode(dims):
+    A = rand_tensor(dims)
+    for k, n in enumerate(dims):
+        x = synth.vector("u64", 1, synth.stream_x(k), n)
+        want = np.tensordot(A, x, axes=([k], [0]))
+        got = oracle.tvc(A, k, x)
+        assert got.shape == want.shape
+        np.testing.assert_allclose(got, want, rtol=1e-13, atol=1e-13)
+
+
+def _unfold(A, k):
+    """Mode-k unfolding by explicit index arithmetic: row j = n_k index,
+    column = the other indices in row-major order (a brute-force route)."""
+    dims = A.shape
+    others = [i for i in range(len(dims)) if i != k]
+    cols = list(itertools.product(*[range(dims[i]) for i in others]))
+    M = [[0.0] * len(cols) for _ in range(dims[k])]
+    for j in range(dims[k]):
+        for c, idx in enumerate(cols):
+            full = list(idx[:k]) + [j] + list(idx[k:])
+            M[j][c] = float(A[tuple(full)])
+    return M, cols
+
+
+@pytest.mark.parametrize("dims", [(2, 3, 4), (3, 1, 2, 2), (5, 2)])
+def test_tvc_brute_force_unfolding(dims):
+    A = rand_tensor(dims, sid=3)
+    for k, n in enumerate(dims):
+        x = synth.vector("u64", 2, synth.stream_x(k), n)
+        M, cols = _unfold(A, k)
+        want = [sum(M[j][c] * float(x[j]) for j in range(n)) for c in range(len(cols))]
+        got = oracle.tvc(A, k, x).ravel()
+        np.testing.assert_allclose(got, np.array(want), rtol=1e-14, atol=1e-15)
+
+
+def test_tvc_rank1_closed_form():
+    dims = (4, 5, 6, 3)
+    us = [synth.vector("u64", 5, 30 + j, n) for j, n in enumerate(dims)]
+    A = np.einsum("i,j,k,l->ijkl", *us)
+    for k in range(4):
+        x = synth.vector("u64", 6, synth.stream_x(k), dims[k])
+        rest = [us[j] for j in range(4) if j != k]
+        want = float(np.dot(us[k], x)) * np.einsum("i,j,k->ijk", *rest)
+        np.testing.assert_allclose(oracle.tvc(A, k, x), want, rtol=1e-13, atol=1e-15)
+
+
+def test_tvc_matrix_cases():
+    A = rand_tensor((9, 13))
+    x1 = synth.vector("u64", 1, 1, 13)
+    x0 = synth.vector("u64", 1, 2, 9)
+    np.testing.assert_allclose(oracle.tvc(A, 1, x1), A @ x1, rtol=1e-13)
+    np.testing.assert_allclose(oracle.tvc(A, 0, x0), A.T @ x0, rtol=1e-13)
+
+
+def test_tvc_mode_permutation_invariance():
+    dims = (3, 4, 5, 2)
+    A = rand_tensor(dims)
+    for perm in itertools.permutations(range(4)):
+        B = np.ascontiguousarray(np.transpose(A, perm))
+        for k in range(4):
+            x = synth.vector("u64", 9, 40 + k, dims[k])
+            yA = oracle.tvc(A, k, x)
+            kb = perm.index(k)
+            yB = oracle.tvc(B, kb, x)
+            rest = [p for p in perm if p != k]
+            order = [sorted(rest).index(p) for p in rest]
+            np.testing.assert_allclose(yB, np.transpose(yA, order), rtol=1e-13, atol=1e-15)
+
+
+def test_tvc_integer_inputs_exact():
+    dims = (3, 4, 5)
+    rng = np.random.default_rng(3)
+    Ai = rng.integers(-1000, 1000, size=dims)
+    A = Ai.astype(np.float64)
+    for k in range(3):
+        xi = rng.integers(-1000, 1000, size=dims[k])
+        want = np.tensordot(Ai, xi, axes=([k], [0]))  # exact int64 arithmetic
+        got = oracle.tvc(A, k, xi.astype(np.float64))
+        assert np.array_equal(got, want.astype(np.float64))
+
+
+def test_tvc_linearity_ones_and_alpha_beta():
+    dims = (4, 6, 5)
+    A = rand_tensor(dims)
+    for k in range(3):
+        x = synth.vector("u64", 3, 1, dims[k])
+        z = synth.vector("u64", 3, 2, dims[k])
+        np.testing.assert_allclose(oracle.tvc(A, k, 2.0 * x - 3.0 * z),
+                                   2.0 * oracle.tvc(A, k, x) - 3.0 * oracle.tvc(A, k, z),
+                                   rtol=1e-12, atol=1e-13)
+        ones = np.ones(dims[k])
+        assert abs(oracle.tvc(A, k, ones).sum() - A.sum()) < 1e-12
+        y0 = synth.tensor("u64", 4, [n for i, n in enumerate(dims) if i != k])
+        got = oracle.tvc(A, k, x, y=y0, alpha=0.5, beta=-2.0)
+        np.testing.assert_allclose(got, 0.5 * oracle.tvc(A, k, x) - 2.0 * y0, rtol=1e-13, atol=1e-14)
+        # beta == 0 never reads y (NaN in y is ignored)
+        ynan = np.full_like(y0, np.nan)
+        assert np.all(np.isfinite(oracle.tvc(A, k, x, y=ynan, alpha=1.0, beta=0.0)))
+
+
+def test_tvc_successive_contractions_commute():
+    dims = (3, 4, 5)
+    A = rand_tensor(dims)
+    x0, x2 = synth.vector("u64", 1, 1, 3), synth.vector("u64", 1, 3, 5)
+    a = oracle.tvc(oracle.tvc(A, 0, x0), 1, x2)
+    b = oracle.tvc(oracle.tvc(A, 2, x2), 0, x0)
+    np.testing.assert_allclose(a, b, rtol=1e-13)
+
+
+def test_tvc_narrow_types_dequantise():
+    dims = (3, 4, 5)
+    src = synth.tensor("lognormal", 0, dims).astype(np.float32)
+    for fmt in (oracle.BF16, oracle.E4M3):
+        codes, scales = oracle.quantise(src, fmt)
+        deq = oracle.dequantise(codes, scales)
+        for k in range(3):
+            x = synth.vector("u64", 1, 1, dims[k])
+            np.testing.assert_allclose(oracle.tvc(codes, k, x, scales=scales),
+                                       np.tensordot(deq, x, axes=([k], [0])), rtol=1e-13, atol=1e-13)
+    A32 = synth.tensor("u32", 0, dims)
+    x = synth.vector("u64", 1, 1, 4)
+    np.testing.assert_allclose(oracle.tvc(A32, 1, x),
+                               np.tensordot(A32.astype(np.float64), x, axes=([1], [0])), rtol=1e-13)
+
+
+def test_tvc_bad_arguments():
+    A = rand_tensor((2, 3))
+    with pytest.raises(ValueError):
+        oracle.tvc(A, 2, np.ones(3))
+    with pytest.raises(ValueError):
+        oracle.tvc(A, 0, np.ones(3))
+
+
+# ------------------------------------------------------------ gradients ----
+
+@pytest.mark.parametrize("dims", [(4, 5, 3), (6, 7), (2, 3, 2, 3)])
+def test_grad_adjoint_identity_and_fd(dims):
+    A = rand_tensor(dims)
+    for k in range(len(dims)):
+        x = synth.vector("u64", 2, 1, dims[k])
+        gy = synth.tensor("u64", 3, [n for i, n in enumerate(dims) if i != k])
+        y = oracle.tvc(A, k, x)
+        gx = oracle.tvc_grad_x(A, k, gy)
+        gA = oracle.tvc_grad_A(dims, k, x, gy)
+        lhs = float(np.sum(gy * y))
+        assert abs(lhs - float(np.dot(gx, x))) < 1e-12 * max(1.0, abs(lhs))
+        assert abs(lhs - float(np.sum(gA * A))) < 1e-12 * max(1.0, abs(lhs))
+        # central finite differences of L = <gy, A x_k x> in x and in A
+        h = 1e-6
+        for j in range(dims[k]):
+            e = np.zeros(dims[k]); e[j] = h
+            fd = (np.sum(gy * oracle.tvc(A, k, x + e)) - np.sum(gy * oracle.tvc(A, k, x - e))) / (2 * h)
+            assert abs(fd - gx[j]) < 1e-7 * max(1.0, abs(gx[j]))
+        flat = A.ravel()
+        for f in (0, flat.size // 2, flat.size - 1):
+            Ap, Am = flat.copy(), flat.copy()
+            Ap[f] += h; Am[f] -= h
+            fd = (np.sum(gy * oracle.tvc(Ap.reshape(dims), k, x)) -
+                  np.sum(gy * oracle.tvc(Am.reshape(dims), k, x))) / (2 * h)
+            assert abs(fd - gA.ravel()[f]) < 1e-7
+
+
+# ------------------------------------------------------------------ HOPM ----
+
+def ones_start(dims):
+    return [np.ones(n) / math.sqrt(n) for n in dims]
+
+
+@pytest.mark.parametrize("fn", [oracle.hopm, oracle.hopm3])
+def test_hopm_rank1_converges_in_one_sweep(fn):
+    dims = (5, 4, 6, 3)
+    us = [synth.vector("u64", 8, 50 + j, n) for j, n in enumerate(dims)]
+    A = np.einsum("i,j,k,l->ijkl", *us)
+    r = fn(A, ones_start(dims), iters=1)
+    assert r["status"] == 0
+    lam_true = np.prod([np.linalg.norm(u) for u in us])
+    assert abs(r["lam"] - lam_true) < 1e-12 * lam_true
+    for xj, u in zip(r["x"], us):
+        assert abs(abs(np.dot(xj, u / np.linalg.norm(u))) - 1.0) < 1e-13
+
+
+@pytest.mark.parametrize("fn", [oracle.hopm, oracle.hopm3])
+def test_hopm_matrix_gives_top_singular_value(fn):
+    A = rand_tensor((12, 9))
+    r = fn(A, ones_start(A.shape), iters=500, tol=1e-15)
+    s = np.linalg.svd(A, compute_uv=False)
+    assert abs(r["lam"] - s[0]) < 1e-10 * s[0]
+
+
+@pytest.mark.parametrize("dims", [(6, 5, 4), (4, 3, 5, 3), (3, 3, 2, 3, 2)])
+def test_hopm_sigma_non_decreasing_and_hopm3_equal(dims):
+    A = rand_tensor(dims)
+    a = oracle.hopm(A, ones_start(dims), iters=15)
+    b = oracle.hopm3(A, ones_start(dims), iters=15)
+    assert np.all(np.diff(a["lam_hist"]) >= -1e-13)
+    np.testing.assert_allclose(a["lam_hist"], b["lam_hist"], rtol=1e-12)
+    for xa, xb in zip(a["x"], b["x"]):
+        np.testing.assert_allclose(xa, xb, rtol=1e-10, atol=1e-12)
+    # lambda equals the full contraction A(x_0, ..., x_{d-1}) at the end of a sweep
+    T = A
+    for xj in reversed(a["x"]):
+        T = np.tensordot(T, xj, axes=([T.ndim - 1], [0]))
+    assert abs(float(T) - a["lam"]) < 1e-6 * a["lam"]
+
+
+def test_hopm_start_x0_unused_and_stopping_rule():
+    dims = (4, 5, 3)
+    A = rand_tensor(dims)
+    s1 = ones_start(dims)
+    s2 = [np.full(4, 123.0)] + s1[1:]
+    a = oracle.hopm(A, s1, iters=6)
+    b = oracle.hopm(A, s2, iters=6)
+    np.testing.assert_array_equal(a["lam_hist"], b["lam_hist"])
+    r = oracle.hopm(A, s1, iters=1000, tol=1e-6)
+    assert r["sweeps"] < 1000
+    h = r["lam_hist"]
+    assert abs(h[-1] - h[-2]) <= 1e-6 * h[-1]
+    assert all(abs(h[t] - h[t - 1]) > 1e-6 * h[t] for t in range(1, len(h) - 1))
+
+
+def test_hopm_zero_tensor_status():
+    A = np.zeros((3, 4))
+    r = oracle.hopm(A, ones_start(A.shape), iters=3)
+    assert r["status"] == 5
+
+
+@pytest.mark.parametrize("d", [2, 3, 4, 5, 6])
+def test_algorithm1_contraction_count(d):
+    dims = (2,) * d
+    A = rand_tensor(dims)
+    a = oracle.hopm(A, ones_start(dims), iters=1)
+    b = oracle.hopm3(A, ones_start(dims), iters=1)
+    assert a["tvcs"] == d * (d - 1)
+    assert b["tvcs"] == d * (d - 1) - (d - 1) * (d - 2) // 2
+
+
+@pytest.mark.parametrize("d,n", [(2, 9), (3, 7), (4, 5), (5, 3)])
+def test_eq3_touched_memory_canonical(d, n):
+    A = rand_tensor((n,) * d)
+    r = oracle.hopm(A, ones_start((n,) * d), iters=2)
+    m_seq = n ** d + 2 * sum(n ** k for k in range(2, d)) + (d + 3) * n
+    assert list(r["touched"]) == [d * m_seq] * 2
+
+
+def test_hopm3_streamed_memory_saving_bands():
+    for d_s, lo, hi in golden("hopm3_savings.txt"):
+        d, lo, hi = int(d_s), float(lo), float(hi)
+        n = 64 if d == 3 else 4
+        dims = (n,) * d
+        A = rand_tensor(dims)
+        a = oracle.hopm(A, ones_start(dims), iters=1)
+        b = oracle.hopm3(A, ones_start(dims), iters=1)
+        ratio = a["touched"][0] / b["touched"][0]
+        assert lo <= ratio <= hi, (d, ratio)
+
+
+# --------------------------------------------------------------- storage ----
+
+def test_e4m3_decode_matches_spec_and_torch():
+    torch = pytest.importorskip("torch")
+    for code_s, val_s in golden("e4m3_ocp.txt"):
+        code = int(code_s, 16)
+        got = oracle.decode_e4m3(code)
+        if val_s == "nan":
+            assert math.isnan(got)
+        else:
+            assert got == float(val_s) and math.copysign(1, got) == math.copysign(1, float(val_s))
+    codes = torch.arange(256, dtype=torch.uint8)
+    ref = codes.view(torch.float8_e4m3fn).to(torch.float64).numpy()
+    mine = np.array([oracle.decode_e4m3(c) for c in range(256)])
+    nan = np.isnan(ref)
+    assert np.array_equal(np.isnan(mine), nan)
+    assert np.array_equal(mine[~nan], ref[~nan])
+
+
+def test_e4m3_encode_matches_torch_rne_and_saturates():
+    torch = pytest.importorskip("torch")
+    vals = np.concatenate([
+        synth.tensor("lognormal", 1, [20000]).astype(np.float32) * 20,
+        np.array([0.0, -0.0, 1e-30, 2.0 ** -10, 3 * 2.0 ** -10, 2.0 ** -9 * 1.5, 448.0, 447.0, 464.0,
+                  1e6, -1e6, np.inf, -np.inf], dtype=np.float32),
+    ]).astype(np.float32)
+    # all midpoints between neighbouring E4M3 magnitudes (ties to even)
+    grid = np.array([oracle.decode_e4m3(c) for c in range(0x7F)])
+    mids = ((grid[:-1] + grid[1:]) / 2).astype(np.float32)
+    vals = np.concatenate([vals, mids, -mids])
+    mine = np.array([oracle.e4m3_from_f32(v) for v in vals], dtype=np.uint8)
+    inr = np.abs(vals) <= 448.0
+    ref = torch.from_numpy(vals[inr]).to(torch.float8_e4m3fn).view(torch.uint8).numpy()
+    assert np.array_equal(mine[inr], ref)
+    assert np.all(mine[~inr & (vals > 0)] == 0x7E) and np.all(mine[~inr & (vals < 0)] == 0xFE)
+    assert oracle.e4m3_from_f32(float("nan")) == 0x7F
+
+
+def test_bf16_rne_matches_torch_and_truncation_is_top_half():
+    torch = pytest.importorskip("torch")
+    vals = np.concatenate([synth.tensor("lognormal", 2, [20000]),
+                           synth.tensor("u64", 3, [20000]) * 1e-3]).astype(np.float32)
+    ref = torch.from_numpy(vals).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
+    mine = np.array([oracle.bf16_from_f32(v) for v in vals], dtype=np.uint16)
+    assert np.array_equal(mine, ref)
+    trunc = np.array([oracle.bf16_from_f32(v, truncate=True) for v in vals], dtype=np.uint16)
+    assert np.array_equal(trunc, (vals.view(np.uint32) >> 16).astype(np.uint16))
+
+
+def test_quantise_per_slab_scales():
+    dims = (3, 40, 7)
+    src = synth.tensor("lognormal", 4, dims).astype(np.float32)
+    codes, scales = oracle.quantise(src, oracle.E4M3)
+    for i in range(3):
+        amax = np.float32(np.abs(src[i]).max())
+        assert scales[i] == np.float32(amax / np.float32(448.0))
+        assert np.abs(codes[i] & 0x7F).max() == 0x7E  # the slab maximum maps to 448
+    deq = oracle.dequantise(codes, scales)
+    rel = np.abs(deq - src) / np.abs(src)
+    # E4M3 has 3 mantissa bits: relative rounding error <= 2^-4 for normal codes
+    big = np.abs(src) > scales.reshape(-1, 1, 1) * 2.0 ** -6
+    assert rel[big].max() <= 2.0 ** -4 + 1e-7
+    codes_b, scales_b = oracle.quantise(src, oracle.BF16)
+    assert np.all(scales_b == 1.0)
+    assert np.abs(oracle.dequantise(codes_b, scales_b) - src).max() <= np.abs(src).max() * 2.0 ** -8
+    zero = np.zeros((2, 3), dtype=np.float32)
+    c0, s0 = oracle.quantise(zero, oracle.E4M3)
+    assert np.all(s0 == 1.0) and np.all(c0 == 0)
