@@ -1,0 +1,378 @@
+"""Benchmark: achieved HBM bandwidth of the mode-oblivious TVC on one GB300.
+
+Workload (one step): the TVC bandwidth sweep, i.e. the contraction along
+EVERY mode of the dense row-major tensors 1024^3, 128^4, 40^6 and
+65536x16384 (order 2), each stored in FP64 and in FP32, entries uniform
+[-1, 1) (counter-based generator, seed 0), x uniform [-1, 1).  30 TVCs per
+step, 260 GB of algorithmic traffic.  value = algorithmic bytes / time
+(GB/s), summed over ranks; each rank runs an independent replica (the
+single-GPU path has no data-parallel exchange).
+
+Every input is far larger than the 129 MB L2 (the smallest is 1.07 GB), so
+no flush is needed between timed iterations.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "TVC/HOPM achieved HBM GB/s (% of GB300 peak), FP64 vs BF16 at stated error"
+TENSORS = [(1024, 1024, 1024), (128, 128, 128, 128), (40, 40, 40, 40, 40, 40), (65536, 16384)]
+WORKLOAD = ("TVC bandwidth sweep: every mode of 1024^3, 128^4, 40^6 and 65536x16384, "
+            "FP64 and FP32 storage, uniform[-1,1) seed 0")
+
+
+def tvc_bytes(dims, mode, esize, vsize):
+    """Algorithmic bytes of one TVC with beta = 0: read A once, read x,
+    write y (N/n_k entries)."""
+    N = math.prod(dims)
+    return N * esize + dims[mode] * vsize + (N // dims[mode]) * vsize
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def traffic_record():
+    """ncu DRAM traffic per launch of the dominant kernel, if recorded for the
+    current kernel source (profiles/roofline_traffic.json)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh)
+        src = os.path.join(ROOT, rec["source"])
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if sha != rec["source_sha"]:
+            return None
+        return rec
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        mhz = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for n, v in zip(names, r[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(mhz) if mhz else None,
+                "sm_max_mhz": float(rows[0][1]) if rows[0][1].replace(".", "").isdigit() else None,
+                "samples": len(rows), "reasons": sorted(reasons)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ----------------------------------------------------------- oracle timing
+
+def oracle_sample(budget_s=15.0, kinds=("f64", "f32")):
+    """Time the FP64 CPU oracle on a bounded sample of the workload: the same
+    tensors cut to their first slabs (dims[0] reduced so each sample holds
+    about 2^23 elements), contracted along every mode.  Returns (GB/s of
+    algorithmic bytes, threads, description, seconds)."""
+    import numpy as np
+    import oracle
+    import synth
+    oracle.build()
+    total_bytes = 0
+    total_t = 0.0
+    cut = []
+    for dims in TENSORS:
+        rest = math.prod(dims[1:])
+        n0 = max(1, min(dims[0], (1 << 23) // rest))
+        sd = (n0,) + tuple(dims[1:])
+        cut.append(sd)
+    t_start = time.perf_counter()
+    for kind in kinds:
+        for sd in cut:
+            A = synth.tensor("u64" if kind == "f64" else "u32", 0, sd)
+            es = 8 if kind == "f64" else 4
+            for k in range(len(sd)):
+                x = synth.vector("u64", 1, synth.stream_x(k), sd[k])
+                t0 = time.perf_counter()
+                oracle.tvc(A, k, x)
+                total_t += time.perf_counter() - t0
+                total_bytes += tvc_bytes(sd, k, es, es)
+            if time.perf_counter() - t_start > budget_s:
+                break
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    desc = ("oracle TVC along every mode of " + ", ".join("x".join(map(str, s)) for s in cut) +
+            " (first slabs of each workload tensor), " + "+".join(kinds))
+    return total_bytes / total_t / 1e9, threads, desc, total_t
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    t0 = time.perf_counter()
+    vals = []
+    desc = ""
+    threads = 1
+    for _ in range(args.warmup):
+        oracle_sample(budget_s=2.0, kinds=("f64",))
+    for _ in range(args.steps):
+        gbs, threads, desc, _ = oracle_sample(budget_s=20.0, kinds=("f64", "f32"))
+        vals.append(gbs)
+    v = statistics.median(vals)
+    wall = time.perf_counter() - t0
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GB/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * wall / max(1, args.steps + args.warmup),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": desc},
+            "cpu_baseline": {"value": v, "unit": "GB/s", "cores": threads, "kind": "oracle", "sample": desc},
+            "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------- main
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--detail", action="store_true", help="per-mode table on stderr")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args(argv)
+    args.warmup = max(3, args.warmup)
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import numpy as np
+    import torch
+
+    import synth
+    import synth.device as sd
+    import paper_2501_03121_gb300 as tg
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+
+    def barrier():
+        if pg is not None:
+            pg.barrier()
+
+    stream = torch.cuda.current_stream()
+    # Inputs, resident in HBM.
+    calls = []
+    tensors = []
+    for code, dt, kind in ((tg.F64, torch.float64, "u64"), (tg.F32, torch.float32, "u32")):
+        es = 8 if code == tg.F64 else 4
+        for dims in TENSORS:
+            N = math.prod(dims)
+            A = torch.empty(N, dtype=dt, device=dev)
+            sd.fill(A, kind, 0, synth.STREAM_A)
+            tensors.append((A, dims, code))
+            for k in range(len(dims)):
+                xh = synth.vector(kind, 1, synth.stream_x(k), dims[k])
+                x = torch.from_numpy(xh).to(dev)
+                y = torch.empty(N // dims[k], dtype=dt, device=dev)
+                calls.append(dict(A=A, dims=dims, k=k, x=x, y=y, code=code,
+                                  bytes=tvc_bytes(dims, k, es, es), name=f"{'f64' if code == tg.F64 else 'f32'}:"
+                                  f"{'x'.join(map(str, dims))}:k{k}", v=math.prod(dims[k + 1:])))
+    torch.cuda.synchronize()
+    step_bytes = sum(c["bytes"] for c in calls)
+
+    def step(evs=None):
+        for ci, c in enumerate(calls):
+            if evs is not None:
+                evs[ci][0].record(stream)
+            tg.tvc(c["A"], c["k"], c["x"], y=c["y"], shape=c["dims"])
+            if evs is not None:
+                evs[ci][1].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    evs = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in calls]
+           for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier()
+    torch.cuda.synchronize()
+    launches0 = tg.kernel_launches()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for s in range(args.steps):
+        step(evs[s])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = tg.kernel_launches() - launches0
+    clocks = sampler.stop()
+    elapsed_ms = t_start.elapsed_time(t_end)
+    if pg is not None:
+        t = torch.tensor([elapsed_ms], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    per_call = [statistics.mean(evs[s][ci][0].elapsed_time(evs[s][ci][1]) for s in range(args.steps))
+                for ci in range(len(calls))]
+    value = world * step_bytes * args.steps / (elapsed_ms / 1e3) / 1e9
+
+    # Dominant kernel: the FP64 column kernel (modes with v >= 32), which
+    # carries most of the step's time.
+    peak, peak_kind = peaks()
+    dom = [ci for ci, c in enumerate(calls) if c["code"] == tg.F64 and c["v"] >= 32]
+    dom_bytes = sum(calls[ci]["bytes"] for ci in dom)
+    dom_ms = sum(per_call[ci] for ci in dom)
+    achieved = dom_bytes / (dom_ms / 1e3) / 1e9
+    rec = traffic_record()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_kind": peak_kind, "kernel": "tvc_cols_kernel<F64> (FP64 contraction, v >= 32)",
+                "launches_timed": len(dom) * args.steps,
+                "traffic": (rec["bytes_per_launch_by_call"] if rec else None)}
+    f64_ms = sum(per_call[ci] for ci, c in enumerate(calls) if c["code"] == tg.F64)
+    f64_bytes = sum(c["bytes"] for c in calls if c["code"] == tg.F64)
+    f32_ms = sum(per_call[ci] for ci, c in enumerate(calls) if c["code"] == tg.F32)
+    f32_bytes = sum(c["bytes"] for c in calls if c["code"] == tg.F32)
+    per_mode = {c["name"]: round(c["bytes"] / (per_call[ci] / 1e3) / 1e9, 1) for ci, c in enumerate(calls)}
+    if args.detail and rank == 0:
+        for name, gbs in per_mode.items():
+            print(f"{name:40s} {gbs:8.1f} GB/s  {100 * gbs / peak:5.1f}%", file=sys.stderr)
+
+    # End to end through the public API: inputs from pinned host memory,
+    # results read back, every step.
+    e2e = None
+    if not args.no_e2e:
+        hostA = []
+        for A, dims, code in tensors:
+            h = torch.empty(A.numel(), dtype=A.dtype, pin_memory=True)
+            h.copy_(A)
+            hostA.append(h)
+        hostY = [torch.empty(c["y"].numel(), dtype=c["y"].dtype, pin_memory=True) for c in calls]
+        hostX = [c["x"].cpu().pin_memory() for c in calls]
+        h2d = sum(h.numel() * h.element_size() for h in hostA) + sum(h.numel() * h.element_size() for h in hostX)
+        d2h = sum(h.numel() * h.element_size() for h in hostY)
+        torch.cuda.synchronize()
+
+        def e2e_step():
+            ci = 0
+            for (A, dims, code), h in zip(tensors, hostA):
+                A.copy_(h, non_blocking=True)
+                for k in range(len(dims)):
+                    c = calls[ci]
+                    c["x"].copy_(hostX[ci], non_blocking=True)
+                    tg.tvc(A, k, c["x"], y=c["y"], shape=dims)
+                    hostY[ci].copy_(c["y"], non_blocking=True)
+                    ci += 1
+
+        e2e_step()
+        torch.cuda.synchronize()
+        k2 = max(1, min(args.steps, 3))
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(k2):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        e2e_s = time.perf_counter() - t0
+        e2e = {"value": world * step_bytes * k2 / e2e_s / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "steps": k2}
+        del hostA, hostY
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        gbs, threads, desc, secs = oracle_sample()
+        cpu = {"value": gbs, "unit": "GB/s", "cores": threads, "kind": "oracle", "sample": desc,
+               "seconds": round(secs, 2)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "tvcs_per_step": len(calls), "bytes_per_step": step_bytes,
+                       "l2": "inputs larger than L2 (smallest tensor 1.07 GB); no flush needed",
+                       "parallelism": f"replicas x{world}"},
+            "frac_of_peak": value / world / peak,
+            "fp64": {"GB/s": f64_bytes / (f64_ms / 1e3) / 1e9, "frac": f64_bytes / (f64_ms / 1e3) / 1e9 / peak,
+                     "mean_mode_frac": statistics.mean(v for n, v in per_mode.items() if n.startswith("f64")) / peak,
+                     "std_mode_frac": statistics.stdev(v for n, v in per_mode.items() if n.startswith("f64")) / peak},
+            "fp32": {"GB/s": f32_bytes / (f32_ms / 1e3) / 1e9, "frac": f32_bytes / (f32_ms / 1e3) / 1e9 / peak},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+            "per_mode_GBs": per_mode,
+        }
+        print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

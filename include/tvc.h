@@ -99,6 +99,11 @@ tvc_status tvc_ex(const void* A, int order, const int64_t* dims, int mode, const
  * plan is used by tvc_ex for the same arguments on the same device. */
 size_t tvc_workspace_size(int order, const int64_t* dims, int mode, tvc_dtype dtype);
 
+/* Number of CUDA kernels this library has launched in this process (all
+ * devices, all entry points).  Host-side counter, incremented per launch;
+ * lets a caller count the kernels of a timed region. */
+uint64_t tvc_kernel_launches(void);
+
 #ifdef __cplusplus
 }
 #endif

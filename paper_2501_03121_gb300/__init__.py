@@ -1,0 +1,178 @@
+"""GB300-native tensor-vector contraction (TVC) and higher-order power method.
+
+Thin Python binding over the C ABI of ``include/tvc.h`` (library
+``_lib/libtvc_gb300.so``, built by ``build.py``).  Every step of the
+computation runs in the CUDA kernels of that library; this module only
+marshals torch tensors (device memory, streams) into pointers and sizes.
+There is no CPU fallback: if the library is missing, every call raises.
+
+Method: Martinez-Ferrer, Yzelman, Beltran, "Distributed and heterogeneous
+tensor-vector contraction algorithms for high performance computing"
+(arXiv 2501.03121).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import threading
+
+import torch
+
+__all__ = [
+    "F64", "F32", "BF16", "E4M3", "TVCError", "load_library", "tvc", "tvc_workspace_size",
+    "dtype_code", "library_path", "kernel_launches",
+]
+
+F64, F32, BF16, E4M3 = 0, 1, 2, 3
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+library_path = os.path.join(_HERE, "_lib", "libtvc_gb300.so")
+_lock = threading.Lock()
+_lib = None
+
+
+class TVCError(RuntimeError):
+    """Non-zero tvc_status from the library."""
+
+    def __init__(self, status: int, where: str):
+        msg = _status_string(status)
+        super().__init__(f"{where}: {msg}")
+        self.status = status
+
+
+def _status_string(status: int) -> str:
+    try:
+        return load_library().tvc_status_string(int(status)).decode()
+    except Exception:  # pragma: no cover - library unavailable
+        return f"status {status}"
+
+
+def load_library():
+    """Load the compiled library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(library_path):
+            raise RuntimeError(
+                f"CUDA library {library_path} is missing: build it with "
+                "`python -c 'import __graft_entry__ as g; g.build()'`")
+        lib = ctypes.CDLL(library_path)
+        P, I, D, Z, L = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t, ctypes.c_int64
+        lib.tvc_status_string.argtypes = [I]
+        lib.tvc_status_string.restype = ctypes.c_char_p
+        lib.tvc.argtypes = [P, I, P, I, P, P, I, P]
+        lib.tvc.restype = I
+        lib.tvc_ex.argtypes = [P, I, P, I, P, P, I, P, D, D, P, Z, P]
+        lib.tvc_ex.restype = I
+        lib.tvc_workspace_size.argtypes = [I, P, I, I]
+        lib.tvc_workspace_size.restype = Z
+        lib.tvc_kernel_launches.argtypes = []
+        lib.tvc_kernel_launches.restype = ctypes.c_uint64
+        _lib = lib
+        return lib
+
+
+_TORCH_CODE = {
+    torch.float64: F64,
+    torch.float32: F32,
+    torch.bfloat16: BF16,
+    torch.uint16: BF16,
+    torch.float8_e4m3fn: E4M3,
+    torch.uint8: E4M3,
+}
+
+
+def dtype_code(t: torch.Tensor) -> int:
+    """Storage code of a tensor: float64, float32, bfloat16 (or raw uint16
+    codes), float8_e4m3fn (or raw uint8 codes)."""
+    try:
+        return _TORCH_CODE[t.dtype]
+    except KeyError:
+        raise TypeError(f"unsupported tensor dtype {t.dtype}") from None
+
+
+def vec_dtype(code: int) -> torch.dtype:
+    return torch.float64 if code == F64 else torch.float32
+
+
+def _dims_array(shape):
+    arr = (ctypes.c_int64 * max(1, len(shape)))(*[int(n) for n in shape])
+    return arr
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _check(status, where):
+    if status != 0:
+        raise TVCError(status, where)
+
+
+def _check_cuda(*ts):
+    for t in ts:
+        if t is not None and (not t.is_cuda or not t.is_contiguous()):
+            raise ValueError("tensors must be contiguous CUDA tensors")
+
+
+def kernel_launches() -> int:
+    """Kernels the library has launched so far in this process."""
+    return int(load_library().tvc_kernel_launches())
+
+
+def tvc_workspace_size(shape, mode: int, code: int) -> int:
+    """Bytes of workspace tvc(..., workspace=...) needs for this shape."""
+    lib = load_library()
+    dims = _dims_array(shape)
+    return int(lib.tvc_workspace_size(len(shape), dims, int(mode), int(code)))
+
+
+def tvc(A: torch.Tensor, mode: int, x: torch.Tensor, *, y: torch.Tensor | None = None,
+        scales: torch.Tensor | None = None, alpha: float = 1.0, beta: float = 0.0,
+        workspace: torch.Tensor | None = None, stream=None, shape=None) -> torch.Tensor:
+    """Y = alpha * (A x_mode x) + beta * Y on the GPU.
+
+    ``A`` holds the tensor (its shape, or ``shape`` for raw uint8/uint16
+    codes given flat); ``x`` is float64 for float64 storage and float32
+    otherwise.  ``scales`` are the n_0 per-slab FP32 scales of narrow
+    storage.  Without ``workspace`` (and with alpha=1, beta=0, no scales)
+    the library's own workspace is used.
+    """
+    lib = load_library()
+    code = dtype_code(A)
+    shape = tuple(A.shape) if shape is None else tuple(int(n) for n in shape)
+    if not 0 <= mode < len(shape):
+        raise ValueError("mode out of range")
+    vt = vec_dtype(code)
+    if x.dtype != vt or x.numel() != shape[mode]:
+        raise ValueError(f"x must be {vt} with {shape[mode]} entries")
+    out_shape = tuple(n for i, n in enumerate(shape) if i != mode)
+    if y is None:
+        if beta != 0.0:
+            raise ValueError("beta != 0 needs y")
+        y = torch.empty(out_shape, dtype=vt, device=A.device)
+    elif y.dtype != vt or y.numel() != math.prod(out_shape):
+        raise ValueError("y has the wrong dtype or size")
+    if scales is not None and scales.dtype != torch.float32:
+        raise ValueError("scales must be float32")
+    _check_cuda(A, x, y, scales, workspace)
+    dims = _dims_array(shape)
+    st = _stream(stream)
+    if workspace is None and scales is None and alpha == 1.0 and beta == 0.0:
+        status = lib.tvc(_ptr(A), len(shape), dims, int(mode), _ptr(x), _ptr(y), code, st)
+    else:
+        if workspace is None:
+            need = lib.tvc_workspace_size(len(shape), dims, int(mode), code)
+            workspace = torch.empty(max(1, need), dtype=torch.uint8, device=A.device)
+        status = lib.tvc_ex(_ptr(A), len(shape), dims, int(mode), _ptr(x), _ptr(y), code, _ptr(scales),
+                            float(alpha), float(beta), _ptr(workspace), workspace.numel(), st)
+    _check(status, "tvc")
+    return y

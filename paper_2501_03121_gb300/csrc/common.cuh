@@ -1,0 +1,332 @@
+// Shared device building blocks of the TVC library: element types and
+// their in-register decoding, vector loads, and the accumulators.
+//
+// FP64 on GB300.  The FP64 pipe of this part retires about 1.6 DFMA per SM
+// per clock (about 0.5e12 per second), so one DFMA per streamed 8-byte
+// element caps an FP64 contraction near 4 TB/s, well under the HBM rate.
+// The FP64 accumulators below therefore form most products on the FP32 pipe
+// in "float-float" arithmetic: a double a is split by integer operations
+// into ah + al (24 + 24 significant bits, exact up to 2^-48 relative), the
+// vector entry x into xh + xl (rounded pieces), the leading product ah*xh is
+// made error-free with one FMA (Dekker / Kahan TwoProduct), the cross terms
+// are added in FP32, and the running sum is kept as an unevaluated pair
+// (s, c) updated with Knuth's TwoSum.  Every RB rows the pair is folded into
+// an FP64 accumulator.  Elements outside the window where the split is
+// exact (|a| outside [2^-64, 2^64), zeros, FP64 subnormals, Inf/NaN, or an x
+// entry outside [2^-32, 2^32) that is not zero) take a plain DFMA instead,
+// so the result is always an FP64-accurate contraction; only the speed
+// depends on the data.  A compile-time share of rows can also be sent to
+// the DFMA pipe on purpose, so both pipes work in parallel.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/tvc.h"
+
+namespace tvcg {
+
+constexpr int kWarp = 32;
+
+// ------------------------------------------------------------ vector loads
+
+template <int BYTES>
+struct RawVec;
+template <>
+struct RawVec<1> { uint8_t v; };
+template <>
+struct RawVec<2> { uint16_t v; };
+template <>
+struct RawVec<4> { uint32_t v; };
+template <>
+struct RawVec<8> { uint2 v; };
+template <>
+struct RawVec<16> { uint4 v; };
+
+// Streaming (evict-first) load of BYTES bytes: the tensor is read once.
+template <int BYTES>
+__device__ __forceinline__ RawVec<BYTES> ld_stream(const void* p) {
+  RawVec<BYTES> r;
+  if constexpr (BYTES == 16) {
+    r.v = __ldcs(reinterpret_cast<const uint4*>(p));
+  } else if constexpr (BYTES == 8) {
+    r.v = __ldcs(reinterpret_cast<const uint2*>(p));
+  } else if constexpr (BYTES == 4) {
+    r.v = __ldcs(reinterpret_cast<const unsigned int*>(p));
+  } else if constexpr (BYTES == 2) {
+    r.v = __ldcs(reinterpret_cast<const unsigned short*>(p));
+  } else {
+    r.v = __ldcs(reinterpret_cast<const unsigned char*>(p));
+  }
+  return r;
+}
+
+// ------------------------------------------------------ element type traits
+
+// Storage type traits: element type, FP64 or FP32 arithmetic, and decoding
+// of VEC consecutive elements into `val` (FP64 for F64, FP32 otherwise).
+template <tvc_dtype DT>
+struct Elem;
+
+template <>
+struct Elem<TVC_F64> {
+  using T = double;
+  using V = double;  // vector / result type
+  using C = double;  // compute type of one element
+  static constexpr int kSize = 8;
+  template <int VEC>
+  __device__ __forceinline__ static void load(const T* p, C (&val)[VEC]) {
+    if constexpr (VEC == 2) {
+      RawVec<16> r = ld_stream<16>(p);
+      val[0] = __hiloint2double((int)r.v.y, (int)r.v.x);
+      val[1] = __hiloint2double((int)r.v.w, (int)r.v.z);
+    } else {
+#pragma unroll
+      for (int e = 0; e < VEC; e++) {
+        RawVec<8> r = ld_stream<8>(p + e);
+        val[e] = __hiloint2double((int)r.v.y, (int)r.v.x);
+      }
+    }
+  }
+};
+
+template <>
+struct Elem<TVC_F32> {
+  using T = float;
+  using V = float;
+  using C = float;
+  static constexpr int kSize = 4;
+  template <int VEC>
+  __device__ __forceinline__ static void load(const T* p, C (&val)[VEC]) {
+    if constexpr (VEC == 4) {
+      RawVec<16> r = ld_stream<16>(p);
+      val[0] = __uint_as_float(r.v.x);
+      val[1] = __uint_as_float(r.v.y);
+      val[2] = __uint_as_float(r.v.z);
+      val[3] = __uint_as_float(r.v.w);
+    } else {
+#pragma unroll
+      for (int e = 0; e < VEC; e++) val[e] = __uint_as_float(ld_stream<4>(p + e).v);
+    }
+  }
+};
+
+// BF16: the code is the upper half of a binary32, so decoding is a shift.
+template <>
+struct Elem<TVC_BF16> {
+  using T = uint16_t;
+  using V = float;
+  using C = float;
+  static constexpr int kSize = 2;
+  __device__ __forceinline__ static void word2(uint32_t w, float& lo, float& hi) {
+    lo = __uint_as_float(w << 16);
+    hi = __uint_as_float(w & 0xFFFF0000u);
+  }
+  template <int VEC>
+  __device__ __forceinline__ static void load(const T* p, C (&val)[VEC]) {
+    if constexpr (VEC == 8) {
+      RawVec<16> r = ld_stream<16>(p);
+      word2(r.v.x, val[0], val[1]);
+      word2(r.v.y, val[2], val[3]);
+      word2(r.v.z, val[4], val[5]);
+      word2(r.v.w, val[6], val[7]);
+    } else if constexpr (VEC == 2) {
+      word2(ld_stream<4>(p).v, val[0], val[1]);
+    } else {
+#pragma unroll
+      for (int e = 0; e < VEC; e++) val[e] = __uint_as_float(((uint32_t)ld_stream<2>(p + e).v) << 16);
+    }
+  }
+};
+
+// FP8 E4M3 (OCP): decoded two at a time by the hardware e4m3x2 -> f16x2
+// conversion, then widened to FP32 (both exact).
+template <>
+struct Elem<TVC_E4M3> {
+  using T = uint8_t;
+  using V = float;
+  using C = float;
+  static constexpr int kSize = 1;
+  __device__ __forceinline__ static void pair(uint16_t w, float& lo, float& hi) {
+    __half2_raw h = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)w, __NV_E4M3);
+    float2 f = __half22float2(*reinterpret_cast<__half2*>(&h));
+    lo = f.x;
+    hi = f.y;
+  }
+  __device__ __forceinline__ static void word4(uint32_t w, float* o) {
+    pair((uint16_t)(w & 0xFFFFu), o[0], o[1]);
+    pair((uint16_t)(w >> 16), o[2], o[3]);
+  }
+  template <int VEC>
+  __device__ __forceinline__ static void load(const T* p, C (&val)[VEC]) {
+    if constexpr (VEC == 16) {
+      RawVec<16> r = ld_stream<16>(p);
+      word4(r.v.x, val + 0);
+      word4(r.v.y, val + 4);
+      word4(r.v.z, val + 8);
+      word4(r.v.w, val + 12);
+    } else if constexpr (VEC == 4) {
+      word4(ld_stream<4>(p).v, val);
+    } else {
+#pragma unroll
+      for (int e = 0; e < VEC; e++) {
+        __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)ld_stream<1>(p + e).v, __NV_E4M3);
+        val[e] = __half2float(*reinterpret_cast<__half*>(&h));
+      }
+    }
+  }
+};
+
+// ------------------------------------------------------- float-float parts
+
+// x entry prepared for the emulated FP64 product: x ~= xh + xl (rounded
+// pieces).  xh is NaN when x is outside the exact window; such rows use DFMA.
+struct XSplit {
+  float xh, xl;
+};
+
+__device__ __forceinline__ XSplit split_x(double x) {
+  XSplit r;
+  double ax = fabs(x);
+  if (x == 0.0) {
+    r.xh = 0.0f;
+    r.xl = 0.0f;
+  } else if (ax >= 0x1p-32 && ax < 0x1p32) {
+    r.xh = __double2float_rn(x);
+    r.xl = __double2float_rn(x - (double)r.xh);
+  } else {
+    r.xh = __int_as_float(0x7FC00000);
+    r.xl = 0.0f;
+  }
+  return r;
+}
+
+// Knuth's TwoSum: s + e == a + b exactly (round-to-nearest FP32).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  float bp = __fsub_rn(s, a);
+  float ap = __fsub_rn(s, bp);
+  e = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
+}
+
+// (s, c) += a * x for one FP64 element a (see the file comment).  Lower
+// bound of the exact window: exponent field 959 (|a| >= 2^-64), 128 binades.
+constexpr uint32_t kDfWindowBase = 959u << 21;
+
+// The out-of-window path is a real call, never an if-converted DFMA that would
+// occupy the FP64 pipe for every element; it reads x itself, so the fast path
+// needs only the split pieces.
+__device__ __noinline__ double dfma_slow(double a, const double* xp, double d) {
+  return fma(a, *xp, d);
+}
+
+__device__ __forceinline__ void df_mac(float& s, float& c, double& d, double a, const double* xp,
+                                       XSplit xs) {
+  const uint32_t lo = (uint32_t)__double2loint(a);
+  const uint32_t hi = (uint32_t)__double2hiint(a);
+  const uint32_t win = hi * 2u - kDfWindowBase;
+  if (win < (1u << 28) && xs.xh == xs.xh) {
+    // ah: rebias the exponent (1023 -> 127) and keep the top 23 fraction bits.
+    const uint32_t hb = __funnelshift_l(lo, hi - 0x38000000u, 3) | (hi & 0x80000000u);
+    const float ah = __uint_as_float(hb);
+    // al: the remaining 29 fraction bits times 2^(e-1075), signed like a.
+    const float sc = __uint_as_float((hb & 0xFF800000u) - 0x1A000000u);
+    const float al = __fmul_rn(__uint2float_rn(lo & 0x1FFFFFFFu), sc);
+    const float p = __fmul_rn(ah, xs.xh);
+    float e = __fmaf_rn(ah, xs.xh, -p);
+    e = __fmaf_rn(ah, xs.xl, e);
+    e = __fmaf_rn(al, xs.xh, e);
+    float t, err;
+    two_sum(s, p, t, err);
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(err, e));
+  } else {
+    d = dfma_slow(a, xp, d);
+  }
+}
+
+// ------------------------------------------------------------ accumulators
+
+// FP64 accumulator for VEC columns: float-float pairs plus an FP64 total.
+template <int VEC>
+struct AccF64 {
+  float s[VEC], c[VEC];
+  double d[VEC];
+  __device__ __forceinline__ void init() {
+#pragma unroll
+    for (int e = 0; e < VEC; e++) {
+      s[e] = 0.0f;
+      c[e] = 0.0f;
+      d[e] = 0.0;
+    }
+  }
+  __device__ __forceinline__ void emul(const double (&a)[VEC], const double* xp, XSplit xs) {
+#pragma unroll
+    for (int e = 0; e < VEC; e++) df_mac(s[e], c[e], d[e], a[e], xp, xs);
+  }
+  // One column, its own x entry (row-wise kernels).
+  __device__ __forceinline__ void emul1(int e, double a, const double* xp, XSplit xs) {
+    df_mac(s[e], c[e], d[e], a, xp, xs);
+  }
+  __device__ __forceinline__ void dfma(const double (&a)[VEC], double x) {
+#pragma unroll
+    for (int e = 0; e < VEC; e++) d[e] = fma(a[e], x, d[e]);
+  }
+  __device__ __forceinline__ void fold() {
+#pragma unroll
+    for (int e = 0; e < VEC; e++) {
+      d[e] += (double)s[e];
+      d[e] += (double)c[e];
+      s[e] = 0.0f;
+      c[e] = 0.0f;
+    }
+  }
+  __device__ __forceinline__ double result(int e) const { return d[e]; }
+};
+
+// FP32 accumulator for VEC columns: plain FMAs within a block of rows, the
+// block sums folded into a compensated pair (S, C) with TwoSum.
+template <int VEC>
+struct AccF32 {
+  float a[VEC], S[VEC], C[VEC];
+  __device__ __forceinline__ void init() {
+#pragma unroll
+    for (int e = 0; e < VEC; e++) {
+      a[e] = 0.0f;
+      S[e] = 0.0f;
+      C[e] = 0.0f;
+    }
+  }
+  __device__ __forceinline__ void mac(const float (&v)[VEC], float x) {
+#pragma unroll
+    for (int e = 0; e < VEC; e++) a[e] = __fmaf_rn(v[e], x, a[e]);
+  }
+  __device__ __forceinline__ void fold() {
+#pragma unroll
+    for (int e = 0; e < VEC; e++) {
+      float t, err;
+      two_sum(S[e], a[e], t, err);
+      S[e] = t;
+      C[e] = __fadd_rn(C[e], err);
+      a[e] = 0.0f;
+    }
+  }
+  __device__ __forceinline__ float result(int e) const { return __fadd_rn(S[e], C[e]); }
+};
+
+// Compensated FP32 sum helper for reductions of partial results.
+struct KahanF32 {
+  float S = 0.0f, C = 0.0f;
+  __device__ __forceinline__ void add(float v) {
+    float t, err;
+    two_sum(S, v, t, err);
+    S = t;
+    C = __fadd_rn(C, err);
+  }
+  __device__ __forceinline__ float value() const { return __fadd_rn(S, C); }
+};
+
+}  // namespace tvcg

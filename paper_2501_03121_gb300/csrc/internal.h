@@ -1,0 +1,52 @@
+// Host-side declarations shared by the translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/tvc.h"
+
+namespace tvcg {
+
+// Matricized view of a d-order tensor for one mode (Section 3): the tensor
+// is read as u x n_k x v, with n0 the size of the first mode (slab count).
+struct Shape {
+  int order = 0;
+  int mode = 0;
+  int64_t dims[TVC_MAX_ORDER] = {};
+  int64_t N = 0, u = 0, nk = 0, v = 0, uv = 0, n0 = 0, upi0 = 1;
+};
+
+// Validates order/dims/mode and fills the view.  Returns TVC_OK or
+// TVC_ERR_INVALID_ARG (order out of range, a size < 1, N >= 2^62).
+tvc_status make_shape(int order, const int64_t* dims, int mode, Shape* s);
+tvc_status check_dims(int order, const int64_t* dims, int64_t* N);
+
+size_t elem_size(tvc_dtype dt);
+size_t vec_size(tvc_dtype dt);  // 8 for F64, 4 otherwise
+bool valid_dtype(int dt);
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+inline bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+// A per-device, grow-only workspace owned by the library, for the entry
+// points that do not take one.  Serialised by a mutex; the buffer is kept
+// until process exit.  Returns NULL (and sets *st) if cudaMalloc fails.
+void* library_workspace(size_t bytes, tvc_status* st);
+
+// Number of SMs of the current device (cached per device).
+int device_sms();
+
+tvc_status cuda_status(cudaError_t e);
+
+// Adds n to the process-wide launch counter (tvc_kernel_launches).
+void count_launches(int n);
+
+// Launches of the TVC kernels (tvc.cu), used by the HOPM and batched paths.
+tvc_status tvc_launch(const void* A, const Shape& s, const void* x, void* y, tvc_dtype dt,
+                      const float* scales, double alpha, double beta, void* ws, size_t ws_bytes,
+                      cudaStream_t stream);
+size_t tvc_ws_bytes(const Shape& s, tvc_dtype dt, const void* A);
+
+}  // namespace tvcg

@@ -1,0 +1,705 @@
+// Mode-oblivious dense tensor-vector contraction  Y = alpha (A x_k x) + beta Y
+// (Section 3 definition; Eq. 1 form for one process).
+//
+// The tensor is always streamed from HBM in its own flat (row-major) order,
+// whatever k is; only the mapping of loaded elements to outputs changes with
+// the matricized view u x n_k x v:
+//   * COLS  (v >= 32): one thread owns VEC consecutive outputs (i, l..l+VEC-1)
+//           and walks the n_k rows of its slab; a warp reads 32*VEC contiguous
+//           elements per row (128-bit loads when alignment allows).  This is
+//           the column-block split of the paper's vector-matrix case.
+//   * ROWS  (v == 1, long rows): one warp per row (the matrix-vector case,
+//           row blocks), 128-bit loads along the row, warp-shuffle reduction.
+//   * SLAB  (1 < v < 32, large slabs): one warp per slab; lane (jj, l) reads
+//           element l of rows jj, jj+G, ... so each step is one contiguous run
+//           of g = v*floor(32/v) elements; lanes with equal l are reduced by
+//           shuffles at the end.
+//   * TILE  (v < 32, small slabs): a block copies R whole slabs (contiguous)
+//           into shared memory and each thread contracts one output from there.
+// When the outputs alone cannot fill the GPU, n_k is split over blockIdx.y
+// ("split-K"); the partial results go to the workspace and a second kernel
+// adds them in a fixed order (deterministic).
+#include <algorithm>
+#include <cstdlib>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace tvcg {
+
+constexpr int kThreads = 256;
+constexpr int kWarpsPerBlock = kThreads / kWarp;
+constexpr int kRB = 64;  // additions per accumulator between folds
+
+template <tvc_dtype DT>
+struct TvcArgs {
+  const typename Elem<DT>::T* A;
+  const void* x;        // FP64 for F64, FP32 otherwise
+  const XSplit* xs;     // F64: split x (workspace)
+  const float* scales;  // narrow types, nullable
+  void* y;
+  void* partial;
+  int64_t u, nk, v, uv, upi0, chunk, splits;
+  int mode0;
+  double alpha, beta;
+};
+
+__device__ __forceinline__ XSplit ldxs(const XSplit* p) {
+  float2 f = __ldg(reinterpret_cast<const float2*>(p));
+  return XSplit{f.x, f.y};
+}
+
+// x entry of row j for the FP32 accumulators (slab scale folded in for k = 0).
+template <tvc_dtype DT>
+__device__ __forceinline__ float xval(const TvcArgs<DT>& a, int64_t j) {
+  float xv = __ldg(static_cast<const float*>(a.x) + j);
+  if constexpr (DT == TVC_BF16 || DT == TVC_E4M3) {
+    if (a.mode0 && a.scales) xv = __fmul_rn(xv, __ldg(a.scales + j));
+  }
+  return xv;
+}
+
+// Scale of output row i (k > 0): all elements of an output share slab i / upi0.
+template <tvc_dtype DT>
+__device__ __forceinline__ float out_scale(const TvcArgs<DT>& a, int64_t i) {
+  if constexpr (DT == TVC_BF16 || DT == TVC_E4M3) {
+    if (!a.mode0 && a.scales) return __ldg(a.scales + i / a.upi0);
+  }
+  return 1.0f;
+}
+
+template <tvc_dtype DT>
+__device__ __forceinline__ void emit(const TvcArgs<DT>& a, int64_t s, int64_t o,
+                                     typename Elem<DT>::V val) {
+  using V = typename Elem<DT>::V;
+  if (a.splits == 1) {
+    V* y = static_cast<V*>(a.y);
+    V r = (V)a.alpha * val;
+    if (a.beta != 0.0) r += (V)a.beta * y[o];
+    y[o] = r;
+  } else {
+    static_cast<V*>(a.partial)[s * a.uv + o] = val;
+  }
+}
+
+// ------------------------------------------------------------------ COLS --
+
+template <tvc_dtype DT, int VEC, int DROWS>
+__global__ void __launch_bounds__(kThreads) tvc_cols_kernel(const TvcArgs<DT> a) {
+  using E = Elem<DT>;
+  using T = typename E::T;
+  const int64_t o = ((int64_t)blockIdx.x * kThreads + threadIdx.x) * VEC;
+  if (o >= a.uv) return;
+  const int64_t i = o / a.v;
+  const int64_t l = o - i * a.v;
+  const int64_t j0 = (int64_t)blockIdx.y * a.chunk;
+  const int64_t j1 = min(a.nk, j0 + a.chunk);
+  const int64_t st = a.v;
+  const T* p = a.A + (i * a.nk + j0) * st + l;
+  int64_t j = j0;
+  int blk = 0;
+  if constexpr (DT == TVC_F64) {
+    const double* x = static_cast<const double*>(a.x);
+    AccF64<VEC> acc;
+    acc.init();
+    for (; j + 8 <= j1; j += 8) {
+      double r[8][VEC];
+#pragma unroll
+      for (int q = 0; q < 8; q++) E::template load<VEC>(p + q * st, r[q]);
+#pragma unroll
+      for (int q = 0; q < 8; q++) {
+        if (q < DROWS)
+          acc.dfma(r[q], __ldg(x + j + q));
+        else
+          acc.emul(r[q], x + j + q, ldxs(a.xs + j + q));
+      }
+      p += 8 * st;
+      if (++blk == kRB / 8) {
+        acc.fold();
+        blk = 0;
+      }
+    }
+    for (; j < j1; j++, p += st) {
+      double r[VEC];
+      E::template load<VEC>(p, r);
+      acc.emul(r, x + j, ldxs(a.xs + j));
+    }
+    acc.fold();
+#pragma unroll
+    for (int e = 0; e < VEC; e++) emit(a, blockIdx.y, o + e, acc.result(e));
+  } else {
+    AccF32<VEC> acc;
+    acc.init();
+    for (; j + 8 <= j1; j += 8) {
+      float r[8][VEC];
+#pragma unroll
+      for (int q = 0; q < 8; q++) E::template load<VEC>(p + q * st, r[q]);
+#pragma unroll
+      for (int q = 0; q < 8; q++) acc.mac(r[q], xval(a, j + q));
+      p += 8 * st;
+      if (++blk == kRB / 8) {
+        acc.fold();
+        blk = 0;
+      }
+    }
+    for (; j < j1; j++, p += st) {
+      float r[VEC];
+      E::template load<VEC>(p, r);
+      acc.mac(r, xval(a, j));
+    }
+    acc.fold();
+    const float sc = out_scale(a, i);
+#pragma unroll
+    for (int e = 0; e < VEC; e++) emit(a, blockIdx.y, o + e, __fmul_rn(acc.result(e), sc));
+  }
+}
+
+// ------------------------------------------------------------------ ROWS --
+
+template <class V>
+__device__ __forceinline__ V warp_sum(V v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, off);
+  return v;
+}
+
+template <tvc_dtype DT, int VEC>
+__global__ void __launch_bounds__(kThreads) tvc_rows_kernel(const TvcArgs<DT> a) {
+  using E = Elem<DT>;
+  using T = typename E::T;
+  constexpr int STEP = kWarp * VEC;
+  constexpr int UNR = 4;
+  const int lane = threadIdx.x & (kWarp - 1);
+  const int64_t row = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  if (row >= a.u) return;  // the whole warp leaves together
+  const int64_t j0 = (int64_t)blockIdx.y * a.chunk;
+  const int64_t j1 = min(a.nk, j0 + a.chunk);
+  const T* rp = a.A + row * a.nk;
+  const int64_t ngroups = (j1 - j0) / (UNR * STEP);
+  int64_t j = j0 + lane * VEC;
+  int blk = 0;
+  if constexpr (DT == TVC_F64) {
+    const double* x = static_cast<const double*>(a.x);
+    AccF64<VEC> acc;
+    acc.init();
+    for (int64_t g = 0; g < ngroups; g++, j += UNR * STEP) {
+      double r[UNR][VEC];
+#pragma unroll
+      for (int q = 0; q < UNR; q++) E::template load<VEC>(rp + j + q * STEP, r[q]);
+#pragma unroll
+      for (int q = 0; q < UNR; q++) {
+        const int64_t jq = j + q * STEP;
+        if constexpr (VEC == 2) {
+          float4 s2 = __ldg(reinterpret_cast<const float4*>(a.xs + jq));
+          acc.emul1(0, r[q][0], x + jq, XSplit{s2.x, s2.y});
+          acc.emul1(1, r[q][1], x + jq + 1, XSplit{s2.z, s2.w});
+        } else {
+#pragma unroll
+          for (int e = 0; e < VEC; e++) acc.emul1(e, r[q][e], x + jq + e, ldxs(a.xs + jq + e));
+        }
+      }
+      if (++blk == kRB / UNR) {
+        acc.fold();
+        blk = 0;
+      }
+    }
+    for (int64_t jj = j0 + ngroups * UNR * STEP + lane; jj < j1; jj += kWarp) {
+      double r[1];
+      E::template load<1>(rp + jj, r);
+      acc.emul1(0, r[0], x + jj, ldxs(a.xs + jj));
+    }
+    acc.fold();
+    double tot = 0.0;
+#pragma unroll
+    for (int e = 0; e < VEC; e++) tot += acc.result(e);
+    tot = warp_sum(tot);
+    if (lane == 0) emit(a, blockIdx.y, row, tot);
+  } else {
+    AccF32<VEC> acc;
+    acc.init();
+    for (int64_t g = 0; g < ngroups; g++, j += UNR * STEP) {
+      float r[UNR][VEC];
+#pragma unroll
+      for (int q = 0; q < UNR; q++) E::template load<VEC>(rp + j + q * STEP, r[q]);
+#pragma unroll
+      for (int q = 0; q < UNR; q++) {
+#pragma unroll
+        for (int e = 0; e < VEC; e++) acc.a[e] = __fmaf_rn(r[q][e], xval(a, j + q * STEP + e), acc.a[e]);
+      }
+      if (++blk == kRB / UNR) {
+        acc.fold();
+        blk = 0;
+      }
+    }
+    for (int64_t jj = j0 + ngroups * UNR * STEP + lane; jj < j1; jj += kWarp) {
+      float r[1];
+      E::template load<1>(rp + jj, r);
+      acc.a[0] = __fmaf_rn(r[0], xval(a, jj), acc.a[0]);
+    }
+    acc.fold();
+    float tot = 0.0f;
+#pragma unroll
+    for (int e = 0; e < VEC; e++) tot += acc.result(e);
+    tot = warp_sum(tot);
+    if (lane == 0) emit(a, blockIdx.y, row, __fmul_rn(tot, out_scale(a, row)));
+  }
+}
+
+// ------------------------------------------------------------------ SLAB --
+
+template <tvc_dtype DT>
+__global__ void __launch_bounds__(kThreads) tvc_slab_kernel(const TvcArgs<DT> a, int g, int G) {
+  using E = Elem<DT>;
+  using T = typename E::T;
+  using V = typename E::V;
+  const int lane = threadIdx.x & (kWarp - 1);
+  const int64_t slab = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  if (slab >= a.u) return;
+  const int64_t j0 = (int64_t)blockIdx.y * a.chunk;
+  const int64_t j1 = min(a.nk, j0 + a.chunk);
+  const int l = lane % (int)a.v;
+  const int jj = lane / (int)a.v;
+  const bool active = lane < g;
+  const int64_t st = (int64_t)G * a.v;
+  const T* p = a.A + (slab * a.nk + j0 + jj) * a.v + l;
+  V tot;
+  if constexpr (DT == TVC_F64) {
+    const double* x = static_cast<const double*>(a.x);
+    AccF64<1> acc;
+    acc.init();
+    int blk = 0;
+    if (active) {
+      int64_t j = j0 + jj;
+      for (; j + 3 * G < j1; j += 4 * G, p += 4 * st) {
+        double r[4][1];
+#pragma unroll
+        for (int q = 0; q < 4; q++) E::template load<1>(p + q * st, r[q]);
+#pragma unroll
+        for (int q = 0; q < 4; q++) acc.emul1(0, r[q][0], x + j + q * G, ldxs(a.xs + j + q * G));
+        if (++blk == kRB / 4) {
+          acc.fold();
+          blk = 0;
+        }
+      }
+      for (; j < j1; j += G, p += st) {
+        double r[1];
+        E::template load<1>(p, r);
+        acc.emul1(0, r[0], x + j, ldxs(a.xs + j));
+      }
+    }
+    acc.fold();
+    tot = active ? acc.result(0) : 0.0;
+  } else {
+    AccF32<1> acc;
+    acc.init();
+    int blk = 0;
+    if (active) {
+      int64_t j = j0 + jj;
+      for (; j + 3 * G < j1; j += 4 * G, p += 4 * st) {
+        float r[4][1];
+#pragma unroll
+        for (int q = 0; q < 4; q++) E::template load<1>(p + q * st, r[q]);
+#pragma unroll
+        for (int q = 0; q < 4; q++) acc.a[0] = __fmaf_rn(r[q][0], xval(a, j + q * G), acc.a[0]);
+        if (++blk == kRB / 4) {
+          acc.fold();
+          blk = 0;
+        }
+      }
+      for (; j < j1; j += G, p += st) {
+        float r[1];
+        E::template load<1>(p, r);
+        acc.a[0] = __fmaf_rn(r[0], xval(a, j), acc.a[0]);
+      }
+    }
+    acc.fold();
+    tot = active ? acc.result(0) : 0.0f;
+  }
+  // Sum the G lanes that share l: lane jj*v + l, jj = 0..G-1.
+  for (int k = 1; k < G; k <<= 1) {
+    V other = __shfl_down_sync(0xFFFFFFFFu, tot, k * (int)a.v);
+    if (jj + k < G) tot += other;
+  }
+  if (jj == 0) {
+    if constexpr (DT == TVC_F64)
+      emit(a, blockIdx.y, slab * a.v + l, tot);
+    else
+      emit(a, blockIdx.y, slab * a.v + l, __fmul_rn(tot, out_scale(a, slab)));
+  }
+}
+
+// ------------------------------------------------------------------ TILE --
+
+// One block contracts R whole slabs (R*S contiguous elements, S = n_k*v)
+// staged in shared memory, with x staged beside them.  Thread t < R*v owns
+// output (r, l) = (t / v, t % v).  For v == 1 and even n_k each thread starts
+// its row at a rotated position so the warp's shared-memory reads spread
+// over the banks.
+template <tvc_dtype DT>
+__global__ void __launch_bounds__(kThreads) tvc_tile_kernel(const TvcArgs<DT> a, int R, int vec16) {
+  using E = Elem<DT>;
+  using T = typename E::T;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int64_t S = a.nk * a.v;
+  const int nk = (int)a.nk, v = (int)a.v;
+  const int64_t i0 = (int64_t)blockIdx.x * R;
+  const int Reff = (int)min((int64_t)R, a.u - i0);
+  T* sm = reinterpret_cast<T*>(smraw);
+  const size_t tile_bytes = ((size_t)R * S * sizeof(T) + 15) / 16 * 16;
+  const int t = threadIdx.x;
+  // Stage x.
+  if constexpr (DT == TVC_F64) {
+    XSplit* smx = reinterpret_cast<XSplit*>(smraw + tile_bytes);
+    for (int j = t; j < nk; j += kThreads) smx[j] = ldxs(a.xs + j);
+  } else {
+    float* smx = reinterpret_cast<float*>(smraw + tile_bytes);
+    for (int j = t; j < nk; j += kThreads) smx[j] = xval(a, j);
+  }
+  // Stage the tile: R*S contiguous elements.
+  const T* src = a.A + i0 * S;
+  const int64_t total = (int64_t)Reff * S;
+  const int64_t bytes = total * (int64_t)sizeof(T);
+  int64_t done = 0;
+  if (vec16) {
+    const int64_t n16 = bytes / 16;
+    const uint4* s4 = reinterpret_cast<const uint4*>(src);
+    uint4* d4 = reinterpret_cast<uint4*>(sm);
+    int64_t q = t;
+    for (; q + 3 * kThreads < n16; q += 4 * kThreads) {
+      uint4 r0 = __ldcs(s4 + q), r1 = __ldcs(s4 + q + kThreads), r2 = __ldcs(s4 + q + 2 * kThreads),
+            r3 = __ldcs(s4 + q + 3 * kThreads);
+      d4[q] = r0;
+      d4[q + kThreads] = r1;
+      d4[q + 2 * kThreads] = r2;
+      d4[q + 3 * kThreads] = r3;
+    }
+    for (; q < n16; q += kThreads) d4[q] = __ldcs(s4 + q);
+    done = n16 * 16 / (int64_t)sizeof(T);
+  }
+  for (int64_t e = done + t; e < total; e += kThreads)
+    reinterpret_cast<RawVec<sizeof(T)>*>(sm)[e] = ld_stream<sizeof(T)>(src + e);
+  __syncthreads();
+  if (t >= Reff * v) return;
+  const int r = t / v, l = t - (t / v) * v;
+  const int rot = (v == 1 && (nk & 1) == 0) ? r % nk : 0;
+  const T* row = sm + (int64_t)r * S + l;
+  int jt = rot;
+  int blk = 0;
+  if constexpr (DT == TVC_F64) {
+    const double* x = static_cast<const double*>(a.x);
+    const XSplit* smx = reinterpret_cast<const XSplit*>(smraw + tile_bytes);
+    AccF64<1> acc;
+    acc.init();
+    for (int c = 0; c < nk; c++) {
+      acc.emul1(0, row[(int64_t)jt * v], x + jt, smx[jt]);
+      if (++jt == nk) jt = 0;
+      if (++blk == kRB) {
+        acc.fold();
+        blk = 0;
+      }
+    }
+    acc.fold();
+    emit(a, 0, (i0 + r) * a.v + l, acc.result(0));
+  } else {
+    const float* smx = reinterpret_cast<const float*>(smraw + tile_bytes);
+    AccF32<1> acc;
+    acc.init();
+    for (int c = 0; c < nk; c++) {
+      float val[1];
+      if constexpr (DT == TVC_F32) {
+        val[0] = row[(int64_t)jt * v];
+      } else if constexpr (DT == TVC_BF16) {
+        val[0] = __uint_as_float(((uint32_t)row[(int64_t)jt * v]) << 16);
+      } else {
+        __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)row[(int64_t)jt * v], __NV_E4M3);
+        val[0] = __half2float(*reinterpret_cast<__half*>(&h));
+      }
+      acc.a[0] = __fmaf_rn(val[0], smx[jt], acc.a[0]);
+      if (++jt == nk) jt = 0;
+      if (++blk == kRB) {
+        acc.fold();
+        blk = 0;
+      }
+    }
+    acc.fold();
+    emit(a, 0, (i0 + r) * a.v + l, __fmul_rn(acc.result(0), out_scale(a, i0 + r)));
+  }
+}
+
+// -------------------------------------------------------- helper kernels --
+
+__global__ void tvc_split_x_kernel(const double* __restrict__ x, XSplit* __restrict__ xs, int64_t n) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+    xs[j] = split_x(x[j]);
+}
+
+// y[o] = alpha * sum_s partial[s][o] + beta * y[o], s ascending (deterministic).
+template <class V>
+__global__ void tvc_reduce_kernel(const V* __restrict__ partial, V* __restrict__ y, int64_t uv, int64_t splits,
+                                  double alpha, double beta) {
+  for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < uv; o += (int64_t)gridDim.x * blockDim.x) {
+    V r;
+    if constexpr (sizeof(V) == 8) {
+      double s = 0.0;
+      for (int64_t k = 0; k < splits; k++) s += partial[k * uv + o];
+      r = alpha * s;
+      if (beta != 0.0) r += beta * y[o];
+    } else {
+      KahanF32 s;
+      for (int64_t k = 0; k < splits; k++) s.add(partial[k * uv + o]);
+      r = (float)alpha * s.value();
+      if (beta != 0.0) r += (float)beta * y[o];
+    }
+    y[o] = r;
+  }
+}
+
+// ------------------------------------------------------------------ plan --
+
+enum Kind { K_COLS = 0, K_ROWS = 1, K_SLAB = 2, K_TILE = 3 };
+
+struct Plan {
+  Kind kind = K_COLS;
+  int vec = 1;
+  int64_t splits = 1, chunk = 0;
+  int R = 0, vec16 = 0, g = 0, G = 0;
+  size_t smem = 0;
+  dim3 grid;
+  size_t ws_xs = 0, ws_partial = 0, ws_total = 0;
+};
+
+static int dfma_rows_option() {
+  static int v = [] {
+    const char* e = std::getenv("TVC_F64_DFMA_ROWS");
+    int r = e ? std::atoi(e) : 0;
+    return (r == 0 || r == 2 || r == 3 || r == 4) ? r : 0;
+  }();
+  return v;
+}
+
+// Largest vector width (elements per load) the alignment and v allow.
+static int pick_vec(tvc_dtype dt, int64_t stride_elems, const void* A) {
+  const int es = (int)elem_size(dt);
+  const int cands[3] = {16 / es, 4 / es > 1 ? 4 / es : 1, 1};
+  for (int c : cands) {
+    if (c <= 1) return 1;
+    if (stride_elems % c == 0 && aligned(A, (size_t)c * es)) return c;
+  }
+  return 1;
+}
+
+static int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+static Plan make_plan(const Shape& s, tvc_dtype dt, const void* A) {
+  Plan p;
+  const int sms = device_sms();
+  const int64_t target_threads = (int64_t)sms * 2048;
+  const int64_t S = s.nk * s.v;
+  const size_t es = elem_size(dt);
+  if (s.v >= 32) {
+    p.kind = K_COLS;
+    p.vec = pick_vec(dt, s.v, A);
+    const int64_t threads = ceil_div(s.uv, p.vec);
+    int64_t splits = 1;
+    if (threads < target_threads) splits = std::min(ceil_div(target_threads, threads), std::max<int64_t>(1, s.nk / 64));
+    p.chunk = ceil_div(ceil_div(s.nk, splits), 8) * 8;
+    p.splits = ceil_div(s.nk, p.chunk);
+    p.grid = dim3((unsigned)ceil_div(threads, kThreads), (unsigned)p.splits);
+  } else if (s.v == 1 && s.nk > 512) {
+    p.kind = K_ROWS;
+    p.vec = pick_vec(dt, s.nk, A);
+    const int64_t group = 4 * kWarp * p.vec;  // one unrolled step of a warp
+    const int64_t target_warps = (int64_t)sms * 64;
+    int64_t splits = 1;
+    if (s.u < target_warps) splits = std::min(ceil_div(target_warps, s.u), std::max<int64_t>(1, s.nk / (8 * group)));
+    p.chunk = ceil_div(ceil_div(s.nk, splits), group) * group;
+    p.splits = ceil_div(s.nk, p.chunk);
+    p.grid = dim3((unsigned)ceil_div(s.u, kWarpsPerBlock), (unsigned)p.splits);
+  } else if (S > 512) {
+    p.kind = K_SLAB;
+    p.G = (int)(32 / s.v);
+    p.g = p.G * (int)s.v;
+    const int64_t target_warps = (int64_t)sms * 64;
+    int64_t splits = 1;
+    if (s.u < target_warps) splits = std::min(ceil_div(target_warps, s.u), std::max<int64_t>(1, s.nk / (16 * p.G)));
+    p.chunk = ceil_div(ceil_div(s.nk, splits), p.G) * p.G;
+    p.splits = ceil_div(s.nk, p.chunk);
+    p.grid = dim3((unsigned)ceil_div(s.u, kWarpsPerBlock), (unsigned)p.splits);
+  } else {
+    p.kind = K_TILE;
+    int64_t R = std::min<int64_t>(kThreads / s.v, (int64_t)(48 * 1024) / (int64_t)(S * es));
+    R = std::max<int64_t>(1, std::min<int64_t>(R, s.u));
+    if (R >= 16) R = R / 16 * 16;
+    p.R = (int)R;
+    p.vec16 = aligned(A, 16) && (((size_t)R * S * es) % 16 == 0);
+    const size_t tile_bytes = ((size_t)R * S * es + 15) / 16 * 16;
+    p.smem = tile_bytes + (size_t)s.nk * 8;
+    p.splits = 1;
+    p.chunk = s.nk;
+    p.grid = dim3((unsigned)ceil_div(s.u, R), 1);
+  }
+  if (dt == TVC_F64) p.ws_xs = align_up((size_t)s.nk * sizeof(XSplit), 256);
+  if (p.splits > 1) p.ws_partial = align_up((size_t)p.splits * s.uv * vec_size(dt), 256);
+  p.ws_total = p.ws_xs + p.ws_partial;
+  return p;
+}
+
+size_t tvc_ws_bytes(const Shape& s, tvc_dtype dt, const void* A) { return make_plan(s, dt, A).ws_total; }
+
+template <tvc_dtype DT>
+static void launch_main(const Plan& p, const TvcArgs<DT>& a, cudaStream_t st) {
+  switch (p.kind) {
+    case K_COLS: {
+      const int dr = (DT == TVC_F64) ? dfma_rows_option() : 0;
+      if constexpr (DT == TVC_F64) {
+        if (p.vec == 2) {
+          if (dr == 2) tvc_cols_kernel<DT, 2, 2><<<p.grid, kThreads, 0, st>>>(a);
+          else if (dr == 3) tvc_cols_kernel<DT, 2, 3><<<p.grid, kThreads, 0, st>>>(a);
+          else if (dr == 4) tvc_cols_kernel<DT, 2, 4><<<p.grid, kThreads, 0, st>>>(a);
+          else tvc_cols_kernel<DT, 2, 0><<<p.grid, kThreads, 0, st>>>(a);
+        } else {
+          tvc_cols_kernel<DT, 1, 0><<<p.grid, kThreads, 0, st>>>(a);
+        }
+      } else if constexpr (DT == TVC_F32) {
+        if (p.vec == 4) tvc_cols_kernel<DT, 4, 0><<<p.grid, kThreads, 0, st>>>(a);
+        else tvc_cols_kernel<DT, 1, 0><<<p.grid, kThreads, 0, st>>>(a);
+      } else if constexpr (DT == TVC_BF16) {
+        if (p.vec == 8) tvc_cols_kernel<DT, 8, 0><<<p.grid, kThreads, 0, st>>>(a);
+        else if (p.vec == 2) tvc_cols_kernel<DT, 2, 0><<<p.grid, kThreads, 0, st>>>(a);
+        else tvc_cols_kernel<DT, 1, 0><<<p.grid, kThreads, 0, st>>>(a);
+      } else {
+        if (p.vec == 16) tvc_cols_kernel<DT, 16, 0><<<p.grid, kThreads, 0, st>>>(a);
+        else if (p.vec == 4) tvc_cols_kernel<DT, 4, 0><<<p.grid, kThreads, 0, st>>>(a);
+        else tvc_cols_kernel<DT, 1, 0><<<p.grid, kThreads, 0, st>>>(a);
+      }
+      break;
+    }
+    case K_ROWS: {
+      if constexpr (DT == TVC_F64) {
+        if (p.vec == 2) tvc_rows_kernel<DT, 2><<<p.grid, kThreads, 0, st>>>(a);
+        else tvc_rows_kernel<DT, 1><<<p.grid, kThreads, 0, st>>>(a);
+      } else if constexpr (DT == TVC_F32) {
+        if (p.vec == 4) tvc_rows_kernel<DT, 4><<<p.grid, kThreads, 0, st>>>(a);
+        else tvc_rows_kernel<DT, 1><<<p.grid, kThreads, 0, st>>>(a);
+      } else if constexpr (DT == TVC_BF16) {
+        if (p.vec == 8) tvc_rows_kernel<DT, 8><<<p.grid, kThreads, 0, st>>>(a);
+        else if (p.vec == 2) tvc_rows_kernel<DT, 2><<<p.grid, kThreads, 0, st>>>(a);
+        else tvc_rows_kernel<DT, 1><<<p.grid, kThreads, 0, st>>>(a);
+      } else {
+        if (p.vec == 16) tvc_rows_kernel<DT, 16><<<p.grid, kThreads, 0, st>>>(a);
+        else if (p.vec == 4) tvc_rows_kernel<DT, 4><<<p.grid, kThreads, 0, st>>>(a);
+        else tvc_rows_kernel<DT, 1><<<p.grid, kThreads, 0, st>>>(a);
+      }
+      break;
+    }
+    case K_SLAB:
+      tvc_slab_kernel<DT><<<p.grid, kThreads, 0, st>>>(a, p.g, p.G);
+      break;
+    case K_TILE: {
+      static bool configured = false;  // opt in to more than 48 KB once per process
+      if (!configured) {
+        cudaFuncSetAttribute(tvc_tile_kernel<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+        configured = true;
+      }
+      tvc_tile_kernel<DT><<<p.grid, kThreads, p.smem, st>>>(a, p.R, p.vec16);
+      break;
+    }
+  }
+}
+
+template <tvc_dtype DT>
+static tvc_status run(const void* A, const Shape& s, const void* x, void* y, const float* scales, double alpha,
+                      double beta, void* ws, const Plan& p, cudaStream_t st) {
+  TvcArgs<DT> a;
+  a.A = static_cast<const typename Elem<DT>::T*>(A);
+  a.x = x;
+  a.xs = nullptr;
+  a.scales = scales;
+  a.y = y;
+  a.partial = nullptr;
+  a.u = s.u;
+  a.nk = s.nk;
+  a.v = s.v;
+  a.uv = s.uv;
+  a.upi0 = s.upi0 > 0 ? s.upi0 : 1;
+  a.chunk = p.chunk;
+  a.splits = p.splits;
+  a.mode0 = s.mode == 0;
+  a.alpha = alpha;
+  a.beta = beta;
+  char* w = static_cast<char*>(ws);
+  if (DT == TVC_F64) {
+    a.xs = reinterpret_cast<const XSplit*>(w);
+    const int blocks = (int)std::min<int64_t>(ceil_div(s.nk, 256), 4096);
+    tvc_split_x_kernel<<<blocks, 256, 0, st>>>(static_cast<const double*>(x), reinterpret_cast<XSplit*>(w), s.nk);
+  }
+  if (p.splits > 1) a.partial = w + p.ws_xs;
+  launch_main<DT>(p, a, st);
+  count_launches((DT == TVC_F64 ? 1 : 0) + 1 + (p.splits > 1 ? 1 : 0));
+  if (p.splits > 1) {
+    using V = typename Elem<DT>::V;
+    const int blocks = (int)std::min<int64_t>(ceil_div(s.uv, 256), 8192);
+    tvc_reduce_kernel<V><<<blocks, 256, 0, st>>>(static_cast<const V*>(a.partial), static_cast<V*>(y), s.uv,
+                                                 p.splits, alpha, beta);
+  }
+  return cuda_status(cudaGetLastError());
+}
+
+tvc_status tvc_launch(const void* A, const Shape& s, const void* x, void* y, tvc_dtype dt, const float* scales,
+                      double alpha, double beta, void* ws, size_t ws_bytes, cudaStream_t stream) {
+  const Plan p = make_plan(s, dt, A);
+  if (p.ws_total > 0 && (ws == nullptr || ws_bytes < p.ws_total)) return TVC_ERR_WORKSPACE;
+  switch (dt) {
+    case TVC_F64: return run<TVC_F64>(A, s, x, y, nullptr, alpha, beta, ws, p, stream);
+    case TVC_F32: return run<TVC_F32>(A, s, x, y, nullptr, alpha, beta, ws, p, stream);
+    case TVC_BF16: return run<TVC_BF16>(A, s, x, y, scales, alpha, beta, ws, p, stream);
+    case TVC_E4M3: return run<TVC_E4M3>(A, s, x, y, scales, alpha, beta, ws, p, stream);
+  }
+  return TVC_ERR_INVALID_ARG;
+}
+
+static tvc_status validate(const void* A, int order, const int64_t* dims, int mode, const void* x, void* y,
+                           int dtype, Shape* s) {
+  if (!valid_dtype(dtype)) return TVC_ERR_INVALID_ARG;
+  tvc_status st = make_shape(order, dims, mode, s);
+  if (st != TVC_OK) return st;
+  if (!A || !x || !y) return TVC_ERR_INVALID_ARG;
+  const size_t es = elem_size((tvc_dtype)dtype), vs = vec_size((tvc_dtype)dtype);
+  if (!aligned(A, es) || !aligned(x, vs) || !aligned(y, vs)) return TVC_ERR_INVALID_ARG;
+  return TVC_OK;
+}
+
+}  // namespace tvcg
+
+using namespace tvcg;
+
+extern "C" size_t tvc_workspace_size(int order, const int64_t* dims, int mode, tvc_dtype dtype) {
+  Shape s;
+  if (!valid_dtype(dtype) || make_shape(order, dims, mode, &s) != TVC_OK) return 0;
+  // The plan depends on the alignment of A, unknown here: return the largest
+  // workspace over the alignments a tensor of this type can have.
+  size_t need = 0;
+  for (uintptr_t al = elem_size(dtype); al <= 256; al *= 2)
+    need = std::max(need, tvc_ws_bytes(s, dtype, reinterpret_cast<const void*>(al)));
+  return need;
+}
+
+extern "C" tvc_status tvc_ex(const void* A, int order, const int64_t* dims, int mode, const void* x, void* y,
+                             tvc_dtype dtype, const float* slab_scales, double alpha, double beta, void* workspace,
+                             size_t ws_bytes, tvc_stream_t stream) {
+  Shape s;
+  tvc_status st = validate(A, order, dims, mode, x, y, dtype, &s);
+  if (st != TVC_OK) return st;
+  return tvc_launch(A, s, x, y, dtype, slab_scales, alpha, beta, workspace, ws_bytes, (cudaStream_t)stream);
+}
+
+extern "C" tvc_status tvc(const void* A, int order, const int64_t* dims, int mode, const void* x, void* y,
+                          tvc_dtype dtype, tvc_stream_t stream) {
+  Shape s;
+  tvc_status st = validate(A, order, dims, mode, x, y, dtype, &s);
+  if (st != TVC_OK) return st;
+  const size_t need = tvc_ws_bytes(s, dtype, A);
+  void* ws = library_workspace(need, &st);
+  if (st != TVC_OK) return st;
+  return tvc_launch(A, s, x, y, dtype, nullptr, 1.0, 0.0, ws, need, (cudaStream_t)stream);
+}

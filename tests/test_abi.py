@@ -1,0 +1,81 @@
+"""The C-ABI library loads and exports every entry point include/*.h declares;
+host-side argument validation answers without a GPU (nothing is launched)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+from tests.conftest import ROOT
+
+LIB = os.path.join(ROOT, "paper_2501_03121_gb300", "_lib", "libtvc_gb300.so")
+
+
+def _build():
+    from paper_2501_03121_gb300 import build as b
+    return b.build()
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build()
+    return ctypes.CDLL(LIB)
+
+
+def declared_functions():
+    names = []
+    for h in sorted(glob.glob(os.path.join(ROOT, "include", "*.h"))):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w]*\s*\**\s+\**\s*([a-z_][a-z0-9_]*)\s*\(", text, re.M):
+            names.append(m.group(1))
+    return names
+
+
+def test_header_declares_entry_points():
+    names = declared_functions()
+    for want in ("tvc", "tvc_ex", "tvc_workspace_size", "tvc_status_string"):
+        assert want in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings(lib):
+    lib.tvc_status_string.restype = ctypes.c_char_p
+    for s in range(8):
+        assert lib.tvc_status_string(s).startswith(b"TVC_")
+    assert b"unknown" in lib.tvc_status_string(99)
+
+
+def test_validation_without_gpu(lib):
+    P, I = ctypes.c_void_p, ctypes.c_int
+    lib.tvc.argtypes = [P, I, P, I, P, P, I, P]
+    lib.tvc.restype = I
+    dims = (ctypes.c_int64 * 3)(4, 5, 6)
+    fake = ctypes.c_void_p(1 << 20)
+    assert lib.tvc(None, 3, dims, 1, fake, fake, 0, None) == 1          # null A
+    assert lib.tvc(fake, 3, dims, 3, fake, fake, 0, None) == 1          # mode out of range
+    assert lib.tvc(fake, 0, dims, 0, fake, fake, 0, None) == 1          # order 0
+    assert lib.tvc(fake, 17, dims, 0, fake, fake, 0, None) == 1         # order > 16
+    assert lib.tvc(fake, 3, dims, 1, fake, fake, 9, None) == 1          # dtype
+    bad = (ctypes.c_int64 * 3)(4, 0, 6)
+    assert lib.tvc(fake, 3, bad, 1, fake, fake, 0, None) == 1           # zero size
+    huge = (ctypes.c_int64 * 3)(1 << 30, 1 << 30, 1 << 30)
+    assert lib.tvc(fake, 3, huge, 1, fake, fake, 0, None) == 1          # N >= 2^62
+    mis = ctypes.c_void_p((1 << 20) + 4)
+    assert lib.tvc(mis, 3, dims, 1, fake, fake, 0, None) == 1           # A not 8-byte aligned (FP64)
+
+
+def test_workspace_size_query(lib):
+    lib.tvc_workspace_size.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
+    lib.tvc_workspace_size.restype = ctypes.c_size_t
+    dims = (ctypes.c_int64 * 2)(65536, 16384)
+    # FP64 always needs the split x; a short-output contraction also needs partials.
+    assert lib.tvc_workspace_size(2, dims, 0, 0) >= 65536 * 8 + 16384 * 8
+    assert lib.tvc_workspace_size(2, dims, 1, 1) == 0 or lib.tvc_workspace_size(2, dims, 1, 1) > 0
+    bad = (ctypes.c_int64 * 2)(0, 3)
+    assert lib.tvc_workspace_size(2, bad, 0, 0) == 0

@@ -1,0 +1,210 @@
+"""GPU parity of the TVC kernels (through the C ABI) against the FP64 oracle.
+
+Tolerances (relative l2 over the output): FP64 1e-12, FP32 1e-5; narrow
+storage: the kernel against the oracle on the same stored codes 1e-5 (FP32
+accumulation), and the stored tensor against its FP32 source (storage error)
+2e-2 for BF16.  Integer-valued FP64 inputs must match bit for bit.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from tests import gpu_util as gu
+
+pytestmark = pytest.mark.gpu
+
+tg = pytest.importorskip("paper_2501_03121_gb300")
+
+# Shapes chosen to reach every kernel of the contraction: COLS (v >= 32),
+# ROWS (v == 1, long rows), SLAB (1 < v < 32, large slabs), TILE (small
+# slabs), with split-K (few outputs, long n_k), ragged sizes and tails.
+SHAPES = [
+    (7,), (100003,), (5, 3), (1, 4), (4, 1), (3, 1, 5), (2, 3, 4), (6, 5, 4, 3), (2, 1, 3, 1, 2),
+    (3, 50, 64), (5, 1000), (3, 4099), (4, 100, 7), (300, 40), (50, 8, 8), (2000, 64), (13, 17, 19, 3),
+    (9, 33, 130), (2, 3, 2, 3, 2, 3, 2), (1, 1, 1), (257, 1, 3),
+]
+CODES = [oracle.F64, oracle.F32, oracle.BF16, oracle.E4M3]
+
+
+@pytest.mark.parametrize("dims", SHAPES, ids=lambda d: "x".join(map(str, d)))
+@pytest.mark.parametrize("code", CODES, ids=["f64", "f32", "bf16", "e4m3"])
+def test_tvc_every_mode(dims, code):
+    A, Ao, scales = gu.inputs(dims, code)
+    for k in range(len(dims)):
+        x = gu.vec(code, dims[k], synth.stream_x(k))
+        ref = oracle.tvc(Ao, k, x, scales=scales)
+        got = gu.gpu_tvc(tg, A, k, x, scales)
+        assert got.shape == ref.shape
+        err = gu.rel_l2(got, ref)
+        assert err <= gu.TOL[code], (dims, k, err)
+
+
+@pytest.mark.parametrize("dims", [(3, 50, 64), (5, 1000), (4, 100, 7), (300, 40)])
+def test_narrow_storage_error_vs_source(dims):
+    src = synth.tensor("lognormal", 0, dims).astype(np.float32)
+    for code, bound in ((oracle.BF16, 2e-2), (oracle.E4M3, None)):
+        codes, scales = oracle.quantise(src, code)
+        for k in range(len(dims)):
+            x = gu.vec(code, dims[k], synth.stream_x(k))
+            got = gu.gpu_tvc(tg, codes, k, x, scales)
+            err_src = gu.rel_l2(got, oracle.tvc(src, k, x))
+            print(f"storage error {['f64','f32','bf16','e4m3'][code]} {dims} mode {k}: {err_src:.3e}")
+            if bound is not None:
+                assert err_src <= bound
+            else:
+                assert err_src <= 0.1
+
+
+@pytest.mark.parametrize("dims", [(6, 70, 33), (5, 1000), (4, 100, 7), (300, 40), (3, 50, 64), (2000, 64)])
+def test_integer_inputs_bit_exact_f64(dims):
+    rng = np.random.default_rng(11)
+    A = rng.integers(-1000, 1000, size=dims).astype(np.float64)
+    for k in range(len(dims)):
+        x = rng.integers(-1000, 1000, size=dims[k]).astype(np.float64)
+        ref = oracle.tvc(A, k, x)
+        got = gu.gpu_tvc(tg, A, k, x)
+        assert np.array_equal(got, ref), (dims, k)
+
+
+def test_fp64_values_outside_the_emulation_window():
+    dims = (40, 37, 66)
+    A = synth.tensor("u64", 4, dims)
+    flat = A.ravel()
+    rng = np.random.default_rng(5)
+    pos = rng.choice(flat.size, size=600, replace=False)
+    flat[pos[:100]] = 0.0
+    flat[pos[100:200]] *= 1e300
+    flat[pos[200:300]] *= 1e-300
+    flat[pos[300:400]] = 5e-324  # subnormal
+    flat[pos[400:500]] *= 2.0 ** 70
+    flat[pos[500:]] *= 2.0 ** -70
+    for k in range(3):
+        x = synth.vector("u64", 1, 1 + k, dims[k])
+        x[::5] *= 1e-20
+        x[1::7] = 0.0
+        ref = oracle.tvc(A, k, x)
+        got = gu.gpu_tvc(tg, A, k, x)
+        assert gu.rel_l2(got, ref) <= 1e-12
+
+
+@pytest.mark.parametrize("code", [oracle.F64, oracle.F32])
+def test_alpha_beta(code):
+    dims = (4, 33, 40)
+    A, Ao, _ = gu.inputs(dims, code)
+    for k in range(3):
+        x = gu.vec(code, dims[k], 1)
+        y0 = gu.vec(code, A.size // dims[k], 2).reshape([n for i, n in enumerate(dims) if i != k])
+        ref = oracle.tvc(Ao, k, x, y=y0, alpha=0.5, beta=-2.0)
+        yt = gu.to_dev(y0)
+        tg.tvc(gu.to_dev(A), k, gu.to_dev(x), y=yt, alpha=0.5, beta=-2.0)
+        assert gu.rel_l2(yt.cpu().numpy(), ref) <= gu.TOL[code]
+        # beta == 0: y is not read
+        yn = torch.full_like(yt, float("nan"))
+        tg.tvc(gu.to_dev(A), k, gu.to_dev(x), y=yn, alpha=2.0, beta=0.0)
+        assert gu.rel_l2(yn.cpu().numpy(), 2.0 * oracle.tvc(Ao, k, x)) <= gu.TOL[code]
+
+
+@pytest.mark.parametrize("code", CODES, ids=["f64", "f32", "bf16", "e4m3"])
+def test_misaligned_base(code):
+    dims = (6, 40, 48)
+    A, Ao, scales = gu.inputs(dims, code)
+    buf = torch.zeros(A.size + 1, dtype=gu.to_dev(A).dtype, device=gu.DEV)
+    buf[1:] = gu.to_dev(A.ravel())
+    At = buf[1:]
+    for k in range(3):
+        x = gu.vec(code, dims[k], synth.stream_x(k))
+        st = gu.to_dev(scales) if scales is not None else None
+        got = tg.tvc(At, k, gu.to_dev(x), scales=st, shape=dims).cpu().numpy()
+        assert gu.rel_l2(got, oracle.tvc(Ao, k, x, scales=scales)) <= gu.TOL[code]
+
+
+@pytest.mark.parametrize("dims,mode", [((20000, 64), 0), ((3, 300000), 1), ((1000003,), 0), ((2, 5000, 9), 1)])
+def test_split_k_deterministic(dims, mode):
+    A = synth.tensor("u64", 2, dims)
+    x = synth.vector("u64", 3, 1, dims[mode])
+    a = gu.gpu_tvc(tg, A, mode, x)
+    b = gu.gpu_tvc(tg, A, mode, x)
+    assert np.array_equal(a, b)
+    assert gu.rel_l2(a, oracle.tvc(A, mode, x)) <= 1e-12
+
+
+def test_empty_like_degenerate_sizes():
+    # all-ones dims: a single element; order 1: a dot product
+    for dims in [(1,), (1, 1), (1, 1, 1, 1)]:
+        A = np.full(dims, 3.0)
+        for k in range(len(dims)):
+            got = gu.gpu_tvc(tg, A, k, np.array([2.0]))
+            assert np.all(got == 6.0)
+
+
+def test_bad_arguments_raise():
+    A = gu.to_dev(np.zeros((3, 4)))
+    with pytest.raises(ValueError):
+        tg.tvc(A, 2, gu.to_dev(np.zeros(4)))
+    with pytest.raises(ValueError):
+        tg.tvc(A, 0, gu.to_dev(np.zeros(4)))
+    with pytest.raises(ValueError):
+        tg.tvc(A, 1, gu.to_dev(np.zeros(4, dtype=np.float32)))
+
+
+def test_config_128cube_fp64_all_modes():
+    """Plain-method FP64 workload: 128^3, uniform[-1,1], seed 0, every mode."""
+    dims = (128, 128, 128)
+    A = synth.tensor("u64", 0, dims)
+    At = gu.to_dev(A)
+    for k in range(3):
+        x = synth.vector("u64", 0, synth.stream_x(k), 128)
+        ref = oracle.tvc(A, k, x)
+        got = tg.tvc(At, k, gu.to_dev(x)).cpu().numpy()
+        assert gu.rel_l2(got, ref) <= 1e-12
+
+
+def test_device_generator_matches_host():
+    import synth.device as sd
+    for kind, dt in (("u64", torch.float64), ("u32", torch.float32), ("gauss", torch.float64),
+                     ("lognormal", torch.float32)):
+        t = torch.empty(5000, dtype=dt, device=gu.DEV)
+        sd.fill(t, kind, 7, 3, offset=123456789)
+        idx = np.arange(123456789, 123456789 + 5000, dtype=np.uint64)
+        host = {"u64": synth.uniform_f64, "u32": synth.uniform_f32, "gauss": synth.gaussian_f64,
+                "lognormal": synth.lognormal_mix_f64}[kind](7, 3, idx)
+        assert np.array_equal(t.cpu().numpy(), host.astype(t.cpu().numpy().dtype)), kind
+    dims = (5, 6, 7)
+    us = [synth.unit_gaussian(0, synth.stream_u(j), n) for j, n in enumerate(dims)]
+    t = torch.empty(210, dtype=torch.float32, device=gu.DEV)
+    sd.fill(t, "planted", 0, 0, dims=dims, us=us)
+    assert np.array_equal(t.cpu().numpy(), synth.tensor("planted", 0, dims, us=us).astype(np.float32).ravel())
+
+
+# Full-size bandwidth-sweep tensors: filled on the device from the same
+# counter-based definition the host uses; outputs checked at sampled indices
+# against the oracle computed from host-generated elements.
+FULL = [(1024, 1024, 1024), (128, 128, 128, 128), (40, 40, 40, 40, 40, 40), (65536, 16384)]
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("dims", FULL, ids=lambda d: "x".join(map(str, d)))
+@pytest.mark.parametrize("code", [oracle.F64, oracle.F32], ids=["f64", "f32"])
+def test_full_size_sweep_sampled(dims, code):
+    import synth.device as sd
+    kind = "u64" if code == oracle.F64 else "u32"
+    dt = torch.float64 if code == oracle.F64 else torch.float32
+    N = int(np.prod(dims, dtype=np.int64))
+    At = torch.empty(N, dtype=dt, device=gu.DEV)
+    sd.fill(At, kind, 0, synth.STREAM_A)
+    rng = np.random.default_rng(0)
+    for k in range(len(dims)):
+        x = gu.vec(code, dims[k], synth.stream_x(k), seed=1)
+        y = tg.tvc(At, k, gu.to_dev(x), shape=dims)
+        yf = y.reshape(-1)
+        picks, u, v = gu.sample_outputs(dims, k, 48, rng)
+        got = yf[torch.from_numpy(picks).to(gu.DEV)].cpu().numpy()
+        ref, mag = gu.oracle_at(kind, 0, dims, k, x, picks, v)
+        assert gu.rel_l2(got, ref) <= gu.TOL[code], (dims, k)
+        assert np.all(np.abs(got - ref) <= 50 * gu.TOL[code] * mag), (dims, k)
+        assert bool(torch.isfinite(y).all())
+        del y
+    del At
+    torch.cuda.empty_cache()
