@@ -130,62 +130,75 @@ def dist_setup():
 
 # ----------------------------------------------------------- oracle timing
 
-def oracle_sample(budget_s=15.0, kinds=("f64", "f32")):
-    """Time the FP64 CPU oracle on a bounded sample of the workload: the same
-    tensors cut to their first slabs (dims[0] reduced so each sample holds
-    about 2^23 elements), contracted along every mode.  Returns (GB/s of
-    algorithmic bytes, threads, description, seconds)."""
-    import numpy as np
-    import oracle
-    import synth
-    oracle.build()
-    total_bytes = 0
-    total_t = 0.0
-    cut = []
-    for dims in TENSORS:
-        rest = math.prod(dims[1:])
-        n0 = max(1, min(dims[0], (1 << 23) // rest))
-        sd = (n0,) + tuple(dims[1:])
-        cut.append(sd)
-    t_start = time.perf_counter()
-    for kind in kinds:
-        for sd in cut:
-            A = synth.tensor("u64" if kind == "f64" else "u32", 0, sd)
-            es = 8 if kind == "f64" else 4
+class OracleSample:
+    """A bounded sample of the workload for the FP64 CPU oracle: each tensor
+    cut to its first slabs (dims[0] reduced so the cut holds about 2^22
+    elements), in FP64 and FP32 storage, contracted along every mode."""
+
+    def __init__(self, elems=1 << 22):
+        import oracle
+        import synth
+        oracle.build()
+        self.oracle = oracle
+        self.cut = []
+        for dims in TENSORS:
+            rest = math.prod(dims[1:])
+            n0 = max(1, min(dims[0], elems // rest))
+            self.cut.append((n0,) + tuple(dims[1:]))
+        self.items = []
+        for kind, es in (("u64", 8), ("u32", 4)):
+            for sd in self.cut:
+                A = synth.tensor(kind, 0, sd)
+                xs = [synth.vector("u64", 1, synth.stream_x(k), sd[k]) for k in range(len(sd))]
+                self.items.append((A, sd, xs, es))
+        self.desc = ("oracle TVC along every mode of " + ", ".join("x".join(map(str, c)) for c in self.cut) +
+                     " (the first slabs of each workload tensor), FP64 and FP32 storage")
+
+    def run_once(self):
+        nbytes, secs = 0, 0.0
+        for A, sd, xs, es in self.items:
             for k in range(len(sd)):
-                x = synth.vector("u64", 1, synth.stream_x(k), sd[k])
                 t0 = time.perf_counter()
-                oracle.tvc(A, k, x)
-                total_t += time.perf_counter() - t0
-                total_bytes += tvc_bytes(sd, k, es, es)
-            if time.perf_counter() - t_start > budget_s:
-                break
-    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    desc = ("oracle TVC along every mode of " + ", ".join("x".join(map(str, s)) for s in cut) +
-            " (first slabs of each workload tensor), " + "+".join(kinds))
-    return total_bytes / total_t / 1e9, threads, desc, total_t
+                self.oracle.tvc(A, k, xs[k])
+                secs += time.perf_counter() - t0
+                nbytes += tvc_bytes(sd, k, es, es)
+        return nbytes, secs
+
+    def timed(self, min_seconds):
+        nbytes, secs = 0, 0.0
+        while secs < min_seconds:
+            b, t = self.run_once()
+            nbytes += b
+            secs += t
+        return nbytes / secs / 1e9, secs
+
+
+def oracle_threads():
+    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
 
 
 def run_reference(args, world, rank):
     if rank != 0:
         return 0
     t0 = time.perf_counter()
-    vals = []
-    desc = ""
-    threads = 1
+    smp = OracleSample()
     for _ in range(args.warmup):
-        oracle_sample(budget_s=2.0, kinds=("f64",))
+        smp.run_once()
+    vals = []
+    t1 = time.perf_counter()
     for _ in range(args.steps):
-        gbs, threads, desc, _ = oracle_sample(budget_s=20.0, kinds=("f64", "f32"))
-        vals.append(gbs)
+        b, t = smp.run_once()
+        vals.append(b / t / 1e9)
+    step_s = (time.perf_counter() - t1) / max(1, args.steps)
     v = statistics.median(vals)
-    wall = time.perf_counter() - t0
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GB/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * wall / max(1, args.steps + args.warmup),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * step_s,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": desc},
-            "cpu_baseline": {"value": v, "unit": "GB/s", "cores": threads, "kind": "oracle", "sample": desc},
-            "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "config": {"workload": WORKLOAD, "sample": smp.desc},
+            "cpu_baseline": {"value": v, "unit": "GB/s", "cores": oracle_threads(), "kind": "oracle",
+                             "sample": smp.desc},
+            "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": round(time.perf_counter() - t0, 1)}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -348,8 +361,9 @@ def main(argv=None):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        gbs, threads, desc, secs = oracle_sample()
-        cpu = {"value": gbs, "unit": "GB/s", "cores": threads, "kind": "oracle", "sample": desc,
+        smp = OracleSample()
+        gbs, secs = smp.timed(10.0)
+        cpu = {"value": gbs, "unit": "GB/s", "cores": oracle_threads(), "kind": "oracle", "sample": smp.desc,
                "seconds": round(secs, 2)}
 
     if rank == 0:

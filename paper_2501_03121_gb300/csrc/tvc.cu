@@ -8,13 +8,13 @@
 //           and walks the n_k rows of its slab; a warp reads 32*VEC contiguous
 //           elements per row (128-bit loads when alignment allows).  This is
 //           the column-block split of the paper's vector-matrix case.
-//   * ROWS  (v == 1, long rows): one warp per row (the matrix-vector case,
-//           row blocks), 128-bit loads along the row, warp-shuffle reduction.
+//   * ROWS  (v == 1): a group of G lanes per row (the matrix-vector case,
+//           row blocks), 128-bit loads along the row, shuffle reduction.
 //   * SLAB  (1 < v < 32, large slabs): one warp per slab; lane (jj, l) reads
 //           element l of rows jj, jj+G, ... so each step is one contiguous run
 //           of g = v*floor(32/v) elements; lanes with equal l are reduced by
 //           shuffles at the end.
-//   * TILE  (v < 32, small slabs): a block copies R whole slabs (contiguous)
+//   * TILE  (1 < v < 32, small slabs): a block copies R whole slabs (contiguous)
 //           into shared memory and each thread contracts one output from there.
 // When the outputs alone cannot fill the GPU, n_k is split over blockIdx.y
 // ("split-K"); the partial results go to the workspace and a second kernel
@@ -163,20 +163,29 @@ __device__ __forceinline__ V warp_sum(V v) {
   return v;
 }
 
-template <tvc_dtype DT, int VEC>
+// Rows of the matrix-vector case (v == 1): a group of G lanes (G a power of
+// two <= 32) owns one row segment; lane p of the group loads VEC consecutive
+// elements at p*VEC + step*G*VEC, so a warp reads 32/G rows at once, each
+// as one contiguous run per step.  The group's partial sums are reduced by
+// xor-shuffles; for FP64 the float-float pairs are reduced in FP32 with
+// TwoSum, so the reduction stays off the FP64 pipe.
+template <tvc_dtype DT, int VEC, int G>
 __global__ void __launch_bounds__(kThreads) tvc_rows_kernel(const TvcArgs<DT> a) {
   using E = Elem<DT>;
   using T = typename E::T;
-  constexpr int STEP = kWarp * VEC;
+  constexpr int STEP = G * VEC;
   constexpr int UNR = 4;
+  constexpr int RPW = kWarp / G;  // rows per warp
   const int lane = threadIdx.x & (kWarp - 1);
-  const int64_t row = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-  if (row >= a.u) return;  // the whole warp leaves together
+  const int p = lane & (G - 1);
+  const int64_t row = ((int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5)) * RPW + lane / G;
+  const bool active = row < a.u;
   const int64_t j0 = (int64_t)blockIdx.y * a.chunk;
   const int64_t j1 = min(a.nk, j0 + a.chunk);
-  const T* rp = a.A + row * a.nk;
-  const int64_t ngroups = (j1 - j0) / (UNR * STEP);
-  int64_t j = j0 + lane * VEC;
+  const T* rp = a.A + (active ? row : 0) * a.nk;
+  const int64_t ngroups = active ? (j1 - j0) / (UNR * STEP) : 0;
+  const int64_t jt0 = j0 + ngroups * UNR * STEP;  // start of the ragged tail
+  int64_t j = j0 + p * VEC;
   int blk = 0;
   if constexpr (DT == TVC_F64) {
     const double* x = static_cast<const double*>(a.x);
@@ -203,17 +212,38 @@ __global__ void __launch_bounds__(kThreads) tvc_rows_kernel(const TvcArgs<DT> a)
         blk = 0;
       }
     }
-    for (int64_t jj = j0 + ngroups * UNR * STEP + lane; jj < j1; jj += kWarp) {
-      double r[1];
-      E::template load<1>(rp + jj, r);
-      acc.emul1(0, r[0], x + jj, ldxs(a.xs + jj));
-    }
-    acc.fold();
-    double tot = 0.0;
+    if (active)
+      for (int64_t jj = jt0 + p; jj < j1; jj += G) {
+        double r[1];
+        E::template load<1>(rp + jj, r);
+        acc.emul1(0, r[0], x + jj, ldxs(a.xs + jj));
+      }
+    // Combine the VEC columns of the lane into pair 0 (and total d).
+    float s = acc.s[0], c = acc.c[0];
+    double d = acc.d[0];
 #pragma unroll
-    for (int e = 0; e < VEC; e++) tot += acc.result(e);
-    tot = warp_sum(tot);
-    if (lane == 0) emit(a, blockIdx.y, row, tot);
+    for (int e = 1; e < VEC; e++) {
+      float t, err;
+      two_sum(s, acc.s[e], t, err);
+      s = t;
+      c = __fadd_rn(c, __fadd_rn(acc.c[e], err));
+      d += acc.d[e];
+    }
+    const bool need_d = __any_sync(0xFFFFFFFFu, d != 0.0);
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) {
+      const float s2 = __shfl_xor_sync(0xFFFFFFFFu, s, off);
+      const float c2 = __shfl_xor_sync(0xFFFFFFFFu, c, off);
+      float t, err;
+      two_sum(s, s2, t, err);
+      s = t;
+      c = __fadd_rn(c, __fadd_rn(c2, err));
+    }
+    if (need_d) {
+#pragma unroll
+      for (int off = G / 2; off > 0; off >>= 1) d += __shfl_xor_sync(0xFFFFFFFFu, d, off);
+    }
+    if (active && p == 0) emit(a, blockIdx.y, row, (d + (double)s) + (double)c);
   } else {
     AccF32<VEC> acc;
     acc.init();
@@ -231,17 +261,19 @@ __global__ void __launch_bounds__(kThreads) tvc_rows_kernel(const TvcArgs<DT> a)
         blk = 0;
       }
     }
-    for (int64_t jj = j0 + ngroups * UNR * STEP + lane; jj < j1; jj += kWarp) {
-      float r[1];
-      E::template load<1>(rp + jj, r);
-      acc.a[0] = __fmaf_rn(r[0], xval(a, jj), acc.a[0]);
-    }
+    if (active)
+      for (int64_t jj = jt0 + p; jj < j1; jj += G) {
+        float r[1];
+        E::template load<1>(rp + jj, r);
+        acc.a[0] = __fmaf_rn(r[0], xval(a, jj), acc.a[0]);
+      }
     acc.fold();
     float tot = 0.0f;
 #pragma unroll
     for (int e = 0; e < VEC; e++) tot += acc.result(e);
-    tot = warp_sum(tot);
-    if (lane == 0) emit(a, blockIdx.y, row, __fmul_rn(tot, out_scale(a, row)));
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) tot += __shfl_xor_sync(0xFFFFFFFFu, tot, off);
+    if (active && p == 0) emit(a, blockIdx.y, row, __fmul_rn(tot, out_scale(a, row)));
   }
 }
 
@@ -505,16 +537,22 @@ static Plan make_plan(const Shape& s, tvc_dtype dt, const void* A) {
     p.chunk = ceil_div(ceil_div(s.nk, splits), 8) * 8;
     p.splits = ceil_div(s.nk, p.chunk);
     p.grid = dim3((unsigned)ceil_div(threads, kThreads), (unsigned)p.splits);
-  } else if (s.v == 1 && s.nk > 512) {
+  } else if (s.v == 1) {
     p.kind = K_ROWS;
     p.vec = pick_vec(dt, s.nk, A);
-    const int64_t group = 4 * kWarp * p.vec;  // one unrolled step of a warp
-    const int64_t target_warps = (int64_t)sms * 64;
+    // Lanes per row: the largest power of two <= 32 that still gives every
+    // lane at least four loads of its row (at least 2 lanes).
+    int G = 32;
+    while (G > 2 && (int64_t)G * p.vec * 4 > s.nk) G >>= 1;
+    p.G = G;
+    const int64_t group = 4 * (int64_t)G * p.vec;  // one unrolled step of a group
+    const int64_t rows_per_block = (int64_t)kWarpsPerBlock * (kWarp / G);
+    const int64_t target_groups = (int64_t)sms * 64 * (kWarp / G);
     int64_t splits = 1;
-    if (s.u < target_warps) splits = std::min(ceil_div(target_warps, s.u), std::max<int64_t>(1, s.nk / (8 * group)));
+    if (s.u < target_groups) splits = std::min(ceil_div(target_groups, s.u), std::max<int64_t>(1, s.nk / (8 * group)));
     p.chunk = ceil_div(ceil_div(s.nk, splits), group) * group;
     p.splits = ceil_div(s.nk, p.chunk);
-    p.grid = dim3((unsigned)ceil_div(s.u, kWarpsPerBlock), (unsigned)p.splits);
+    p.grid = dim3((unsigned)ceil_div(s.u, rows_per_block), (unsigned)p.splits);
   } else if (S > 512) {
     p.kind = K_SLAB;
     p.G = (int)(32 / s.v);
@@ -546,6 +584,36 @@ static Plan make_plan(const Shape& s, tvc_dtype dt, const void* A) {
 
 size_t tvc_ws_bytes(const Shape& s, tvc_dtype dt, const void* A) { return make_plan(s, dt, A).ws_total; }
 
+template <tvc_dtype DT, int VEC>
+static void launch_rows_vec(const Plan& p, const TvcArgs<DT>& a, cudaStream_t st) {
+  switch (p.G) {
+    case 2: tvc_rows_kernel<DT, VEC, 2><<<p.grid, kThreads, 0, st>>>(a); break;
+    case 4: tvc_rows_kernel<DT, VEC, 4><<<p.grid, kThreads, 0, st>>>(a); break;
+    case 8: tvc_rows_kernel<DT, VEC, 8><<<p.grid, kThreads, 0, st>>>(a); break;
+    case 16: tvc_rows_kernel<DT, VEC, 16><<<p.grid, kThreads, 0, st>>>(a); break;
+    default: tvc_rows_kernel<DT, VEC, 32><<<p.grid, kThreads, 0, st>>>(a); break;
+  }
+}
+
+template <tvc_dtype DT>
+static void launch_rows(const Plan& p, const TvcArgs<DT>& a, cudaStream_t st) {
+  if constexpr (DT == TVC_F64) {
+    if (p.vec == 2) launch_rows_vec<DT, 2>(p, a, st);
+    else launch_rows_vec<DT, 1>(p, a, st);
+  } else if constexpr (DT == TVC_F32) {
+    if (p.vec == 4) launch_rows_vec<DT, 4>(p, a, st);
+    else launch_rows_vec<DT, 1>(p, a, st);
+  } else if constexpr (DT == TVC_BF16) {
+    if (p.vec == 8) launch_rows_vec<DT, 8>(p, a, st);
+    else if (p.vec == 2) launch_rows_vec<DT, 2>(p, a, st);
+    else launch_rows_vec<DT, 1>(p, a, st);
+  } else {
+    if (p.vec == 16) launch_rows_vec<DT, 16>(p, a, st);
+    else if (p.vec == 4) launch_rows_vec<DT, 4>(p, a, st);
+    else launch_rows_vec<DT, 1>(p, a, st);
+  }
+}
+
 template <tvc_dtype DT>
 static void launch_main(const Plan& p, const TvcArgs<DT>& a, cudaStream_t st) {
   switch (p.kind) {
@@ -574,24 +642,9 @@ static void launch_main(const Plan& p, const TvcArgs<DT>& a, cudaStream_t st) {
       }
       break;
     }
-    case K_ROWS: {
-      if constexpr (DT == TVC_F64) {
-        if (p.vec == 2) tvc_rows_kernel<DT, 2><<<p.grid, kThreads, 0, st>>>(a);
-        else tvc_rows_kernel<DT, 1><<<p.grid, kThreads, 0, st>>>(a);
-      } else if constexpr (DT == TVC_F32) {
-        if (p.vec == 4) tvc_rows_kernel<DT, 4><<<p.grid, kThreads, 0, st>>>(a);
-        else tvc_rows_kernel<DT, 1><<<p.grid, kThreads, 0, st>>>(a);
-      } else if constexpr (DT == TVC_BF16) {
-        if (p.vec == 8) tvc_rows_kernel<DT, 8><<<p.grid, kThreads, 0, st>>>(a);
-        else if (p.vec == 2) tvc_rows_kernel<DT, 2><<<p.grid, kThreads, 0, st>>>(a);
-        else tvc_rows_kernel<DT, 1><<<p.grid, kThreads, 0, st>>>(a);
-      } else {
-        if (p.vec == 16) tvc_rows_kernel<DT, 16><<<p.grid, kThreads, 0, st>>>(a);
-        else if (p.vec == 4) tvc_rows_kernel<DT, 4><<<p.grid, kThreads, 0, st>>>(a);
-        else tvc_rows_kernel<DT, 1><<<p.grid, kThreads, 0, st>>>(a);
-      }
+    case K_ROWS:
+      launch_rows<DT>(p, a, st);
       break;
-    }
     case K_SLAB:
       tvc_slab_kernel<DT><<<p.grid, kThreads, 0, st>>>(a, p.g, p.G);
       break;

@@ -1,0 +1,52 @@
+"""One contraction case, repeated, for profiling (ncu) and quick timing.
+
+    python -m paper_2501_03121_gb300.profile_case --dims 512 1024 1024 --mode 1 --dtype f64 --reps 3
+
+Fills A (uniform [-1, 1), seed 0) on the device, runs `reps` contractions
+and prints the CUDA-event time and achieved GB/s of the last one.
+"""
+import argparse
+import math
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main(argv=None):
+    import torch
+
+    import synth
+    import synth.device as sd
+    import paper_2501_03121_gb300 as tg
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--dims", type=int, nargs="+", required=True)
+    ap.add_argument("--mode", type=int, default=0)
+    ap.add_argument("--dtype", default="f64", choices=["f64", "f32"])
+    ap.add_argument("--reps", type=int, default=3)
+    a = ap.parse_args(argv)
+    dt = torch.float64 if a.dtype == "f64" else torch.float32
+    kind = "u64" if a.dtype == "f64" else "u32"
+    N = math.prod(a.dims)
+    A = torch.empty(N, dtype=dt, device="cuda")
+    sd.fill(A, kind, 0, synth.STREAM_A)
+    x = torch.from_numpy(synth.vector(kind, 1, synth.stream_x(a.mode), a.dims[a.mode])).cuda()
+    y = torch.empty(N // a.dims[a.mode], dtype=dt, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms = 0.0
+    for _ in range(a.reps):
+        e0.record()
+        tg.tvc(A, a.mode, x, y=y, shape=a.dims)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+    es = A.element_size()
+    nbytes = N * es + a.dims[a.mode] * es + (N // a.dims[a.mode]) * es
+    print(f"dims={a.dims} mode={a.mode} {a.dtype}: {ms:.3f} ms  {nbytes / ms / 1e6:.1f} GB/s")
+
+
+if __name__ == "__main__":
+    main()
