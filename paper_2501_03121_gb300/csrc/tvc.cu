@@ -41,6 +41,7 @@ struct TvcArgs {
   void* partial;
   int64_t u, nk, v, uv, upi0, chunk, splits;
   int mode0;
+  int plain;  // splits == 1, alpha == 1, beta == 0: y[o] = value
   double alpha, beta;
 };
 
@@ -72,7 +73,9 @@ template <tvc_dtype DT>
 __device__ __forceinline__ void emit(const TvcArgs<DT>& a, int64_t s, int64_t o,
                                      typename Elem<DT>::V val) {
   using V = typename Elem<DT>::V;
-  if (a.splits == 1) {
+  if (a.plain) {
+    static_cast<V*>(a.y)[o] = val;
+  } else if (a.splits == 1) {
     V* y = static_cast<V*>(a.y);
     V r = (V)a.alpha * val;
     if (a.beta != 0.0) r += (V)a.beta * y[o];
@@ -274,6 +277,137 @@ __global__ void __launch_bounds__(kThreads) tvc_rows_kernel(const TvcArgs<DT> a)
 #pragma unroll
     for (int off = G / 2; off > 0; off >>= 1) tot += __shfl_xor_sync(0xFFFFFFFFu, tot, off);
     if (active && p == 0) emit(a, blockIdx.y, row, __fmul_rn(tot, out_scale(a, row)));
+  }
+}
+
+// Short rows (v == 1, n_k <= NST*G*VEC): a group of G lanes (runtime, power
+// of two <= 32) owns B rows per iteration; lane p covers the NST steps
+// j = p*VEC + q*G*VEC of each.  Those positions are the same in every row,
+// so each lane keeps its pieces of x in registers while the groups walk the
+// rows persistently (grid-stride).  All B*NST loads of an iteration are
+// issued before any arithmetic, which keeps enough bytes in flight.
+template <tvc_dtype DT, int VEC, int NST>
+__global__ void __launch_bounds__(kThreads) tvc_rows_short_kernel(const TvcArgs<DT> a, int G) {
+  // Rows per group per iteration: about 32 elements of loads per lane.
+  constexpr int B = (32 / (NST * VEC)) < 1 ? 1 : ((32 / (NST * VEC)) > 4 ? 4 : (32 / (NST * VEC)));
+  using E = Elem<DT>;
+  using T = typename E::T;
+  using Cm = typename E::C;
+  const int lane = threadIdx.x & (kWarp - 1);
+  const int p = lane & (G - 1);
+  const int rpw = kWarp / G;
+  const int64_t warp_row0 = ((int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5)) * rpw * B;
+  const int64_t rows_per_iter = (int64_t)gridDim.x * kWarpsPerBlock * rpw * B;
+  const int nk = (int)a.nk;
+  const int step = G * VEC;
+  float xh[NST][VEC], xl[NST][VEC];
+#pragma unroll
+  for (int q = 0; q < NST; q++)
+#pragma unroll
+    for (int e = 0; e < VEC; e++) {
+      const int j = p * VEC + q * step + e;
+      if constexpr (DT == TVC_F64) {
+        XSplit t = (j < nk) ? ldxs(a.xs + j) : XSplit{0.0f, 0.0f};
+        xh[q][e] = t.xh;
+        xl[q][e] = t.xl;
+      } else {
+        xh[q][e] = (j < nk) ? xval(a, j) : 0.0f;
+        xl[q][e] = 0.0f;
+      }
+    }
+  // Row b of the warp's iteration: wr + b*rpw + lane/G.
+  for (int64_t wr = warp_row0; wr < a.u; wr += rows_per_iter) {
+    Cm r[B][NST][VEC];
+#pragma unroll
+    for (int b = 0; b < B; b++) {
+      const int64_t row = wr + (int64_t)b * rpw + lane / G;
+      const T* rp = a.A + row * a.nk;
+#pragma unroll
+      for (int q = 0; q < NST; q++) {
+        const int j = p * VEC + q * step;
+        if (row < a.u && j < nk) {
+          E::template load<VEC>(rp + j, r[b][q]);
+        } else {
+#pragma unroll
+          for (int e = 0; e < VEC; e++) r[b][q][e] = (Cm)0;
+        }
+      }
+    }
+    if constexpr (DT == TVC_F64) {
+      const double* x = static_cast<const double*>(a.x);
+      float sb[B], cb[B];
+      double db[B];
+      bool anyd = false;
+#pragma unroll
+      for (int b = 0; b < B; b++) {
+        const int64_t row = wr + (int64_t)b * rpw + lane / G;
+        float s = 0.0f, c = 0.0f;
+        double d = 0.0;
+#pragma unroll
+        for (int q = 0; q < NST; q++) {
+          // Skip padding (past the row or past the last row): a zero would
+          // take the out-of-window path.
+          if (row < a.u && p * VEC + q * step < nk) {
+#pragma unroll
+            for (int e = 0; e < VEC; e++)
+              df_mac(s, c, d, r[b][q][e], x + (p * VEC + q * step + e), XSplit{xh[q][e], xl[q][e]});
+          }
+        }
+        sb[b] = s;
+        cb[b] = c;
+        db[b] = d;
+        anyd |= (__double_as_longlong(d) != 0);  // integer test: no FP64 pipe
+      }
+      // Group reductions of the B rows (independent, so they interleave).
+      for (int off = G / 2; off > 0; off >>= 1) {
+#pragma unroll
+        for (int b = 0; b < B; b++) {
+          const float s2 = __shfl_xor_sync(0xFFFFFFFFu, sb[b], off);
+          const float c2 = __shfl_xor_sync(0xFFFFFFFFu, cb[b], off);
+          float t, err;
+          two_sum(sb[b], s2, t, err);
+          sb[b] = t;
+          cb[b] = __fadd_rn(cb[b], __fadd_rn(c2, err));
+        }
+      }
+      if (__any_sync(0xFFFFFFFFu, anyd)) {
+        for (int off = G / 2; off > 0; off >>= 1) {
+#pragma unroll
+          for (int b = 0; b < B; b++) db[b] += __shfl_xor_sync(0xFFFFFFFFu, db[b], off);
+        }
+      }
+      // Epilogue: every lane of a group holds the B results; lane p takes
+      // rows b = p, p + G, ... (picked with selects, not register indexing),
+      // so one FP64 conversion serves up to B rows per group.
+      for (int b0 = 0; b0 < B; b0 += G) {
+        const int bsel = b0 + p;
+        float s = 0.0f, c = 0.0f;
+        double d = 0.0;
+#pragma unroll
+        for (int b = 0; b < B; b++)
+          if (b == bsel) {
+            s = sb[b];
+            c = cb[b];
+            d = db[b];
+          }
+        const int64_t row = wr + (int64_t)bsel * rpw + lane / G;
+        if (bsel < B && row < a.u) emit(a, 0, row, (d + (double)s) + (double)c);
+      }
+    } else {
+#pragma unroll
+    for (int b = 0; b < B; b++) {
+      const int64_t row = wr + (int64_t)b * rpw + lane / G;
+      {
+        float acc = 0.0f;
+#pragma unroll
+        for (int q = 0; q < NST; q++)
+#pragma unroll
+          for (int e = 0; e < VEC; e++) acc = __fmaf_rn(r[b][q][e], xh[q][e], acc);
+        for (int off = G / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, off);
+        if (row < a.u && p == 0) emit(a, 0, row, __fmul_rn(acc, out_scale(a, row)));
+      }
+    }
+    }
   }
 }
 
@@ -488,13 +622,13 @@ __global__ void tvc_reduce_kernel(const V* __restrict__ partial, V* __restrict__
 
 // ------------------------------------------------------------------ plan --
 
-enum Kind { K_COLS = 0, K_ROWS = 1, K_SLAB = 2, K_TILE = 3 };
+enum Kind { K_COLS = 0, K_ROWS = 1, K_SLAB = 2, K_TILE = 3, K_ROWS_SHORT = 4 };
 
 struct Plan {
   Kind kind = K_COLS;
   int vec = 1;
   int64_t splits = 1, chunk = 0;
-  int R = 0, vec16 = 0, g = 0, G = 0;
+  int R = 0, vec16 = 0, g = 0, G = 0, nst = 0;
   size_t smem = 0;
   dim3 grid;
   size_t ws_xs = 0, ws_partial = 0, ws_total = 0;
@@ -510,11 +644,12 @@ static int dfma_rows_option() {
 }
 
 // Largest vector width (elements per load) the alignment and v allow.
-static int pick_vec(tvc_dtype dt, int64_t stride_elems, const void* A) {
+static int pick_vec(tvc_dtype dt, int64_t stride_elems, const void* A, int max_vec = 16) {
   const int es = (int)elem_size(dt);
   const int cands[3] = {16 / es, 4 / es > 1 ? 4 / es : 1, 1};
   for (int c : cands) {
     if (c <= 1) return 1;
+    if (c > max_vec) continue;
     if (stride_elems % c == 0 && aligned(A, (size_t)c * es)) return c;
   }
   return 1;
@@ -537,6 +672,23 @@ static Plan make_plan(const Shape& s, tvc_dtype dt, const void* A) {
     p.chunk = ceil_div(ceil_div(s.nk, splits), 8) * 8;
     p.splits = ceil_div(s.nk, p.chunk);
     p.grid = dim3((unsigned)ceil_div(threads, kThreads), (unsigned)p.splits);
+  } else if (s.v == 1 && s.nk <= 8 * 32 * (int64_t)pick_vec(dt, s.nk, A, 4)) {
+    // Short rows: the smallest group whose 4 steps cover the row (8 steps
+    // at G = 32); each group takes several rows per iteration (see the
+    // kernel) so that enough loads are in flight.
+    p.kind = K_ROWS_SHORT;
+    p.vec = pick_vec(dt, s.nk, A, 4);
+    int G = 1;
+    while (G < 32 && (int64_t)G * p.vec * 4 < s.nk) G <<= 1;
+    p.G = G;
+    const int64_t nst = ceil_div(s.nk, (int64_t)G * p.vec);
+    p.nst = nst <= 2 ? 2 : (nst <= 4 ? 4 : 8);
+    const int B = std::max(1, std::min(4, 32 / (p.nst * p.vec)));  // as in the kernel
+    const int64_t rows_per_block = (int64_t)kWarpsPerBlock * (kWarp / G) * B;
+    const int64_t blocks = std::min<int64_t>(ceil_div(s.u, rows_per_block), (int64_t)sms * 4);
+    p.splits = 1;
+    p.chunk = s.nk;
+    p.grid = dim3((unsigned)std::max<int64_t>(1, blocks), 1);
   } else if (s.v == 1) {
     p.kind = K_ROWS;
     p.vec = pick_vec(dt, s.nk, A);
@@ -614,6 +766,26 @@ static void launch_rows(const Plan& p, const TvcArgs<DT>& a, cudaStream_t st) {
   }
 }
 
+template <tvc_dtype DT, int VEC>
+static void launch_rows_short_vec(const Plan& p, const TvcArgs<DT>& a, cudaStream_t st) {
+  if (p.nst == 2) tvc_rows_short_kernel<DT, VEC, 2><<<p.grid, kThreads, 0, st>>>(a, p.G);
+  else if (p.nst == 4) tvc_rows_short_kernel<DT, VEC, 4><<<p.grid, kThreads, 0, st>>>(a, p.G);
+  else tvc_rows_short_kernel<DT, VEC, 8><<<p.grid, kThreads, 0, st>>>(a, p.G);
+}
+
+template <tvc_dtype DT>
+static void launch_rows_short(const Plan& p, const TvcArgs<DT>& a, cudaStream_t st) {
+  // The planner caps the vector width of short rows at 4 elements.
+  if constexpr (DT == TVC_F64) {
+    if (p.vec == 2) launch_rows_short_vec<DT, 2>(p, a, st);
+    else launch_rows_short_vec<DT, 1>(p, a, st);
+  } else {
+    if (p.vec == 4) launch_rows_short_vec<DT, 4>(p, a, st);
+    else if (p.vec == 2) launch_rows_short_vec<DT, 2>(p, a, st);
+    else launch_rows_short_vec<DT, 1>(p, a, st);
+  }
+}
+
 template <tvc_dtype DT>
 static void launch_main(const Plan& p, const TvcArgs<DT>& a, cudaStream_t st) {
   switch (p.kind) {
@@ -644,6 +816,9 @@ static void launch_main(const Plan& p, const TvcArgs<DT>& a, cudaStream_t st) {
     }
     case K_ROWS:
       launch_rows<DT>(p, a, st);
+      break;
+    case K_ROWS_SHORT:
+      launch_rows_short<DT>(p, a, st);
       break;
     case K_SLAB:
       tvc_slab_kernel<DT><<<p.grid, kThreads, 0, st>>>(a, p.g, p.G);
@@ -678,6 +853,7 @@ static tvc_status run(const void* A, const Shape& s, const void* x, void* y, con
   a.chunk = p.chunk;
   a.splits = p.splits;
   a.mode0 = s.mode == 0;
+  a.plain = (p.splits == 1 && alpha == 1.0 && beta == 0.0) ? 1 : 0;
   a.alpha = alpha;
   a.beta = beta;
   char* w = static_cast<char*>(ws);
