@@ -99,6 +99,56 @@ tvc_status tvc_ex(const void* A, int order, const int64_t* dims, int mode, const
  * plan is used by tvc_ex for the same arguments on the same device. */
 size_t tvc_workspace_size(int order, const int64_t* dims, int mode, tvc_dtype dtype);
 
+/* -------------------------------------------------------------- storage */
+
+/*
+ * Per-slab low-precision storage of an FP32 tensor (Section 5.5 uses low
+ * precision as a storage format only; arithmetic is promoted).  One FP32
+ * scale per slab A[i_0, ...] (n_0 scales):
+ *   TVC_E4M3: scale = amax(slab)/448 (1 for an all-zero slab), code =
+ *             E4M3(value/scale) rounded to nearest even, saturating to +-448.
+ *   TVC_BF16: scale = 1, code = BF16(value) rounded to nearest even, or the
+ *             upper half of the binary32 when truncate != 0 (the paper's
+ *             truncating "brain" format).
+ * src: N floats; codes: N bytes (E4M3) or N uint16 (BF16); scales: n_0
+ * floats; status_out: 1 device int, set to TVC_ERR_NONFINITE when an E4M3
+ * slab holds NaN or Inf (its codes are then meaningless).  All device
+ * pointers.  workspace: tvc_quantise_workspace_size(...) bytes.
+ */
+tvc_status tvc_quantise(const float* src, int order, const int64_t* dims, tvc_dtype dtype, void* codes,
+                        float* scales, int truncate, int* status_out, void* workspace, size_t ws_bytes,
+                        tvc_stream_t stream);
+size_t tvc_quantise_workspace_size(int order, const int64_t* dims);
+
+/* ----------------------------------------------------------------- HOPM */
+
+/*
+ * Higher-order power method (Section 3; three-buffer Algorithm 1 for one
+ * process): Gauss-Seidel sweeps over j = 0..order-1 of
+ *     z_j = A x_{m != j} x_m,   x_j = z_j / ||z_j||_2,
+ * for at most `iters` sweeps.  x[m] (m < order) are device vectors of n_m
+ * entries (FP64 for TVC_F64, FP32 otherwise) holding the start vectors on
+ * entry and the result on exit; x[0] is not read (the first update
+ * overwrites it).  lambda = ||z_{order-1}|| of the last sweep, which equals
+ * A(x_0, ..., x_{order-1}) at the end of that sweep.
+ * Stopping rule (the paper gives none): after sweep t >= 2, stop when
+ * tol > 0 and |lambda_t - lambda_{t-1}| <= tol * lambda_t; tol = 0 runs all
+ * sweeps.  The whole run is queued on `stream` without host synchronisation.
+ * Device outputs (nullable): lambda_out (1 double), sweeps_out (1 int),
+ * status_out (1 int: TVC_OK, TVC_ERR_ZERO_NORM or TVC_ERR_NONFINITE; on
+ * either error the offending x_j keeps its previous value and the run
+ * stops), lambda_hist (iters doubles: lambda of each completed sweep).
+ * A is streamed twice per sweep.  order >= 2.  Workspace: at least
+ * hopm_workspace_size(order, dims, dtype) bytes of device memory, 256-byte
+ * aligned; it holds the run's state, so concurrent runs need separate ones.
+ */
+tvc_status hopm(const void* A, int order, const int64_t* dims, void* const* x, int iters, double tol,
+                double* lambda_out, int* sweeps_out, int* status_out, double* lambda_hist, tvc_dtype dtype,
+                const float* slab_scales, void* workspace, size_t ws_bytes, tvc_stream_t stream);
+
+/* Bytes of workspace hopm needs (0 for invalid arguments). */
+size_t hopm_workspace_size(int order, const int64_t* dims, tvc_dtype dtype);
+
 /* Number of CUDA kernels this library has launched in this process (all
  * devices, all entry points).  Host-side counter, incremented per launch;
  * lets a caller count the kernels of a timed region. */

@@ -21,7 +21,7 @@ import torch
 
 __all__ = [
     "F64", "F32", "BF16", "E4M3", "TVCError", "load_library", "tvc", "tvc_workspace_size",
-    "dtype_code", "library_path", "kernel_launches",
+    "dtype_code", "library_path", "kernel_launches", "hopm", "hopm_workspace_size", "HopmResult", "quantise",
 ]
 
 F64, F32, BF16, E4M3 = 0, 1, 2, 3
@@ -68,6 +68,14 @@ def load_library():
         lib.tvc_ex.restype = I
         lib.tvc_workspace_size.argtypes = [I, P, I, I]
         lib.tvc_workspace_size.restype = Z
+        lib.hopm.argtypes = [P, I, P, P, I, D, P, P, P, P, I, P, P, Z, P]
+        lib.hopm.restype = I
+        lib.hopm_workspace_size.argtypes = [I, P, I]
+        lib.hopm_workspace_size.restype = Z
+        lib.tvc_quantise.argtypes = [P, I, P, I, P, P, I, P, P, Z, P]
+        lib.tvc_quantise.restype = I
+        lib.tvc_quantise_workspace_size.argtypes = [I, P]
+        lib.tvc_quantise_workspace_size.restype = Z
         lib.tvc_kernel_launches.argtypes = []
         lib.tvc_kernel_launches.restype = ctypes.c_uint64
         _lib = lib
@@ -176,3 +184,79 @@ def tvc(A: torch.Tensor, mode: int, x: torch.Tensor, *, y: torch.Tensor | None =
                             float(alpha), float(beta), _ptr(workspace), workspace.numel(), st)
     _check(status, "tvc")
     return y
+
+
+class HopmResult:
+    """Device outputs of :func:`hopm` (all torch tensors on the GPU)."""
+
+    def __init__(self, xs, lam, sweeps, status, lam_hist):
+        self.x = xs
+        self.lam = lam
+        self.sweeps = sweeps
+        self.status = status
+        self.lam_hist = lam_hist
+
+    def check(self):
+        st = int(self.status.item())
+        if st != 0:
+            raise TVCError(st, "hopm (device status)")
+        return self
+
+
+def hopm_workspace_size(shape, code: int) -> int:
+    lib = load_library()
+    return int(lib.hopm_workspace_size(len(shape), _dims_array(shape), int(code)))
+
+
+def hopm(A: torch.Tensor, xs, iters: int, tol: float = 0.0, *, scales: torch.Tensor | None = None,
+         workspace: torch.Tensor | None = None, stream=None, shape=None, inplace: bool = False) -> HopmResult:
+    """Higher-order power method on the GPU (Gauss-Seidel sweeps of
+    x_j = A x_{m != j} x_m / ||.||).  ``xs`` are the start vectors (x[0] is
+    not read); unless ``inplace`` they are copied first.  Returns device
+    tensors: x, lam, sweeps, status, lam_hist (lambda per completed sweep)."""
+    lib = load_library()
+    code = dtype_code(A)
+    shape = tuple(A.shape) if shape is None else tuple(int(n) for n in shape)
+    if len(shape) < 2 or len(xs) != len(shape):
+        raise ValueError("hopm needs order >= 2 and one start vector per mode")
+    vt = vec_dtype(code)
+    xs = [v if inplace else v.clone() for v in xs]
+    for m, v in enumerate(xs):
+        if v.dtype != vt or v.numel() != shape[m]:
+            raise ValueError(f"x[{m}] must be {vt} with {shape[m]} entries")
+    _check_cuda(A, scales, workspace, *xs)
+    dev = A.device
+    lam = torch.zeros(1, dtype=torch.float64, device=dev)
+    sweeps = torch.zeros(1, dtype=torch.int32, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    hist = torch.zeros(max(1, iters), dtype=torch.float64, device=dev)
+    dims = _dims_array(shape)
+    if workspace is None:
+        need = lib.hopm_workspace_size(len(shape), dims, code)
+        workspace = torch.empty(max(1, need), dtype=torch.uint8, device=dev)
+    ptrs = (ctypes.c_void_p * len(xs))(*[v.data_ptr() for v in xs])
+    st = lib.hopm(_ptr(A), len(shape), dims, ptrs, int(iters), float(tol), _ptr(lam), _ptr(sweeps), _ptr(status),
+                  _ptr(hist), code, _ptr(scales), _ptr(workspace), workspace.numel(), _stream(stream))
+    _check(st, "hopm")
+    return HopmResult(xs, lam, sweeps, status, hist)
+
+
+def quantise(src: torch.Tensor, code: int, *, truncate: bool = False, stream=None):
+    """Per-slab quantisation of a float32 CUDA tensor to BF16 (uint16 codes)
+    or E4M3 (uint8 codes); returns (codes, scales, status) on the device."""
+    lib = load_library()
+    if src.dtype != torch.float32:
+        raise ValueError("src must be float32")
+    if code not in (BF16, E4M3):
+        raise ValueError("code must be BF16 or E4M3")
+    _check_cuda(src)
+    shape = tuple(src.shape)
+    dims = _dims_array(shape)
+    codes = torch.empty(shape, dtype=torch.uint8 if code == E4M3 else torch.uint16, device=src.device)
+    scales = torch.empty(shape[0], dtype=torch.float32, device=src.device)
+    status = torch.zeros(1, dtype=torch.int32, device=src.device)
+    ws = torch.empty(max(1, lib.tvc_quantise_workspace_size(len(shape), dims)), dtype=torch.uint8, device=src.device)
+    st = lib.tvc_quantise(_ptr(src), len(shape), dims, code, _ptr(codes), _ptr(scales), int(bool(truncate)),
+                          _ptr(status), _ptr(ws), ws.numel(), _stream(stream))
+    _check(st, "quantise")
+    return codes, scales, status

@@ -219,7 +219,7 @@ constexpr uint32_t kDfWindowBase = 959u << 21;
 // The out-of-window path is a real call, never an if-converted DFMA that would
 // occupy the FP64 pipe for every element; it reads x itself, so the fast path
 // needs only the split pieces.
-__device__ __noinline__ double dfma_slow(double a, const double* xp, double d) {
+static __device__ __noinline__ double dfma_slow(double a, const double* xp, double d) {
   return fma(a, *xp, d);
 }
 

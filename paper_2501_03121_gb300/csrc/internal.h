@@ -44,9 +44,11 @@ tvc_status cuda_status(cudaError_t e);
 void count_launches(int n);
 
 // Launches of the TVC kernels (tvc.cu), used by the HOPM and batched paths.
+// done (nullable, device): every kernel of the launch returns at once when
+// *done != 0 (work queued behind a converged power method).
 tvc_status tvc_launch(const void* A, const Shape& s, const void* x, void* y, tvc_dtype dt,
                       const float* scales, double alpha, double beta, void* ws, size_t ws_bytes,
-                      cudaStream_t stream);
+                      cudaStream_t stream, const int* done = nullptr);
 size_t tvc_ws_bytes(const Shape& s, tvc_dtype dt, const void* A);
 
 }  // namespace tvcg

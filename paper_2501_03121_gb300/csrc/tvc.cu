@@ -43,7 +43,13 @@ struct TvcArgs {
   int mode0;
   int plain;  // splits == 1, alpha == 1, beta == 0: y[o] = value
   double alpha, beta;
+  const int* done;  // nullable: when *done != 0 the kernel returns at once
 };
+
+// Early exit of work queued behind a converged (or failed) power method.
+__device__ __forceinline__ bool skip(const int* done) {
+  return done != nullptr && *reinterpret_cast<const volatile int*>(done) != 0;
+}
 
 __device__ __forceinline__ XSplit ldxs(const XSplit* p) {
   float2 f = __ldg(reinterpret_cast<const float2*>(p));
@@ -89,6 +95,7 @@ __device__ __forceinline__ void emit(const TvcArgs<DT>& a, int64_t s, int64_t o,
 
 template <tvc_dtype DT, int VEC, int DROWS>
 __global__ void __launch_bounds__(kThreads) tvc_cols_kernel(const TvcArgs<DT> a) {
+  if (skip(a.done)) return;
   using E = Elem<DT>;
   using T = typename E::T;
   const int64_t o = ((int64_t)blockIdx.x * kThreads + threadIdx.x) * VEC;
@@ -174,6 +181,7 @@ __device__ __forceinline__ V warp_sum(V v) {
 // TwoSum, so the reduction stays off the FP64 pipe.
 template <tvc_dtype DT, int VEC, int G>
 __global__ void __launch_bounds__(kThreads) tvc_rows_kernel(const TvcArgs<DT> a) {
+  if (skip(a.done)) return;
   using E = Elem<DT>;
   using T = typename E::T;
   constexpr int STEP = G * VEC;
@@ -288,6 +296,7 @@ __global__ void __launch_bounds__(kThreads) tvc_rows_kernel(const TvcArgs<DT> a)
 // issued before any arithmetic, which keeps enough bytes in flight.
 template <tvc_dtype DT, int VEC, int NST>
 __global__ void __launch_bounds__(kThreads) tvc_rows_short_kernel(const TvcArgs<DT> a, int G) {
+  if (skip(a.done)) return;
   // Rows per group per iteration: about 32 elements of loads per lane.
   constexpr int B = (32 / (NST * VEC)) < 1 ? 1 : ((32 / (NST * VEC)) > 4 ? 4 : (32 / (NST * VEC)));
   using E = Elem<DT>;
@@ -415,6 +424,7 @@ __global__ void __launch_bounds__(kThreads) tvc_rows_short_kernel(const TvcArgs<
 
 template <tvc_dtype DT>
 __global__ void __launch_bounds__(kThreads) tvc_slab_kernel(const TvcArgs<DT> a, int g, int G) {
+  if (skip(a.done)) return;
   using E = Elem<DT>;
   using T = typename E::T;
   using V = typename E::V;
@@ -503,6 +513,7 @@ __global__ void __launch_bounds__(kThreads) tvc_slab_kernel(const TvcArgs<DT> a,
 // over the banks.
 template <tvc_dtype DT>
 __global__ void __launch_bounds__(kThreads) tvc_tile_kernel(const TvcArgs<DT> a, int R, int vec16) {
+  if (skip(a.done)) return;
   using E = Elem<DT>;
   using T = typename E::T;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -594,7 +605,9 @@ __global__ void __launch_bounds__(kThreads) tvc_tile_kernel(const TvcArgs<DT> a,
 
 // -------------------------------------------------------- helper kernels --
 
-__global__ void tvc_split_x_kernel(const double* __restrict__ x, XSplit* __restrict__ xs, int64_t n) {
+__global__ void tvc_split_x_kernel(const double* __restrict__ x, XSplit* __restrict__ xs, int64_t n,
+                                   const int* done) {
+  if (skip(done)) return;
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
     xs[j] = split_x(x[j]);
 }
@@ -602,7 +615,8 @@ __global__ void tvc_split_x_kernel(const double* __restrict__ x, XSplit* __restr
 // y[o] = alpha * sum_s partial[s][o] + beta * y[o], s ascending (deterministic).
 template <class V>
 __global__ void tvc_reduce_kernel(const V* __restrict__ partial, V* __restrict__ y, int64_t uv, int64_t splits,
-                                  double alpha, double beta) {
+                                  double alpha, double beta, const int* done) {
+  if (skip(done)) return;
   for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < uv; o += (int64_t)gridDim.x * blockDim.x) {
     V r;
     if constexpr (sizeof(V) == 8) {
@@ -837,7 +851,7 @@ static void launch_main(const Plan& p, const TvcArgs<DT>& a, cudaStream_t st) {
 
 template <tvc_dtype DT>
 static tvc_status run(const void* A, const Shape& s, const void* x, void* y, const float* scales, double alpha,
-                      double beta, void* ws, const Plan& p, cudaStream_t st) {
+                      double beta, void* ws, const Plan& p, cudaStream_t st, const int* done) {
   TvcArgs<DT> a;
   a.A = static_cast<const typename Elem<DT>::T*>(A);
   a.x = x;
@@ -856,11 +870,12 @@ static tvc_status run(const void* A, const Shape& s, const void* x, void* y, con
   a.plain = (p.splits == 1 && alpha == 1.0 && beta == 0.0) ? 1 : 0;
   a.alpha = alpha;
   a.beta = beta;
+  a.done = done;
   char* w = static_cast<char*>(ws);
   if (DT == TVC_F64) {
     a.xs = reinterpret_cast<const XSplit*>(w);
     const int blocks = (int)std::min<int64_t>(ceil_div(s.nk, 256), 4096);
-    tvc_split_x_kernel<<<blocks, 256, 0, st>>>(static_cast<const double*>(x), reinterpret_cast<XSplit*>(w), s.nk);
+    tvc_split_x_kernel<<<blocks, 256, 0, st>>>(static_cast<const double*>(x), reinterpret_cast<XSplit*>(w), s.nk, done);
   }
   if (p.splits > 1) a.partial = w + p.ws_xs;
   launch_main<DT>(p, a, st);
@@ -869,20 +884,20 @@ static tvc_status run(const void* A, const Shape& s, const void* x, void* y, con
     using V = typename Elem<DT>::V;
     const int blocks = (int)std::min<int64_t>(ceil_div(s.uv, 256), 8192);
     tvc_reduce_kernel<V><<<blocks, 256, 0, st>>>(static_cast<const V*>(a.partial), static_cast<V*>(y), s.uv,
-                                                 p.splits, alpha, beta);
+                                                 p.splits, alpha, beta, done);
   }
   return cuda_status(cudaGetLastError());
 }
 
 tvc_status tvc_launch(const void* A, const Shape& s, const void* x, void* y, tvc_dtype dt, const float* scales,
-                      double alpha, double beta, void* ws, size_t ws_bytes, cudaStream_t stream) {
+                      double alpha, double beta, void* ws, size_t ws_bytes, cudaStream_t stream, const int* done) {
   const Plan p = make_plan(s, dt, A);
   if (p.ws_total > 0 && (ws == nullptr || ws_bytes < p.ws_total)) return TVC_ERR_WORKSPACE;
   switch (dt) {
-    case TVC_F64: return run<TVC_F64>(A, s, x, y, nullptr, alpha, beta, ws, p, stream);
-    case TVC_F32: return run<TVC_F32>(A, s, x, y, nullptr, alpha, beta, ws, p, stream);
-    case TVC_BF16: return run<TVC_BF16>(A, s, x, y, scales, alpha, beta, ws, p, stream);
-    case TVC_E4M3: return run<TVC_E4M3>(A, s, x, y, scales, alpha, beta, ws, p, stream);
+    case TVC_F64: return run<TVC_F64>(A, s, x, y, nullptr, alpha, beta, ws, p, stream, done);
+    case TVC_F32: return run<TVC_F32>(A, s, x, y, nullptr, alpha, beta, ws, p, stream, done);
+    case TVC_BF16: return run<TVC_BF16>(A, s, x, y, scales, alpha, beta, ws, p, stream, done);
+    case TVC_E4M3: return run<TVC_E4M3>(A, s, x, y, scales, alpha, beta, ws, p, stream, done);
   }
   return TVC_ERR_INVALID_ARG;
 }
