@@ -99,6 +99,31 @@ tvc_status tvc_ex(const void* A, int order, const int64_t* dims, int mode, const
  * plan is used by tvc_ex for the same arguments on the same device. */
 size_t tvc_workspace_size(int order, const int64_t* dims, int mode, tvc_dtype dtype);
 
+/*
+ * tvc_noalloc: the same contraction as tvc_ex() with alpha = 1, beta = 0,
+ * for callers that cannot allocate device memory (code run from a host
+ * callback queued with cudaLaunchHostFunc, where CUDA API calls are not
+ * allowed; plug-ins whose host framework owns every device allocation;
+ * real-time or certified deployments that forbid device allocation after
+ * start-up).  The paper has no counterpart: this is an interface of this
+ * library only.
+ * It allocates nothing and needs no workspace: its scratch (the split
+ * pieces of x for FP64 and the split-K partial sums) is a fixed array of
+ * TVC_NOALLOC_SCRATCH_BYTES that is part of the library's device image, so
+ * every GPU that loads the library holds that memory until the process
+ * exits.  Contractions whose scratch need (tvc_workspace_size) is larger
+ * are refused with TVC_ERR_WORKSPACE before anything is launched.
+ * The first call on a device looks up the scratch's device address (one
+ * cudaGetSymbolAddress with that device current); make that first call
+ * before any stream capture.  All calls on a device share the one array,
+ * whose contents persist from call to call; calls that can overlap on the
+ * GPU (different streams without ordering) race on it and give wrong
+ * results, so order them on one stream or with events.
+ */
+#define TVC_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+tvc_status tvc_noalloc(const void* A, int order, const int64_t* dims, int mode, const void* x, void* y,
+                       tvc_dtype dtype, const float* slab_scales, tvc_stream_t stream);
+
 /* -------------------------------------------------------------- storage */
 
 /*
