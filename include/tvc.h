@@ -124,6 +124,27 @@ size_t tvc_workspace_size(int order, const int64_t* dims, int mode, tvc_dtype dt
 tvc_status tvc_noalloc(const void* A, int order, const int64_t* dims, int mode, const void* x, void* y,
                        tvc_dtype dtype, const float* slab_scales, tvc_stream_t stream);
 
+/* -------------------------------------------------------------- adjoint */
+
+/*
+ * Adjoints of Y = A x_mode x (by differentiation of the Section 3
+ * definition; the paper gives no passage for them).  With gy the gradient
+ * of a loss with respect to Y (N/n_mode entries, the layout of y):
+ *     gx[j]       = sum_{i,l} A[(i*n_k + j)*v + l] * gy[i*v + l]
+ *     gA[(i*n_k+j)*v+l] = gy[i*v + l] * x[j] + beta_A * gA[...]
+ * gx (n_mode entries) is computed when gx != NULL (needs A; narrow storage
+ * uses its slab scales, i.e. gx is the gradient with respect to x of the
+ * dequantised contraction); gA (N entries, FP64 for TVC_F64, FP32
+ * otherwise: the gradient with respect to the dequantised values) is
+ * written when gA != NULL (needs x; beta_A == 0 means gA is not read).
+ * workspace: tvc_backward_workspace_size(...) bytes (for gx).  Results are
+ * deterministic (fixed-order reductions).
+ */
+tvc_status tvc_backward(const void* A, int order, const int64_t* dims, int mode, const void* x, const void* gy,
+                        void* gx, void* gA, tvc_dtype dtype, const float* slab_scales, double beta_A,
+                        void* workspace, size_t ws_bytes, tvc_stream_t stream);
+size_t tvc_backward_workspace_size(int order, const int64_t* dims, int mode, tvc_dtype dtype);
+
 /* -------------------------------------------------------------- storage */
 
 /*

@@ -21,7 +21,7 @@ import torch
 
 __all__ = [
     "F64", "F32", "BF16", "E4M3", "TVCError", "load_library", "tvc", "tvc_workspace_size",
-    "dtype_code", "library_path", "kernel_launches", "hopm", "hopm_workspace_size", "HopmResult", "quantise",
+    "dtype_code", "library_path", "kernel_launches", "hopm", "hopm_workspace_size", "HopmResult", "quantise", "tvc_backward", "TVCFunction", "tvc_autograd",
 ]
 
 F64, F32, BF16, E4M3 = 0, 1, 2, 3
@@ -76,6 +76,10 @@ def load_library():
         lib.tvc_quantise.restype = I
         lib.tvc_quantise_workspace_size.argtypes = [I, P]
         lib.tvc_quantise_workspace_size.restype = Z
+        lib.tvc_backward.argtypes = [P, I, P, I, P, P, P, P, I, P, D, P, Z, P]
+        lib.tvc_backward.restype = I
+        lib.tvc_backward_workspace_size.argtypes = [I, P, I, I]
+        lib.tvc_backward_workspace_size.restype = Z
         lib.tvc_kernel_launches.argtypes = []
         lib.tvc_kernel_launches.restype = ctypes.c_uint64
         _lib = lib
@@ -260,3 +264,58 @@ def quantise(src: torch.Tensor, code: int, *, truncate: bool = False, stream=Non
                           _ptr(status), _ptr(ws), ws.numel(), _stream(stream))
     _check(st, "quantise")
     return codes, scales, status
+
+
+def tvc_backward(A: torch.Tensor | None, mode: int, x: torch.Tensor | None, gy: torch.Tensor, *, need_x: bool = True,
+                 need_A: bool = True, scales: torch.Tensor | None = None, gA: torch.Tensor | None = None,
+                 beta_A: float = 0.0, shape=None, code: int | None = None, stream=None):
+    """Adjoints of Y = A x_mode x: returns (gx, gA) (None where not asked).
+    gx = sum_{i,l} A[i,j,l] gy[i,l]; gA = gy (x) x along mode (+ beta_A gA)."""
+    lib = load_library()
+    if code is None:
+        code = dtype_code(A)
+    shape = tuple(A.shape) if shape is None else tuple(int(n) for n in shape)
+    vt = vec_dtype(code)
+    dev = gy.device
+    N = math.prod(shape)
+    if gy.dtype != vt or gy.numel() != N // shape[mode]:
+        raise ValueError("gy has the wrong dtype or size")
+    gx = torch.empty(shape[mode], dtype=vt, device=dev) if need_x else None
+    if need_A and gA is None:
+        gA = torch.empty(shape, dtype=vt, device=dev)
+    if not need_A:
+        gA = None
+    _check_cuda(A, x, gy, gx, gA, scales)
+    dims = _dims_array(shape)
+    need = lib.tvc_backward_workspace_size(len(shape), dims, int(mode), code) if need_x else 0
+    ws = torch.empty(max(1, need), dtype=torch.uint8, device=dev)
+    st = lib.tvc_backward(_ptr(A), len(shape), dims, int(mode), _ptr(x), _ptr(gy), _ptr(gx), _ptr(gA), code,
+                          _ptr(scales), float(beta_A), _ptr(ws), ws.numel(), _stream(stream))
+    _check(st, "tvc_backward")
+    return gx, gA
+
+
+class TVCFunction(torch.autograd.Function):
+    """Autograd wrapper of the contraction: forward tvc(), backward
+    tvc_backward() (gradient for x always; for A when A is a float tensor
+    that requires grad; narrow codes carry no gradient)."""
+
+    @staticmethod
+    def forward(ctx, A, x, mode, scales=None):
+        ctx.mode = int(mode)
+        ctx.save_for_backward(A, x, scales)
+        return tvc(A, ctx.mode, x, scales=scales)
+
+    @staticmethod
+    def backward(ctx, gy):
+        A, x, scales = ctx.saved_tensors
+        need_x = ctx.needs_input_grad[1]
+        need_A = ctx.needs_input_grad[0] and A.is_floating_point() and A.dtype in (torch.float64, torch.float32)
+        gy = gy.contiguous()
+        gx, gA = tvc_backward(A, ctx.mode, x, gy, need_x=need_x, need_A=need_A, scales=scales)
+        return gA, gx, None, None
+
+
+def tvc_autograd(A, x, mode, scales=None):
+    """Differentiable y = A x_mode x (see :class:`TVCFunction`)."""
+    return TVCFunction.apply(A, x, mode, scales)
