@@ -195,6 +195,28 @@ tvc_status hopm(const void* A, int order, const int64_t* dims, void* const* x, i
 /* Bytes of workspace hopm needs (0 for invalid arguments). */
 size_t hopm_workspace_size(int order, const int64_t* dims, tvc_dtype dtype);
 
+/*
+ * Reverse-mode gradient of `iters` HOPM sweeps (fixed count: the run this
+ * differentiates used tol = 0, or pass the sweep count it reported) started
+ * from x0[m] (device, not modified).  Upstream gradients: gx_final[m]
+ * (device vectors of n_m, for the final x_m; the array or any entry may be
+ * NULL = zero) and g_lambda (device double, NULL = zero).  Outputs: gA (N
+ * entries, written; FP64 for TVC_F64, FP32 otherwise, the gradient with
+ * respect to the dequantised values for narrow storage) and gstart[m]
+ * (nullable array/entries: gradients with respect to the start vectors;
+ * that of x0[0] is zero since x0[0] is never read).
+ * The iterates are recomputed, not stored: only the d vectors at the start
+ * of each sweep are kept (iters * sum(n_m) numbers), and every sweep is
+ * recomputed from them during the reverse pass.  Cost per sweep: the two
+ * forward passes over A, one pass per update for A x_j gz, and one update
+ * of gA.  Workspace: hopm_backward_workspace_size(order, dims, dtype, iters).
+ */
+tvc_status hopm_backward(const void* A, int order, const int64_t* dims, void* const* x0, int iters,
+                         void* const* gx_final, const double* g_lambda, void* gA, void* const* gstart,
+                         tvc_dtype dtype, const float* slab_scales, void* workspace, size_t ws_bytes,
+                         tvc_stream_t stream);
+size_t hopm_backward_workspace_size(int order, const int64_t* dims, tvc_dtype dtype, int iters);
+
 /* Number of CUDA kernels this library has launched in this process (all
  * devices, all entry points).  Host-side counter, incremented per launch;
  * lets a caller count the kernels of a timed region. */

@@ -21,7 +21,7 @@ import torch
 
 __all__ = [
     "F64", "F32", "BF16", "E4M3", "TVCError", "load_library", "tvc", "tvc_workspace_size",
-    "dtype_code", "library_path", "kernel_launches", "hopm", "hopm_workspace_size", "HopmResult", "quantise", "tvc_backward", "TVCFunction", "tvc_autograd",
+    "dtype_code", "library_path", "kernel_launches", "hopm", "hopm_workspace_size", "HopmResult", "quantise", "tvc_backward", "TVCFunction", "tvc_autograd", "hopm_backward", "HOPMFunction", "hopm_autograd",
 ]
 
 F64, F32, BF16, E4M3 = 0, 1, 2, 3
@@ -80,6 +80,10 @@ def load_library():
         lib.tvc_backward.restype = I
         lib.tvc_backward_workspace_size.argtypes = [I, P, I, I]
         lib.tvc_backward_workspace_size.restype = Z
+        lib.hopm_backward.argtypes = [P, I, P, P, I, P, P, P, P, I, P, P, Z, P]
+        lib.hopm_backward.restype = I
+        lib.hopm_backward_workspace_size.argtypes = [I, P, I, I]
+        lib.hopm_backward_workspace_size.restype = Z
         lib.tvc_kernel_launches.argtypes = []
         lib.tvc_kernel_launches.restype = ctypes.c_uint64
         _lib = lib
@@ -319,3 +323,57 @@ class TVCFunction(torch.autograd.Function):
 def tvc_autograd(A, x, mode, scales=None):
     """Differentiable y = A x_mode x (see :class:`TVCFunction`)."""
     return TVCFunction.apply(A, x, mode, scales)
+
+
+def hopm_backward(A: torch.Tensor, x0, iters: int, gx_final=None, g_lambda: torch.Tensor | None = None, *,
+                  scales: torch.Tensor | None = None, shape=None, stream=None):
+    """Gradients of `iters` HOPM sweeps from start vectors x0: returns
+    (gA, gstart) given upstream gradients of the final vectors (list,
+    entries may be None) and of lambda (1-element float64 device tensor)."""
+    lib = load_library()
+    code = dtype_code(A)
+    shape = tuple(A.shape) if shape is None else tuple(int(n) for n in shape)
+    vt = vec_dtype(code)
+    d = len(shape)
+    dev = A.device
+    x0 = [v.contiguous() for v in x0]
+    gA = torch.empty(shape, dtype=vt, device=dev)
+    gstart = [torch.zeros(n, dtype=vt, device=dev) for n in shape]
+    gfin = [None] * d if gx_final is None else [None if g is None else g.contiguous() for g in gx_final]
+    if g_lambda is not None:
+        g_lambda = g_lambda.to(device=dev, dtype=torch.float64).reshape(1).contiguous()
+    _check_cuda(A, scales, *x0, *[g for g in gfin if g is not None])
+    dims = _dims_array(shape)
+    need = lib.hopm_backward_workspace_size(d, dims, code, int(iters))
+    ws = torch.empty(max(1, need), dtype=torch.uint8, device=dev)
+    P = ctypes.c_void_p
+    x0p = (P * d)(*[v.data_ptr() for v in x0])
+    gfp = (P * d)(*[(g.data_ptr() if g is not None else None) for g in gfin])
+    gsp = (P * d)(*[g.data_ptr() for g in gstart])
+    st = lib.hopm_backward(_ptr(A), d, dims, x0p, int(iters), gfp, _ptr(g_lambda), _ptr(gA), gsp, code,
+                           _ptr(scales), _ptr(ws), ws.numel(), _stream(stream))
+    _check(st, "hopm_backward")
+    return gA, gstart
+
+
+class HOPMFunction(torch.autograd.Function):
+    """Autograd wrapper of a fixed-count HOPM: forward returns (lambda,
+    x_0, ..., x_{d-1}); backward recomputes the sweeps (see hopm_backward)."""
+
+    @staticmethod
+    def forward(ctx, A, iters, *x0):
+        ctx.iters = int(iters)
+        ctx.save_for_backward(A, *x0)
+        r = hopm(A, list(x0), ctx.iters, 0.0).check()
+        return (r.lam.clone(),) + tuple(r.x)
+
+    @staticmethod
+    def backward(ctx, g_lam, *gxs):
+        A, *x0 = ctx.saved_tensors
+        gA, gstart = hopm_backward(A, x0, ctx.iters, list(gxs), g_lam)
+        return (gA, None) + tuple(gstart)
+
+
+def hopm_autograd(A, x0, iters):
+    """Differentiable (lambda, x_0..x_{d-1}) of `iters` HOPM sweeps."""
+    return HOPMFunction.apply(A, iters, *x0)

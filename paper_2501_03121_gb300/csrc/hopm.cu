@@ -84,7 +84,8 @@ template <class V>
 __global__ void __launch_bounds__(kNormThreads) hopm_normalize_kernel(const V* __restrict__ z, V* __restrict__ xj,
                                                                      int64_t n, int last, double tol, HopmState* st,
                                                                      double* lam_out, int* sweeps_out,
-                                                                     int* status_out, double* lam_hist) {
+                                                                     int* status_out, double* lam_hist,
+                                                                     double* sigma_cap) {
   if (hskip(st)) return;
   __shared__ double red[kNormThreads];
   double ss = 0.0;
@@ -105,6 +106,7 @@ __global__ void __launch_bounds__(kNormThreads) hopm_normalize_kernel(const V* _
     for (int64_t i = threadIdx.x; i < n; i += kNormThreads) xj[i] = (V)((double)z[i] / sigma);
   }
   if (threadIdx.x == 0) {
+    if (sigma_cap) *sigma_cap = sigma;
     int status = TVC_OK;
     if (!finite) status = TVC_ERR_NONFINITE;
     else if (zero) status = TVC_ERR_ZERO_NORM;
@@ -126,19 +128,95 @@ __global__ void __launch_bounds__(kNormThreads) hopm_normalize_kernel(const V* _
   }
 }
 
+// --------------------------------------------------- backward kernels ----
+
+// Adjoint of the normalisation x = z/||z|| (sigma = ||z||):
+//   gz = (g - x <x, g>) / sigma + g_sigma x
+// with <x, g> in FP64 (fixed-order block reduction).  g_sigma (nullable) is
+// the upstream gradient of lambda, used for the last update only.
+template <class V>
+__global__ void __launch_bounds__(kNormThreads) hopm_bw_gz_kernel(const V* __restrict__ x, const V* __restrict__ g,
+                                                                 const double* sigma, const double* gsig, int64_t n,
+                                                                 V* __restrict__ gz) {
+  __shared__ double red[kNormThreads];
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += kNormThreads) s = fma((double)x[i], (double)g[i], s);
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int off = kNormThreads / 2; off > 0; off >>= 1) {
+    if ((int)threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
+    __syncthreads();
+  }
+  const double dot = red[0];
+  const double inv = 1.0 / *sigma;
+  const double gs = gsig ? *gsig : 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += kNormThreads) {
+    const double xi = (double)x[i];
+    gz[i] = (V)(((double)g[i] - xi * dot) * inv + gs * xi);
+  }
+}
+
+template <class V>
+__global__ void hopm_axpy_kernel(V* __restrict__ y, const V* __restrict__ x, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] += x[i];
+}
+
+// gA += sum_r prod_m F[r][m][i_m]  (R rank-1 terms of order d, row-major).
+constexpr int kCpMaxR = 16;
+struct CpArgs {
+  int d, R;
+  int64_t dims[TVC_MAX_ORDER];
+  const void* f[kCpMaxR][TVC_MAX_ORDER];
+};
+
+template <class V>
+__global__ void __launch_bounds__(256) hopm_cp_kernel(V* __restrict__ gA, int64_t rows, CpArgs ca) {
+  // A block handles RB rows (all leading indices but the last mode) per
+  // iteration; thread t covers row t / nl, position t % nl of the last mode.
+  const int64_t nl = ca.dims[ca.d - 1];
+  const int RB = nl >= 256 ? 1 : (int)(256 / nl);
+  __shared__ double P[256][kCpMaxR];
+  for (int64_t r0 = (int64_t)blockIdx.x * RB; r0 < rows; r0 += (int64_t)gridDim.x * RB) {
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < RB * ca.R; idx += 256) {
+      const int rb = idx / ca.R, r = idx % ca.R;
+      const int64_t row = r0 + rb;
+      double pr = 0.0;
+      if (row < rows) {
+        int64_t rem = row;
+        pr = 1.0;
+        for (int m = ca.d - 2; m >= 0; m--) {
+          const int64_t im = rem % ca.dims[m];
+          rem /= ca.dims[m];
+          pr *= (double)static_cast<const V*>(ca.f[r][m])[im];
+        }
+      }
+      P[rb][r] = pr;
+    }
+    __syncthreads();
+    const int rb = (nl >= 256) ? 0 : (int)(threadIdx.x / nl);
+    if (rb >= RB) continue;
+    const int64_t row = r0 + rb;
+    if (row >= rows) continue;
+    for (int64_t k = (nl >= 256) ? threadIdx.x : threadIdx.x % nl; k < nl; k += (nl >= 256) ? 256 : nl) {
+      double acc = 0.0;
+      for (int r = 0; r < ca.R; r++) acc = fma(P[rb][r], (double)static_cast<const V*>(ca.f[r][ca.d - 1])[k], acc);
+      V* p = gA + row * nl + k;
+      *p = (V)((double)*p + acc);
+    }
+  }
+}
+
 // ---------------------------------------------------------------- host ----
 
 namespace {
 
-struct HopmPlan {
-  int d = 0;
-  int64_t dims[TVC_MAX_ORDER] = {};
-  int64_t N = 0;
-  size_t vs = 8;
-  // workspace layout (byte offsets)
-  size_t off_state = 0, off_bufA = 0, off_bufB = 0, off_w = 0, off_z = 0, off_tvc = 0, total = 0;
-  size_t tvc_ws = 0;
-};
+int64_t prod_range(const int64_t* dims, int lo, int hi) {
+  int64_t p = 1;
+  for (int i = lo; i < hi; i++) p *= dims[i];
+  return p;
+}
 
 Shape shape2(int64_t a, int64_t b, int mode) {
   Shape s;
@@ -147,191 +225,443 @@ Shape shape2(int64_t a, int64_t b, int mode) {
   return s;
 }
 
-int64_t prod_range(const int64_t* dims, int lo, int hi) {
-  int64_t p = 1;
-  for (int i = lo; i < hi; i++) p *= dims[i];
-  return p;
-}
+int grid_for(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 4096)); }
 
-// The contractions one sweep issues, as (shape, dtype) pairs, for sizing.
-template <class F>
-void for_each_tvc(const HopmPlan& hp, tvc_dtype dt, F f) {
-  const int d = hp.d;
-  const int64_t* n = hp.dims;
-  const tvc_dtype vdt = (dt == TVC_F64) ? TVC_F64 : TVC_F32;
-  Shape s;
-  if (d == 2) {
-    make_shape(2, n, 1, &s);
-    f(s, dt);
-    make_shape(2, n, 0, &s);
-    f(s, dt);
-    return;
-  }
-  make_shape(d, n, 1, &s);  // T = A x_1 x_1
-  f(s, dt);
-  f(shape2(n[0], prod_range(n, 2, d), 1), vdt);
-  make_shape(d, n, 0, &s);  // W_1 = A x_0 x_0
-  f(s, dt);
-  f(shape2(n[1], prod_range(n, 2, d), 1), vdt);
-  for (int j = 2; j < d; j++) {
-    f(shape2(n[j - 1], prod_range(n, j, d), 0), vdt);
-    if (j < d - 1) f(shape2(n[j], prod_range(n, j + 1, d), 1), vdt);
-  }
-}
+// Launch context of one power-method run.  In "dry" mode nothing is
+// launched: the calls only record the largest TVC workspace they would use,
+// which is how the workspace size is computed (the same code path sizes and
+// runs).
+struct Ctx {
+  bool dry = true;
+  const void* A = nullptr;
+  int d = 0;
+  int64_t n[TVC_MAX_ORDER] = {};
+  int64_t N = 0;
+  tvc_dtype dt = TVC_F64, vdt = TVC_F64;
+  const float* scales = nullptr;
+  cudaStream_t st = nullptr;
+  HopmState* state = nullptr;
+  const int* done = nullptr;
+  void *bufA = nullptr, *bufB = nullptr, *wv = nullptr, *z = nullptr, *tws = nullptr;
+  size_t tws_bytes = 0;
+  size_t tvc_need = 0;
+  tvc_status rc = TVC_OK;
+  int launches = 0;
+  void* wchain = nullptr;  // W_j of the running sweep
+  void* wother = nullptr;
 
-HopmPlan make_hopm_plan(int order, const int64_t* dims, tvc_dtype dt) {
-  HopmPlan hp;
-  hp.d = order;
-  for (int i = 0; i < order; i++) hp.dims[i] = dims[i];
-  hp.N = prod_range(dims, 0, order);
-  hp.vs = vec_size(dt);
+  bool f64() const { return dt == TVC_F64; }
+
+  void tvc(const void* X, const Shape& s, const void* xv, void* y, tvc_dtype t, const float* sc, double beta = 0.0) {
+    if (rc != TVC_OK) return;
+    if (dry) {
+      for (uintptr_t al = elem_size(t); al <= 256; al *= 2)
+        tvc_need = std::max(tvc_need, tvc_ws_bytes(s, t, reinterpret_cast<const void*>(al)));
+      return;
+    }
+    rc = tvc_launch(X, s, xv, y, t, sc, 1.0, beta, tws, tws_bytes, st, done);
+  }
+  void tvcA(int mode, const void* xv, void* y) {
+    Shape s;
+    make_shape(d, n, mode, &s);
+    tvc(A, s, xv, y, dt, scales);
+  }
+  void outer(int from, void* const* xs) {  // wv = x_from (x) ... (x) x_{d-1}
+    if (dry || rc != TVC_OK) return;
+    OuterArgs oa{};
+    oa.nm = d - from;
+    for (int m = from; m < d; m++) {
+      oa.dims[m - from] = n[m];
+      oa.xs[m - from] = xs[m];
+    }
+    const int64_t len = prod_range(n, from, d);
+    if (f64())
+      hopm_outer_kernel<double><<<grid_for(len), 256, 0, st>>>(static_cast<double*>(wv), len, oa, state);
+    else
+      hopm_outer_kernel<float><<<grid_for(len), 256, 0, st>>>(static_cast<float*>(wv), len, oa, state);
+    launches++;
+  }
+  // z_j = A x_{m != j} x_m with the current vectors xs; updates j of one
+  // sweep must come in order 0..d-1 (the W chain).  Returns the buffer of z_j.
+  void* z_for(int j, void* const* xs) {
+    if (d == 2) {
+      tvcA(1 - j, xs[1 - j], z);
+      return z;
+    }
+    if (j == 0 || j == 1) {
+      void* T = bufA;
+      tvcA(j == 0 ? 1 : 0, xs[j == 0 ? 1 : 0], T);
+      const int64_t rest2 = prod_range(n, 2, d);
+      if (d == 3) {
+        tvc(T, shape2(n[j], n[2], 1), xs[2], z, vdt, nullptr);
+      } else {
+        outer(2, xs);
+        tvc(T, shape2(n[j], rest2, 1), wv, z, vdt, nullptr);
+      }
+      wchain = bufA;
+      wother = bufB;
+      return z;
+    }
+    void* next = wother;
+    tvc(wchain, shape2(n[j - 1], prod_range(n, j, d), 0), xs[j - 1], next, vdt, nullptr);
+    wother = wchain;
+    wchain = next;
+    if (j == d - 1) return next;
+    if (j == d - 2) {
+      tvc(next, shape2(n[j], n[d - 1], 1), xs[d - 1], z, vdt, nullptr);
+    } else {
+      outer(j + 1, xs);
+      tvc(next, shape2(n[j], prod_range(n, j + 1, d), 1), wv, z, vdt, nullptr);
+    }
+    return z;
+  }
+  void normalize(const void* zz, int j, void* xj, double tol, double* lam_out, int* sweeps_out, int* status_out,
+                 double* lam_hist, double* sigma_cap) {
+    if (dry || rc != TVC_OK) return;
+    const int last = (j == d - 1);
+    if (f64())
+      hopm_normalize_kernel<double><<<1, kNormThreads, 0, st>>>(static_cast<const double*>(zz), static_cast<double*>(xj),
+                                                                n[j], last, tol, state, lam_out, sweeps_out, status_out,
+                                                                lam_hist, sigma_cap);
+    else
+      hopm_normalize_kernel<float><<<1, kNormThreads, 0, st>>>(static_cast<const float*>(zz), static_cast<float*>(xj),
+                                                               n[j], last, tol, state, lam_out, sweeps_out, status_out,
+                                                               lam_hist, sigma_cap);
+    launches++;
+  }
+  void init_state() {
+    if (dry) return;
+    hopm_init_kernel<<<1, 1, 0, st>>>(state);
+    launches++;
+  }
+  // One Gauss-Seidel sweep on the vectors xs (updated in place).
+  void sweep(void* const* xs, double tol, double* lam_out, int* sweeps_out, int* status_out, double* lam_hist,
+             double* sigma_cap) {
+    for (int j = 0; j < d && rc == TVC_OK; j++) {
+      void* zz = z_for(j, xs);
+      normalize(zz, j, xs[j], tol, lam_out, sweeps_out, status_out, lam_hist, sigma_cap ? sigma_cap + j : nullptr);
+    }
+  }
+};
+
+// Workspace layout of a forward run.
+struct FwdLayout {
+  size_t off_state = 0, off_bufA = 0, off_bufB = 0, off_w = 0, off_z = 0, off_tvc = 0, total = 0, tvc = 0;
+};
+
+FwdLayout fwd_layout(int order, const int64_t* dims, tvc_dtype dt, size_t base) {
+  FwdLayout L;
+  const size_t vs = vec_size(dt);
+  const int64_t N = prod_range(dims, 0, order);
   const int64_t n0 = dims[0], n1 = dims[1];
-  const int64_t bufA = std::max(hp.N / n0, hp.N / n1);
-  const int64_t bufB = (order >= 3) ? hp.N / (n0 * n1) : 1;
-  const int64_t wlen = (order >= 4) ? hp.N / (n0 * n1) : 1;
+  const int64_t bufA = std::max(N / n0, N / n1);
+  const int64_t bufB = (order >= 3) ? N / (n0 * n1) : 1;
+  const int64_t wlen = (order >= 4) ? N / (n0 * n1) : 1;
   int64_t zlen = 1;
   for (int i = 0; i < order; i++) zlen = std::max(zlen, dims[i]);
-  size_t tw = 0;
-  // Plan every TVC for a 256-byte aligned operand (the workspace and torch
-  // buffers are), keeping the largest workspace any of them needs; operands
-  // of other alignments only use smaller plans.
-  for_each_tvc(hp, dt, [&](const Shape& s, tvc_dtype t) {
-    for (uintptr_t al = elem_size(t); al <= 256; al *= 2)
-      tw = std::max(tw, tvc_ws_bytes(s, t, reinterpret_cast<const void*>(al)));
-  });
-  hp.tvc_ws = tw;
-  size_t off = 0;
-  hp.off_state = off;
+  Ctx c;
+  c.dry = true;
+  c.d = order;
+  for (int i = 0; i < order; i++) c.n[i] = dims[i];
+  c.dt = dt;
+  c.vdt = (dt == TVC_F64) ? TVC_F64 : TVC_F32;
+  void* dummy[TVC_MAX_ORDER] = {};
+  c.sweep(dummy, 0.0, nullptr, nullptr, nullptr, nullptr, nullptr);
+  size_t off = base;
+  L.off_state = off;
   off += align_up(sizeof(HopmState), 256);
-  hp.off_bufA = off;
-  off += align_up((size_t)bufA * hp.vs, 256);
-  hp.off_bufB = off;
-  off += align_up((size_t)bufB * hp.vs, 256);
-  hp.off_w = off;
-  off += align_up((size_t)wlen * hp.vs, 256);
-  hp.off_z = off;
-  off += align_up((size_t)zlen * hp.vs, 256);
-  hp.off_tvc = off;
-  off += align_up(tw, 256);
-  hp.total = off;
-  return hp;
+  L.off_bufA = off;
+  off += align_up((size_t)bufA * vs, 256);
+  L.off_bufB = off;
+  off += align_up((size_t)bufB * vs, 256);
+  L.off_w = off;
+  off += align_up((size_t)wlen * vs, 256);
+  L.off_z = off;
+  off += align_up((size_t)zlen * vs, 256);
+  L.off_tvc = off;
+  L.tvc = c.tvc_need;
+  off += align_up(c.tvc_need, 256);
+  L.total = off;
+  return L;
 }
 
-int grid_for(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 4096)); }
+void bind(Ctx& c, const FwdLayout& L, void* ws, const void* A, int order, const int64_t* dims, tvc_dtype dt,
+          const float* scales, cudaStream_t st) {
+  char* w = static_cast<char*>(ws);
+  c.dry = false;
+  c.A = A;
+  c.d = order;
+  for (int i = 0; i < order; i++) c.n[i] = dims[i];
+  c.N = prod_range(dims, 0, order);
+  c.dt = dt;
+  c.vdt = (dt == TVC_F64) ? TVC_F64 : TVC_F32;
+  c.scales = scales;
+  c.st = st;
+  c.state = reinterpret_cast<HopmState*>(w + L.off_state);
+  c.done = &c.state->done;
+  c.bufA = w + L.off_bufA;
+  c.bufB = w + L.off_bufB;
+  c.wv = w + L.off_w;
+  c.z = w + L.off_z;
+  c.tws = w + L.off_tvc;
+  c.tws_bytes = L.tvc;
+}
 
 }  // namespace
 
-size_t hopm_ws_bytes(int order, const int64_t* dims, tvc_dtype dt) { return make_hopm_plan(order, dims, dt).total; }
+size_t hopm_ws_bytes(int order, const int64_t* dims, tvc_dtype dt) { return fwd_layout(order, dims, dt, 0).total; }
 
 // Queues `iters` sweeps on `stream`.  x[m] are device vectors (FP64 for F64,
 // FP32 otherwise), updated in place.
 tvc_status hopm_launch(const void* A, int order, const int64_t* dims, void* const* x, int iters, double tol,
                        double* lam_out, int* sweeps_out, int* status_out, double* lam_hist, tvc_dtype dt,
                        const float* scales, void* ws, size_t ws_bytes, cudaStream_t st) {
-  const HopmPlan hp = make_hopm_plan(order, dims, dt);
-  if (ws == nullptr || ws_bytes < hp.total) return TVC_ERR_WORKSPACE;
-  char* w = static_cast<char*>(ws);
-  HopmState* state = reinterpret_cast<HopmState*>(w + hp.off_state);
-  const int* done = &state->done;
-  void* bufA = w + hp.off_bufA;
-  void* bufB = w + hp.off_bufB;
-  void* wv = w + hp.off_w;
-  void* z = w + hp.off_z;
-  void* tws = w + hp.off_tvc;
-  const int d = order;
-  const int64_t* n = dims;
-  const tvc_dtype vdt = (dt == TVC_F64) ? TVC_F64 : TVC_F32;
-  const bool f64 = (dt == TVC_F64);
-  tvc_status rc = TVC_OK;
-  int launches = 0;
-  auto tvc2 = [&](const void* X, int64_t a, int64_t b, int mode, const void* xv, void* y, tvc_dtype t,
-                  const float* sc) {
-    if (rc != TVC_OK) return;
-    rc = tvc_launch(X, shape2(a, b, mode), xv, y, t, sc, 1.0, 0.0, tws, hp.tvc_ws, st, done);
-  };
-  auto tvcd = [&](int mode, const void* xv, void* y) {
-    if (rc != TVC_OK) return;
-    Shape s;
-    make_shape(d, n, mode, &s);
-    rc = tvc_launch(A, s, xv, y, dt, scales, 1.0, 0.0, tws, hp.tvc_ws, st, done);
-  };
-  auto outer = [&](int from) {  // w = x_from (x) ... (x) x_{d-1}
-    OuterArgs oa{};
-    oa.nm = d - from;
-    for (int m = from; m < d; m++) {
-      oa.dims[m - from] = n[m];
-      oa.xs[m - from] = x[m];
-    }
-    const int64_t len = prod_range(n, from, d);
-    if (f64)
-      hopm_outer_kernel<double><<<grid_for(len), 256, 0, st>>>(static_cast<double*>(wv), len, oa, state);
-    else
-      hopm_outer_kernel<float><<<grid_for(len), 256, 0, st>>>(static_cast<float*>(wv), len, oa, state);
-    launches++;
-  };
-  auto normalize = [&](const void* zz, int j) {
-    const int last = (j == d - 1);
-    if (f64)
-      hopm_normalize_kernel<double><<<1, kNormThreads, 0, st>>>(static_cast<const double*>(zz), static_cast<double*>(x[j]),
-                                                                n[j], last, tol, state, lam_out, sweeps_out, status_out,
-                                                                lam_hist);
-    else
-      hopm_normalize_kernel<float><<<1, kNormThreads, 0, st>>>(static_cast<const float*>(zz), static_cast<float*>(x[j]),
-                                                               n[j], last, tol, state, lam_out, sweeps_out, status_out,
-                                                               lam_hist);
-    launches++;
-  };
-  hopm_init_kernel<<<1, 1, 0, st>>>(state);
-  launches++;
-  for (int it = 0; it < iters && rc == TVC_OK; it++) {
-    if (d == 2) {
-      tvcd(1, x[1], z);
-      normalize(z, 0);
-      tvcd(0, x[0], z);
-      normalize(z, 1);
-      continue;
-    }
-    const int64_t rest2 = prod_range(n, 2, d);
-    // j = 0
-    tvcd(1, x[1], bufA);
-    if (d == 3) {
-      tvc2(bufA, n[0], n[2], 1, x[2], z, vdt, nullptr);
-    } else {
-      outer(2);
-      tvc2(bufA, n[0], rest2, 1, wv, z, vdt, nullptr);
-    }
-    normalize(z, 0);
-    // j = 1
-    tvcd(0, x[0], bufA);
-    if (d == 3) {
-      tvc2(bufA, n[1], n[2], 1, x[2], z, vdt, nullptr);
-    } else {
-      outer(2);
-      tvc2(bufA, n[1], rest2, 1, wv, z, vdt, nullptr);
-    }
-    normalize(z, 1);
-    // j >= 2
-    void* prev = bufA;
-    void* next = bufB;
-    for (int j = 2; j < d && rc == TVC_OK; j++) {
-      tvc2(prev, n[j - 1], prod_range(n, j, d), 0, x[j - 1], next, vdt, nullptr);
-      if (j == d - 1) {
-        normalize(next, j);
-      } else {
-        if (j == d - 2) {
-          tvc2(next, n[j], n[d - 1], 1, x[d - 1], z, vdt, nullptr);
-        } else {
-          outer(j + 1);
-          tvc2(next, n[j], prod_range(n, j + 1, d), 1, wv, z, vdt, nullptr);
-        }
-        normalize(z, j);
-      }
-      std::swap(prev, next);
-    }
-  }
-  count_launches(launches);
-  if (rc != TVC_OK) return rc;
+  const FwdLayout L = fwd_layout(order, dims, dt, 0);
+  if (ws == nullptr || ws_bytes < L.total) return TVC_ERR_WORKSPACE;
+  Ctx c;
+  bind(c, L, ws, A, order, dims, dt, scales, st);
+  c.init_state();
+  for (int it = 0; it < iters && c.rc == TVC_OK; it++) c.sweep(x, tol, lam_out, sweeps_out, status_out, lam_hist, nullptr);
+  count_launches(c.launches);
+  if (c.rc != TVC_OK) return c.rc;
   return cuda_status(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------- backward
+
+namespace {
+
+// Backward workspace: the forward layout, then
+//   ckpt  iters x sum(n) vectors (the vectors at the start of every sweep)
+//   xw    sum(n)   working vectors (recomputed iterates of one sweep)
+//   gbar  sum(n)   adjoints of the current vectors
+//   gzs   sum(n)   adjoints of z_j of one sweep (the rank-1 factors of gA)
+//   sig   d doubles (norms of one sweep)
+//   W, P0, P1      N / min_j n_j each (A x_j gz and its further contractions)
+struct BwdLayout {
+  FwdLayout f;
+  size_t off_ckpt = 0, off_xw = 0, off_gbar = 0, off_gzs = 0, off_sig = 0, off_W = 0, off_P0 = 0, off_P1 = 0;
+  size_t total = 0;
+  int64_t sumn = 0, wmax = 0;
+};
+
+// Contracts the (d-1)-tensor X (modes `ids`, sizes `sz`) with vecs[k] for
+// every mode k other than `keep`, leaving the n_keep-vector; the last
+// contraction adds into gout (beta = 1).
+void all_but_one(Ctx& c, const void* X, int nd, const int* ids, const int64_t* sz, int keep, void* const* vecs,
+                 void* gout, void* P0, void* P1) {
+  int cid[TVC_MAX_ORDER];
+  int64_t csz[TVC_MAX_ORDER];
+  for (int q = 0; q < nd; q++) {
+    cid[q] = ids[q];
+    csz[q] = sz[q];
+  }
+  const void* cur = X;
+  void* bufs[2] = {P0, P1};
+  int nb = 0;
+  if (nd == 1) {  // X is already the vector
+    if (!c.dry && c.rc == TVC_OK) {
+      const int64_t len = csz[0];
+      if (c.f64())
+        hopm_axpy_kernel<double><<<grid_for(len), 256, 0, c.st>>>(static_cast<double*>(gout),
+                                                                  static_cast<const double*>(cur), len);
+      else
+        hopm_axpy_kernel<float><<<grid_for(len), 256, 0, c.st>>>(static_cast<float*>(gout),
+                                                                 static_cast<const float*>(cur), len);
+      c.launches++;
+    }
+    return;
+  }
+  while (nd > 1) {
+    int p = (cid[0] != keep) ? 0 : 1;  // first mode that is not kept
+    Shape s;
+    make_shape(nd, csz, p, &s);
+    const bool last = (nd == 2);
+    void* out = last ? gout : bufs[nb];
+    c.tvc(cur, s, vecs[cid[p]], out, c.vdt, nullptr, last ? 1.0 : 0.0);
+    for (int q = p; q < nd - 1; q++) {
+      cid[q] = cid[q + 1];
+      csz[q] = csz[q + 1];
+    }
+    nd--;
+    cur = out;
+    nb ^= 1;
+  }
+}
+
+BwdLayout bwd_layout(int order, const int64_t* dims, tvc_dtype dt, int iters) {
+  BwdLayout L;
+  L.f = fwd_layout(order, dims, dt, 0);
+  const size_t vs = vec_size(dt);
+  int64_t sumn = 0, nmin = dims[0];
+  for (int i = 0; i < order; i++) {
+    sumn += dims[i];
+    nmin = std::min(nmin, dims[i]);
+  }
+  const int64_t N = prod_range(dims, 0, order);
+  L.sumn = sumn;
+  L.wmax = N / nmin;
+  // Size the TVCs of the reverse pass with a dry run of it.
+  Ctx c;
+  c.dry = true;
+  c.d = order;
+  for (int i = 0; i < order; i++) c.n[i] = dims[i];
+  c.dt = dt;
+  c.vdt = (dt == TVC_F64) ? TVC_F64 : TVC_F32;
+  void* dummy[TVC_MAX_ORDER] = {};
+  for (int j = 0; j < order; j++) {
+    c.tvcA(j, nullptr, nullptr);
+    int ids[TVC_MAX_ORDER];
+    int64_t sz[TVC_MAX_ORDER];
+    int nd = 0;
+    for (int m = 0; m < order; m++)
+      if (m != j) {
+        ids[nd] = m;
+        sz[nd] = dims[m];
+        nd++;
+      }
+    for (int m = 0; m < order; m++)
+      if (m != j) all_but_one(c, nullptr, nd, ids, sz, m, dummy, nullptr, nullptr, nullptr);
+  }
+  size_t off = L.f.total;
+  // The forward's TVC region must hold the reverse pass's TVCs too.
+  const size_t extra_tvc = c.tvc_need > L.f.tvc ? align_up(c.tvc_need - L.f.tvc, 256) : 0;
+  L.f.tvc = std::max(L.f.tvc, c.tvc_need);
+  off += extra_tvc;
+  L.off_ckpt = off;
+  off += align_up((size_t)iters * sumn * vs, 256);
+  L.off_xw = off;
+  off += align_up((size_t)sumn * vs, 256);
+  L.off_gbar = off;
+  off += align_up((size_t)sumn * vs, 256);
+  L.off_gzs = off;
+  off += align_up((size_t)sumn * vs, 256);
+  L.off_sig = off;
+  off += align_up((size_t)order * 8, 256);
+  L.off_W = off;
+  off += align_up((size_t)L.wmax * vs, 256);
+  L.off_P0 = off;
+  off += align_up((size_t)L.wmax * vs, 256);
+  L.off_P1 = off;
+  off += align_up((size_t)L.wmax * vs, 256);
+  L.total = off;
+  return L;
+}
+
+}  // namespace
+
+// Reverse-mode gradient of a fixed-count power method (iters sweeps, no
+// early stop) with respect to A and to the start vectors, given upstream
+// gradients of the final vectors (gx_final[m], nullable) and of lambda
+// (g_lambda, device double, nullable).  Per sweep (last to first): the
+// sweep is recomputed from its checkpoint, then the updates are reversed:
+//   gz  = normalisation adjoint of x_j = z_j/||z_j||
+//   gA += gz (at mode j) (x) the other vectors as they were at the update
+//   W   = A x_j gz;  gbar_m += W contracted with the other vectors, m != j
+//   gbar_j = 0 (x_j's old value was overwritten)
+// gA is written (not accumulated); gstart[m] (nullable) receive gbar_m.
+tvc_status hopm_backward_launch(const void* A, int order, const int64_t* dims, void* const* x0, int iters,
+                                void* const* gx_final, const double* g_lambda, void* gA, void* const* gstart,
+                                tvc_dtype dt, const float* scales, void* ws, size_t ws_bytes, cudaStream_t st) {
+  const BwdLayout L = bwd_layout(order, dims, dt, iters);
+  if (ws == nullptr || ws_bytes < L.total) return TVC_ERR_WORKSPACE;
+  const size_t vs = vec_size(dt);
+  char* w = static_cast<char*>(ws);
+  Ctx c;
+  bind(c, L.f, ws, A, order, dims, dt, scales, st);
+  const int d = order;
+  int64_t off[TVC_MAX_ORDER + 1];
+  off[0] = 0;
+  for (int m = 0; m < d; m++) off[m + 1] = off[m] + dims[m];
+  auto vec_at = [&](size_t base, int m) -> void* { return w + base + (size_t)off[m] * vs; };
+  void* xw[TVC_MAX_ORDER];
+  void* gbar[TVC_MAX_ORDER];
+  void* gzs[TVC_MAX_ORDER];
+  for (int m = 0; m < d; m++) {
+    xw[m] = vec_at(L.off_xw, m);
+    gbar[m] = vec_at(L.off_gbar, m);
+    gzs[m] = vec_at(L.off_gzs, m);
+  }
+  auto ckpt = [&](int t, int m) -> void* { return w + L.off_ckpt + ((size_t)t * L.sumn + off[m]) * vs; };
+  double* sig = reinterpret_cast<double*>(w + L.off_sig);
+  void* W = w + L.off_W;
+  void* P0 = w + L.off_P0;
+  void* P1 = w + L.off_P1;
+  const int64_t N = prod_range(dims, 0, d);
+  // 1. forward with checkpoints
+  c.init_state();
+  for (int m = 0; m < d; m++) cudaMemcpyAsync(xw[m], x0[m], dims[m] * vs, cudaMemcpyDeviceToDevice, st);
+  for (int t = 0; t < iters && c.rc == TVC_OK; t++) {
+    for (int m = 0; m < d; m++) cudaMemcpyAsync(ckpt(t, m), xw[m], dims[m] * vs, cudaMemcpyDeviceToDevice, st);
+    c.sweep(xw, 0.0, nullptr, nullptr, nullptr, nullptr, nullptr);
+  }
+  // 2. adjoints of the final vectors
+  for (int m = 0; m < d; m++) {
+    if (gx_final && gx_final[m])
+      cudaMemcpyAsync(gbar[m], gx_final[m], dims[m] * vs, cudaMemcpyDeviceToDevice, st);
+    else
+      cudaMemsetAsync(gbar[m], 0, dims[m] * vs, st);
+  }
+  cudaMemsetAsync(gA, 0, (size_t)N * vs, st);
+  // 3. reverse over sweeps
+  for (int t = iters - 1; t >= 0 && c.rc == TVC_OK; t--) {
+    for (int m = 0; m < d; m++) cudaMemcpyAsync(xw[m], ckpt(t, m), dims[m] * vs, cudaMemcpyDeviceToDevice, st);
+    c.init_state();
+    c.sweep(xw, 0.0, nullptr, nullptr, nullptr, nullptr, sig);  // xw now holds the sweep's new vectors
+    for (int j = d - 1; j >= 0 && c.rc == TVC_OK; j--) {
+      // vectors at the time of update j: new for m < j, old (checkpoint) for m > j
+      void* cur[TVC_MAX_ORDER];
+      for (int m = 0; m < d; m++) cur[m] = (m < j) ? xw[m] : ckpt(t, m);
+      const double* gs = (t == iters - 1 && j == d - 1) ? g_lambda : nullptr;
+      if (c.f64())
+        hopm_bw_gz_kernel<double><<<1, kNormThreads, 0, st>>>(static_cast<const double*>(xw[j]),
+                                                              static_cast<const double*>(gbar[j]), sig + j, gs,
+                                                              dims[j], static_cast<double*>(gzs[j]));
+      else
+        hopm_bw_gz_kernel<float><<<1, kNormThreads, 0, st>>>(static_cast<const float*>(xw[j]),
+                                                             static_cast<const float*>(gbar[j]), sig + j, gs, dims[j],
+                                                             static_cast<float*>(gzs[j]));
+      c.launches++;
+      c.tvcA(j, gzs[j], W);
+      int ids[TVC_MAX_ORDER];
+      int64_t sz[TVC_MAX_ORDER];
+      int nd = 0;
+      for (int m = 0; m < d; m++)
+        if (m != j) {
+          ids[nd] = m;
+          sz[nd] = dims[m];
+          nd++;
+        }
+      for (int m = 0; m < d; m++)
+        if (m != j) all_but_one(c, W, nd, ids, sz, m, cur, gbar[m], P0, P1);
+      cudaMemsetAsync(gbar[j], 0, dims[j] * vs, st);
+    }
+    // gA += sum_j gz_j (x) (the other vectors at update j)
+    CpArgs ca{};
+    ca.d = d;
+    ca.R = d;
+    for (int m = 0; m < d; m++) ca.dims[m] = dims[m];
+    for (int j = 0; j < d; j++)
+      for (int m = 0; m < d; m++) ca.f[j][m] = (m == j) ? gzs[j] : ((m < j) ? xw[m] : ckpt(t, m));
+    const int64_t rows = N / dims[d - 1];
+    const int64_t RB = dims[d - 1] >= 256 ? 1 : 256 / dims[d - 1];
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((rows + RB - 1) / RB, (int64_t)device_sms() * 8));
+    if (c.f64())
+      hopm_cp_kernel<double><<<blocks, 256, 0, st>>>(static_cast<double*>(gA), rows, ca);
+    else
+      hopm_cp_kernel<float><<<blocks, 256, 0, st>>>(static_cast<float*>(gA), rows, ca);
+    c.launches++;
+  }
+  if (gstart)
+    for (int m = 0; m < d; m++)
+      if (gstart[m]) cudaMemcpyAsync(gstart[m], gbar[m], dims[m] * vs, cudaMemcpyDeviceToDevice, st);
+  count_launches(c.launches);
+  if (c.rc != TVC_OK) return c.rc;
+  return cuda_status(cudaGetLastError());
+}
+
+size_t hopm_bwd_ws_bytes(int order, const int64_t* dims, tvc_dtype dt, int iters) {
+  return bwd_layout(order, dims, dt, iters).total;
 }
 
 }  // namespace tvcg
@@ -355,4 +685,23 @@ extern "C" tvc_status hopm(const void* A, int order, const int64_t* dims, void* 
     if (!x[m] || !aligned(x[m], vs)) return TVC_ERR_INVALID_ARG;
   return hopm_launch(A, order, dims, x, iters, tol, lambda_out, sweeps_out, status_out, lambda_hist, dtype,
                      slab_scales, workspace, ws_bytes, (cudaStream_t)stream);
+}
+
+extern "C" size_t hopm_backward_workspace_size(int order, const int64_t* dims, tvc_dtype dtype, int iters) {
+  if (!valid_dtype(dtype) || order < 2 || iters < 0 || check_dims(order, dims, nullptr) != TVC_OK) return 0;
+  return hopm_bwd_ws_bytes(order, dims, dtype, iters);
+}
+
+extern "C" tvc_status hopm_backward(const void* A, int order, const int64_t* dims, void* const* x0, int iters,
+                                    void* const* gx_final, const double* g_lambda, void* gA, void* const* gstart,
+                                    tvc_dtype dtype, const float* slab_scales, void* workspace, size_t ws_bytes,
+                                    tvc_stream_t stream) {
+  if (!valid_dtype(dtype) || order < 2 || !A || !x0 || !gA || iters < 0) return TVC_ERR_INVALID_ARG;
+  if (check_dims(order, dims, nullptr) != TVC_OK) return TVC_ERR_INVALID_ARG;
+  const size_t vs = vec_size(dtype);
+  if (!aligned(A, elem_size(dtype)) || !aligned(gA, vs)) return TVC_ERR_INVALID_ARG;
+  for (int m = 0; m < order; m++)
+    if (!x0[m] || !aligned(x0[m], vs)) return TVC_ERR_INVALID_ARG;
+  return hopm_backward_launch(A, order, dims, x0, iters, gx_final, g_lambda, gA, gstart, dtype, slab_scales,
+                              workspace, ws_bytes, (cudaStream_t)stream);
 }
