@@ -217,6 +217,60 @@ tvc_status hopm_backward(const void* A, int order, const int64_t* dims, void* co
                          tvc_stream_t stream);
 size_t hopm_backward_workspace_size(int order, const int64_t* dims, tvc_dtype dtype, int iters);
 
+/* -------------------------------------------------------------- batches */
+
+/*
+ * Many independent FP32 tensors of any order and shape in one persistent
+ * launch (the paper's task-based overlap of many contractions, Section
+ * 4.3, done as a device work queue): one descriptor per tensor, processed
+ * largest first by blocks that pull tensors from an atomic counter.
+ * All pointers in a descriptor are device pointers, FP32, dense row-major.
+ */
+typedef struct {
+  const float* A;
+  int order;
+  int mode;
+  int64_t dims[TVC_MAX_ORDER];
+  const float* x; /* n_mode entries (forward, and gA)                  */
+  float* y;       /* N/n_mode entries: y = A x_mode x (NULL: skip)     */
+  const float* gy; /* N/n_mode entries (adjoints)                       */
+  float* gx;      /* n_mode: sum_{i,l} A[i,j,l] gy[i,l] (NULL: skip)   */
+  float* gA;      /* N: gy (x) x along mode (NULL: skip)               */
+} tvc_batch_desc;
+
+typedef struct {
+  const float* A;
+  int order; /* >= 2 */
+  int64_t dims[TVC_MAX_ORDER];
+  float* x[TVC_MAX_ORDER]; /* start vectors in, result out (x[0] not read) */
+  double* lambda_out;      /* 1 double (nullable): norm of the last update  */
+  int* status_out;         /* 1 int (nullable): TVC_OK / ZERO_NORM / NONFINITE */
+} hopm_batch_desc;
+
+/* Reuse the descriptors uploaded by the previous call on this workspace
+ * (same count): the call then issues one memset and one kernel and does
+ * not synchronise, so it can be captured in a CUDA graph. */
+#define TVC_BATCH_PREUPLOADED 1
+
+/* Without TVC_BATCH_PREUPLOADED the call uploads the descriptors and waits
+ * for that copy (the host array may be freed on return). */
+tvc_status tvc_batched(const tvc_batch_desc* descs, int count, int flags, void* workspace, size_t ws_bytes,
+                       tvc_stream_t stream);
+size_t tvc_batched_workspace_size(const tvc_batch_desc* descs, int count);
+
+/* Times the candidate block mappings (lanes per output) on one tensor of
+ * each shape class of the batch and keeps the fastest for later calls of
+ * tvc_batched / hopm_batched in this process; synchronises the stream.
+ * workspace: at least tvc_batched_workspace_size(descs, 1) bytes. */
+tvc_status tvc_batched_autotune(const tvc_batch_desc* descs, int count, void* workspace, size_t ws_bytes,
+                                tvc_stream_t stream);
+
+/* `iters` Gauss-Seidel HOPM sweeps (Section 3, Algorithm 1's schedule) on
+ * every tensor of the batch, one block per tensor; FP64 norms. */
+tvc_status hopm_batched(const hopm_batch_desc* descs, int count, int iters, int flags, void* workspace,
+                        size_t ws_bytes, tvc_stream_t stream);
+size_t hopm_batched_workspace_size(const hopm_batch_desc* descs, int count);
+
 /* Number of CUDA kernels this library has launched in this process (all
  * devices, all entry points).  Host-side counter, incremented per launch;
  * lets a caller count the kernels of a timed region. */

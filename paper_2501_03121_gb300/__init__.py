@@ -21,7 +21,7 @@ import torch
 
 __all__ = [
     "F64", "F32", "BF16", "E4M3", "TVCError", "load_library", "tvc", "tvc_workspace_size",
-    "dtype_code", "library_path", "kernel_launches", "hopm", "hopm_workspace_size", "HopmResult", "quantise", "tvc_backward", "TVCFunction", "tvc_autograd", "hopm_backward", "HOPMFunction", "hopm_autograd",
+    "dtype_code", "library_path", "kernel_launches", "hopm", "hopm_workspace_size", "HopmResult", "quantise", "tvc_backward", "TVCFunction", "tvc_autograd", "hopm_backward", "HOPMFunction", "hopm_autograd", "TVCBatch", "HOPMBatch", "BATCH_PREUPLOADED",
 ]
 
 F64, F32, BF16, E4M3 = 0, 1, 2, 3
@@ -84,6 +84,16 @@ def load_library():
         lib.hopm_backward.restype = I
         lib.hopm_backward_workspace_size.argtypes = [I, P, I, I]
         lib.hopm_backward_workspace_size.restype = Z
+        lib.tvc_batched.argtypes = [P, I, I, P, Z, P]
+        lib.tvc_batched.restype = I
+        lib.tvc_batched_workspace_size.argtypes = [P, I]
+        lib.tvc_batched_workspace_size.restype = Z
+        lib.tvc_batched_autotune.argtypes = [P, I, P, Z, P]
+        lib.tvc_batched_autotune.restype = I
+        lib.hopm_batched.argtypes = [P, I, I, I, P, Z, P]
+        lib.hopm_batched.restype = I
+        lib.hopm_batched_workspace_size.argtypes = [P, I]
+        lib.hopm_batched_workspace_size.restype = Z
         lib.tvc_kernel_launches.argtypes = []
         lib.tvc_kernel_launches.restype = ctypes.c_uint64
         _lib = lib
@@ -377,3 +387,99 @@ class HOPMFunction(torch.autograd.Function):
 def hopm_autograd(A, x0, iters):
     """Differentiable (lambda, x_0..x_{d-1}) of `iters` HOPM sweeps."""
     return HOPMFunction.apply(A, iters, *x0)
+
+
+MAX_ORDER = 16
+BATCH_PREUPLOADED = 1
+
+
+class _TvcBatchDesc(ctypes.Structure):
+    _fields_ = [("A", ctypes.c_void_p), ("order", ctypes.c_int), ("mode", ctypes.c_int),
+                ("dims", ctypes.c_int64 * MAX_ORDER), ("x", ctypes.c_void_p), ("y", ctypes.c_void_p),
+                ("gy", ctypes.c_void_p), ("gx", ctypes.c_void_p), ("gA", ctypes.c_void_p)]
+
+
+class _HopmBatchDesc(ctypes.Structure):
+    _fields_ = [("A", ctypes.c_void_p), ("order", ctypes.c_int), ("dims", ctypes.c_int64 * MAX_ORDER),
+                ("x", ctypes.c_void_p * MAX_ORDER), ("lambda_out", ctypes.c_void_p), ("status_out", ctypes.c_void_p)]
+
+
+def _p(t):
+    return None if t is None else t.data_ptr()
+
+
+class TVCBatch:
+    """A batch of FP32 contractions (+ adjoints) run by one persistent
+    launch.  items: dicts with A (float32 CUDA tensor), mode, x, and any of
+    y / gy, gx / gA (outputs preallocated by the caller; None to skip).
+    The descriptors are uploaded once (first run); later runs reuse them
+    and can be captured in a CUDA graph."""
+
+    def __init__(self, items):
+        self.items = items
+        n = len(items)
+        arr = (_TvcBatchDesc * max(1, n))()
+        for b, it in enumerate(items):
+            A = it["A"]
+            shape = tuple(it.get("shape") or A.shape)
+            d = arr[b]
+            d.A = _p(A)
+            d.order = len(shape)
+            d.mode = int(it["mode"])
+            for m, v in enumerate(shape):
+                d.dims[m] = int(v)
+            d.x, d.y, d.gy, d.gx, d.gA = (_p(it.get(k)) for k in ("x", "y", "gy", "gx", "gA"))
+        self._arr = arr
+        self.count = n
+        lib = load_library()
+        dev = items[0]["A"].device if items else torch.device("cuda")
+        need = lib.tvc_batched_workspace_size(arr, n)
+        self.workspace = torch.empty(max(1, need), dtype=torch.uint8, device=dev)
+        self._uploaded = False
+
+    def autotune(self, stream=None):
+        lib = load_library()
+        _check(lib.tvc_batched_autotune(self._arr, self.count, _ptr(self.workspace), self.workspace.numel(),
+                                        _stream(stream)), "tvc_batched_autotune")
+        self._uploaded = False  # choices changed: upload again
+
+    def run(self, stream=None):
+        lib = load_library()
+        flags = BATCH_PREUPLOADED if self._uploaded else 0
+        _check(lib.tvc_batched(self._arr, self.count, flags, _ptr(self.workspace), self.workspace.numel(),
+                               _stream(stream)), "tvc_batched")
+        self._uploaded = True
+
+
+class HOPMBatch:
+    """A batch of FP32 power methods (one block per tensor, `iters` sweeps)."""
+
+    def __init__(self, items, iters):
+        self.iters = int(iters)
+        n = len(items)
+        arr = (_HopmBatchDesc * max(1, n))()
+        for b, it in enumerate(items):
+            A = it["A"]
+            shape = tuple(it.get("shape") or A.shape)
+            d = arr[b]
+            d.A = _p(A)
+            d.order = len(shape)
+            for m, v in enumerate(shape):
+                d.dims[m] = int(v)
+                d.x[m] = _p(it["x"][m])
+            d.lambda_out = _p(it.get("lam"))
+            d.status_out = _p(it.get("status"))
+        self._arr = arr
+        self.count = n
+        lib = load_library()
+        dev = items[0]["A"].device if items else torch.device("cuda")
+        need = lib.hopm_batched_workspace_size(arr, n)
+        self.workspace = torch.empty(max(1, need), dtype=torch.uint8, device=dev)
+        self._uploaded = False
+
+    def run(self, stream=None):
+        lib = load_library()
+        flags = BATCH_PREUPLOADED if self._uploaded else 0
+        _check(lib.hopm_batched(self._arr, self.count, self.iters, flags, _ptr(self.workspace),
+                                self.workspace.numel(), _stream(stream)), "hopm_batched")
+        self._uploaded = True
