@@ -203,6 +203,147 @@ def run_reference(args, world, rank):
     return 0
 
 
+# ------------------------------------------------------------ secondary
+
+def _timed(fn, reps, warm=1):
+    import torch
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def hopm_bytes(dims, es, vs):
+    """Algorithmic bytes of one sweep of the two-pass HOPM: A read twice,
+    W_1 and later prefix tensors written and read once, T written and read."""
+    N = math.prod(dims)
+    d = len(dims)
+    b = 2 * N * es
+    b += 2 * (N // dims[1]) * vs  # T = A x_1 x_1
+    w = N // dims[0]
+    for j in range(1, d):
+        b += 2 * w * vs  # W_j written, then read
+        if j + 1 < d:
+            w //= dims[j]
+    return b
+
+
+def secondary(dev):
+    """HOPM and batched figures (other workloads; not part of `value`)."""
+    import numpy as np
+    import torch
+    import synth
+    import synth.device as sd
+    import paper_2501_03121_gb300 as tg
+    out = {}
+    # 128^3 FP64, 20 sweeps from normalised ones
+    dims = (128, 128, 128)
+    A = torch.empty(math.prod(dims), dtype=torch.float64, device=dev)
+    sd.fill(A, "u64", 0, synth.STREAM_A)
+    xs = [torch.full((n,), 1 / math.sqrt(n), dtype=torch.float64, device=dev) for n in dims]
+    ws = torch.empty(tg.hopm_workspace_size(dims, tg.F64), dtype=torch.uint8, device=dev)
+    ms = _timed(lambda: tg.hopm(A, xs, 20, shape=dims, workspace=ws), 5)
+    out["hopm_128cube_f64_20sweeps"] = {"ms": ms, "sweeps_per_s": 20 / (ms / 1e3),
+                                        "GB/s_effective_L2": 20 * hopm_bytes(dims, 8, 8) / (ms / 1e3) / 1e9,
+                                        "note": "16.8 MB tensor: L2-resident"}
+    del A, ws
+    # planted rank-1 + noise 256^4 FP32, 50 sweeps, tol 1e-8
+    dims = (256, 256, 256, 256)
+    us = [synth.unit_gaussian(0, synth.stream_u(j), n) for j, n in enumerate(dims)]
+    A = torch.empty(math.prod(dims), dtype=torch.float32, device=dev)
+    sd.fill(A, "planted", 0, 0, dims=dims, us=us)
+    xs = [torch.full((n,), 1 / math.sqrt(n), dtype=torch.float32, device=dev) for n in dims]
+    ws = torch.empty(tg.hopm_workspace_size(dims, tg.F32), dtype=torch.uint8, device=dev)
+    r = tg.hopm(A, xs, 50, 1e-8, shape=dims, workspace=ws)
+    torch.cuda.synchronize()
+    sweeps = int(r.sweeps.item())
+    sub = max(math.sqrt(max(0.0, 1 - float(np.dot(x.cpu().numpy().astype(np.float64), u)) ** 2))
+              for x, u in zip(r.x, us))
+    ms = _timed(lambda: tg.hopm(A, xs, 50, 0.0, shape=dims, workspace=ws), 2)
+    bps = hopm_bytes(dims, 4, 4)
+    out["hopm_planted_256^4_f32"] = {"lambda": r.lam.item(), "sweeps_to_tol_1e-8": sweeps,
+                                    "subspace_error": sub, "sweeps_per_s": 50 / (ms / 1e3),
+                                    "GB/s": 50 * bps / (ms / 1e3) / 1e9}
+    del A, ws, r
+    torch.cuda.empty_cache()
+    # 2048^3 N(0,1)exp(U[-3,3]): FP32 vs BF16 vs E4M3 storage, 30 sweeps
+    dims = (2048, 2048, 2048)
+    src = torch.empty(math.prod(dims), dtype=torch.float32, device=dev)
+    sd.fill(src, "lognormal", 0, synth.STREAM_A)
+    res = {}
+    xs0 = [torch.full((n,), 1 / math.sqrt(n), dtype=torch.float32, device=dev) for n in dims]
+    lam = {}
+    for name, code in (("f32", tg.F32), ("bf16", tg.BF16), ("e4m3", tg.E4M3)):
+        if code == tg.F32:
+            A, sc = src, None
+        else:
+            A, sc, st = tg.quantise(src.view(dims), code)
+            A = A.view(-1)
+        ws = torch.empty(tg.hopm_workspace_size(dims, code), dtype=torch.uint8, device=dev)
+        r = tg.hopm(A, xs0, 30, 0.0, scales=sc, shape=dims, workspace=ws)
+        torch.cuda.synchronize()
+        lam[name] = r.lam.item()
+        ms = _timed(lambda: tg.hopm(A, xs0, 30, 0.0, scales=sc, shape=dims, workspace=ws), 2)
+        es = {"f32": 4, "bf16": 2, "e4m3": 1}[name]
+        res[name] = {"sweeps_per_s": 30 / (ms / 1e3), "GB/s": 30 * hopm_bytes(dims, es, 4) / (ms / 1e3) / 1e9,
+                     "lambda": lam[name]}
+        del A, ws, r
+        torch.cuda.empty_cache()
+    res["bf16_over_f32_sweeps"] = res["bf16"]["sweeps_per_s"] / res["f32"]["sweeps_per_s"]
+    res["e4m3_over_f32_sweeps"] = res["e4m3"]["sweeps_per_s"] / res["f32"]["sweeps_per_s"]
+    res["lambda_rel_diff_bf16_vs_f32"] = abs(lam["bf16"] - lam["f32"]) / lam["f32"]
+    res["lambda_rel_diff_e4m3_vs_f32"] = abs(lam["e4m3"] - lam["f32"]) / lam["f32"]
+    out["hopm_mixed_2048^3"] = res
+    del src
+    torch.cuda.empty_cache()
+    # batched: 4096 FP32 tensors (order 3/4, dims U[8,192], <= 2^24 elements)
+    rng = np.random.default_rng(0)
+    spec = []
+    for b in range(4096):
+        d = 3 if rng.random() < 0.5 else 4
+        while True:
+            dd = tuple(int(n) for n in rng.integers(8, 193, size=d))
+            if math.prod(dd) <= (1 << 24):
+                break
+        spec.append((dd, int(rng.integers(0, d))))
+    total = sum(math.prod(dd) for dd, _ in spec)
+    pool = torch.empty(total, dtype=torch.float32, device=dev)
+    sd.fill(pool, "u32", 0, synth.STREAM_A)
+    gApool = torch.empty(total, dtype=torch.float32, device=dev)
+    items, hitems, off, nbytes = [], [], 0, 0
+    for b, (dd, mode) in enumerate(spec):
+        N = math.prod(dd)
+        A = pool[off:off + N]
+        gA = gApool[off:off + N]
+        off += N
+        x = torch.full((dd[mode],), 0.5, dtype=torch.float32, device=dev)
+        gy = torch.full((N // dd[mode],), 0.25, dtype=torch.float32, device=dev)
+        items.append(dict(A=A, shape=dd, mode=mode, x=x, y=torch.empty_like(gy), gy=gy,
+                          gx=torch.empty(dd[mode], dtype=torch.float32, device=dev), gA=gA))
+        nbytes += 2 * N * 4 + N * 4 + 2 * (N // dd[mode]) * 4 + N * 4  # A twice, gy, y, gA write
+        hitems.append(dict(A=A, shape=dd, x=[torch.full((n,), 1 / math.sqrt(n), dtype=torch.float32, device=dev)
+                                             for n in dd]))
+    batch = tg.TVCBatch(items)
+    batch.run()
+    ms = _timed(batch.run, 3)
+    hb = tg.HOPMBatch(hitems, 10)
+    hb.run()
+    hms = _timed(hb.run, 2)
+    hbytes = sum(10 * hopm_bytes(dd, 4, 4) for dd, _ in spec)
+    out["batched_4096"] = {"elements": total, "fwd_bwd_ms": ms, "fwd_bwd_GB/s": nbytes / (ms / 1e3) / 1e9,
+                           "hopm10_ms": hms, "hopm10_GB/s": hbytes / (hms / 1e3) / 1e9,
+                           "note": "one persistent launch each; effective GB/s (part of the data is L2-resident)"}
+    del pool, gApool, items, hitems, batch, hb
+    torch.cuda.empty_cache()
+    return out
+
+
 # ------------------------------------------------------------------- main
 
 def main(argv=None):
@@ -214,6 +355,7 @@ def main(argv=None):
     ap.add_argument("--detail", action="store_true", help="per-mode table on stderr")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the HOPM / batched figures")
     args = ap.parse_args(argv)
     args.warmup = max(3, args.warmup)
     world, rank, local = dist_setup()
@@ -359,6 +501,14 @@ def main(argv=None):
                "d2h_bytes_per_step": d2h, "steps": k2}
         del hostA, hostY
 
+    # free the sweep's tensors before the other workloads
+    n_calls = len(calls)
+    del tensors, calls, evs
+    torch.cuda.empty_cache()
+    sec = None
+    if world == 1 and not args.no_secondary:
+        sec = secondary(dev)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         smp = OracleSample()
@@ -371,7 +521,7 @@ def main(argv=None):
             "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "tvcs_per_step": len(calls), "bytes_per_step": step_bytes,
+            "config": {"workload": WORKLOAD, "tvcs_per_step": n_calls, "bytes_per_step": step_bytes,
                        "l2": "inputs larger than L2 (smallest tensor 1.07 GB); no flush needed",
                        "parallelism": f"replicas x{world}"},
             "frac_of_peak": value / world / peak,
@@ -381,6 +531,7 @@ def main(argv=None):
             "fp32": {"GB/s": f32_bytes / (f32_ms / 1e3) / 1e9, "frac": f32_bytes / (f32_ms / 1e3) / 1e9 / peak},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
             "per_mode_GBs": per_mode,
+            "secondary": sec,
         }
         print(json.dumps(line), flush=True)
     if pg is not None:

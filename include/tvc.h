@@ -271,6 +271,14 @@ tvc_status hopm_batched(const hopm_batch_desc* descs, int count, int iters, int 
                         size_t ws_bytes, tvc_stream_t stream);
 size_t hopm_batched_workspace_size(const hopm_batch_desc* descs, int count);
 
+/* Sticky device error of the staged (TMA-fed) kernels: every wait in them
+ * is bounded, and a wait that gives up records a nonzero code (1: the copy
+ * engine's producer waited for a free buffer, 2: a consumer waited for a
+ * tile, 3: draining copies at exit) and lets the kernel finish; its
+ * results are then invalid.  Synchronises the device; returns
+ * TVC_ERR_TIMEOUT when a code is set (and clears it when clear != 0). */
+tvc_status tvc_device_error(int* code_out, int clear);
+
 /* Number of CUDA kernels this library has launched in this process (all
  * devices, all entry points).  Host-side counter, incremented per launch;
  * lets a caller count the kernels of a timed region. */

@@ -64,6 +64,32 @@ __device__ __forceinline__ RawVec<BYTES> ld_stream(const void* p) {
   return r;
 }
 
+// Plain (generic-address) load: works on shared and global memory.
+template <int BYTES>
+__device__ __forceinline__ RawVec<BYTES> ld_plain(const void* p) {
+  RawVec<BYTES> r;
+  if constexpr (BYTES == 16) {
+    r.v = *reinterpret_cast<const uint4*>(p);
+  } else if constexpr (BYTES == 8) {
+    r.v = *reinterpret_cast<const uint2*>(p);
+  } else if constexpr (BYTES == 4) {
+    r.v = *reinterpret_cast<const unsigned int*>(p);
+  } else if constexpr (BYTES == 2) {
+    r.v = *reinterpret_cast<const unsigned short*>(p);
+  } else {
+    r.v = *reinterpret_cast<const unsigned char*>(p);
+  }
+  return r;
+}
+
+template <int BYTES, bool PLAIN>
+__device__ __forceinline__ RawVec<BYTES> ld_any(const void* p) {
+  if constexpr (PLAIN)
+    return ld_plain<BYTES>(p);
+  else
+    return ld_stream<BYTES>(p);
+}
+
 // ------------------------------------------------------ element type traits
 
 // Storage type traits: element type, FP64 or FP32 arithmetic, and decoding
@@ -77,16 +103,16 @@ struct Elem<TVC_F64> {
   using V = double;  // vector / result type
   using C = double;  // compute type of one element
   static constexpr int kSize = 8;
-  template <int VEC>
+  template <int VEC, bool PLAIN = false>
   __device__ __forceinline__ static void load(const T* p, C (&val)[VEC]) {
     if constexpr (VEC == 2) {
-      RawVec<16> r = ld_stream<16>(p);
+      RawVec<16> r = ld_any<16, PLAIN>(p);
       val[0] = __hiloint2double((int)r.v.y, (int)r.v.x);
       val[1] = __hiloint2double((int)r.v.w, (int)r.v.z);
     } else {
 #pragma unroll
       for (int e = 0; e < VEC; e++) {
-        RawVec<8> r = ld_stream<8>(p + e);
+        RawVec<8> r = ld_any<8, PLAIN>(p + e);
         val[e] = __hiloint2double((int)r.v.y, (int)r.v.x);
       }
     }
@@ -99,17 +125,21 @@ struct Elem<TVC_F32> {
   using V = float;
   using C = float;
   static constexpr int kSize = 4;
-  template <int VEC>
+  template <int VEC, bool PLAIN = false>
   __device__ __forceinline__ static void load(const T* p, C (&val)[VEC]) {
     if constexpr (VEC == 4) {
-      RawVec<16> r = ld_stream<16>(p);
+      RawVec<16> r = ld_any<16, PLAIN>(p);
       val[0] = __uint_as_float(r.v.x);
       val[1] = __uint_as_float(r.v.y);
       val[2] = __uint_as_float(r.v.z);
       val[3] = __uint_as_float(r.v.w);
+    } else if constexpr (VEC == 2) {
+      RawVec<8> r = ld_any<8, PLAIN>(p);
+      val[0] = __uint_as_float(r.v.x);
+      val[1] = __uint_as_float(r.v.y);
     } else {
 #pragma unroll
-      for (int e = 0; e < VEC; e++) val[e] = __uint_as_float(ld_stream<4>(p + e).v);
+      for (int e = 0; e < VEC; e++) val[e] = __uint_as_float(ld_any<4, PLAIN>(p + e).v);
     }
   }
 };
@@ -125,19 +155,23 @@ struct Elem<TVC_BF16> {
     lo = __uint_as_float(w << 16);
     hi = __uint_as_float(w & 0xFFFF0000u);
   }
-  template <int VEC>
+  template <int VEC, bool PLAIN = false>
   __device__ __forceinline__ static void load(const T* p, C (&val)[VEC]) {
     if constexpr (VEC == 8) {
-      RawVec<16> r = ld_stream<16>(p);
+      RawVec<16> r = ld_any<16, PLAIN>(p);
       word2(r.v.x, val[0], val[1]);
       word2(r.v.y, val[2], val[3]);
       word2(r.v.z, val[4], val[5]);
       word2(r.v.w, val[6], val[7]);
+    } else if constexpr (VEC == 4) {
+      RawVec<8> r = ld_any<8, PLAIN>(p);
+      word2(r.v.x, val[0], val[1]);
+      word2(r.v.y, val[2], val[3]);
     } else if constexpr (VEC == 2) {
-      word2(ld_stream<4>(p).v, val[0], val[1]);
+      word2(ld_any<4, PLAIN>(p).v, val[0], val[1]);
     } else {
 #pragma unroll
-      for (int e = 0; e < VEC; e++) val[e] = __uint_as_float(((uint32_t)ld_stream<2>(p + e).v) << 16);
+      for (int e = 0; e < VEC; e++) val[e] = __uint_as_float(((uint32_t)ld_any<2, PLAIN>(p + e).v) << 16);
     }
   }
 };
@@ -160,20 +194,24 @@ struct Elem<TVC_E4M3> {
     pair((uint16_t)(w & 0xFFFFu), o[0], o[1]);
     pair((uint16_t)(w >> 16), o[2], o[3]);
   }
-  template <int VEC>
+  template <int VEC, bool PLAIN = false>
   __device__ __forceinline__ static void load(const T* p, C (&val)[VEC]) {
     if constexpr (VEC == 16) {
-      RawVec<16> r = ld_stream<16>(p);
+      RawVec<16> r = ld_any<16, PLAIN>(p);
       word4(r.v.x, val + 0);
       word4(r.v.y, val + 4);
       word4(r.v.z, val + 8);
       word4(r.v.w, val + 12);
+    } else if constexpr (VEC == 8) {
+      RawVec<8> r = ld_any<8, PLAIN>(p);
+      word4(r.v.x, val + 0);
+      word4(r.v.y, val + 4);
     } else if constexpr (VEC == 4) {
-      word4(ld_stream<4>(p).v, val);
+      word4(ld_any<4, PLAIN>(p).v, val);
     } else {
 #pragma unroll
       for (int e = 0; e < VEC; e++) {
-        __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)ld_stream<1>(p + e).v, __NV_E4M3);
+        __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)ld_any<1, PLAIN>(p + e).v, __NV_E4M3);
         val[e] = __half2float(*reinterpret_cast<__half*>(&h));
       }
     }
@@ -246,6 +284,54 @@ __device__ __forceinline__ void df_mac(float& s, float& c, double& d, double a, 
   } else {
     d = dfma_slow(a, xp, d);
   }
+}
+
+// df_mac without the window test, for elements already known to be in the
+// window (see df_out_of_window); x must be in its window too.
+__device__ __forceinline__ void df_mac_fast(float& s, float& c, double a, XSplit xs) {
+  const uint32_t lo = (uint32_t)__double2loint(a);
+  const uint32_t hi = (uint32_t)__double2hiint(a);
+  const uint32_t hb = __funnelshift_l(lo, hi - 0x38000000u, 3) | (hi & 0x80000000u);
+  const float ah = __uint_as_float(hb);
+  const float sc = __uint_as_float((hb & 0xFF800000u) - 0x1A000000u);
+  const float al = __fmul_rn(__uint2float_rn(lo & 0x1FFFFFFFu), sc);
+  const float p = __fmul_rn(ah, xs.xh);
+  float e = __fmaf_rn(ah, xs.xh, -p);
+  e = __fmaf_rn(ah, xs.xl, e);
+  e = __fmaf_rn(al, xs.xh, e);
+  float t, err;
+  two_sum(s, p, t, err);
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(err, e));
+}
+
+// Nonzero when a is outside the exact window of the float-float split
+// (two integer operations; OR it over many elements, test once).
+__device__ __forceinline__ uint32_t df_out_of_window(double a) {
+  return ((uint32_t)__double2hiint(a) * 2u - kDfWindowBase) >> 28;
+}
+
+// Adds an FP64 partial d into the float-float pair (s, c): d is split like
+// an element (ah + al, integer operations only) when it lies in the window
+// (the callers keep out-of-window partials in FP64); zero is skipped.
+__device__ __forceinline__ void df_add_double(float& s, float& c, double d) {
+  float hi, lo;
+  if (df_out_of_window(d) == 0) {
+    const uint32_t l = (uint32_t)__double2loint(d);
+    const uint32_t h = (uint32_t)__double2hiint(d);
+    const uint32_t hb = __funnelshift_l(l, h - 0x38000000u, 3) | (h & 0x80000000u);
+    hi = __uint_as_float(hb);
+    lo = __fmul_rn(__uint2float_rn(l & 0x1FFFFFFFu), __uint_as_float((hb & 0xFF800000u) - 0x1A000000u));
+  } else if (d == 0.0) {
+    return;
+  } else {
+    hi = __double2float_rn(d);
+    lo = __double2float_rn(d - (double)hi);
+  }
+  float t, err;
+  two_sum(s, hi, t, err);
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(err, lo));
 }
 
 // ------------------------------------------------------------ accumulators

@@ -21,11 +21,19 @@
 // adds them in a fixed order (deterministic).
 #include <algorithm>
 #include <cstdlib>
+#include <mutex>
+#include <set>
 
 #include "common.cuh"
 #include "internal.h"
+#include "tma.cuh"
 
 namespace tvcg {
+
+// Sticky device error word of the staged kernels: a bounded wait that gave
+// up writes its code here (1: producer waited for a free stage, 2: a
+// consumer waited for a tile).  Read and cleared by tvc_device_error().
+__device__ int g_tvc_device_error = 0;
 
 constexpr int kThreads = 256;
 constexpr int kWarpsPerBlock = kThreads / kWarp;
@@ -420,6 +428,247 @@ __global__ void __launch_bounds__(kThreads) tvc_rows_short_kernel(const TvcArgs<
   }
 }
 
+// Staged rows (v == 1, n_k <= nst*G*VEC): the matrix-vector case with short
+// rows, fed by the TMA engine.  One producer lane copies tiles of R whole
+// rows (contiguous, R*n_k elements) into an S-stage ring of shared memory
+// with cp.async.bulk; eight consumer warps reduce the rows of each tile from
+// shared memory (a group of G lanes per row, the lane's pieces of x kept in
+// registers), then each warp converts and stores its RW rows with one
+// coalesced store per lane.  Full/empty mbarriers order the ring; every wait
+// is bounded (tma.cuh).  A ragged last tile (byte count not a multiple of
+// 16) is read by the consumers straight from global memory.
+// A tile goes through the copy engine only when its source address and size
+// are multiples of 16 bytes (the stage buffers are 16-byte aligned: the
+// planner makes the tile size a multiple of 16); otherwise the consumers
+// read it from global memory.  Producer and consumers decide alike.
+template <class T>
+__device__ __forceinline__ bool tile_by_copy(const T* src, uint64_t bytes) {
+  return ((bytes & 15) == 0) && ((reinterpret_cast<uintptr_t>(src) & 15) == 0);
+}
+
+struct RowsTmaParams {
+  int R, RW, S, G, nst, dq;  // dq: steps per lane sent to the DFMA pipe (FP64)
+  int64_t ntiles;
+  uint32_t tile_bytes;
+};
+
+constexpr int kTmaConsumerWarps = 8;
+constexpr int kTmaThreads = (kTmaConsumerWarps + 1) * kWarp;
+
+template <tvc_dtype DT, int VEC, int NST>
+__global__ void __launch_bounds__(kTmaThreads, 2) tvc_rows_tma_kernel(const TvcArgs<DT> a, RowsTmaParams prm) {
+  if (skip(a.done)) return;
+  using E = Elem<DT>;
+  using T = typename E::T;
+  using Cm = typename E::C;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  const int S = prm.S, R = prm.R, RW = prm.RW;
+  unsigned char* stages = smraw;
+  size_t off = (size_t)S * prm.tile_bytes;
+  float2* wres = reinterpret_cast<float2*>(smraw + off);  // [warps][RW]
+  off += (size_t)kTmaConsumerWarps * RW * sizeof(float2);
+  double* wd = reinterpret_cast<double*>(smraw + off);  // [warps][RW]
+  off += (size_t)kTmaConsumerWarps * RW * sizeof(double);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smraw + off);
+  uint64_t* empty = full + S;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < S; q++) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], kTmaConsumerWarps);
+    }
+    mbar_fence_init();
+  }
+  __syncthreads();
+  const int nk = (int)a.nk;
+  if (warp == kTmaConsumerWarps) {  // producer warp
+    if (lane == 0) {
+      int k = 0;
+      for (int64_t t = blockIdx.x; t < prm.ntiles; t += gridDim.x, k++) {
+        const int st = k % S;
+        if (k >= S && !mbar_wait(&empty[st], ((k / S) - 1) & 1, &g_tvc_device_error, 1)) break;
+        const int64_t rows = min((int64_t)R, a.u - t * R);
+        const uint64_t bytes = (uint64_t)rows * nk * sizeof(T);
+        if (tile_by_copy(a.A + t * R * a.nk, bytes)) {
+          mbar_arrive_expect_tx(&full[st], (uint32_t)bytes);
+          tma_load_1d(stages + (size_t)st * prm.tile_bytes, a.A + t * R * a.nk, (uint32_t)bytes, &full[st]);
+        } else {
+          mbar_arrive(&full[st]);
+        }
+      }
+      // Never leave with copies in flight: wait (bounded) for the last
+      // phases issued on every stage.
+      for (int q = 0; q < S && q < k; q++) {
+        const int kk = k - 1 - q;
+        mbar_wait(&full[kk % S], (kk / S) & 1, &g_tvc_device_error, 3, 400000000LL);
+      }
+    }
+    return;
+  }
+  const int G = prm.G;
+  const int p = lane & (G - 1);
+  const int gpw = kWarp / G;               // groups per warp
+  const int gw = lane / G;                 // group within the warp
+  const int step = G * VEC;
+  float xh[NST][VEC], xl[NST][VEC];
+  bool x_in_window = true;  // every x piece of this lane can take the fast path
+#pragma unroll
+  for (int q = 0; q < NST; q++)
+#pragma unroll
+    for (int e = 0; e < VEC; e++) {
+      const int j = p * VEC + q * step + e;
+      const bool ok = q < prm.nst && j < nk;
+      if constexpr (DT == TVC_F64) {
+        XSplit t = ok ? ldxs(a.xs + j) : XSplit{0.0f, 0.0f};
+        xh[q][e] = t.xh;
+        xl[q][e] = t.xl;
+        if (!(t.xh == t.xh)) x_in_window = false;
+      } else {
+        xh[q][e] = ok ? xval(a, j) : 0.0f;
+        xl[q][e] = 0.0f;
+      }
+    }
+  float2* myres = wres + warp * RW;
+  // FP64: finished rows wait in per-lane slots (lane L holds slot L) until
+  // 32 have gathered, so that the FP64 conversions and stores run on full
+  // warps (the FP64 pipe takes a warp instruction at the same cost whatever
+  // its active mask).
+  float slot_s = 0.0f, slot_c = 0.0f;
+  double slot_d = 0.0;
+  int64_t slot_row = -1;
+  int nslot = 0;
+  auto flush = [&]() {
+    if constexpr (DT == TVC_F64) {
+      if (lane < nslot && slot_row >= 0) emit(a, 0, slot_row, (slot_d + (double)slot_s) + (double)slot_c);
+      slot_row = -1;
+      nslot = 0;
+    }
+  };
+  int k = 0;
+  for (int64_t t = blockIdx.x; t < prm.ntiles; t += gridDim.x, k++) {
+    const int st = k % S;
+    if (!mbar_wait(&full[st], (k / S) & 1, &g_tvc_device_error, 2)) break;
+    const int64_t row0 = t * R;
+    const int64_t rows = min((int64_t)R, a.u - row0);
+    const uint64_t bytes = (uint64_t)rows * nk * sizeof(T);
+    const T* src = tile_by_copy(a.A + row0 * a.nk, bytes)
+                       ? reinterpret_cast<const T*>(stages + (size_t)st * prm.tile_bytes)
+                       : a.A + row0 * a.nk;
+    // rows of this warp: warp*RW .. warp*RW + RW-1; group gw takes every gpw-th
+    for (int lr = gw; lr < RW; lr += gpw) {
+      const int r = warp * RW + lr;
+      const bool active = r < rows;
+      const T* rp = src + (int64_t)(active ? r : 0) * nk;
+      Cm v[NST][VEC];
+#pragma unroll
+      for (int q = 0; q < NST; q++) {
+        const int j = p * VEC + q * step;
+        if (active && q < prm.nst && j < nk) {
+          E::template load<VEC, true>(rp + j, v[q]);
+        } else {
+#pragma unroll
+          for (int e = 0; e < VEC; e++) v[q][e] = (Cm)0;
+        }
+      }
+      if constexpr (DT == TVC_F64) {
+        const double* x = static_cast<const double*>(a.x);
+        float sacc = 0.0f, cacc = 0.0f;
+        double d = 0.0;
+        // One warp vote decides between the branch-free path (every element
+        // and x piece in the split window) and the checked one.
+        uint32_t bad = x_in_window ? 0u : 1u;
+#pragma unroll
+        for (int q = 0; q < NST; q++)
+          if (active && q < prm.nst && p * VEC + q * step < nk) {
+#pragma unroll
+            for (int e = 0; e < VEC; e++) bad |= df_out_of_window(v[q][e]);
+          }
+        if (!__any_sync(0xFFFFFFFFu, bad != 0)) {
+          // The first dq steps go to the FP64 pipe, the rest to the FP32
+          // pipe in float-float arithmetic: both pipes share the work.
+#pragma unroll
+          for (int q = 0; q < NST; q++) {
+            if (active && q < prm.nst && p * VEC + q * step < nk) {
+              if (q < prm.dq) {
+#pragma unroll
+                for (int e = 0; e < VEC; e++) d = fma(v[q][e], x[p * VEC + q * step + e], d);
+              } else {
+#pragma unroll
+                for (int e = 0; e < VEC; e++) df_mac_fast(sacc, cacc, v[q][e], XSplit{xh[q][e], xl[q][e]});
+              }
+            }
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < NST; q++) {
+            if (active && q < prm.nst && p * VEC + q * step < nk) {
+#pragma unroll
+              for (int e = 0; e < VEC; e++)
+                df_mac(sacc, cacc, d, v[q][e], x + (p * VEC + q * step + e), XSplit{xh[q][e], xl[q][e]});
+            }
+          }
+        }
+        // The FP64 partial (DFMA share, out-of-window elements) joins the
+        // float-float pair before the group reduction when it fits the
+        // split window; otherwise (huge or tiny values) it stays FP64 and is
+        // reduced on its own (rare: a warp vote).
+        double drest = 0.0;
+        if (df_out_of_window(d) == 0)
+          df_add_double(sacc, cacc, d);
+        else
+          drest = d;
+        const bool anyd = __any_sync(0xFFFFFFFFu, __double_as_longlong(drest) != 0);
+        for (int o = G / 2; o > 0; o >>= 1) {
+          const float s2 = __shfl_xor_sync(0xFFFFFFFFu, sacc, o);
+          const float c2 = __shfl_xor_sync(0xFFFFFFFFu, cacc, o);
+          float tt, err;
+          two_sum(sacc, s2, tt, err);
+          sacc = tt;
+          cacc = __fadd_rn(cacc, __fadd_rn(c2, err));
+        }
+        if (anyd)
+          for (int o = G / 2; o > 0; o >>= 1) drest += __shfl_xor_sync(0xFFFFFFFFu, drest, o);
+        // Move the gpw finished rows (lanes 0, G, 2G, ...) into slots
+        // nslot .. nslot+gpw-1 (nslot is a multiple of gpw).
+        const int rel = lane - nslot;
+        const int srcl = (rel >= 0 && rel < gpw) ? rel * G : 0;
+        const float ss = __shfl_sync(0xFFFFFFFFu, sacc, srcl);
+        const float cc = __shfl_sync(0xFFFFFFFFu, cacc, srcl);
+        double dd = 0.0;
+        if (anyd) dd = __shfl_sync(0xFFFFFFFFu, drest, srcl);
+        if (rel >= 0 && rel < gpw) {
+          const int rr = warp * RW + (lr - gw) + rel;  // the row group `rel` computed
+          slot_s = ss;
+          slot_c = cc;
+          slot_d = dd;
+          slot_row = (rr < rows) ? row0 + rr : -1;
+        }
+        nslot += gpw;
+        if (nslot == kWarp) flush();
+      } else {
+        float acc = 0.0f;
+#pragma unroll
+        for (int q = 0; q < NST; q++)
+#pragma unroll
+          for (int e = 0; e < VEC; e++) acc = __fmaf_rn(v[q][e], xh[q][e], acc);
+        for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+        if (p == 0) myres[lr] = make_float2(acc, 0.0f);
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[st]);
+    if constexpr (DT != TVC_F64) {
+      // One coalesced store per lane for the warp's rows.
+      for (int lr = lane; lr < RW; lr += kWarp) {
+        const int64_t row = row0 + warp * RW + lr;
+        if (warp * RW + lr < rows) emit(a, 0, row, __fmul_rn(myres[lr].x, out_scale(a, row)));
+      }
+      __syncwarp();
+    }
+  }
+  flush();
+}
+
 // ------------------------------------------------------------------ SLAB --
 
 template <tvc_dtype DT>
@@ -516,7 +765,7 @@ __global__ void __launch_bounds__(kThreads) tvc_tile_kernel(const TvcArgs<DT> a,
   if (skip(a.done)) return;
   using E = Elem<DT>;
   using T = typename E::T;
-  extern __shared__ __align__(16) unsigned char smraw[];
+  extern __shared__ __align__(128) unsigned char smraw[];
   const int64_t S = a.nk * a.v;
   const int nk = (int)a.nk, v = (int)a.v;
   const int64_t i0 = (int64_t)blockIdx.x * R;
@@ -636,17 +885,65 @@ __global__ void tvc_reduce_kernel(const V* __restrict__ partial, V* __restrict__
 
 // ------------------------------------------------------------------ plan --
 
-enum Kind { K_COLS = 0, K_ROWS = 1, K_SLAB = 2, K_TILE = 3, K_ROWS_SHORT = 4 };
+enum Kind { K_COLS = 0, K_ROWS = 1, K_SLAB = 2, K_TILE = 3, K_ROWS_SHORT = 4, K_ROWS_TMA = 5 };
 
 struct Plan {
   Kind kind = K_COLS;
   int vec = 1;
   int64_t splits = 1, chunk = 0;
-  int R = 0, vec16 = 0, g = 0, G = 0, nst = 0;
+  int R = 0, vec16 = 0, g = 0, G = 0, nst = 0, RW = 0, S = 0, dq = 0;
+  int64_t ntiles = 0;
+  uint32_t tile_bytes = 0;
   size_t smem = 0;
   dim3 grid;
   size_t ws_xs = 0, ws_partial = 0, ws_total = 0;
 };
+
+// Opts a kernel in to `bytes` of dynamic shared memory, once per kernel and
+// device (the attribute is per device function).
+static void opt_in_smem(const void* kern, int bytes) {
+  static std::mutex mu;
+  static std::set<std::pair<int, const void*>> done;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  if (done.insert({dev, kern}).second) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    // prefer the largest shared-memory carveout so that two blocks fit
+    cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  }
+}
+
+// Steps per lane of the staged rows kernel (4: fewer registers; 8: fewer
+// lanes per row and shorter reductions).  TVC_STAGED_STEPS overrides.
+static int staged_steps_target() {
+  static int v = [] {
+    const char* e = std::getenv("TVC_STAGED_STEPS");
+    const int r = e ? std::atoi(e) : 4;
+    return (r == 4 || r == 8) ? r : 4;
+  }();
+  return v;
+}
+
+// Steps per lane of FP64 staged rows sent to the DFMA pipe: about a third
+// of them by default (TVC_STAGED_DFMA = steps overrides, -1 = default).
+static int staged_dfma_steps(int nst) {
+  static int v = [] {
+    const char* e = std::getenv("TVC_STAGED_DFMA");
+    return e ? std::atoi(e) : -1;
+  }();
+  if (v >= 0) return v;
+  return nst / 3;
+}
+
+// Staged (TMA) rows kernel on by default; TVC_STAGED_ROWS=0 turns it off.
+static bool staged_rows_enabled() {
+  static bool v = [] {
+    const char* e = std::getenv("TVC_STAGED_ROWS");
+    return !(e && std::atoi(e) == 0);
+  }();
+  return v;
+}
 
 static int dfma_rows_option() {
   static int v = [] {
@@ -671,7 +968,13 @@ static int pick_vec(tvc_dtype dt, int64_t stride_elems, const void* A, int max_v
 
 static int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
-static Plan make_plan(const Shape& s, tvc_dtype dt, const void* A) {
+static Plan make_plan_impl(const Shape& s, tvc_dtype dt, const void* A, bool allow_staged);
+static Plan make_plan_unstaged(const Shape& s, tvc_dtype dt, const void* A) {
+  return make_plan_impl(s, dt, A, false);
+}
+static Plan make_plan(const Shape& s, tvc_dtype dt, const void* A) { return make_plan_impl(s, dt, A, true); }
+
+static Plan make_plan_impl(const Shape& s, tvc_dtype dt, const void* A, bool allow_staged) {
   Plan p;
   const int sms = device_sms();
   const int64_t target_threads = (int64_t)sms * 2048;
@@ -686,7 +989,40 @@ static Plan make_plan(const Shape& s, tvc_dtype dt, const void* A) {
     p.chunk = ceil_div(ceil_div(s.nk, splits), 8) * 8;
     p.splits = ceil_div(s.nk, p.chunk);
     p.grid = dim3((unsigned)ceil_div(threads, kThreads), (unsigned)p.splits);
-  } else if (s.v == 1 && s.nk <= 8 * 32 * (int64_t)pick_vec(dt, s.nk, A, 4)) {
+  } else if (s.v == 1 && dt != TVC_F64 && allow_staged && staged_rows_enabled() && aligned(A, 16) &&
+             s.nk <= 8 * 32 * (int64_t)pick_vec(dt, s.nk, A, 4) && s.u >= 8) {
+    // Staged short rows: tiles of R = 8*RW whole rows through shared memory.
+    p.kind = K_ROWS_TMA;
+    p.vec = pick_vec(dt, s.nk, A, 4);
+    int G = 1;
+    while (G < 32 && (int64_t)G * p.vec * staged_steps_target() < s.nk) G <<= 1;
+    p.G = G;
+    p.nst = (int)ceil_div(s.nk, (int64_t)G * p.vec);
+    p.dq = (dt == TVC_F64) ? std::min(p.nst - 1, staged_dfma_steps(p.nst)) : 0;
+    const int gpw = kWarp / G;
+    const int64_t row_bytes = s.nk * (int64_t)es;
+    int RW = gpw;  // at least one row per group
+    while (RW * 2 <= 32 && (int64_t)kTmaConsumerWarps * RW * 2 * row_bytes <= 24 * 1024) RW *= 2;
+    // tiles must keep 16-byte alignment of every tile start and stage buffer
+    while (((int64_t)kTmaConsumerWarps * RW * row_bytes) % 16 != 0 && RW < 64) RW *= 2;
+    p.RW = RW;
+    if (((int64_t)kTmaConsumerWarps * RW * row_bytes) % 16 != 0) {
+      // cannot happen for 8 warps and RW a power of two >= 2 (8*2*es*n_k is a
+      // multiple of 16); kept as a guard: fall back to the register kernels.
+      return make_plan_unstaged(s, dt, A);
+    }
+    p.R = kTmaConsumerWarps * RW;
+    p.tile_bytes = (uint32_t)(p.R * row_bytes);
+    p.S = (int)std::max<int64_t>(2, std::min<int64_t>(6, (int64_t)(96 * 1024) / p.tile_bytes));
+    p.ntiles = ceil_div(s.u, p.R);
+    p.smem = (size_t)p.S * p.tile_bytes + (size_t)kTmaConsumerWarps * RW * (sizeof(float2) + sizeof(double)) +
+             2 * (size_t)p.S * sizeof(uint64_t);
+    p.splits = 1;
+    p.chunk = s.nk;
+    p.grid = dim3((unsigned)std::max<int64_t>(1, std::min<int64_t>(p.ntiles, (int64_t)sms * 2)), 1);
+  } else if (s.v == 1 && dt != TVC_F64 && s.nk <= 8 * 32 * (int64_t)pick_vec(dt, s.nk, A, 4)) {
+    // (FP64 rows, short or long, measured fastest with the grouped-row
+    // kernel below; the staged kernel serves the narrow types.)
     // Short rows: the smallest group whose 4 steps cover the row (8 steps
     // at G = 32); each group takes several rows per iteration (see the
     // kernel) so that enough loads are in flight.
@@ -801,6 +1137,32 @@ static void launch_rows_short(const Plan& p, const TvcArgs<DT>& a, cudaStream_t 
 }
 
 template <tvc_dtype DT>
+static void launch_rows_tma(const Plan& p, const TvcArgs<DT>& a, cudaStream_t st) {
+  RowsTmaParams prm;
+  prm.R = p.R;
+  prm.RW = p.RW;
+  prm.S = p.S;
+  prm.G = p.G;
+  prm.nst = p.nst;
+  prm.dq = p.dq;
+  prm.ntiles = p.ntiles;
+  prm.tile_bytes = p.tile_bytes;
+  auto go = [&](auto kern) {
+    opt_in_smem(reinterpret_cast<const void*>(kern), 200 * 1024);
+    kern<<<p.grid, kTmaThreads, p.smem, st>>>(a, prm);
+  };
+  const bool n4 = p.nst <= 4;
+  if constexpr (DT == TVC_F64) {
+    if (p.vec == 2) n4 ? go(tvc_rows_tma_kernel<DT, 2, 4>) : go(tvc_rows_tma_kernel<DT, 2, 8>);
+    else n4 ? go(tvc_rows_tma_kernel<DT, 1, 4>) : go(tvc_rows_tma_kernel<DT, 1, 8>);
+  } else {
+    if (p.vec == 4) n4 ? go(tvc_rows_tma_kernel<DT, 4, 4>) : go(tvc_rows_tma_kernel<DT, 4, 8>);
+    else if (p.vec == 2) n4 ? go(tvc_rows_tma_kernel<DT, 2, 4>) : go(tvc_rows_tma_kernel<DT, 2, 8>);
+    else n4 ? go(tvc_rows_tma_kernel<DT, 1, 4>) : go(tvc_rows_tma_kernel<DT, 1, 8>);
+  }
+}
+
+template <tvc_dtype DT>
 static void launch_main(const Plan& p, const TvcArgs<DT>& a, cudaStream_t st) {
   switch (p.kind) {
     case K_COLS: {
@@ -834,15 +1196,14 @@ static void launch_main(const Plan& p, const TvcArgs<DT>& a, cudaStream_t st) {
     case K_ROWS_SHORT:
       launch_rows_short<DT>(p, a, st);
       break;
+    case K_ROWS_TMA:
+      launch_rows_tma<DT>(p, a, st);
+      break;
     case K_SLAB:
       tvc_slab_kernel<DT><<<p.grid, kThreads, 0, st>>>(a, p.g, p.G);
       break;
     case K_TILE: {
-      static bool configured = false;  // opt in to more than 48 KB once per process
-      if (!configured) {
-        cudaFuncSetAttribute(tvc_tile_kernel<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
-        configured = true;
-      }
+      opt_in_smem(reinterpret_cast<const void*>(tvc_tile_kernel<DT>), 64 * 1024);
       tvc_tile_kernel<DT><<<p.grid, kThreads, p.smem, st>>>(a, p.R, p.vec16);
       break;
     }
@@ -916,6 +1277,17 @@ static tvc_status validate(const void* A, int order, const int64_t* dims, int mo
 }  // namespace tvcg
 
 using namespace tvcg;
+
+extern "C" tvc_status tvc_device_error(int* code_out, int clear) {
+  int v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_tvc_device_error, sizeof(int)) != cudaSuccess) return TVC_ERR_CUDA;
+  if (clear) {
+    const int z = 0;
+    if (cudaMemcpyToSymbol(g_tvc_device_error, &z, sizeof(int)) != cudaSuccess) return TVC_ERR_CUDA;
+  }
+  if (code_out) *code_out = v;
+  return v ? TVC_ERR_TIMEOUT : TVC_OK;
+}
 
 extern "C" size_t tvc_workspace_size(int order, const int64_t* dims, int mode, tvc_dtype dtype) {
   Shape s;
