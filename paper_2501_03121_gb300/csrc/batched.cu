@@ -30,7 +30,7 @@ namespace tvcg {
 namespace {
 
 constexpr int kBBT = 256;        // threads per block
-constexpr int kBBlocksPerSM = 2;
+constexpr int kBBlocksPerSM = 8;
 
 struct BItem {
   const float* A;
@@ -70,13 +70,12 @@ __device__ void blk_tvc(const float* __restrict__ A, int64_t u, int64_t nk, int6
       const int64_t i = o / v, l = o - i * v;
       const float* row = A + i * nk * v + l;
       int64_t j = p;
-      for (; j + 3 * G < nk; j += 4 * G) {
-        const float a0 = __ldcs(row + j * v), a1 = __ldcs(row + (j + G) * v), a2 = __ldcs(row + (j + 2 * G) * v),
-                    a3 = __ldcs(row + (j + 3 * G) * v);
-        acc = __fmaf_rn(a0, __ldg(x + j), acc);
-        acc = __fmaf_rn(a1, __ldg(x + j + G), acc);
-        acc = __fmaf_rn(a2, __ldg(x + j + 2 * G), acc);
-        acc = __fmaf_rn(a3, __ldg(x + j + 3 * G), acc);
+      for (; j + 7 * G < nk; j += 8 * G) {  // eight loads in flight per lane
+        float av[8];
+#pragma unroll
+        for (int q = 0; q < 8; q++) av[q] = __ldcs(row + (j + q * G) * v);
+#pragma unroll
+        for (int q = 0; q < 8; q++) acc = __fmaf_rn(av[q], __ldg(x + j + q * G), acc);
       }
       for (; j < nk; j += G) acc = __fmaf_rn(__ldcs(row + j * v), __ldg(x + j), acc);
     }
@@ -102,6 +101,7 @@ __device__ void blk_gx(const float* __restrict__ A, int64_t u, int64_t nk, int64
           const float* a = A + (i * nk + j) * v;
           const float* g = gy + i * v;
           float part = 0.0f;
+#pragma unroll 8
           for (int64_t l = p; l < v; l += G) part = __fmaf_rn(__ldcs(a + l), __ldg(g + l), part);
           acc.add(part);
         }
@@ -110,6 +110,7 @@ __device__ void blk_gx(const float* __restrict__ A, int64_t u, int64_t nk, int64
           const float* a = A + (i * nk + j) * v;
           const float* g = gy + i * v;
           float part = 0.0f;
+#pragma unroll 8
           for (int64_t l = 0; l < v; l++) part = __fmaf_rn(__ldcs(a + l), __ldg(g + l), part);
           acc.add(part);
         }

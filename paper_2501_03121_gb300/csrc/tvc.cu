@@ -74,6 +74,29 @@ __device__ __forceinline__ float xval(const TvcArgs<DT>& a, int64_t j) {
   return xv;
 }
 
+// x entries j .. j+VEC-1 (j a multiple of VEC): 16-byte loads when x is
+// 16-byte aligned and no per-row slab scale applies (k > 0), else one by one.
+template <tvc_dtype DT, int VEC>
+__device__ __forceinline__ void xvec(const TvcArgs<DT>& a, int64_t j, float (&xq)[VEC]) {
+  const float* x = static_cast<const float*>(a.x);
+  const bool fold = (DT == TVC_BF16 || DT == TVC_E4M3) && a.mode0 && a.scales;
+  if constexpr (VEC % 4 == 0) {
+    if (!fold && ((reinterpret_cast<uintptr_t>(x) & 15) == 0)) {
+#pragma unroll
+      for (int e = 0; e < VEC; e += 4) {
+        const float4 f = __ldg(reinterpret_cast<const float4*>(x + j + e));
+        xq[e] = f.x;
+        xq[e + 1] = f.y;
+        xq[e + 2] = f.z;
+        xq[e + 3] = f.w;
+      }
+      return;
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < VEC; e++) xq[e] = xval(a, j + e);
+}
+
 // Scale of output row i (k > 0): all elements of an output share slab i / upi0.
 template <tvc_dtype DT>
 __device__ __forceinline__ float out_scale(const TvcArgs<DT>& a, int64_t i) {
@@ -170,6 +193,72 @@ __global__ void __launch_bounds__(kThreads) tvc_cols_kernel(const TvcArgs<DT> a)
 #pragma unroll
     for (int e = 0; e < VEC; e++) emit(a, blockIdx.y, o + e, __fmul_rn(acc.result(e), sc));
   }
+}
+
+// Columns with a per-thread asynchronous pipeline (narrow storage): each
+// thread keeps the next D rows of its 16-byte column piece in flight with
+// cp.async (global -> its own shared-memory slots, no registers held), and
+// consumes row j while row j + D is being fetched.  Each thread waits only
+// for its own copies (cp.async.wait_group), so no block barrier is needed.
+// This keeps D * 16 bytes per thread in flight, which the register-bound
+// column kernel cannot for 8- or 16-element vectors.
+constexpr int kAsyncDepth = 10;
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+template <tvc_dtype DT, int VEC>
+__global__ void __launch_bounds__(kThreads) tvc_cols_async_kernel(const TvcArgs<DT> a) {
+  if (skip(a.done)) return;
+  using E = Elem<DT>;
+  using T = typename E::T;
+  static_assert(VEC * sizeof(T) == 16, "16-byte column pieces");
+  __shared__ __align__(16) uint4 stage[kAsyncDepth][kThreads];
+  const int64_t o = ((int64_t)blockIdx.x * kThreads + threadIdx.x) * VEC;
+  const bool active = o < a.uv;
+  const int64_t oo = active ? o : 0;
+  const int64_t i = oo / a.v;
+  const int64_t l = oo - i * a.v;
+  const int64_t j0 = (int64_t)blockIdx.y * a.chunk;
+  const int64_t j1 = min(a.nk, j0 + a.chunk);
+  const int64_t st = a.v;
+  const T* p = a.A + (i * a.nk + j0) * st + l;
+  const int64_t n = active ? (j1 - j0) : 0;
+#pragma unroll
+  for (int d = 0; d < kAsyncDepth; d++) {
+    if (d < n) cp_async16(&stage[d][threadIdx.x], p + d * st);
+    cp_async_commit();
+  }
+  AccF32<VEC> acc;
+  acc.init();
+  int blk = 0;
+  for (int64_t r = 0; r < n; r++) {
+    cp_async_wait<kAsyncDepth - 1>();
+    const int slot = (int)(r % kAsyncDepth);
+    float v[VEC];
+    E::template load<VEC, true>(reinterpret_cast<const T*>(&stage[slot][threadIdx.x]), v);
+    const float xv = xval(a, j0 + r);
+    // the slot is free again: fetch row r + D into it
+    if (r + kAsyncDepth < n) cp_async16(&stage[slot][threadIdx.x], p + (r + kAsyncDepth) * st);
+    cp_async_commit();
+    acc.mac(v, xv);
+    if (++blk == kRB) {
+      acc.fold();
+      blk = 0;
+    }
+  }
+  cp_async_wait<0>();
+  if (!active) return;
+  acc.fold();
+  const float sc = out_scale(a, i);
+#pragma unroll
+  for (int e = 0; e < VEC; e++) emit(a, blockIdx.y, o + e, __fmul_rn(acc.result(e), sc));
 }
 
 // ------------------------------------------------------------------ ROWS --
@@ -272,8 +361,10 @@ __global__ void __launch_bounds__(kThreads) tvc_rows_kernel(const TvcArgs<DT> a)
       for (int q = 0; q < UNR; q++) E::template load<VEC>(rp + j + q * STEP, r[q]);
 #pragma unroll
       for (int q = 0; q < UNR; q++) {
+        float xq[VEC];
+        xvec<DT, VEC>(a, j + q * STEP, xq);
 #pragma unroll
-        for (int e = 0; e < VEC; e++) acc.a[e] = __fmaf_rn(r[q][e], xval(a, j + q * STEP + e), acc.a[e]);
+        for (int e = 0; e < VEC; e++) acc.a[e] = __fmaf_rn(r[q][e], xq[e], acc.a[e]);
       }
       if (++blk == kRB / UNR) {
         acc.fold();
@@ -294,6 +385,85 @@ __global__ void __launch_bounds__(kThreads) tvc_rows_kernel(const TvcArgs<DT> a)
     for (int off = G / 2; off > 0; off >>= 1) tot += __shfl_xor_sync(0xFFFFFFFFu, tot, off);
     if (active && p == 0) emit(a, blockIdx.y, row, __fmul_rn(tot, out_scale(a, row)));
   }
+}
+
+// FP64 rows with G < 32 lanes per row (short rows): each warp takes 32 rows
+// in G passes of 32/G rows, keeps every finished row in a per-lane slot
+// (lane L holds row L of the warp), and converts and stores the 32 results
+// with full-warp FP64 instructions.  The FP64 pipe takes a warp instruction
+// at the same cost whatever its active mask, so converting per pass would
+// spend it G times over.  Products and reductions stay on the FP32 pipe.
+template <int VEC, int G>
+__global__ void __launch_bounds__(kThreads) tvc_rows_f64_slots_kernel(const TvcArgs<TVC_F64> a) {
+  if (skip(a.done)) return;
+  using E = Elem<TVC_F64>;
+  constexpr int STEP = G * VEC;
+  constexpr int GPW = kWarp / G;
+  const int lane = threadIdx.x & (kWarp - 1);
+  const int p = lane & (G - 1);
+  const int gw = lane / G;
+  const int64_t wrow0 = ((int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5)) * kWarp;
+  if (wrow0 >= a.u) return;  // whole warp
+  const int64_t j0 = (int64_t)blockIdx.y * a.chunk;
+  const int64_t j1 = min(a.nk, j0 + a.chunk);
+  const double* x = static_cast<const double*>(a.x);
+  float slot_s = 0.0f, slot_c = 0.0f;
+  double slot_d = 0.0;
+  for (int it = 0; it < G; it++) {
+    const int64_t row = wrow0 + it * GPW + gw;
+    const bool active = row < a.u;
+    const double* rp = a.A + (active ? row : 0) * a.nk;
+    float sacc = 0.0f, cacc = 0.0f;
+    double d = 0.0;
+    if (active) {
+      int64_t jj = j0 + p * VEC;
+      for (; jj + 3 * STEP + VEC <= j1; jj += 4 * STEP) {
+        double r[4][VEC];
+#pragma unroll
+        for (int q = 0; q < 4; q++) E::template load<VEC>(rp + jj + q * STEP, r[q]);
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+#pragma unroll
+          for (int e = 0; e < VEC; e++) df_mac(sacc, cacc, d, r[q][e], x + jj + q * STEP + e, ldxs(a.xs + jj + q * STEP + e));
+      }
+      for (; jj + VEC <= j1; jj += STEP) {
+        double r[VEC];
+        E::template load<VEC>(rp + jj, r);
+#pragma unroll
+        for (int e = 0; e < VEC; e++) df_mac(sacc, cacc, d, r[e], x + jj + e, ldxs(a.xs + jj + e));
+      }
+    }
+    const bool anyd = __any_sync(0xFFFFFFFFu, __double_as_longlong(d) != 0);
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) {
+      const float s2 = __shfl_xor_sync(0xFFFFFFFFu, sacc, off);
+      const float c2 = __shfl_xor_sync(0xFFFFFFFFu, cacc, off);
+      float t, err;
+      two_sum(sacc, s2, t, err);
+      sacc = t;
+      cacc = __fadd_rn(cacc, __fadd_rn(c2, err));
+    }
+    if (anyd) {
+#pragma unroll
+      for (int off = G / 2; off > 0; off >>= 1) d += __shfl_xor_sync(0xFFFFFFFFu, d, off);
+    }
+    // lanes it*GPW .. it*GPW + GPW - 1 take the rows of this pass
+    const int rel = lane - it * GPW;
+    const bool mine = rel >= 0 && rel < GPW;
+    const int srcl = mine ? rel * G : 0;
+    const float ss = __shfl_sync(0xFFFFFFFFu, sacc, srcl);
+    const float cc = __shfl_sync(0xFFFFFFFFu, cacc, srcl);
+    if (mine) {
+      slot_s = ss;
+      slot_c = cc;
+    }
+    if (anyd) {
+      const double dd = __shfl_sync(0xFFFFFFFFu, d, srcl);
+      if (mine) slot_d = dd;
+    }
+  }
+  const int64_t row = wrow0 + lane;
+  if (row < a.u) emit(a, blockIdx.y, row, (slot_d + (double)slot_s) + (double)slot_c);
 }
 
 // Short rows (v == 1, n_k <= NST*G*VEC): a group of G lanes (runtime, power
@@ -885,7 +1055,7 @@ __global__ void tvc_reduce_kernel(const V* __restrict__ partial, V* __restrict__
 
 // ------------------------------------------------------------------ plan --
 
-enum Kind { K_COLS = 0, K_ROWS = 1, K_SLAB = 2, K_TILE = 3, K_ROWS_SHORT = 4, K_ROWS_TMA = 5 };
+enum Kind { K_COLS = 0, K_ROWS = 1, K_SLAB = 2, K_TILE = 3, K_ROWS_SHORT = 4, K_ROWS_TMA = 5, K_ROWS_F64S = 6 };
 
 struct Plan {
   Kind kind = K_COLS;
@@ -1048,7 +1218,11 @@ static Plan make_plan_impl(const Shape& s, tvc_dtype dt, const void* A, bool all
     while (G > 2 && (int64_t)G * p.vec * 4 > s.nk) G >>= 1;
     p.G = G;
     const int64_t group = 4 * (int64_t)G * p.vec;  // one unrolled step of a group
-    const int64_t rows_per_block = (int64_t)kWarpsPerBlock * (kWarp / G);
+    int64_t rows_per_block = (int64_t)kWarpsPerBlock * (kWarp / G);
+    if (dt == TVC_F64 && G < 32) {
+      p.kind = K_ROWS_F64S;  // 32 rows per warp, results converted in slots
+      rows_per_block = (int64_t)kWarpsPerBlock * kWarp;
+    }
     const int64_t target_groups = (int64_t)sms * 64 * (kWarp / G);
     int64_t splits = 1;
     if (s.u < target_groups) splits = std::min(ceil_div(target_groups, s.u), std::max<int64_t>(1, s.nk / (8 * group)));
@@ -1162,6 +1336,17 @@ static void launch_rows_tma(const Plan& p, const TvcArgs<DT>& a, cudaStream_t st
   }
 }
 
+template <int VEC>
+static void launch_rows_f64s_vec(const Plan& p, const TvcArgs<TVC_F64>& a, cudaStream_t st) {
+  switch (p.G) {
+    case 1: tvc_rows_f64_slots_kernel<VEC, 1><<<p.grid, kThreads, 0, st>>>(a); break;
+    case 2: tvc_rows_f64_slots_kernel<VEC, 2><<<p.grid, kThreads, 0, st>>>(a); break;
+    case 4: tvc_rows_f64_slots_kernel<VEC, 4><<<p.grid, kThreads, 0, st>>>(a); break;
+    case 8: tvc_rows_f64_slots_kernel<VEC, 8><<<p.grid, kThreads, 0, st>>>(a); break;
+    default: tvc_rows_f64_slots_kernel<VEC, 16><<<p.grid, kThreads, 0, st>>>(a); break;
+  }
+}
+
 template <tvc_dtype DT>
 static void launch_main(const Plan& p, const TvcArgs<DT>& a, cudaStream_t st) {
   switch (p.kind) {
@@ -1180,11 +1365,11 @@ static void launch_main(const Plan& p, const TvcArgs<DT>& a, cudaStream_t st) {
         if (p.vec == 4) tvc_cols_kernel<DT, 4, 0><<<p.grid, kThreads, 0, st>>>(a);
         else tvc_cols_kernel<DT, 1, 0><<<p.grid, kThreads, 0, st>>>(a);
       } else if constexpr (DT == TVC_BF16) {
-        if (p.vec == 8) tvc_cols_kernel<DT, 8, 0><<<p.grid, kThreads, 0, st>>>(a);
+        if (p.vec == 8) tvc_cols_async_kernel<DT, 8><<<p.grid, kThreads, 0, st>>>(a);
         else if (p.vec == 2) tvc_cols_kernel<DT, 2, 0><<<p.grid, kThreads, 0, st>>>(a);
         else tvc_cols_kernel<DT, 1, 0><<<p.grid, kThreads, 0, st>>>(a);
       } else {
-        if (p.vec == 16) tvc_cols_kernel<DT, 16, 0><<<p.grid, kThreads, 0, st>>>(a);
+        if (p.vec == 16) tvc_cols_async_kernel<DT, 16><<<p.grid, kThreads, 0, st>>>(a);
         else if (p.vec == 4) tvc_cols_kernel<DT, 4, 0><<<p.grid, kThreads, 0, st>>>(a);
         else tvc_cols_kernel<DT, 1, 0><<<p.grid, kThreads, 0, st>>>(a);
       }
@@ -1198,6 +1383,12 @@ static void launch_main(const Plan& p, const TvcArgs<DT>& a, cudaStream_t st) {
       break;
     case K_ROWS_TMA:
       launch_rows_tma<DT>(p, a, st);
+      break;
+    case K_ROWS_F64S:
+      if constexpr (DT == TVC_F64) {
+        if (p.vec == 2) launch_rows_f64s_vec<2>(p, a, st);
+        else launch_rows_f64s_vec<1>(p, a, st);
+      }
       break;
     case K_SLAB:
       tvc_slab_kernel<DT><<<p.grid, kThreads, 0, st>>>(a, p.g, p.G);

@@ -25,7 +25,7 @@ def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--dims", type=int, nargs="+", required=True)
     ap.add_argument("--mode", type=int, default=0)
-    ap.add_argument("--dtype", default="f64", choices=["f64", "f32"])
+    ap.add_argument("--dtype", default="f64", choices=["f64", "f32", "bf16", "e4m3"])
     ap.add_argument("--reps", type=int, default=3)
     a = ap.parse_args(argv)
     dt = torch.float64 if a.dtype == "f64" else torch.float32
@@ -33,13 +33,18 @@ def main(argv=None):
     N = math.prod(a.dims)
     A = torch.empty(N, dtype=dt, device="cuda")
     sd.fill(A, kind, 0, synth.STREAM_A)
+    scales = None
+    if a.dtype in ("bf16", "e4m3"):
+        A, scales, _ = tg.quantise(A.view(a.dims), tg.BF16 if a.dtype == "bf16" else tg.E4M3)
+        A = A.view(-1)
     x = torch.from_numpy(synth.vector(kind, 1, synth.stream_x(a.mode), a.dims[a.mode])).cuda()
     y = torch.empty(N // a.dims[a.mode], dtype=dt, device="cuda")
+    ws = torch.empty(max(1, tg.tvc_workspace_size(a.dims, a.mode, tg.dtype_code(A))), dtype=torch.uint8, device="cuda")
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ms = 0.0
     for _ in range(a.reps):
         e0.record()
-        tg.tvc(A, a.mode, x, y=y, shape=a.dims)
+        tg.tvc(A, a.mode, x, y=y, shape=a.dims, scales=scales, workspace=ws)
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
