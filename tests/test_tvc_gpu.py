@@ -208,3 +208,19 @@ def test_full_size_sweep_sampled(dims, code):
         del y
     del At
     torch.cuda.empty_cache()
+
+
+def test_staged_kernel_waits_never_time_out():
+    """The TMA-staged row kernel bounds every wait and records a timeout in a
+    sticky device word; after a run over many tiles the word must be 0."""
+    import ctypes
+    lib = tg.load_library()
+    code = ctypes.c_int(-1)
+    lib.tvc_device_error(ctypes.byref(code), 1)  # clear
+    for dims, dt in (((200000, 40), "u32"), ((4096, 128), "u32"), ((30001, 8), "u32")):
+        A = synth.tensor(dt, 3, dims)
+        x = synth.vector(dt, 4, 2, dims[1])
+        got = gu.gpu_tvc(tg, A, 1, x)
+        assert gu.rel_l2(got, oracle.tvc(A, 1, x)) <= 1e-5
+    torch.cuda.synchronize()
+    assert lib.tvc_device_error(ctypes.byref(code), 0) == 0 and code.value == 0
