@@ -293,7 +293,7 @@ def secondary(dev):
     bps = hopm_bytes(dims, 4, 4)
     out["hopm_planted_256^4_f32"] = {"from_ones": planted_run(ones), "from_overlapping_start": planted_run(pert),
                                     "sweeps_per_s": 50 / (ms / 1e3), "GB/s": 50 * bps / (ms / 1e3) / 1e9}
-    del A, ws, r
+    del A, ws
     torch.cuda.empty_cache()
     # 2048^3 N(0,1)exp(U[-3,3]): FP32 vs BF16 vs E4M3 storage, 30 sweeps
     dims = (2048, 2048, 2048)

@@ -222,8 +222,11 @@ size_t hopm_backward_workspace_size(int order, const int64_t* dims, tvc_dtype dt
 /*
  * Many independent FP32 tensors of any order and shape in one persistent
  * launch (the paper's task-based overlap of many contractions, Section
- * 4.3, done as a device work queue): one descriptor per tensor, processed
- * largest first by blocks that pull tensors from an atomic counter.
+ * 4.3, done as a device work queue): one descriptor per tensor; the work is
+ * cut into items of about 2^20 elements (output ranges of the contraction,
+ * row ranges of gx, slab/row rectangles of gA), largest tensors first, and
+ * pulled by persistent blocks from an atomic counter.  (hopm_batched runs
+ * one block per tensor.)
  * All pointers in a descriptor are device pointers, FP32, dense row-major.
  */
 typedef struct {
@@ -261,7 +264,9 @@ size_t tvc_batched_workspace_size(const tvc_batch_desc* descs, int count);
 /* Times the candidate block mappings (lanes per output) on one tensor of
  * each shape class of the batch and keeps the fastest for later calls of
  * tvc_batched / hopm_batched in this process; synchronises the stream.
- * workspace: at least tvc_batched_workspace_size(descs, 1) bytes. */
+ * workspace: tvc_batched_workspace_size(descs, count) bytes; a batch
+ * uploaded on it before must be uploaded again (call without
+ * TVC_BATCH_PREUPLOADED). */
 tvc_status tvc_batched_autotune(const tvc_batch_desc* descs, int count, void* workspace, size_t ws_bytes,
                                 tvc_stream_t stream);
 

@@ -30,7 +30,7 @@ namespace tvcg {
 namespace {
 
 constexpr int kBBT = 256;        // threads per block
-constexpr int kBBlocksPerSM = 8;
+constexpr int kBBlocksPerSM = 6;
 
 struct BItem {
   const float* A;
@@ -57,27 +57,30 @@ struct HItem {
 
 // y[o] = sum_j A[(i*nk + j)*v + l] x[j], o = i*v + l < u*v; G lanes per output.
 __device__ void blk_tvc(const float* __restrict__ A, int64_t u, int64_t nk, int64_t v, const float* __restrict__ x,
-                        float* __restrict__ y, int G) {
+                        float* __restrict__ y, int G, int64_t o_begin = 0, int64_t o_end = -1) {
   const int lane = threadIdx.x & 31;
   const int p = lane & (G - 1);
   const int gw = 32 / G;  // groups per warp
-  const int64_t uv = u * v;
+  const int64_t uv = (o_end < 0) ? u * v : o_end;
   const int64_t ngroups = (int64_t)(kBBT / 32) * gw;
-  for (int64_t base = (int64_t)(threadIdx.x >> 5) * gw; base < uv; base += ngroups) {
+  for (int64_t base = o_begin + (int64_t)(threadIdx.x >> 5) * gw; base < uv; base += ngroups) {
     const int64_t o = base + lane / G;
     float acc = 0.0f;
     if (o < uv) {
       const int64_t i = o / v, l = o - i * v;
       const float* row = A + i * nk * v + l;
-      int64_t j = p;
-      for (; j + 7 * G < nk; j += 8 * G) {  // eight loads in flight per lane
-        float av[8];
+      // eight (predicated) loads in flight per lane, also for short rows
+      for (int64_t j = p; j < nk; j += 8 * G) {
+        float av[8], xv[8];
 #pragma unroll
-        for (int q = 0; q < 8; q++) av[q] = __ldcs(row + (j + q * G) * v);
+        for (int q = 0; q < 8; q++) {
+          const bool ok = j + q * G < nk;
+          av[q] = ok ? __ldcs(row + (j + q * G) * v) : 0.0f;
+          xv[q] = ok ? __ldg(x + j + q * G) : 0.0f;
+        }
 #pragma unroll
-        for (int q = 0; q < 8; q++) acc = __fmaf_rn(av[q], __ldg(x + j + q * G), acc);
+        for (int q = 0; q < 8; q++) acc = __fmaf_rn(av[q], xv[q], acc);
       }
-      for (; j < nk; j += G) acc = __fmaf_rn(__ldcs(row + j * v), __ldg(x + j), acc);
     }
     for (int off = G / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, off);
     if (o < uv && p == 0) y[o] = acc;
@@ -87,57 +90,126 @@ __device__ void blk_tvc(const float* __restrict__ A, int64_t u, int64_t nk, int6
 // gx[j] = sum_{i,l} A[(i*nk + j)*v + l] gy[i*v + l]; a group of G lanes per j.
 // Compensated FP32 sums (the reduction can be long).
 __device__ void blk_gx(const float* __restrict__ A, int64_t u, int64_t nk, int64_t v, const float* __restrict__ gy,
-                       float* __restrict__ gx, int G) {
+                       float* __restrict__ gx, int G, int64_t j_begin = 0, int64_t j_end = -1) {
   const int lane = threadIdx.x & 31;
   const int p = lane & (G - 1);
   const int gw = 32 / G;
+  const int64_t je = (j_end < 0) ? nk : j_end;
   const int64_t ngroups = (int64_t)(kBBT / 32) * gw;
-  for (int64_t base = (int64_t)(threadIdx.x >> 5) * gw; base < nk; base += ngroups) {
+  for (int64_t base = j_begin + (int64_t)(threadIdx.x >> 5) * gw; base < je; base += ngroups) {
     const int64_t j = base + lane / G;
     KahanF32 acc;
-    if (j < nk) {
+    if (j < je) {
       if (v >= G) {
         for (int64_t i = 0; i < u; i++) {
           const float* a = A + (i * nk + j) * v;
           const float* g = gy + i * v;
           float part = 0.0f;
-#pragma unroll 8
-          for (int64_t l = p; l < v; l += G) part = __fmaf_rn(__ldcs(a + l), __ldg(g + l), part);
+          for (int64_t l = p; l < v; l += 8 * G) {  // eight predicated loads in flight
+            float av[8], gv[8];
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+              const bool ok = l + q * G < v;
+              av[q] = ok ? __ldcs(a + l + q * G) : 0.0f;
+              gv[q] = ok ? __ldg(g + l + q * G) : 0.0f;
+            }
+#pragma unroll
+            for (int q = 0; q < 8; q++) part = __fmaf_rn(av[q], gv[q], part);
+          }
           acc.add(part);
         }
       } else {
-        for (int64_t i = p; i < u; i += G) {
-          const float* a = A + (i * nk + j) * v;
-          const float* g = gy + i * v;
-          float part = 0.0f;
-#pragma unroll 8
-          for (int64_t l = 0; l < v; l++) part = __fmaf_rn(__ldcs(a + l), __ldg(g + l), part);
-          acc.add(part);
+        // v < G: lanes split the slabs i, eight slabs in flight per lane
+        for (int64_t i = p; i < u; i += 8 * G) {
+          for (int64_t l = 0; l < v; l++) {
+            float av[8], gv[8];
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+              const int64_t ii = i + q * G;
+              const bool ok = ii < u;
+              av[q] = ok ? __ldcs(A + (ii * nk + j) * v + l) : 0.0f;
+              gv[q] = ok ? __ldg(gy + ii * v + l) : 0.0f;
+            }
+            float part = 0.0f;
+#pragma unroll
+            for (int q = 0; q < 8; q++) part = __fmaf_rn(av[q], gv[q], part);
+            acc.add(part);
+          }
         }
       }
     }
     float t = acc.value();
     for (int off = G / 2; off > 0; off >>= 1) t += __shfl_xor_sync(0xFFFFFFFFu, t, off);
-    if (j < nk && p == 0) gx[j] = t;
+    if (j < je && p == 0) gx[j] = t;
   }
 }
 
-// gA[(i*nk + j)*v + l] = gy[i*v + l] * x[j] with coalesced stores.
-__device__ void blk_gA(const float* __restrict__ gy, const float* __restrict__ x, float* __restrict__ gA, int64_t u,
-                       int64_t nk, int64_t v) {
-  if (v >= 32) {
-    for (int64_t o = threadIdx.x; o < u * v; o += kBBT) {
-      const int64_t i = o / v, l = o - i * v;
-      const float g = gy[o];
-      float* p = gA + i * nk * v + l;
-      for (int64_t j = 0; j < nk; j++) __stcs(p + j * v, g * __ldg(x + j));
+// gx[j] for a few j (<= 8) with all 256 threads: a team of T = 256/J
+// threads (whole warps) per j splits the (i, l) space (lane t: l = t % v'
+// and i = t / v' with v' = min(v, T), stepping by T / v'), compensated sums,
+// then warp shuffles and a fixed-order sum of the team's warps.
+__device__ void blk_gx_teams(const float* __restrict__ A, int64_t u, int64_t nk, int64_t v,
+                             const float* __restrict__ gy, float* __restrict__ gx, int64_t j_begin, int64_t j_end,
+                             float* red /* shared, kBBT/32 floats */) {
+  const int J = (int)(j_end - j_begin);
+  int T = 256;
+  while (T > 32 && T * J > 256) T >>= 1;
+  const int team = threadIdx.x / T, t = threadIdx.x % T;
+  const int64_t j = j_begin + team;
+  const int64_t vv = v < T ? v : T;
+  const int lanes = (int)((T / vv) * vv);
+  KahanF32 acc;
+  if (team < J && t < lanes) {
+    const int64_t l0 = t % vv, i0 = t / vv, istep = T / vv;
+    for (int64_t i = i0; i < u; i += istep) {
+      const float* a = A + (i * nk + j) * v;
+      const float* g = gy + i * v;
+      float part = 0.0f;
+      for (int64_t l = l0; l < v; l += 8 * vv) {
+        float av[8], gv[8];
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+          const bool ok = l + q * vv < v;
+          av[q] = ok ? __ldcs(a + l + q * vv) : 0.0f;
+          gv[q] = ok ? __ldg(g + l + q * vv) : 0.0f;
+        }
+#pragma unroll
+        for (int q = 0; q < 8; q++) part = __fmaf_rn(av[q], gv[q], part);
+      }
+      acc.add(part);
     }
+  }
+  float s = acc.value();
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (t == 0 && team < J) {
+    float tot = 0.0f;
+    for (int w = 0; w < T / 32; w++) tot += red[team * (T / 32) + w];
+    gx[j] = tot;
+  }
+  __syncthreads();
+}
+
+// gA[(i*nk + j)*v + l] = gy[i*v + l] * x[j] over slabs i in [i0, i1) and
+// rows j in [j0, j1), with coalesced stores: threads own columns l (v >= 32)
+// or positions q = j*v + l of the slab (v < 32, whole slabs).
+__device__ void blk_gA(const float* __restrict__ gy, const float* __restrict__ x, float* __restrict__ gA, int64_t nk,
+                       int64_t v, int64_t i0, int64_t i1, int64_t j0, int64_t j1) {
+  if (v >= 32) {
+    for (int64_t l = threadIdx.x; l < v; l += kBBT)
+      for (int64_t i = i0; i < i1; i++) {
+        const float g = __ldg(gy + i * v + l);
+        float* p = gA + (i * nk + j0) * v + l;
+        for (int64_t j = j0; j < j1; j++, p += v) __stcs(p, g * __ldg(x + j));
+      }
   } else {
     const int64_t S = nk * v;
     for (int64_t q = threadIdx.x; q < S; q += kBBT) {
       const int64_t j = q / v, l = q - j * v;
-      const float xj = x[j];
-      for (int64_t i = 0; i < u; i++) __stcs(gA + i * S + q, __ldg(gy + i * v + l) * xj);
+      const float xj = __ldg(x + j);
+      for (int64_t i = i0; i < i1; i++) __stcs(gA + i * S + q, __ldg(gy + i * v + l) * xj);
     }
   }
 }
@@ -187,13 +259,30 @@ __device__ int grab(int* counter, int* slot) {
 
 // ------------------------------------------------------------ the kernels
 
-__global__ void __launch_bounds__(kBBT) tvc_batched_kernel(const BItem* __restrict__ items, int count, int* counter) {
+// A unit of work: kind 0 = outputs [a0, a1) of the forward contraction,
+// 1 = gx[j] for j in [a0, a1), 2 = gA over slabs [a0, a1) and rows [c0, c1).
+struct WItem {
+  int b, kind;
+  int64_t a0, a1, c0, c1;
+};
+
+__global__ void __launch_bounds__(kBBT, 6) tvc_batched_kernel(const BItem* __restrict__ items,
+                                                           const WItem* __restrict__ work, int nwork, int* counter) {
   __shared__ int slot;
-  for (int b = grab(counter, &slot); b < count; b = grab(counter, &slot)) {
-    const BItem it = items[b];
-    if (it.y) blk_tvc(it.A, it.u, it.nk, it.v, it.x, it.y, it.gf);
-    if (it.gx) blk_gx(it.A, it.u, it.nk, it.v, it.gy, it.gx, it.gb);
-    if (it.gA) blk_gA(it.gy, it.x, it.gA, it.u, it.nk, it.v);
+  __shared__ float red[kBBT / 32];
+  for (int w = grab(counter, &slot); w < nwork; w = grab(counter, &slot)) {
+    const WItem wi = work[w];
+    const BItem it = items[wi.b];
+    if (wi.kind == 0)
+      blk_tvc(it.A, it.u, it.nk, it.v, it.x, it.y, it.gf, wi.a0, wi.a1);
+    else if (wi.kind == 1) {
+      if (wi.a1 - wi.a0 <= 8)
+        blk_gx_teams(it.A, it.u, it.nk, it.v, it.gy, it.gx, wi.a0, wi.a1, red);
+      else
+        blk_gx(it.A, it.u, it.nk, it.v, it.gy, it.gx, it.gb, wi.a0, wi.a1);
+    }
+    else
+      blk_gA(it.gy, it.x, it.gA, it.nk, it.v, wi.a0, wi.a1, wi.c0, wi.c1);
   }
 }
 
@@ -289,6 +378,7 @@ int64_t clog2(int64_t x) {
 // Autotuner cache: (kind, log2 v, log2 n_k) -> G.
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int>, int> g_tune;
+std::map<void*, int> g_nwork;  // work items uploaded per workspace
 
 int rule_G(int kind, int64_t nk, int64_t v) {
   if (kind == 0) {  // forward: lanes split n_k
@@ -296,9 +386,8 @@ int rule_G(int kind, int64_t nk, int64_t v) {
     if (v >= 8) return 4;
     return nk >= 64 ? 32 : 8;
   }
-  // gx: lanes split the (i, l) columns
-  if (v >= 32) return 32;
-  return v >= 8 ? 8 : 1;
+  // gx: lanes split the (i, l) columns (for v < 8 the slabs i)
+  return v >= 32 ? 32 : 8;
 }
 
 int pick_G(int kind, int64_t nk, int64_t v) {
@@ -313,11 +402,53 @@ struct BLayout {
   int blocks = 0;
 };
 
-BLayout layout_tvc(int count) {
+// Work of about this many elements per item (a few MB): large tensors
+// spread over many blocks, small ones make a single item.
+constexpr int64_t kItemElems = 1 << 20;
+
+int64_t cdiv64(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+void make_work(const std::vector<BItem>& items, std::vector<WItem>* work) {
+  work->clear();
+  for (int b = 0; b < (int)items.size(); b++) {
+    const BItem& it = items[b];
+    const int64_t uv = it.u * it.v, N = uv * it.nk;
+    if (it.y) {
+      const int64_t per = std::max<int64_t>(256, cdiv64(kItemElems, it.nk) / 256 * 256);
+      for (int64_t o = 0; o < uv; o += per) work->push_back({b, 0, o, std::min(uv, o + per), 0, 0});
+    }
+    if (it.gx) {
+      const int64_t per = std::max<int64_t>(1, kItemElems / std::max<int64_t>(1, uv));
+      for (int64_t j = 0; j < it.nk; j += per) work->push_back({b, 1, j, std::min(it.nk, j + per), 0, 0});
+    }
+    if (it.gA) {
+      const int64_t S = it.nk * it.v;
+      if (it.v >= 32) {
+        // rectangles of slabs x rows
+        const int64_t rows = std::max<int64_t>(1, std::min<int64_t>(it.nk, kItemElems / it.v));
+        const int64_t slabs = std::max<int64_t>(1, kItemElems / (rows * it.v));
+        for (int64_t i = 0; i < it.u; i += slabs)
+          for (int64_t j = 0; j < it.nk; j += rows)
+            work->push_back({b, 2, i, std::min(it.u, i + slabs), j, std::min(it.nk, j + rows)});
+      } else {
+        const int64_t slabs = std::max<int64_t>(1, kItemElems / S);
+        for (int64_t i = 0; i < it.u; i += slabs) work->push_back({b, 2, i, std::min(it.u, i + slabs), 0, it.nk});
+      }
+    }
+    (void)N;
+  }
+}
+
+// Workspace of a tensor batch: header, descriptors, work items (the exact
+// count, from the same construction the call uses).
+tvc_status check_tvc_descs(const tvc_batch_desc* d, int count, std::vector<BItem>* items);
+
+BLayout layout_tvc_items(const std::vector<BItem>& items, size_t nwork) {
   BLayout L;
   L.off_counter = 0;
   L.off_items = 256;
-  L.total = L.off_items + align_up((size_t)count * sizeof(BItem), 256);
+  L.off_scratch = L.off_items + align_up(items.size() * sizeof(BItem), 256);
+  L.total = L.off_scratch + align_up(nwork * sizeof(WItem), 256);
   L.blocks = device_sms() * kBBlocksPerSM;
   return L;
 }
@@ -387,31 +518,50 @@ using namespace tvcg;
 
 extern "C" size_t tvc_batched_workspace_size(const tvc_batch_desc* descs, int count) {
   if (count < 0 || (count > 0 && !descs)) return 0;
-  return layout_tvc(count).total;
+  std::vector<BItem> items;
+  if (check_tvc_descs(descs, count, &items) != TVC_OK) return 0;
+  std::vector<WItem> work;
+  make_work(items, &work);
+  return layout_tvc_items(items, work.size()).total;
 }
 
 extern "C" tvc_status tvc_batched(const tvc_batch_desc* descs, int count, int flags, void* workspace, size_t ws_bytes,
                                   tvc_stream_t stream) {
-  if (count < 0) return TVC_ERR_INVALID_ARG;
+  if (count < 0 || !descs) return TVC_ERR_INVALID_ARG;
   if (count == 0) return TVC_OK;
-  const BLayout L = layout_tvc(count);
+  std::vector<BItem> items;
+  tvc_status rc = check_tvc_descs(descs, count, &items);
+  if (rc != TVC_OK) return rc;
+  std::vector<WItem> work;
+  make_work(items, &work);
+  const BLayout L = layout_tvc_items(items, work.size());
   if (!workspace || ws_bytes < L.total) return TVC_ERR_WORKSPACE;
   cudaStream_t st = (cudaStream_t)stream;
   char* w = static_cast<char*>(workspace);
+  int* hdr = reinterpret_cast<int*>(w + L.off_counter);
   if (!(flags & TVC_BATCH_PREUPLOADED)) {
-    if (!descs) return TVC_ERR_INVALID_ARG;
-    std::vector<BItem> items;
-    tvc_status rc = check_tvc_descs(descs, count, &items);
-    if (rc != TVC_OK) return rc;
+    const int nwork = (int)work.size();
     if (cudaMemcpyAsync(w + L.off_items, items.data(), items.size() * sizeof(BItem), cudaMemcpyHostToDevice, st) !=
-        cudaSuccess)
+            cudaSuccess ||
+        cudaMemcpyAsync(w + L.off_scratch, work.data(), work.size() * sizeof(WItem), cudaMemcpyHostToDevice, st) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(hdr + 1, &nwork, sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess)
       return TVC_ERR_CUDA;
-    // The host vector dies here: wait for the copy (pageable source).
+    // The host vectors die here: wait for the copies (pageable sources).
     if (cudaStreamSynchronize(st) != cudaSuccess) return TVC_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_nwork[workspace] = nwork;
   }
-  cudaMemsetAsync(w + L.off_counter, 0, sizeof(int), st);
-  tvc_batched_kernel<<<L.blocks, kBBT, 0, st>>>(reinterpret_cast<const BItem*>(w + L.off_items), count,
-                                               reinterpret_cast<int*>(w + L.off_counter));
+  int nwork = 0;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto itn = g_nwork.find(workspace);
+    if (itn == g_nwork.end()) return TVC_ERR_INVALID_ARG;  // PREUPLOADED without a prior upload
+    nwork = itn->second;
+  }
+  cudaMemsetAsync(hdr, 0, sizeof(int), st);
+  tvc_batched_kernel<<<L.blocks, kBBT, 0, st>>>(reinterpret_cast<const BItem*>(w + L.off_items),
+                                               reinterpret_cast<const WItem*>(w + L.off_scratch), nwork, hdr);
   count_launches(1);
   return cuda_status(cudaGetLastError());
 }
@@ -421,53 +571,57 @@ extern "C" tvc_status tvc_batched_autotune(const tvc_batch_desc* descs, int coun
   // Times the candidate lane counts on one tensor of every shape class
   // (forward contraction and gx) and records the fastest; synchronises.
   if (count <= 0 || !descs) return TVC_ERR_INVALID_ARG;
-  const BLayout L = layout_tvc(1);
-  if (!workspace || ws_bytes < L.total) return TVC_ERR_WORKSPACE;
-  cudaStream_t st = (cudaStream_t)stream;
-  char* w = static_cast<char*>(workspace);
   std::vector<BItem> items;
   tvc_status rc = check_tvc_descs(descs, count, &items);
   if (rc != TVC_OK) return rc;
-  std::map<std::tuple<int, int, int>, BItem> reps;
+  std::vector<WItem> allwork;
+  make_work(items, &allwork);
+  const BLayout L = layout_tvc_items(items, allwork.size());
+  if (!workspace || ws_bytes < L.total) return TVC_ERR_WORKSPACE;
+  cudaStream_t st = (cudaStream_t)stream;
+  char* w = static_cast<char*>(workspace);
+  // every shape class with the tensors that belong to it (forward, gx)
+  std::map<std::tuple<int, int, int>, std::vector<BItem>> classes;
   for (const BItem& it : items)
     for (int kind = 0; kind < 2; kind++) {
       if (kind == 0 && !it.y) continue;
       if (kind == 1 && !it.gx) continue;
-      reps.emplace(std::make_tuple(kind, (int)clog2(it.v), (int)clog2(it.nk)), it);
+      BItem one = it;
+      one.y = kind == 0 ? it.y : nullptr;
+      one.gx = kind == 1 ? it.gx : nullptr;
+      one.gA = nullptr;
+      classes[std::make_tuple(kind, (int)clog2(it.v), (int)clog2(it.nk))].push_back(one);
     }
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   const int cands[5] = {1, 4, 8, 16, 32};
-  for (auto& kv : reps) {
+  for (auto& kv : classes) {
     const int kind = std::get<0>(kv.first);
+    std::vector<BItem> sub = kv.second;  // at most 256 tensors of the class
+    if (sub.size() > 256) sub.resize(256);
     float best = 1e30f;
-    int bestG = rule_G(kind, kv.second.nk, kv.second.v);
+    int bestG = rule_G(kind, sub[0].nk, sub[0].v);
     for (int G : cands) {
-      BItem it = kv.second;
-      if (kind == 0) {
-        it.gx = nullptr;
-        it.gA = nullptr;
-        it.gf = G;
-      } else {
-        it.y = nullptr;
-        it.gA = nullptr;
-        it.gb = G;
-      }
-      cudaMemcpy(w + L.off_items, &it, sizeof(BItem), cudaMemcpyHostToDevice);
+      for (BItem& it : sub) (kind == 0 ? it.gf : it.gb) = G;
+      std::vector<WItem> wk;
+      make_work(sub, &wk);
+      cudaMemcpy(w + L.off_items, sub.data(), sub.size() * sizeof(BItem), cudaMemcpyHostToDevice);
+      cudaMemcpy(w + L.off_scratch, wk.data(), wk.size() * sizeof(WItem), cudaMemcpyHostToDevice);
       float tot = 0.0f;
-      for (int rep = 0; rep < 4; rep++) {
+      for (int rep = 0; rep < 3; rep++) {
         cudaMemsetAsync(w + L.off_counter, 0, sizeof(int), st);
         cudaEventRecord(e0, st);
-        tvc_batched_kernel<<<1, kBBT, 0, st>>>(reinterpret_cast<const BItem*>(w + L.off_items), 1,
-                                              reinterpret_cast<int*>(w + L.off_counter));
+        tvc_batched_kernel<<<L.blocks, kBBT, 0, st>>>(reinterpret_cast<const BItem*>(w + L.off_items),
+                                                     reinterpret_cast<const WItem*>(w + L.off_scratch),
+                                                     (int)wk.size(), reinterpret_cast<int*>(w + L.off_counter));
         cudaEventRecord(e1, st);
         cudaEventSynchronize(e1);
         float ms = 0.0f;
         cudaEventElapsedTime(&ms, e0, e1);
         if (rep > 0) tot += ms;
       }
-      count_launches(4);
+      count_launches(3);
       if (tot < best) {
         best = tot;
         bestG = G;
@@ -475,6 +629,10 @@ extern "C" tvc_status tvc_batched_autotune(const tvc_batch_desc* descs, int coun
     }
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune[kv.first] = bestG;
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_nwork.erase(workspace);  // the workspace no longer holds an uploaded batch
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

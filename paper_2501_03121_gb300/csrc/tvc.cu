@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(kThreads) tvc_cols_kernel(const TvcArgs<DT> a)
 // for its own copies (cp.async.wait_group), so no block barrier is needed.
 // This keeps D * 16 bytes per thread in flight, which the register-bound
 // column kernel cannot for 8- or 16-element vectors.
-constexpr int kAsyncDepth = 10;
+constexpr int kAsyncDepth = 12;
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
@@ -238,9 +238,9 @@ __global__ void __launch_bounds__(kThreads) tvc_cols_async_kernel(const TvcArgs<
   AccF32<VEC> acc;
   acc.init();
   int blk = 0;
+  int slot = 0;
   for (int64_t r = 0; r < n; r++) {
     cp_async_wait<kAsyncDepth - 1>();
-    const int slot = (int)(r % kAsyncDepth);
     float v[VEC];
     E::template load<VEC, true>(reinterpret_cast<const T*>(&stage[slot][threadIdx.x]), v);
     const float xv = xval(a, j0 + r);
@@ -248,6 +248,7 @@ __global__ void __launch_bounds__(kThreads) tvc_cols_async_kernel(const TvcArgs<
     if (r + kAsyncDepth < n) cp_async16(&stage[slot][threadIdx.x], p + (r + kAsyncDepth) * st);
     cp_async_commit();
     acc.mac(v, xv);
+    if (++slot == kAsyncDepth) slot = 0;
     if (++blk == kRB) {
       acc.fold();
       blk = 0;
@@ -393,7 +394,7 @@ __global__ void __launch_bounds__(kThreads) tvc_rows_kernel(const TvcArgs<DT> a)
 // with full-warp FP64 instructions.  The FP64 pipe takes a warp instruction
 // at the same cost whatever its active mask, so converting per pass would
 // spend it G times over.  Products and reductions stay on the FP32 pipe.
-template <int VEC, int G>
+template <int VEC, int G, int DQ>
 __global__ void __launch_bounds__(kThreads) tvc_rows_f64_slots_kernel(const TvcArgs<TVC_F64> a) {
   if (skip(a.done)) return;
   using E = Elem<TVC_F64>;
@@ -424,7 +425,12 @@ __global__ void __launch_bounds__(kThreads) tvc_rows_f64_slots_kernel(const TvcA
 #pragma unroll
         for (int q = 0; q < 4; q++)
 #pragma unroll
-          for (int e = 0; e < VEC; e++) df_mac(sacc, cacc, d, r[q][e], x + jj + q * STEP + e, ldxs(a.xs + jj + q * STEP + e));
+          for (int e = 0; e < VEC; e++) {
+            if (q < DQ)  // this share of the steps runs on the FP64 pipe
+              d = fma(r[q][e], __ldg(x + jj + q * STEP + e), d);
+            else
+              df_mac(sacc, cacc, d, r[q][e], x + jj + q * STEP + e, ldxs(a.xs + jj + q * STEP + e));
+          }
       }
       for (; jj + VEC <= j1; jj += STEP) {
         double r[VEC];
@@ -432,6 +438,10 @@ __global__ void __launch_bounds__(kThreads) tvc_rows_f64_slots_kernel(const TvcA
 #pragma unroll
         for (int e = 0; e < VEC; e++) df_mac(sacc, cacc, d, r[e], x + jj + e, ldxs(a.xs + jj + e));
       }
+    }
+    if (DQ > 0 && df_out_of_window(d) == 0) {  // fold the DFMA share into the pair
+      df_add_double(sacc, cacc, d);
+      d = 0.0;
     }
     const bool anyd = __any_sync(0xFFFFFFFFu, __double_as_longlong(d) != 0);
 #pragma unroll
@@ -1336,15 +1346,35 @@ static void launch_rows_tma(const Plan& p, const TvcArgs<DT>& a, cudaStream_t st
   }
 }
 
+template <int VEC, int DQ>
+static void launch_rows_f64s_dq(const Plan& p, const TvcArgs<TVC_F64>& a, cudaStream_t st) {
+  switch (p.G) {
+    case 1: tvc_rows_f64_slots_kernel<VEC, 1, DQ><<<p.grid, kThreads, 0, st>>>(a); break;
+    case 2: tvc_rows_f64_slots_kernel<VEC, 2, DQ><<<p.grid, kThreads, 0, st>>>(a); break;
+    case 4: tvc_rows_f64_slots_kernel<VEC, 4, DQ><<<p.grid, kThreads, 0, st>>>(a); break;
+    case 8: tvc_rows_f64_slots_kernel<VEC, 8, DQ><<<p.grid, kThreads, 0, st>>>(a); break;
+    default: tvc_rows_f64_slots_kernel<VEC, 16, DQ><<<p.grid, kThreads, 0, st>>>(a); break;
+  }
+}
+
+// Share (of 4 unrolled steps) of the FP64 short-row products sent to the
+// DFMA pipe: 0 by default (1 and 2 measured within noise on 40- and
+// 128-element rows); TVC_F64_ROWS_DFMA (0..2) overrides.
+static int slots_dfma_steps() {
+  static int v = [] {
+    const char* e = std::getenv("TVC_F64_ROWS_DFMA");
+    const int r = e ? std::atoi(e) : 0;
+    return (r >= 0 && r <= 2) ? r : 0;
+  }();
+  return v;
+}
+
 template <int VEC>
 static void launch_rows_f64s_vec(const Plan& p, const TvcArgs<TVC_F64>& a, cudaStream_t st) {
-  switch (p.G) {
-    case 1: tvc_rows_f64_slots_kernel<VEC, 1><<<p.grid, kThreads, 0, st>>>(a); break;
-    case 2: tvc_rows_f64_slots_kernel<VEC, 2><<<p.grid, kThreads, 0, st>>>(a); break;
-    case 4: tvc_rows_f64_slots_kernel<VEC, 4><<<p.grid, kThreads, 0, st>>>(a); break;
-    case 8: tvc_rows_f64_slots_kernel<VEC, 8><<<p.grid, kThreads, 0, st>>>(a); break;
-    default: tvc_rows_f64_slots_kernel<VEC, 16><<<p.grid, kThreads, 0, st>>>(a); break;
-  }
+  const int dq = slots_dfma_steps();
+  if (dq == 0) launch_rows_f64s_dq<VEC, 0>(p, a, st);
+  else if (dq == 1) launch_rows_f64s_dq<VEC, 1>(p, a, st);
+  else launch_rows_f64s_dq<VEC, 2>(p, a, st);
 }
 
 template <tvc_dtype DT>
