@@ -125,6 +125,14 @@ struct Elem<TVC_F32> {
   using V = float;
   using C = float;
   static constexpr int kSize = 4;
+  // Decoding of one 16-byte word of codes (the narrow long-row kernel keeps
+  // codes packed until they are used).
+  __device__ __forceinline__ static void decode16(const uint4& w, float (&val)[4]) {
+    val[0] = __uint_as_float(w.x);
+    val[1] = __uint_as_float(w.y);
+    val[2] = __uint_as_float(w.z);
+    val[3] = __uint_as_float(w.w);
+  }
   template <int VEC, bool PLAIN = false>
   __device__ __forceinline__ static void load(const T* p, C (&val)[VEC]) {
     if constexpr (VEC == 4) {
@@ -151,6 +159,12 @@ struct Elem<TVC_BF16> {
   using V = float;
   using C = float;
   static constexpr int kSize = 2;
+  __device__ __forceinline__ static void decode16(const uint4& w, float (&val)[8]) {
+    word2(w.x, val[0], val[1]);
+    word2(w.y, val[2], val[3]);
+    word2(w.z, val[4], val[5]);
+    word2(w.w, val[6], val[7]);
+  }
   __device__ __forceinline__ static void word2(uint32_t w, float& lo, float& hi) {
     lo = __uint_as_float(w << 16);
     hi = __uint_as_float(w & 0xFFFF0000u);
@@ -184,6 +198,12 @@ struct Elem<TVC_E4M3> {
   using V = float;
   using C = float;
   static constexpr int kSize = 1;
+  __device__ __forceinline__ static void decode16(const uint4& w, float (&val)[16]) {
+    word4(w.x, val + 0);
+    word4(w.y, val + 4);
+    word4(w.z, val + 8);
+    word4(w.w, val + 12);
+  }
   __device__ __forceinline__ static void pair(uint16_t w, float& lo, float& hi) {
     __half2_raw h = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)w, __NV_E4M3);
     float2 f = __half22float2(*reinterpret_cast<__half2*>(&h));

@@ -388,6 +388,95 @@ __global__ void __launch_bounds__(kThreads) tvc_rows_kernel(const TvcArgs<DT> a)
   }
 }
 
+// Long rows of the FP32/BF16/E4M3 types (v == 1): the whole warp walks RB
+// consecutive rows together, lane p taking VEC elements at p*VEC + step*32*VEC
+// of each, so that every piece of x held in registers serves RB rows.  With
+// one row per lane group (tvc_rows_kernel) the FP32 x is read through L1 at
+// s_x/s_A times the rate of A (4x for E4M3 codes, 2x for BF16), which held
+// the narrow long rows far below the HBM rate.  Each row keeps two FP32
+// accumulators, folded into a compensated sum every 64 products.
+template <tvc_dtype DT, int VEC, int RB, int UNR>
+__global__ void __launch_bounds__(kThreads) tvc_rows_multi_kernel(const TvcArgs<DT> a) {
+  static_assert(DT != TVC_F64, "FP64 rows use the float-float kernels");
+  static_assert(VEC * sizeof(typename Elem<DT>::T) == 16, "16-byte pieces");
+  if (skip(a.done)) return;
+  using E = Elem<DT>;
+  using T = typename E::T;
+  constexpr int STEP = kWarp * VEC;
+  constexpr int FOLD = (2 * kRB / VEC) / UNR;  // groups between folds
+  static_assert(FOLD >= 1, "fold interval");
+  const int lane = threadIdx.x & (kWarp - 1);
+  const int64_t row0 = ((int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5)) * RB;
+  if (row0 >= a.u) return;  // warp-uniform; no block-wide barrier follows
+  const int64_t j0 = (int64_t)blockIdx.y * a.chunk;
+  const int64_t j1 = min(a.nk, j0 + a.chunk);
+  const int nr = (int)min((int64_t)RB, a.u - row0);  // rows of this warp (warp-uniform)
+  const T* rp[RB];
+#pragma unroll
+  for (int r = 0; r < RB; r++) rp[r] = a.A + min(row0 + r, a.u - 1) * a.nk;
+  float acc[RB][2];
+  KahanF32 tot[RB];
+#pragma unroll
+  for (int r = 0; r < RB; r++) acc[r][0] = acc[r][1] = 0.0f;
+  auto fold = [&]() {
+#pragma unroll
+    for (int r = 0; r < RB; r++) {
+      tot[r].add(acc[r][0]);
+      tot[r].add(acc[r][1]);
+      acc[r][0] = acc[r][1] = 0.0f;
+    }
+  };
+  const int64_t ngroups = (j1 - j0) / (UNR * STEP);
+  int64_t j = j0 + lane * VEC;
+  int blk = 0;
+  for (int64_t g = 0; g < ngroups; g++, j += UNR * STEP) {
+    uint4 w[UNR][RB];  // packed codes, decoded where they are used
+#pragma unroll
+    for (int q = 0; q < UNR; q++)
+#pragma unroll
+      for (int r = 0; r < RB; r++) w[q][r] = (r < nr) ? ld_stream<16>(rp[r] + j + q * STEP).v : make_uint4(0, 0, 0, 0);
+#pragma unroll
+    for (int q = 0; q < UNR; q++) {
+      float xq[VEC];
+      xvec<DT, VEC>(a, j + q * STEP, xq);
+#pragma unroll
+      for (int r = 0; r < RB; r++) {
+        float v[VEC];
+        E::decode16(w[q][r], v);
+#pragma unroll
+        for (int e = 0; e < VEC; e++) acc[r][e & 1] = __fmaf_rn(v[e], xq[e], acc[r][e & 1]);
+      }
+    }
+    if (++blk == FOLD) {
+      fold();
+      blk = 0;
+    }
+  }
+  // Tail of fewer than UNR steps: (j1 - j0) is a multiple of VEC (the planner
+  // takes VEC dividing n_k and a chunk that is a multiple of 32*VEC).
+  for (; j < j1; j += STEP) {
+    float xq[VEC];
+    xvec<DT, VEC>(a, j, xq);
+#pragma unroll
+    for (int r = 0; r < RB; r++) {
+      if (r < nr) {
+        float v[VEC];
+        E::template load<VEC>(rp[r] + j, v);
+#pragma unroll
+        for (int e = 0; e < VEC; e++) acc[r][e & 1] = __fmaf_rn(v[e], xq[e], acc[r][e & 1]);
+      }
+    }
+  }
+  fold();
+  float mine = 0.0f;
+#pragma unroll
+  for (int r = 0; r < RB; r++) {
+    const float t = warp_sum(tot[r].value());
+    if (lane == r) mine = t;
+  }
+  if (lane < RB && row0 + lane < a.u) emit(a, blockIdx.y, row0 + lane, __fmul_rn(mine, out_scale(a, row0 + lane)));
+}
+
 // FP64 rows with G < 32 lanes per row (short rows): each warp takes 32 rows
 // in G passes of 32/G rows, keeps every finished row in a per-lane slot
 // (lane L holds row L of the warp), and converts and stores the 32 results
@@ -1065,13 +1154,22 @@ __global__ void tvc_reduce_kernel(const V* __restrict__ partial, V* __restrict__
 
 // ------------------------------------------------------------------ plan --
 
-enum Kind { K_COLS = 0, K_ROWS = 1, K_SLAB = 2, K_TILE = 3, K_ROWS_SHORT = 4, K_ROWS_TMA = 5, K_ROWS_F64S = 6 };
+enum Kind {
+  K_COLS = 0,
+  K_ROWS = 1,
+  K_SLAB = 2,
+  K_TILE = 3,
+  K_ROWS_SHORT = 4,
+  K_ROWS_TMA = 5,
+  K_ROWS_F64S = 6,
+  K_ROWS_MULTI = 7
+};
 
 struct Plan {
   Kind kind = K_COLS;
   int vec = 1;
   int64_t splits = 1, chunk = 0;
-  int R = 0, vec16 = 0, g = 0, G = 0, nst = 0, RW = 0, S = 0, dq = 0;
+  int R = 0, vec16 = 0, g = 0, G = 0, nst = 0, RW = 0, S = 0, dq = 0, rb = 0, unr = 0;
   int64_t ntiles = 0;
   uint32_t tile_bytes = 0;
   size_t smem = 0;
@@ -1132,6 +1230,40 @@ static int dfma_rows_option() {
     return (r == 0 || r == 2 || r == 3 || r == 4) ? r : 0;
   }();
   return v;
+}
+
+// Narrow long-row kernel on by default; TVC_ROWS_MULTI=0 returns those rows
+// to the one-row-per-group kernel.
+static bool rows_multi_enabled() {
+  static bool v = [] {
+    const char* e = std::getenv("TVC_ROWS_MULTI");
+    return !(e && std::atoi(e) == 0);
+  }();
+  return v;
+}
+
+// Rows per warp (2, 4 or 8) and unrolled steps (1 or 2) of the narrow
+// long-row kernel, per storage type as measured on rows of 16384 to 1048576
+// elements: E4M3 8 x 1 (x traffic 0.5x that of A, 128 registers), BF16 2 x 2,
+// FP32 4 x 2.  TVC_ROWS_RB and TVC_ROWS_UNR override.
+// Value of an integer environment switch if it is one of the allowed values, else 0.
+static int env_choice(const char* name, int ok1, int ok2, int ok3) {
+  const char* e = std::getenv(name);
+  if (!e) return 0;
+  const int r = std::atoi(e);
+  return (r == ok1 || r == ok2 || r == ok3) ? r : 0;
+}
+
+static int rows_multi_rb(tvc_dtype dt) {
+  static int v = env_choice("TVC_ROWS_RB", 2, 4, 8);
+  if (v) return v;
+  return dt == TVC_E4M3 ? 8 : (dt == TVC_BF16 ? 2 : 4);
+}
+
+static int rows_multi_unr(tvc_dtype dt) {
+  static int v = env_choice("TVC_ROWS_UNR", 1, 2, 1);
+  if (v) return v;
+  return dt == TVC_E4M3 ? 1 : 2;
 }
 
 // Largest vector width (elements per load) the alignment and v allow.
@@ -1219,6 +1351,20 @@ static Plan make_plan_impl(const Shape& s, tvc_dtype dt, const void* A, bool all
     p.splits = 1;
     p.chunk = s.nk;
     p.grid = dim3((unsigned)std::max<int64_t>(1, blocks), 1);
+  } else if (s.v == 1 && dt != TVC_F64 && rows_multi_enabled() && pick_vec(dt, s.nk, A) * (int)es == 16) {
+    // Long rows of the narrow types: RB rows per warp share each x piece.
+    p.kind = K_ROWS_MULTI;
+    p.vec = pick_vec(dt, s.nk, A);
+    p.rb = rows_multi_rb(dt);
+    p.unr = rows_multi_unr(dt);
+    const int64_t step = (int64_t)kWarp * p.vec;
+    const int64_t warps = ceil_div(s.u, p.rb);
+    const int64_t target_warps = (int64_t)sms * 48;
+    int64_t splits = 1;
+    if (warps < target_warps) splits = std::min(ceil_div(target_warps, warps), std::max<int64_t>(1, s.nk / (4 * step)));
+    p.chunk = ceil_div(ceil_div(s.nk, splits), step) * step;
+    p.splits = ceil_div(s.nk, p.chunk);
+    p.grid = dim3((unsigned)ceil_div(warps, kWarpsPerBlock), (unsigned)p.splits);
   } else if (s.v == 1) {
     p.kind = K_ROWS;
     p.vec = pick_vec(dt, s.nk, A);
@@ -1297,6 +1443,22 @@ static void launch_rows(const Plan& p, const TvcArgs<DT>& a, cudaStream_t st) {
     if (p.vec == 16) launch_rows_vec<DT, 16>(p, a, st);
     else if (p.vec == 4) launch_rows_vec<DT, 4>(p, a, st);
     else launch_rows_vec<DT, 1>(p, a, st);
+  }
+}
+
+template <tvc_dtype DT, int VEC, int RB>
+static void launch_rows_multi_rb(const Plan& p, const TvcArgs<DT>& a, cudaStream_t st) {
+  if (p.unr == 2) tvc_rows_multi_kernel<DT, VEC, RB, 2><<<p.grid, kThreads, 0, st>>>(a);
+  else tvc_rows_multi_kernel<DT, VEC, RB, 1><<<p.grid, kThreads, 0, st>>>(a);
+}
+
+template <tvc_dtype DT>
+static void launch_rows_multi(const Plan& p, const TvcArgs<DT>& a, cudaStream_t st) {
+  if constexpr (DT != TVC_F64) {
+    constexpr int VEC = 16 / (int)sizeof(typename Elem<DT>::T);
+    if (p.rb == 2) launch_rows_multi_rb<DT, VEC, 2>(p, a, st);
+    else if (p.rb == 8) launch_rows_multi_rb<DT, VEC, 8>(p, a, st);
+    else launch_rows_multi_rb<DT, VEC, 4>(p, a, st);
   }
 }
 
@@ -1407,6 +1569,9 @@ static void launch_main(const Plan& p, const TvcArgs<DT>& a, cudaStream_t st) {
     }
     case K_ROWS:
       launch_rows<DT>(p, a, st);
+      break;
+    case K_ROWS_MULTI:
+      launch_rows_multi<DT>(p, a, st);
       break;
     case K_ROWS_SHORT:
       launch_rows_short<DT>(p, a, st);

@@ -48,8 +48,7 @@ def main(argv=None):
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
-    es = A.element_size()
-    nbytes = N * es + a.dims[a.mode] * es + (N // a.dims[a.mode]) * es
+    nbytes = N * A.element_size() + a.dims[a.mode] * x.element_size() + (N // a.dims[a.mode]) * y.element_size()
     print(f"dims={a.dims} mode={a.mode} {a.dtype}: {ms:.3f} ms  {nbytes / ms / 1e6:.1f} GB/s")
 
 

@@ -24,6 +24,9 @@ SHAPES = [
     (7,), (100003,), (5, 3), (1, 4), (4, 1), (3, 1, 5), (2, 3, 4), (6, 5, 4, 3), (2, 1, 3, 1, 2),
     (3, 50, 64), (5, 1000), (3, 4099), (4, 100, 7), (300, 40), (50, 8, 8), (2000, 64), (13, 17, 19, 3),
     (9, 33, 130), (2, 3, 2, 3, 2, 3, 2), (1, 1, 1), (257, 1, 3),
+    # long rows with 16-byte pieces (several rows per warp): ragged row
+    # counts, a single row, split-K, and mode 0 of an order-1 tensor
+    (7, 3072), (19, 2, 1040), (1, 4096), (2048,), (3, 65536), (1001, 1536),
 ]
 CODES = [oracle.F64, oracle.F32, oracle.BF16, oracle.E4M3]
 
