@@ -4,7 +4,7 @@ Workload (one step): the TVC bandwidth sweep, i.e. the contraction along
 EVERY mode of the dense row-major tensors 1024^3, 128^4, 40^6 and
 65536x16384 (order 2), each stored in FP64 and in FP32, entries uniform
 [-1, 1) (counter-based generator, seed 0), x uniform [-1, 1).  30 TVCs per
-step, 260 GB of algorithmic traffic.  value = algorithmic bytes / time
+step, about 380 GB of algorithmic traffic.  value = algorithmic bytes / time
 (GB/s), summed over ranks; each rank runs an independent replica (the
 single-GPU path has no data-parallel exchange).
 
@@ -120,6 +120,17 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(mhz) if mhz else None,
                 "sm_max_mhz": float(rows[0][1]) if rows[0][1].replace(".", "").isdigit() else None,
                 "samples": len(rows), "reasons": sorted(reasons)}
+
+
+def max_over_ranks(value: float, pg, device) -> float:
+    """The largest of the ranks' values (the timed region ends with the
+    slowest replica); pg is torch.distributed (or None for one rank)."""
+    if pg is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
 
 
 def dist_setup():
@@ -454,10 +465,7 @@ def main(argv=None):
     launches = tg.kernel_launches() - launches0
     clocks = sampler.stop()
     elapsed_ms = t_start.elapsed_time(t_end)
-    if pg is not None:
-        t = torch.tensor([elapsed_ms], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = max_over_ranks(elapsed_ms, pg, dev)
     per_call = [statistics.mean(evs[s][ci][0].elapsed_time(evs[s][ci][1]) for s in range(args.steps))
                 for ci in range(len(calls))]
     value = world * step_bytes * args.steps / (elapsed_ms / 1e3) / 1e9

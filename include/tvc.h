@@ -276,6 +276,79 @@ tvc_status hopm_batched(const hopm_batch_desc* descs, int count, int iters, int 
                         size_t ws_bytes, tvc_stream_t stream);
 size_t hopm_batched_workspace_size(const hopm_batch_desc* descs, int count);
 
+/* ------------------------------------------- 1D split over virtual ranks */
+
+/*
+ * The distributed algorithms of Section 3 (dTVC, Eq. 1 and Eq. 2; dHOPM_3,
+ * Algorithm 1) on one GPU: the tensor is cut along one dimension s into
+ * `parts` slabs, each held in its own dense buffer as a rank would hold it,
+ * and every rank's work is launched on the same stream.  Where p processes
+ * would exchange data, the ranks' results are combined on the device: a
+ * fixed-order sum in place of the all-reduce, disjoint writes in place of
+ * the gather.  At most TVC_MAX_PARTS ranks.
+ */
+#define TVC_MAX_PARTS 64
+
+/* Slab boundaries of the 1D split of a dimension of n entries over p ranks
+ * (Section 3.1, "optimal division"): chunk = ceil(n / p) rounded up to a
+ * multiple of `quantum` (>= 1; the vector length in elements, 1 for none),
+ * ranks = ceil(n / chunk) <= p, so p may be lowered (n = 4, p = 3 gives two
+ * ranks of 2).  starts (p + 1 int64, host) receives 0 = starts[0] < ... <
+ * starts[ranks] = n.  Returns the number of ranks, or -1 when n < 1, p < 1,
+ * p > TVC_MAX_PARTS or quantum < 1.  Host only; launches nothing. */
+int tvc_split_1d(int64_t n, int p, int64_t quantum, int64_t* starts);
+
+/* Copies the slab [start, end) along dimension s between a dense tensor of
+ * `dims` and a dense slab of dims with n_s replaced by end - start
+ * (Section 3.1: for s > 0 the slab is prod(n_0 .. n_{s-1}) strided runs of
+ * the tensor).  insert = 0: tensor -> slab (dst is the slab); insert = 1:
+ * slab -> tensor (src is the slab; the rest of the tensor is untouched).
+ * elem_bytes: bytes per element (1, 2, 4 or 8).  Device pointers, no
+ * overlap; stream-ordered. */
+tvc_status tvc_slab_copy(const void* src, void* dst, int order, const int64_t* dims, int s, int64_t start,
+                         int64_t end, size_t elem_bytes, int insert, tvc_stream_t stream);
+
+/*
+ * Distributed TVC over `parts` virtual ranks (Section 3.1).  slabs[r] is
+ * rank r's dense subtensor: dims with n_s replaced by starts[r+1] -
+ * starts[r] (starts as from tvc_split_1d; starts[0] = 0, starts[parts] =
+ * dims[s]).  x: n_mode entries (FP64 for TVC_F64, FP32 otherwise), the
+ * same vector on every rank.
+ *   mode != s (Eq. 1): y[r] (parts device outputs) receives rank r's output
+ *     slab, alpha * slabs[r] x_mode x + beta * y[r]: the output dims with
+ *     the s dimension cut to rank r's range.  No combination step.
+ *   mode == s (Eq. 2): rank r contracts its slab with its part of x,
+ *     x[starts[r] .. starts[r+1]), into a full-size partial (N / n_mode
+ *     entries, in the workspace); y[0] receives alpha * (sum over r, in
+ *     ascending order) + beta * y[0].
+ * slab_scales: the n_0 per-slab scales of the global tensor for narrow
+ * storage (rank r uses scales + starts[r] when s = 0).  Workspace:
+ * dtvc_workspace_size(...) bytes.
+ */
+tvc_status dtvc(const void* const* slabs, int parts, const int64_t* starts, int order, const int64_t* dims, int s,
+                int mode, const void* x, void* const* y, tvc_dtype dtype, const float* slab_scales, double alpha,
+                double beta, void* workspace, size_t ws_bytes, tvc_stream_t stream);
+size_t dtvc_workspace_size(int parts, const int64_t* starts, int order, const int64_t* dims, int s, int mode,
+                           tvc_dtype dtype);
+
+/*
+ * Distributed three-buffer HOPM (dHOPM_3, Algorithm 1) over `parts` virtual
+ * ranks: every rank keeps its own prefix cache W and intermediate buffers
+ * and computes, for each external iteration j, its local contraction of
+ * all modes but j (with x_s restricted to its range for j != s).  For
+ * j != s the n_j-entry partial vectors are summed in ascending rank order
+ * (the all-reduce; Eq. 2's sum deferred to the normalisation); for j = s
+ * each rank writes its disjoint range of z_s (the gather).  Normalisation,
+ * lambda, stopping rule, status and outputs as for hopm().  x: the global
+ * vectors (device, order entries).  Workspace: dhopm_workspace_size(...).
+ */
+tvc_status dhopm(const void* const* slabs, int parts, const int64_t* starts, int order, const int64_t* dims, int s,
+                 void* const* x, int iters, double tol, double* lambda_out, int* sweeps_out, int* status_out,
+                 double* lambda_hist, tvc_dtype dtype, const float* slab_scales, void* workspace, size_t ws_bytes,
+                 tvc_stream_t stream);
+size_t dhopm_workspace_size(int parts, const int64_t* starts, int order, const int64_t* dims, int s,
+                            tvc_dtype dtype);
+
 /* Sticky device error of the staged (TMA-fed) kernels: every wait in them
  * is bounded, and a wait that gives up records a nonzero code (1: the copy
  * engine's producer waited for a free buffer, 2: a consumer waited for a

@@ -22,6 +22,8 @@ import torch
 __all__ = [
     "F64", "F32", "BF16", "E4M3", "TVCError", "load_library", "tvc", "tvc_workspace_size",
     "dtype_code", "library_path", "kernel_launches", "hopm", "hopm_workspace_size", "HopmResult", "quantise", "tvc_backward", "TVCFunction", "tvc_autograd", "hopm_backward", "HOPMFunction", "hopm_autograd", "TVCBatch", "HOPMBatch", "BATCH_PREUPLOADED",
+    "split_1d", "slab_extract", "slab_insert", "split_tensor", "dtvc", "dtvc_workspace_size", "dhopm",
+    "dhopm_workspace_size",
 ]
 
 F64, F32, BF16, E4M3 = 0, 1, 2, 3
@@ -94,6 +96,18 @@ def load_library():
         lib.hopm_batched.restype = I
         lib.hopm_batched_workspace_size.argtypes = [P, I]
         lib.hopm_batched_workspace_size.restype = Z
+        lib.tvc_split_1d.argtypes = [L, I, L, P]
+        lib.tvc_split_1d.restype = I
+        lib.tvc_slab_copy.argtypes = [P, P, I, P, I, L, L, Z, I, P]
+        lib.tvc_slab_copy.restype = I
+        lib.dtvc.argtypes = [P, I, P, I, P, I, I, P, P, I, P, D, D, P, Z, P]
+        lib.dtvc.restype = I
+        lib.dtvc_workspace_size.argtypes = [I, P, I, P, I, I, I]
+        lib.dtvc_workspace_size.restype = Z
+        lib.dhopm.argtypes = [P, I, P, I, P, I, P, I, D, P, P, P, P, I, P, P, Z, P]
+        lib.dhopm.restype = I
+        lib.dhopm_workspace_size.argtypes = [I, P, I, P, I, I]
+        lib.dhopm_workspace_size.restype = Z
         lib.tvc_kernel_launches.argtypes = []
         lib.tvc_kernel_launches.restype = ctypes.c_uint64
         _lib = lib
@@ -483,3 +497,149 @@ class HOPMBatch:
         _check(lib.hopm_batched(self._arr, self.count, self.iters, flags, _ptr(self.workspace),
                                 self.workspace.numel(), _stream(stream)), "hopm_batched")
         self._uploaded = True
+
+
+# ------------------------------------------------ 1D split, virtual ranks
+
+
+def split_1d(n: int, p: int, quantum: int = 1) -> list:
+    """Slab boundaries [0, ..., n] of the 1D split of a dimension of n
+    entries over p ranks (ceil(n/p) rounded up to a multiple of `quantum`;
+    p may come out lower).  Host only."""
+    lib = load_library()
+    starts = (ctypes.c_int64 * (int(p) + 1))()
+    r = lib.tvc_split_1d(int(n), int(p), int(quantum), starts)
+    if r < 0:
+        raise ValueError(f"invalid split: n={n}, p={p}, quantum={quantum}")
+    return [int(starts[i]) for i in range(r + 1)]
+
+
+def _slab_shape(shape, s, start, end):
+    return tuple((end - start) if i == s else n for i, n in enumerate(shape))
+
+
+def slab_extract(A: torch.Tensor, s: int, start: int, end: int, *, shape=None, stream=None) -> torch.Tensor:
+    """Dense copy of the slab [start, end) of A along dimension s."""
+    lib = load_library()
+    shape = tuple(A.shape) if shape is None else tuple(int(n) for n in shape)
+    out = torch.empty(_slab_shape(shape, s, start, end), dtype=A.dtype, device=A.device)
+    _check_cuda(A, out)
+    _check(lib.tvc_slab_copy(_ptr(A), _ptr(out), len(shape), _dims_array(shape), int(s), int(start), int(end),
+                             A.element_size(), 0, _stream(stream)), "tvc_slab_copy")
+    return out
+
+
+def slab_insert(slab: torch.Tensor, out: torch.Tensor, s: int, start: int, end: int, *, shape=None,
+                stream=None) -> torch.Tensor:
+    """Writes a dense slab into the range [start, end) of `out` along s."""
+    lib = load_library()
+    shape = tuple(out.shape) if shape is None else tuple(int(n) for n in shape)
+    if slab.dtype != out.dtype or slab.numel() != math.prod(_slab_shape(shape, s, start, end)):
+        raise ValueError("slab does not match the range")
+    _check_cuda(slab, out)
+    _check(lib.tvc_slab_copy(_ptr(slab), _ptr(out), len(shape), _dims_array(shape), int(s), int(start), int(end),
+                             out.element_size(), 1, _stream(stream)), "tvc_slab_copy")
+    return out
+
+
+def split_tensor(A: torch.Tensor, s: int, starts, *, shape=None, stream=None) -> list:
+    """The ranks' dense subtensors of A cut along s at `starts`."""
+    return [slab_extract(A, s, starts[r], starts[r + 1], shape=shape, stream=stream) for r in range(len(starts) - 1)]
+
+
+def _split_args(slabs, starts, shape):
+    parts = len(starts) - 1
+    if parts < 1 or len(slabs) != parts:
+        raise ValueError("one slab per rank")
+    code = dtype_code(slabs[0])
+    if any(dtype_code(t) != code for t in slabs):
+        raise ValueError("slabs differ in storage type")
+    arr = (ctypes.c_int64 * (parts + 1))(*[int(v) for v in starts])
+    ptrs = (ctypes.c_void_p * parts)(*[t.data_ptr() for t in slabs])
+    return parts, code, arr, ptrs
+
+
+def dtvc_workspace_size(starts, shape, s: int, mode: int, code: int) -> int:
+    lib = load_library()
+    parts = len(starts) - 1
+    arr = (ctypes.c_int64 * (parts + 1))(*[int(v) for v in starts])
+    return int(lib.dtvc_workspace_size(parts, arr, len(shape), _dims_array(shape), int(s), int(mode), int(code)))
+
+
+def dtvc(slabs, starts, shape, s: int, mode: int, x: torch.Tensor, *, y=None, scales: torch.Tensor | None = None,
+         alpha: float = 1.0, beta: float = 0.0, workspace: torch.Tensor | None = None, stream=None):
+    """Distributed TVC over virtual ranks (Eq. 1 / Eq. 2).  slabs[r] is rank
+    r's subtensor of the global tensor `shape` cut along s at `starts`.
+    mode != s: returns the list of the ranks' output slabs; mode == s:
+    returns the summed full-size output."""
+    lib = load_library()
+    shape = tuple(int(n) for n in shape)
+    parts, code, arr, ptrs = _split_args(slabs, starts, shape)
+    vt = vec_dtype(code)
+    if x.dtype != vt or x.numel() != shape[mode]:
+        raise ValueError(f"x must be {vt} with {shape[mode]} entries")
+    dev = slabs[0].device
+    if mode == s:
+        out_shape = tuple(n for i, n in enumerate(shape) if i != mode)
+        if y is None:
+            if beta != 0.0:
+                raise ValueError("beta != 0 needs y")
+            y = torch.empty(out_shape, dtype=vt, device=dev)
+        outs = [y]
+    else:
+        if y is None:
+            if beta != 0.0:
+                raise ValueError("beta != 0 needs y")
+            outs = []
+            for r in range(parts):
+                sh = _slab_shape(shape, s, starts[r], starts[r + 1])
+                outs.append(torch.empty(tuple(n for i, n in enumerate(sh) if i != mode), dtype=vt, device=dev))
+        else:
+            outs = list(y)
+    _check_cuda(x, scales, workspace, *slabs, *outs)
+    if workspace is None:
+        need = lib.dtvc_workspace_size(parts, arr, len(shape), _dims_array(shape), int(s), int(mode), code)
+        workspace = torch.empty(max(1, need), dtype=torch.uint8, device=dev)
+    yp = (ctypes.c_void_p * len(outs))(*[t.data_ptr() for t in outs])
+    _check(lib.dtvc(ptrs, parts, arr, len(shape), _dims_array(shape), int(s), int(mode), _ptr(x), yp, code,
+                    _ptr(scales), float(alpha), float(beta), _ptr(workspace), workspace.numel(), _stream(stream)),
+           "dtvc")
+    return outs[0] if mode == s else outs
+
+
+def dhopm_workspace_size(starts, shape, s: int, code: int) -> int:
+    lib = load_library()
+    parts = len(starts) - 1
+    arr = (ctypes.c_int64 * (parts + 1))(*[int(v) for v in starts])
+    return int(lib.dhopm_workspace_size(parts, arr, len(shape), _dims_array(shape), int(s), int(code)))
+
+
+def dhopm(slabs, starts, shape, s: int, xs, iters: int, tol: float = 0.0, *, scales: torch.Tensor | None = None,
+          workspace: torch.Tensor | None = None, stream=None, inplace: bool = False) -> HopmResult:
+    """Distributed three-buffer HOPM (Algorithm 1) over virtual ranks: the
+    ranks' slabs cut along s at `starts`, global start vectors xs."""
+    lib = load_library()
+    shape = tuple(int(n) for n in shape)
+    if len(shape) < 2 or len(xs) != len(shape):
+        raise ValueError("dhopm needs order >= 2 and one start vector per mode")
+    parts, code, arr, ptrs = _split_args(slabs, starts, shape)
+    vt = vec_dtype(code)
+    xs = [v if inplace else v.clone() for v in xs]
+    for m, v in enumerate(xs):
+        if v.dtype != vt or v.numel() != shape[m]:
+            raise ValueError(f"x[{m}] must be {vt} with {shape[m]} entries")
+    _check_cuda(scales, workspace, *slabs, *xs)
+    dev = slabs[0].device
+    lam = torch.zeros(1, dtype=torch.float64, device=dev)
+    sweeps = torch.zeros(1, dtype=torch.int32, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    hist = torch.zeros(max(1, iters), dtype=torch.float64, device=dev)
+    dims = _dims_array(shape)
+    if workspace is None:
+        need = lib.dhopm_workspace_size(parts, arr, len(shape), dims, int(s), code)
+        workspace = torch.empty(max(1, need), dtype=torch.uint8, device=dev)
+    xp = (ctypes.c_void_p * len(xs))(*[v.data_ptr() for v in xs])
+    _check(lib.dhopm(ptrs, parts, arr, len(shape), dims, int(s), xp, int(iters), float(tol), _ptr(lam), _ptr(sweeps),
+                     _ptr(status), _ptr(hist), code, _ptr(scales), _ptr(workspace), workspace.numel(),
+                     _stream(stream)), "dhopm")
+    return HopmResult(xs, lam, sweeps, status, hist)

@@ -20,6 +20,7 @@
 // host can queue all sweeps without synchronising (and capture them in a
 // CUDA graph).
 #include <algorithm>
+#include <vector>
 
 #include "common.cuh"
 #include "internal.h"
@@ -427,6 +428,102 @@ tvc_status hopm_launch(const void* A, int order, const int64_t* dims, void* cons
   return cuda_status(cudaGetLastError());
 }
 
+// ------------------------------------------- distributed (virtual ranks)
+
+namespace {
+
+// Workspace of dHOPM_3 over virtual ranks: the shared state and the
+// combined vector z, then one forward layout per rank (its W cache,
+// intermediate buffers and TVC workspace).
+struct DLayout {
+  size_t off_state = 0, off_zsum = 0, total = 0;
+  std::vector<FwdLayout> rank;
+};
+
+DLayout dhopm_layout(int parts, const int64_t* starts, int order, const int64_t* dims, int s, tvc_dtype dt) {
+  DLayout D;
+  int64_t zlen = 1;
+  for (int i = 0; i < order; i++) zlen = std::max(zlen, dims[i]);
+  size_t off = 0;
+  D.off_state = off;
+  off += align_up(sizeof(HopmState), 256);
+  D.off_zsum = off;
+  off += align_up((size_t)zlen * vec_size(dt), 256);
+  int64_t dr[TVC_MAX_ORDER];
+  for (int r = 0; r < parts; r++) {
+    slab_dims(order, dims, s, starts, r, dr);
+    D.rank.push_back(fwd_layout(order, dr, dt, off));
+    off = D.rank.back().total;
+  }
+  D.total = off;
+  return D;
+}
+
+}  // namespace
+
+size_t dhopm_ws_bytes(int parts, const int64_t* starts, int order, const int64_t* dims, int s, tvc_dtype dt) {
+  return dhopm_layout(parts, starts, order, dims, s, dt).total;
+}
+
+// Algorithm 1 over `parts` virtual ranks: for each external iteration j,
+// every rank runs its local chain (its own W_j, x_s cut to its range), then
+// the n_j-entry results are summed over ranks (j != s) or gathered (j = s),
+// and the global x_j is normalised once.  All queued on one stream.
+tvc_status dhopm_launch(const void* const* slabs, int parts, const int64_t* starts, int order, const int64_t* dims,
+                        int s, void* const* x, int iters, double tol, double* lam_out, int* sweeps_out,
+                        int* status_out, double* lam_hist, tvc_dtype dt, const float* scales, void* ws,
+                        size_t ws_bytes, cudaStream_t st) {
+  const DLayout D = dhopm_layout(parts, starts, order, dims, s, dt);
+  if (ws == nullptr || ws_bytes < D.total) return TVC_ERR_WORKSPACE;
+  char* w = static_cast<char*>(ws);
+  const size_t vs = vec_size(dt);
+  Ctx g;  // global view: the state, the normalisation of the combined z
+  g.dry = false;
+  g.d = order;
+  for (int i = 0; i < order; i++) g.n[i] = dims[i];
+  g.dt = dt;
+  g.vdt = (dt == TVC_F64) ? TVC_F64 : TVC_F32;
+  g.st = st;
+  g.state = reinterpret_cast<HopmState*>(w + D.off_state);
+  g.done = &g.state->done;
+  void* zsum = w + D.off_zsum;
+  std::vector<Ctx> c(parts);
+  std::vector<std::vector<void*>> xr(parts, std::vector<void*>(order));
+  int64_t dr[TVC_MAX_ORDER];
+  for (int r = 0; r < parts; r++) {
+    slab_dims(order, dims, s, starts, r, dr);
+    const float* sc = scales ? scales + (s == 0 ? starts[r] : 0) : nullptr;
+    bind(c[r], D.rank[r], ws, slabs[r], order, dr, dt, sc, st);
+    c[r].state = g.state;  // one state: the done flag stops every rank
+    c[r].done = g.done;
+    for (int m = 0; m < order; m++)
+      xr[r][m] = (m == s) ? static_cast<void*>(static_cast<char*>(x[m]) + (size_t)starts[r] * vs) : x[m];
+  }
+  g.init_state();
+  tvc_status rc = TVC_OK;
+  int combines = 0;
+  const void* zp[TVC_MAX_PARTS];
+  for (int it = 0; it < iters && rc == TVC_OK; it++) {
+    for (int j = 0; j < order && rc == TVC_OK; j++) {
+      for (int r = 0; r < parts; r++) {
+        zp[r] = c[r].z_for(j, xr[r].data());
+        if (c[r].rc != TVC_OK) rc = c[r].rc;
+      }
+      if (rc != TVC_OK) break;
+      // j != s: array reduction; j == s: array gather (Algorithm 1).
+      rc = combine_parts(zp, parts, starts, dims[j], zsum, g.vdt, j == s ? 1 : 0, 1.0, 0.0, st, g.done);
+      combines++;
+      g.normalize(zsum, j, x[j], tol, lam_out, sweeps_out, status_out, lam_hist, nullptr);
+    }
+  }
+  int launches = g.launches;
+  for (int r = 0; r < parts; r++) launches += c[r].launches;
+  count_launches(launches);
+  (void)combines;  // counted by combine_parts
+  if (rc != TVC_OK) return rc;
+  return cuda_status(cudaGetLastError());
+}
+
 // ---------------------------------------------------------------- backward
 
 namespace {
@@ -685,6 +782,27 @@ extern "C" tvc_status hopm(const void* A, int order, const int64_t* dims, void* 
     if (!x[m] || !aligned(x[m], vs)) return TVC_ERR_INVALID_ARG;
   return hopm_launch(A, order, dims, x, iters, tol, lambda_out, sweeps_out, status_out, lambda_hist, dtype,
                      slab_scales, workspace, ws_bytes, (cudaStream_t)stream);
+}
+
+extern "C" size_t dhopm_workspace_size(int parts, const int64_t* starts, int order, const int64_t* dims, int s,
+                                       tvc_dtype dtype) {
+  if (!valid_dtype(dtype) || order < 2 || check_split(parts, starts, order, dims, s) != TVC_OK) return 0;
+  return dhopm_ws_bytes(parts, starts, order, dims, s, dtype);
+}
+
+extern "C" tvc_status dhopm(const void* const* slabs, int parts, const int64_t* starts, int order,
+                            const int64_t* dims, int s, void* const* x, int iters, double tol, double* lambda_out,
+                            int* sweeps_out, int* status_out, double* lambda_hist, tvc_dtype dtype,
+                            const float* slab_scales, void* workspace, size_t ws_bytes, tvc_stream_t stream) {
+  if (!valid_dtype(dtype) || order < 2 || !slabs || !x || iters < 0 || !(tol >= 0.0)) return TVC_ERR_INVALID_ARG;
+  if (check_split(parts, starts, order, dims, s) != TVC_OK) return TVC_ERR_INVALID_ARG;
+  const size_t vs = vec_size(dtype);
+  for (int r = 0; r < parts; r++)
+    if (!slabs[r] || !aligned(slabs[r], elem_size(dtype))) return TVC_ERR_INVALID_ARG;
+  for (int m = 0; m < order; m++)
+    if (!x[m] || !aligned(x[m], vs)) return TVC_ERR_INVALID_ARG;
+  return dhopm_launch(slabs, parts, starts, order, dims, s, x, iters, tol, lambda_out, sweeps_out, status_out,
+                      lambda_hist, dtype, slab_scales, workspace, ws_bytes, (cudaStream_t)stream);
 }
 
 extern "C" size_t hopm_backward_workspace_size(int order, const int64_t* dims, tvc_dtype dtype, int iters) {

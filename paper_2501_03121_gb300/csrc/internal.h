@@ -51,4 +51,16 @@ tvc_status tvc_launch(const void* A, const Shape& s, const void* x, void* y, tvc
                       cudaStream_t stream, const int* done = nullptr);
 size_t tvc_ws_bytes(const Shape& s, tvc_dtype dt, const void* A);
 
+// 1D split over virtual ranks (split.cu).  check_split validates parts,
+// starts and s against the tensor; slab_dims gives rank r's dims.
+tvc_status check_split(int parts, const int64_t* starts, int order, const int64_t* dims, int s);
+void slab_dims(int order, const int64_t* dims, int s, const int64_t* starts, int r, int64_t* out);
+// Combination of the ranks' vectors on the device: gather = 0 sums the
+// nparts vectors of n entries in ascending order (out = alpha*sum + beta*out);
+// gather = 1 writes part r to out[offs[r] .. offs[r+1]).  vdt: TVC_F64 or
+// TVC_F32 vectors.  done (nullable, device): skip when *done != 0.
+tvc_status combine_parts(const void* const* parts, int nparts, const int64_t* offs, int64_t n, void* out,
+                         tvc_dtype vdt, int gather, double alpha, double beta, cudaStream_t st,
+                         const int* done);
+
 }  // namespace tvcg
