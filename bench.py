@@ -231,6 +231,112 @@ def _timed(fn, reps, warm=1):
     return e0.elapsed_time(e1) / reps
 
 
+# Table 1's FP64 tensors (about 7.5 GB each), every mode: obliviousness to
+# order, mode and sizes that are not multiples of 8.
+PAPER_SHAPES = [(30623, 30623), (979,) * 3, (175,) * 4, (63,) * 5, (31,) * 6, (19,) * 7, (13,) * 8, (10,) * 9,
+                (8,) * 10]
+
+
+class LoopedCublas:
+    """The paper's looped TVC on the GPU (Section 3): one GEMV for the last
+    mode, otherwise u equally sized vector-matrix products in one
+    cublasDgemvStridedBatched call.  A comparator for the bench only (loaded
+    from the CUDA toolkit's cuBLAS through ctypes), never a library path."""
+
+    def __init__(self, stream_ptr):
+        import ctypes
+        lib = None
+        for name in ("libcublas.so.13", "libcublas.so"):
+            try:
+                lib = ctypes.CDLL(name)
+                break
+            except OSError:
+                continue
+        if lib is None:
+            raise OSError("cuBLAS not found")
+        self.ct = ctypes
+        self.lib = lib
+        self.h = ctypes.c_void_p()
+        if lib.cublasCreate_v2(ctypes.byref(self.h)) != 0:
+            raise OSError("cublasCreate failed")
+        lib.cublasSetStream_v2(self.h, ctypes.c_void_p(stream_ptr))
+        P, I, L = ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong
+        lib.cublasDgemv_v2.argtypes = [P, I, I, I, P, P, I, P, I, P, P, I]
+        lib.cublasDgemvStridedBatched.argtypes = [P, I, I, I, P, P, I, L, P, I, L, P, P, I, L, I]
+        self.one = ctypes.c_double(1.0)
+        self.zero = ctypes.c_double(0.0)
+
+    def tvc(self, A, dims, k, x, y):
+        ct = self.ct
+        u = math.prod(dims[:k])
+        nk = dims[k]
+        v = math.prod(dims[k + 1:])
+        a, xp, yp = ct.c_void_p(A.data_ptr()), ct.c_void_p(x.data_ptr()), ct.c_void_p(y.data_ptr())
+        if v == 1:  # Y = A^{u x n_k} x: the row-major matrix is n_k x u column-major, transposed
+            rc = self.lib.cublasDgemv_v2(self.h, 1, nk, u, ct.byref(self.one), a, nk, xp, 1, ct.byref(self.zero),
+                                         yp, 1)
+        else:  # u products x^T A_i^{n_k x v}: A_i is v x n_k column-major
+            rc = self.lib.cublasDgemvStridedBatched(self.h, 0, v, nk, ct.byref(self.one), a, v, nk * v, xp, 1, 0,
+                                                    ct.byref(self.zero), yp, 1, v, u)
+        if rc != 0:
+            raise RuntimeError(f"cuBLAS status {rc}")
+
+    def close(self):
+        self.lib.cublasDestroy_v2(self.h)
+
+
+def paper_shapes(dev, peak):
+    """Per-mode GB/s of the native TVC and of the looped cuBLAS TVC on
+    Table 1's FP64 tensors; mean and sample std over all modes."""
+    import torch
+    import synth
+    import synth.device as sd
+    import paper_2501_03121_gb300 as tg
+    try:
+        looped = LoopedCublas(torch.cuda.current_stream().cuda_stream)
+    except OSError as e:
+        looped = None
+        why = str(e)
+    native, loop, worst = {}, {}, 0.0
+    for dims in PAPER_SHAPES:
+        N = math.prod(dims)
+        A = torch.empty(N, dtype=torch.float64, device=dev)
+        sd.fill(A, "u64", 0, synth.STREAM_A)
+        for k in range(len(dims)):
+            x = torch.from_numpy(synth.vector("u64", 1, synth.stream_x(k), dims[k])).to(dev)
+            y = torch.empty(N // dims[k], dtype=torch.float64, device=dev)
+            nb = tvc_bytes(dims, k, 8, 8)
+            name = f"{dims[0]}^{len(dims)}:k{k}"
+            ms = _timed(lambda: tg.tvc(A, k, x, y=y, shape=dims), 5, warm=2)
+            native[name] = nb / (ms / 1e3) / 1e9
+            if looped is not None:
+                y2 = torch.empty_like(y)
+                ms2 = _timed(lambda: looped.tvc(A, dims, k, x, y2), 5, warm=2)
+                loop[name] = nb / (ms2 / 1e3) / 1e9
+                worst = max(worst, float(((y2 - y).abs().max() / y.abs().max().clamp_min(1e-300)).item()))
+                del y2
+            del x, y
+        del A
+        torch.cuda.empty_cache()
+
+    def summary(d):
+        vals = list(d.values())
+        return {"mean_GBs": statistics.mean(vals), "std_GBs": statistics.stdev(vals),
+                "mean_frac": statistics.mean(vals) / peak, "std_frac": statistics.stdev(vals) / peak,
+                "min_frac": min(vals) / peak, "max_frac": max(vals) / peak}
+
+    out = {"shapes": "Table 1 FP64 tensors 30623^2, 979^3, 175^4, 63^5, 31^6, 19^7, 13^8, 10^9, 8^10; every mode",
+           "native": summary(native), "native_per_mode_GBs": {n: round(v, 1) for n, v in native.items()}}
+    if looped is not None:
+        out["looped_cublas"] = summary(loop)
+        out["looped_cublas_per_mode_GBs"] = {n: round(v, 1) for n, v in loop.items()}
+        out["looped_vs_native_max_rel_diff"] = worst
+        looped.close()
+    else:
+        out["looped_cublas"] = {"unavailable": why}
+    return out
+
+
 def hopm_bytes(dims, es, vs):
     """Algorithmic bytes of one sweep of the two-pass HOPM: A read twice,
     W_1 and later prefix tensors written and read once, T written and read."""
@@ -542,6 +648,7 @@ def main(argv=None):
     sec = None
     if world == 1 and not args.no_secondary:
         sec = secondary(dev)
+        sec["paper_shapes_fp64"] = paper_shapes(dev, peak)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

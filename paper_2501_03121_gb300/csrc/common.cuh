@@ -325,10 +325,21 @@ __device__ __forceinline__ void df_mac_fast(float& s, float& c, double a, XSplit
   c = __fadd_rn(c, __fadd_rn(err, e));
 }
 
+// df_mac_fast with the window bit of a ORed into `bad`: kernels run every
+// element through it and redo the (rare) results that met an element
+// outside the window with DFMA.  An x outside its window needs no test: its
+// NaN pieces make the pair NaN.
+__device__ __forceinline__ void df_step(float& s, float& c, uint32_t& bad, double a, XSplit xs);
+
 // Nonzero when a is outside the exact window of the float-float split
 // (two integer operations; OR it over many elements, test once).
 __device__ __forceinline__ uint32_t df_out_of_window(double a) {
   return ((uint32_t)__double2hiint(a) * 2u - kDfWindowBase) >> 28;
+}
+
+__device__ __forceinline__ void df_step(float& s, float& c, uint32_t& bad, double a, XSplit xs) {
+  bad |= df_out_of_window(a);
+  df_mac_fast(s, c, a, xs);
 }
 
 // Adds an FP64 partial d into the float-float pair (s, c): d is split like

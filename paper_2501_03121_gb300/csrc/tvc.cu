@@ -160,10 +160,14 @@ __global__ void __launch_bounds__(kThreads) tvc_cols_kernel(const TvcArgs<DT> a)
         blk = 0;
       }
     }
-    for (; j < j1; j++, p += st) {
-      double r[VEC];
-      E::template load<VEC>(p, r);
-      acc.emul(r, x + j, ldxs(a.xs + j));
+    if (j < j1) {  // the last < 8 rows: all loads in flight at once
+      double r[7][VEC];
+#pragma unroll
+      for (int q = 0; q < 7; q++)
+        if (j + q < j1) E::template load<VEC>(p + q * st, r[q]);
+#pragma unroll
+      for (int q = 0; q < 7; q++)
+        if (j + q < j1) acc.emul(r[q], x + j + q, ldxs(a.xs + j + q));
     }
     acc.fold();
 #pragma unroll
@@ -300,23 +304,34 @@ __global__ void __launch_bounds__(kThreads) tvc_rows_kernel(const TvcArgs<DT> a)
     const double* x = static_cast<const double*>(a.x);
     AccF64<VEC> acc;
     acc.init();
-    for (int64_t g = 0; g < ngroups; g++, j += UNR * STEP) {
-      double r[UNR][VEC];
+    // kRB / UNR groups per fold.  With 8-byte loads (VEC == 1) the fold sits
+    // outside the inner loop: a fold test per group is if-converted there
+    // into masked FP64 work on every group (measured: 30623-element rows
+    // 4.1 -> 5.1 TB/s); with 16-byte loads the per-group test measured
+    // faster (65536 x 16384: 6.7 vs 6.2 TB/s).
+    constexpr int64_t kGroupsPerFold = (VEC == 1) ? kRB / UNR : 1;
+    for (int64_t g0 = 0; g0 < ngroups; g0 += kGroupsPerFold) {
+      const int64_t g1 = min(ngroups, g0 + kGroupsPerFold);
+      for (int64_t g = g0; g < g1; g++, j += UNR * STEP) {
+        double r[UNR][VEC];
 #pragma unroll
-      for (int q = 0; q < UNR; q++) E::template load<VEC>(rp + j + q * STEP, r[q]);
+        for (int q = 0; q < UNR; q++) E::template load<VEC>(rp + j + q * STEP, r[q]);
 #pragma unroll
-      for (int q = 0; q < UNR; q++) {
-        const int64_t jq = j + q * STEP;
-        if constexpr (VEC == 2) {
-          float4 s2 = __ldg(reinterpret_cast<const float4*>(a.xs + jq));
-          acc.emul1(0, r[q][0], x + jq, XSplit{s2.x, s2.y});
-          acc.emul1(1, r[q][1], x + jq + 1, XSplit{s2.z, s2.w});
-        } else {
+        for (int q = 0; q < UNR; q++) {
+          const int64_t jq = j + q * STEP;
+          if constexpr (VEC == 2) {
+            float4 s2 = __ldg(reinterpret_cast<const float4*>(a.xs + jq));
+            acc.emul1(0, r[q][0], x + jq, XSplit{s2.x, s2.y});
+            acc.emul1(1, r[q][1], x + jq + 1, XSplit{s2.z, s2.w});
+          } else {
 #pragma unroll
-          for (int e = 0; e < VEC; e++) acc.emul1(e, r[q][e], x + jq + e, ldxs(a.xs + jq + e));
+            for (int e = 0; e < VEC; e++) acc.emul1(e, r[q][e], x + jq + e, ldxs(a.xs + jq + e));
+          }
         }
       }
-      if (++blk == kRB / UNR) {
+      if constexpr (VEC == 1) {
+        acc.fold();
+      } else if (++blk == kRB / UNR) {
         acc.fold();
         blk = 0;
       }
@@ -489,6 +504,7 @@ __global__ void __launch_bounds__(kThreads) tvc_rows_f64_slots_kernel(const TvcA
   using E = Elem<TVC_F64>;
   constexpr int STEP = G * VEC;
   constexpr int GPW = kWarp / G;
+  constexpr int UNR = (VEC == 1) ? 8 : 4;  // 8-byte loads: more of them in flight
   const int lane = threadIdx.x & (kWarp - 1);
   const int p = lane & (G - 1);
   const int gw = lane / G;
@@ -505,17 +521,45 @@ __global__ void __launch_bounds__(kThreads) tvc_rows_f64_slots_kernel(const TvcA
     const double* rp = a.A + (active ? row : 0) * a.nk;
     float sacc = 0.0f, cacc = 0.0f;
     double d = 0.0;
-    if (active) {
-      int64_t jj = j0 + p * VEC;
-      for (; jj + 3 * STEP + VEC <= j1; jj += 4 * STEP) {
-        double r[4][VEC];
+    // 8-byte loads (VEC == 1): branch-free steps (df_step) with the window
+    // bits in `bad`, redone with DFMA when set (measured 1.1-1.2x on odd
+    // rows); 16-byte loads keep df_mac's branch, which measured faster there
+    // (fewer registers, more warps in flight).
+    uint32_t bad = 0;
+    if (active && VEC == 1) {
+      // 8-byte loads: every pass issues all its loads before the products,
+      // the last (partial) pass too; steps past the row end are neither
+      // loaded nor multiplied (j1 - j0 is a multiple of VEC).  (Measured on
+      // odd rows of 63 .. 979 elements: 1.3-1.8x; with 16-byte loads the
+      // unpredicated loop below measured faster.)
+      for (int64_t jj = j0 + p * VEC; jj < j1; jj += UNR * STEP) {
+        double r[UNR][VEC];
 #pragma unroll
-        for (int q = 0; q < 4; q++) E::template load<VEC>(rp + jj + q * STEP, r[q]);
+        for (int q = 0; q < UNR; q++)
+          if (jj + q * STEP < j1) E::template load<VEC>(rp + jj + q * STEP, r[q]);
 #pragma unroll
-        for (int q = 0; q < 4; q++)
+        for (int q = 0; q < UNR; q++) {
+          if (jj + q * STEP >= j1) break;
 #pragma unroll
           for (int e = 0; e < VEC; e++) {
             if (q < DQ)  // this share of the steps runs on the FP64 pipe
+              d = fma(r[q][e], __ldg(x + jj + q * STEP + e), d);
+            else
+              df_step(sacc, cacc, bad, r[q][e], ldxs(a.xs + jj + q * STEP + e));
+          }
+        }
+      }
+    } else if (active) {
+      int64_t jj = j0 + p * VEC;
+      for (; jj + (UNR - 1) * STEP + VEC <= j1; jj += UNR * STEP) {
+        double r[UNR][VEC];
+#pragma unroll
+        for (int q = 0; q < UNR; q++) E::template load<VEC>(rp + jj + q * STEP, r[q]);
+#pragma unroll
+        for (int q = 0; q < UNR; q++)
+#pragma unroll
+          for (int e = 0; e < VEC; e++) {
+            if (q < DQ)
               d = fma(r[q][e], __ldg(x + jj + q * STEP + e), d);
             else
               df_mac(sacc, cacc, d, r[q][e], x + jj + q * STEP + e, ldxs(a.xs + jj + q * STEP + e));
@@ -527,6 +571,15 @@ __global__ void __launch_bounds__(kThreads) tvc_rows_f64_slots_kernel(const TvcA
 #pragma unroll
         for (int e = 0; e < VEC; e++) df_mac(sacc, cacc, d, r[e], x + jj + e, ldxs(a.xs + jj + e));
       }
+    }
+    if (VEC == 1 && active && (bad != 0 || sacc != sacc || cacc != cacc)) {
+      // rare: this lane's part of the row again, exactly, on the DFMA pipe
+      sacc = 0.0f;
+      cacc = 0.0f;
+      d = 0.0;
+      for (int64_t jj = j0 + p * VEC; jj < j1; jj += STEP)
+#pragma unroll
+        for (int e = 0; e < VEC; e++) d = fma(rp[jj + e], x[jj + e], d);
     }
     if (DQ > 0 && df_out_of_window(d) == 0) {  // fold the DFMA share into the pair
       df_add_double(sacc, cacc, d);
@@ -940,7 +993,7 @@ __global__ void __launch_bounds__(kTmaThreads, 2) tvc_rows_tma_kernel(const TvcA
 
 // ------------------------------------------------------------------ SLAB --
 
-template <tvc_dtype DT>
+template <tvc_dtype DT, int UNR>
 __global__ void __launch_bounds__(kThreads) tvc_slab_kernel(const TvcArgs<DT> a, int g, int G) {
   if (skip(a.done)) return;
   using E = Elem<DT>;
@@ -961,19 +1014,20 @@ __global__ void __launch_bounds__(kThreads) tvc_slab_kernel(const TvcArgs<DT> a,
     const double* x = static_cast<const double*>(a.x);
     AccF64<1> acc;
     acc.init();
-    int blk = 0;
     if (active) {
       int64_t j = j0 + jj;
-      for (; j + 3 * G < j1; j += 4 * G, p += 4 * st) {
-        double r[4][1];
+      // groups of UNR rows, folded every kRB / UNR groups outside the inner
+      // loop (a fold test per group is if-converted into masked FP64 work on
+      // every group).  The branch-free df_step measured slower here.
+      while (j + (UNR - 1) * G < j1) {
+        for (int g = 0; g < kRB / UNR && j + (UNR - 1) * G < j1; g++, j += UNR * G, p += UNR * st) {
+          double r[UNR][1];
 #pragma unroll
-        for (int q = 0; q < 4; q++) E::template load<1>(p + q * st, r[q]);
+          for (int q = 0; q < UNR; q++) E::template load<1>(p + q * st, r[q]);
 #pragma unroll
-        for (int q = 0; q < 4; q++) acc.emul1(0, r[q][0], x + j + q * G, ldxs(a.xs + j + q * G));
-        if (++blk == kRB / 4) {
-          acc.fold();
-          blk = 0;
+          for (int q = 0; q < UNR; q++) acc.emul1(0, r[q][0], x + j + q * G, ldxs(a.xs + j + q * G));
         }
+        acc.fold();
       }
       for (; j < j1; j += G, p += st) {
         double r[1];
@@ -986,16 +1040,16 @@ __global__ void __launch_bounds__(kThreads) tvc_slab_kernel(const TvcArgs<DT> a,
   } else {
     AccF32<1> acc;
     acc.init();
-    int blk = 0;
+    int blk = 0;  // (the FP32 fold is cheap enough to test per group)
     if (active) {
       int64_t j = j0 + jj;
-      for (; j + 3 * G < j1; j += 4 * G, p += 4 * st) {
-        float r[4][1];
+      for (; j + (UNR - 1) * G < j1; j += UNR * G, p += UNR * st) {
+        float r[UNR][1];
 #pragma unroll
-        for (int q = 0; q < 4; q++) E::template load<1>(p + q * st, r[q]);
+        for (int q = 0; q < UNR; q++) E::template load<1>(p + q * st, r[q]);
 #pragma unroll
-        for (int q = 0; q < 4; q++) acc.a[0] = __fmaf_rn(r[q][0], xval(a, j + q * G), acc.a[0]);
-        if (++blk == kRB / 4) {
+        for (int q = 0; q < UNR; q++) acc.a[0] = __fmaf_rn(r[q][0], xval(a, j + q * G), acc.a[0]);
+        if (++blk == kRB / UNR) {
           acc.fold();
           blk = 0;
         }
@@ -1085,15 +1139,14 @@ __global__ void __launch_bounds__(kThreads) tvc_tile_kernel(const TvcArgs<DT> a,
     const XSplit* smx = reinterpret_cast<const XSplit*>(smraw + tile_bytes);
     AccF64<1> acc;
     acc.init();
-    for (int c = 0; c < nk; c++) {
-      acc.emul1(0, row[(int64_t)jt * v], x + jt, smx[jt]);
-      if (++jt == nk) jt = 0;
-      if (++blk == kRB) {
-        acc.fold();
-        blk = 0;
+    for (int cb = 0; cb < nk; cb += kRB) {  // fold outside the inner loop
+      const int ce = min(nk, cb + kRB);
+      for (int c = cb; c < ce; c++) {
+        acc.emul1(0, row[(int64_t)jt * v], x + jt, smx[jt]);
+        if (++jt == nk) jt = 0;
       }
+      acc.fold();
     }
-    acc.fold();
     emit(a, 0, (i0 + r) * a.v + l, acc.result(0));
   } else {
     const float* smx = reinterpret_cast<const float*>(smraw + tile_bytes);
@@ -1119,6 +1172,130 @@ __global__ void __launch_bounds__(kThreads) tvc_tile_kernel(const TvcArgs<DT> a,
     acc.fold();
     emit(a, 0, (i0 + r) * a.v + l, __fmul_rn(acc.result(0), out_scale(a, i0 + r)));
   }
+}
+
+// Small slabs, persistent and double-buffered: block b contracts tiles
+// b, b + grid, ... of R whole slabs (R*S contiguous elements).  Each tile is
+// fetched with 16-byte cp.async chunks from the 16-byte boundary at or below
+// its first byte (A is 16-byte aligned, so every chunk starts inside A); the
+// one chunk that would run past the end of A is read element by element.
+// The next tile is in flight while the current one is contracted: thread
+// t < R*v owns output (r, l) = (t / v, t % v) and reads its n_k entries from
+// shared memory with stride v.  One tile per block with plain loads (the
+// kernel above) serialised a DRAM round trip per load step whenever R*S*s_A
+// was not a multiple of 16.
+template <tvc_dtype DT>
+__global__ void __launch_bounds__(kThreads) tvc_tile_async_kernel(const TvcArgs<DT> a, int R, int64_t ntiles,
+                                                                  int tile_cap) {
+  if (skip(a.done)) return;
+  using E = Elem<DT>;
+  using T = typename E::T;
+  constexpr int es = (int)sizeof(T);
+  extern __shared__ __align__(128) unsigned char smraw[];
+  const int64_t S = a.nk * a.v;
+  const int nk = (int)a.nk, v = (int)a.v;
+  const int t = threadIdx.x;
+  if ((int64_t)blockIdx.x >= ntiles) return;
+  const int x_bytes = ((nk * (DT == TVC_F64 ? (int)sizeof(XSplit) : 4)) + 15) / 16 * 16;
+  unsigned char* const buf0 = smraw + x_bytes;  // buffer k at buf0 + k * tile_cap
+  __shared__ int x_out;  // FP64: some x_j outside the exact window
+  if constexpr (DT == TVC_F64) {
+    XSplit* smx = reinterpret_cast<XSplit*>(smraw);
+    if (t == 0) x_out = 0;
+    __syncthreads();
+    int bad = 0;
+    for (int j = t; j < nk; j += kThreads) {
+      smx[j] = ldxs(a.xs + j);
+      bad |= (smx[j].xh != smx[j].xh);
+    }
+    if (bad) atomicOr(&x_out, 1);
+  } else {
+    float* smx = reinterpret_cast<float*>(smraw);
+    for (int j = t; j < nk; j += kThreads) smx[j] = xval(a, j);
+  }
+  const char* A0 = reinterpret_cast<const char*>(a.A);
+  const char* Aend = A0 + a.u * S * es;
+  // Queues tile `tile` into `dst`; returns the byte offset of its first element.
+  auto issue = [&](int64_t tile, unsigned char* dst) -> int {
+    const int64_t i0 = tile * R;
+    const int64_t reff = min((int64_t)R, a.u - i0);
+    const char* gs = A0 + i0 * S * es;
+    const char* ge = gs + reff * S * es;
+    const char* c0 = A0 + ((gs - A0) & ~(int64_t)15);
+    const int64_t nch = (ge - c0 + 15) / 16;
+    for (int64_t q = t; q < nch; q += kThreads) {
+      const char* src = c0 + 16 * q;
+      if (src + 16 <= Aend) {
+        cp_async16(dst + 16 * q, src);
+      } else {
+        for (const char* e = src; e < Aend; e += es)
+          *reinterpret_cast<RawVec<es>*>(dst + 16 * q + (e - src)) = ld_plain<es>(e);
+      }
+    }
+    return (int)(gs - c0);
+  };
+  int head0 = issue(blockIdx.x, buf0), head1 = 0;  // first-element offsets in buffers 0 and 1
+  cp_async_commit();
+  int k = 0;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, k ^= 1) {
+    const int64_t nxt = tile + gridDim.x;
+    if (nxt < ntiles) {
+      if (k == 0) head1 = issue(nxt, buf0 + tile_cap);
+      else head0 = issue(nxt, buf0);
+    }
+    cp_async_commit();
+    cp_async_wait<1>();
+    __syncthreads();
+    const int64_t i0 = tile * R;
+    const int reff = (int)min((int64_t)R, a.u - i0);
+    if (t < reff * v) {
+      const int r = t / v, l = t - (t / v) * v;
+      const T* row = reinterpret_cast<const T*>(buf0 + k * tile_cap + (k ? head1 : head0)) + (int64_t)r * S + l;
+      if constexpr (DT == TVC_F64) {
+        const double* x = static_cast<const double*>(a.x);
+        const XSplit* smx = reinterpret_cast<const XSplit*>(smraw);
+        // Branch-free float-float products with the window bits ORed
+        // alongside; an output that met an element (or x) outside the exact
+        // window is recomputed with DFMA.  Blocks of kRB products are folded
+        // outside the inner loop: a fold test inside it is if-converted, and
+        // its FP64 instructions then issue (masked off) for every element.
+        double d = 0.0;
+        uint32_t bad = (uint32_t)x_out;
+        for (int jb = 0; jb < nk; jb += kRB) {
+          const int je = min(nk, jb + kRB);
+          float sf = 0.0f, cf = 0.0f;
+          for (int j = jb; j < je; j++) {
+            const double aj = reinterpret_cast<const double*>(row)[j * v];
+            bad |= df_out_of_window(aj);
+            df_mac_fast(sf, cf, aj, smx[j]);
+          }
+          d += (double)sf;
+          d += (double)cf;
+        }
+        if (bad) {
+          d = 0.0;
+          for (int j = 0; j < nk; j++) d = fma(reinterpret_cast<const double*>(row)[j * v], x[j], d);
+        }
+        emit(a, 0, (i0 + r) * a.v + l, d);
+      } else {
+        const float* smx = reinterpret_cast<const float*>(smraw);
+        AccF32<1> acc;
+        acc.init();
+        for (int jb = 0; jb < nk; jb += kRB) {
+          const int je = min(nk, jb + kRB);
+          for (int j = jb; j < je; j++) {
+            float val[1];
+            E::template load<1, true>(row + j * v, val);
+            acc.a[0] = __fmaf_rn(val[0], smx[j], acc.a[0]);
+          }
+          acc.fold();
+        }
+        emit(a, 0, (i0 + r) * a.v + l, __fmul_rn(acc.result(0), out_scale(a, i0 + r)));
+      }
+    }
+    __syncthreads();  // buf[k] is refilled two tiles on
+  }
+  cp_async_wait<0>();
 }
 
 // -------------------------------------------------------- helper kernels --
@@ -1162,7 +1339,8 @@ enum Kind {
   K_ROWS_SHORT = 4,
   K_ROWS_TMA = 5,
   K_ROWS_F64S = 6,
-  K_ROWS_MULTI = 7
+  K_ROWS_MULTI = 7,
+  K_TILE_ASYNC = 8
 };
 
 struct Plan {
@@ -1232,6 +1410,39 @@ static int dfma_rows_option() {
   return v;
 }
 
+// FP64 short rows through the staged (TMA) kernel: only where the register
+// kernels are left with 8-byte loads (odd n_k); TVC_F64_STAGED=0 turns it
+// off, 1 (default 0 until measured) turns it on.
+static bool f64_staged_rows(int64_t nk, const void* A) {
+  static int v = [] {
+    const char* e = std::getenv("TVC_F64_STAGED");
+    return e ? std::atoi(e) : 0;
+  }();
+  return v == 1 && (nk % 2 == 1 || !aligned(A, 16));
+}
+
+// Longest FP64 rows with 8-byte loads (odd n_k) served by the slots kernel
+// with G = 32 (below it the per-row FP64 epilogue of one row per warp
+// occupies the FP64 pipe; 979-element rows 4.0 -> 5.3 TB/s);
+// TVC_F64_SLOTS_MAX overrides (0: only G < 32).
+static int64_t f64_slots_max_nk() {
+  static int64_t v = [] {
+    const char* e = std::getenv("TVC_F64_SLOTS_MAX");
+    return e ? (int64_t)std::atoll(e) : (int64_t)4096;
+  }();
+  return v;
+}
+
+// Persistent double-buffered small-slab kernel on by default;
+// TVC_TILE_ASYNC=0 returns to one tile per block.
+static bool tile_async_enabled() {
+  static bool v = [] {
+    const char* e = std::getenv("TVC_TILE_ASYNC");
+    return !(e && std::atoi(e) == 0);
+  }();
+  return v;
+}
+
 // Narrow long-row kernel on by default; TVC_ROWS_MULTI=0 returns those rows
 // to the one-row-per-group kernel.
 static bool rows_multi_enabled() {
@@ -1252,6 +1463,14 @@ static int env_choice(const char* name, int ok1, int ok2, int ok3) {
   if (!e) return 0;
   const int r = std::atoi(e);
   return (r == ok1 || r == ok2 || r == ok3) ? r : 0;
+}
+
+// Rows in flight per lane of the slab kernel (4, 8 or 16): 8 for FP64/FP32,
+// 16 for the narrow types (as measured at v = 3 .. 20); TVC_SLAB_UNR overrides.
+static int slab_unroll(tvc_dtype dt) {
+  static int v = env_choice("TVC_SLAB_UNR", 4, 8, 16);
+  if (v) return v;
+  return (dt == TVC_BF16 || dt == TVC_E4M3) ? 16 : 8;  // measured best per type
 }
 
 static int rows_multi_rb(tvc_dtype dt) {
@@ -1301,7 +1520,8 @@ static Plan make_plan_impl(const Shape& s, tvc_dtype dt, const void* A, bool all
     p.chunk = ceil_div(ceil_div(s.nk, splits), 8) * 8;
     p.splits = ceil_div(s.nk, p.chunk);
     p.grid = dim3((unsigned)ceil_div(threads, kThreads), (unsigned)p.splits);
-  } else if (s.v == 1 && dt != TVC_F64 && allow_staged && staged_rows_enabled() && aligned(A, 16) &&
+  } else if (s.v == 1 && (dt != TVC_F64 || f64_staged_rows(s.nk, A)) && allow_staged && staged_rows_enabled() &&
+             aligned(A, 16) &&
              s.nk <= 8 * 32 * (int64_t)pick_vec(dt, s.nk, A, 4) && s.u >= 8) {
     // Staged short rows: tiles of R = 8*RW whole rows through shared memory.
     p.kind = K_ROWS_TMA;
@@ -1369,13 +1589,16 @@ static Plan make_plan_impl(const Shape& s, tvc_dtype dt, const void* A, bool all
     p.kind = K_ROWS;
     p.vec = pick_vec(dt, s.nk, A);
     // Lanes per row: the largest power of two <= 32 that still gives every
-    // lane at least four loads of its row (at least 2 lanes).
+    // lane at least four loads of its row (at least 2 lanes; FP64 short rows
+    // go down to 1 lane, so that rows of 8 .. 15 elements fill one unrolled
+    // pass of the slots kernel).
     int G = 32;
-    while (G > 2 && (int64_t)G * p.vec * 4 > s.nk) G >>= 1;
+    const int gmin = (dt == TVC_F64) ? 1 : 2;
+    while (G > gmin && (int64_t)G * p.vec * 4 > s.nk) G >>= 1;
     p.G = G;
     const int64_t group = 4 * (int64_t)G * p.vec;  // one unrolled step of a group
     int64_t rows_per_block = (int64_t)kWarpsPerBlock * (kWarp / G);
-    if (dt == TVC_F64 && G < 32) {
+    if (dt == TVC_F64 && (G < 32 || (p.vec == 1 && s.nk <= f64_slots_max_nk()))) {
       p.kind = K_ROWS_F64S;  // 32 rows per warp, results converted in slots
       rows_per_block = (int64_t)kWarpsPerBlock * kWarp;
     }
@@ -1395,6 +1618,20 @@ static Plan make_plan_impl(const Shape& s, tvc_dtype dt, const void* A, bool all
     p.chunk = ceil_div(ceil_div(s.nk, splits), p.G) * p.G;
     p.splits = ceil_div(s.nk, p.chunk);
     p.grid = dim3((unsigned)ceil_div(s.u, kWarpsPerBlock), (unsigned)p.splits);
+  } else if (aligned(A, 16) && tile_async_enabled()) {
+    // Small slabs, persistent double-buffered tiles (see the kernel).
+    p.kind = K_TILE_ASYNC;
+    int64_t R = std::min<int64_t>(kThreads / s.v, (int64_t)(48 * 1024) / (int64_t)(S * es));
+    R = std::max<int64_t>(1, std::min<int64_t>(R, s.u));
+    p.R = (int)R;
+    p.ntiles = ceil_div(s.u, R);
+    p.vec16 = (int)(align_up((size_t)R * S * es, 16) + 32);  // tile capacity in bytes
+    const size_t x_bytes = align_up((size_t)s.nk * (dt == TVC_F64 ? sizeof(XSplit) : 4), 16);
+    p.smem = x_bytes + 2 * (size_t)p.vec16;
+    const int bps = (int)std::max<size_t>(1, std::min<size_t>(8, (size_t)(220 * 1024) / p.smem));
+    p.splits = 1;
+    p.chunk = s.nk;
+    p.grid = dim3((unsigned)std::max<int64_t>(1, std::min<int64_t>(p.ntiles, (int64_t)sms * bps)), 1);
   } else {
     p.kind = K_TILE;
     int64_t R = std::min<int64_t>(kThreads / s.v, (int64_t)(48 * 1024) / (int64_t)(S * es));
@@ -1515,7 +1752,8 @@ static void launch_rows_f64s_dq(const Plan& p, const TvcArgs<TVC_F64>& a, cudaSt
     case 2: tvc_rows_f64_slots_kernel<VEC, 2, DQ><<<p.grid, kThreads, 0, st>>>(a); break;
     case 4: tvc_rows_f64_slots_kernel<VEC, 4, DQ><<<p.grid, kThreads, 0, st>>>(a); break;
     case 8: tvc_rows_f64_slots_kernel<VEC, 8, DQ><<<p.grid, kThreads, 0, st>>>(a); break;
-    default: tvc_rows_f64_slots_kernel<VEC, 16, DQ><<<p.grid, kThreads, 0, st>>>(a); break;
+    case 16: tvc_rows_f64_slots_kernel<VEC, 16, DQ><<<p.grid, kThreads, 0, st>>>(a); break;
+    default: tvc_rows_f64_slots_kernel<VEC, 32, DQ><<<p.grid, kThreads, 0, st>>>(a); break;
   }
 }
 
@@ -1586,8 +1824,15 @@ static void launch_main(const Plan& p, const TvcArgs<DT>& a, cudaStream_t st) {
       }
       break;
     case K_SLAB:
-      tvc_slab_kernel<DT><<<p.grid, kThreads, 0, st>>>(a, p.g, p.G);
+      if (slab_unroll(DT) == 16) tvc_slab_kernel<DT, 16><<<p.grid, kThreads, 0, st>>>(a, p.g, p.G);
+      else if (slab_unroll(DT) == 4) tvc_slab_kernel<DT, 4><<<p.grid, kThreads, 0, st>>>(a, p.g, p.G);
+      else tvc_slab_kernel<DT, 8><<<p.grid, kThreads, 0, st>>>(a, p.g, p.G);
       break;
+    case K_TILE_ASYNC: {
+      opt_in_smem(reinterpret_cast<const void*>(tvc_tile_async_kernel<DT>), 200 * 1024);
+      tvc_tile_async_kernel<DT><<<p.grid, kThreads, p.smem, st>>>(a, p.R, p.ntiles, p.vec16);
+      break;
+    }
     case K_TILE: {
       opt_in_smem(reinterpret_cast<const void*>(tvc_tile_kernel<DT>), 64 * 1024);
       tvc_tile_kernel<DT><<<p.grid, kThreads, p.smem, st>>>(a, p.R, p.vec16);

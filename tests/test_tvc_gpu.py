@@ -71,8 +71,13 @@ def test_integer_inputs_bit_exact_f64(dims):
         assert np.array_equal(got, ref), (dims, k)
 
 
-def test_fp64_values_outside_the_emulation_window():
-    dims = (40, 37, 66)
+# shapes reaching the column, slab (1 < v < 32, large slabs), small-slab
+# (tile), odd short-row (8-byte loads) and even short-row kernels
+WINDOW_SHAPES = [(40, 37, 66), (500, 19, 19), (40, 600, 12), (3000, 13), (2001, 175), (300, 40)]
+
+
+@pytest.mark.parametrize("dims", WINDOW_SHAPES, ids=lambda d: "x".join(map(str, d)))
+def test_fp64_values_outside_the_emulation_window(dims):
     A = synth.tensor("u64", 4, dims)
     flat = A.ravel()
     rng = np.random.default_rng(5)
@@ -83,13 +88,16 @@ def test_fp64_values_outside_the_emulation_window():
     flat[pos[300:400]] = 5e-324  # subnormal
     flat[pos[400:500]] *= 2.0 ** 70
     flat[pos[500:]] *= 2.0 ** -70
-    for k in range(3):
+    for k in range(len(dims)):
         x = synth.vector("u64", 1, 1 + k, dims[k])
         x[::5] *= 1e-20
         x[1::7] = 0.0
         ref = oracle.tvc(A, k, x)
         got = gu.gpu_tvc(tg, A, k, x)
-        assert gu.rel_l2(got, ref) <= 1e-12
+        assert gu.rel_l2(got, ref) <= 1e-12, (dims, k)
+        # and with x inside the window (only A's elements fall outside)
+        x = synth.vector("u64", 1, 1 + k, dims[k])
+        assert gu.rel_l2(gu.gpu_tvc(tg, A, k, x), oracle.tvc(A, k, x)) <= 1e-12, (dims, k)
 
 
 @pytest.mark.parametrize("code", [oracle.F64, oracle.F32])
