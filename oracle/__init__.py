@@ -23,14 +23,15 @@ import threading
 import numpy as np
 
 __all__ = [
-    "F64", "F32", "BF16", "E4M3", "build", "tvc", "tvc_grad_x", "tvc_grad_A",
-    "hopm", "hopm3", "quantise", "decode_bf16", "decode_e4m3",
-    "bf16_from_f32", "e4m3_from_f32", "dequantise", "OracleError",
+    "F64", "F32", "BF16", "E4M3", "F16", "build", "tvc", "tvc_grad_x", "tvc_grad_A",
+    "hopm", "hopm3", "quantise", "decode_bf16", "decode_e4m3", "decode_f16",
+    "bf16_from_f32", "e4m3_from_f32", "f16_from_f32", "dequantise", "OracleError",
 ]
 
-F64, F32, BF16, E4M3 = 0, 1, 2, 3
+F64, F32, BF16, E4M3, F16 = 0, 1, 2, 3, 4
+# binary16 codes travel as numpy float16 (the same bits); BF16 codes as uint16
 _DTYPE_OF = {np.dtype(np.float64): F64, np.dtype(np.float32): F32,
-             np.dtype(np.uint16): BF16, np.dtype(np.uint8): E4M3}
+             np.dtype(np.uint16): BF16, np.dtype(np.uint8): E4M3, np.dtype(np.float16): F16}
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "tvc_oracle.c")
@@ -79,6 +80,10 @@ def _load():
             lib.oracle_bf16_from_f32.restype = ctypes.c_uint16
             lib.oracle_e4m3_from_f32.argtypes = [ctypes.c_float]
             lib.oracle_e4m3_from_f32.restype = ctypes.c_uint8
+            lib.oracle_decode_f16.argtypes = [ctypes.c_uint16]
+            lib.oracle_decode_f16.restype = D
+            lib.oracle_f16_from_f32.argtypes = [ctypes.c_float]
+            lib.oracle_f16_from_f32.restype = ctypes.c_uint16
             _lib = lib
     return _lib
 
@@ -103,7 +108,9 @@ def _tensor(A, dims):
 
 
 def _scales(dt, scales, n0):
-    if dt in (BF16, E4M3):
+    if dt == F16 and scales is None:
+        return None  # binary16 without scales: value = decode(code)
+    if dt in (BF16, E4M3, F16):
         if scales is None:
             raise ValueError("narrow storage needs per-slab scales")
         s = np.ascontiguousarray(np.asarray(scales, dtype=np.float32))
@@ -188,15 +195,18 @@ def hopm3(A, xs, iters: int, tol: float = 0.0, *, dims=None, scales=None) -> dic
     return _hopm(_load().oracle_hopm3, A, xs, iters, tol, dims, scales)
 
 
-def quantise(src, fmt: int, *, truncate: bool = False):
-    """Per-slab quantisation of an FP32 tensor: returns (codes, scales)."""
+def quantise(src, fmt: int, *, truncate: bool = False, allow_nonfinite: bool = False):
+    """Per-slab quantisation of an FP32 tensor: returns (codes, scales).
+    F16 codes come back as numpy float16 (the binary16 bits); with
+    allow_nonfinite an F16 overflow returns the codes instead of raising."""
     src = np.ascontiguousarray(np.asarray(src, dtype=np.float32))
     d = _dims(src.shape)
-    codes = np.zeros(src.shape, dtype=np.uint8 if fmt == E4M3 else np.uint16)
+    cdt = {E4M3: np.uint8, BF16: np.uint16, F16: np.float16}.get(fmt, np.uint16)
+    codes = np.zeros(src.shape, dtype=cdt)
     scales = np.zeros(int(d[0]), dtype=np.float32)
     st = _load().oracle_quantise(int(fmt), _p(src), int(d.size), _p(d), _p(codes), _p(scales),
                                  int(bool(truncate)))
-    if st:
+    if st and not (allow_nonfinite and fmt == F16 and st == 6):
         raise OracleError(st, "quantise")
     return codes, scales
 
@@ -217,6 +227,14 @@ def e4m3_from_f32(f: float) -> int:
     return int(_load().oracle_e4m3_from_f32(float(f)))
 
 
+def decode_f16(code: int) -> float:
+    return _load().oracle_decode_f16(int(code))
+
+
+def f16_from_f32(f: float) -> int:
+    return int(_load().oracle_f16_from_f32(float(f)))
+
+
 def dequantise(codes, scales) -> np.ndarray:
     """FP64 values scale[i0] * decode(code) of a narrow tensor (via the
     oracle's own decoders, one code at a time through a 256/65536 table)."""
@@ -225,8 +243,11 @@ def dequantise(codes, scales) -> np.ndarray:
         table = np.array([decode_e4m3(c) for c in range(256)])
     elif codes.dtype == np.uint16:
         table = np.array([decode_bf16(c) for c in range(65536)])
+    elif codes.dtype == np.float16:
+        table = np.array([decode_f16(c) for c in range(65536)])
+        codes = codes.view(np.uint16)
     else:
-        raise TypeError("codes must be uint8 (E4M3) or uint16 (BF16)")
+        raise TypeError("codes must be uint8 (E4M3), uint16 (BF16) or float16 (F16)")
     vals = table[codes]
     s = np.asarray(scales, dtype=np.float64).reshape((-1,) + (1,) * (codes.ndim - 1))
     return vals * s

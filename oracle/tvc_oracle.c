@@ -16,11 +16,13 @@
  * and v = prod_{i>k} n_i the tensor is a u x n_k x v array and
  *     Y[i][l] = sum_{j<n_k} A[i][j][l] x[j].
  *
- * Element types of A: FP64, FP32, BF16 (upper half of binary32) and
- * FP8 E4M3 (OCP 8-bit floating point, bias 7, max 448, no infinities).  The
- * two narrow types carry one FP32 scale per slab A[i_0, ...]; an element's
- * value is scale[i_0] * decode(code), promoted to FP64 before any arithmetic
- * (the storage-only use of low precision of Section 5.5).
+ * Element types of A: FP64, FP32, BF16 (upper half of binary32), FP8 E4M3
+ * (OCP 8-bit floating point, bias 7, max 448, no infinities) and FP16 (IEEE
+ * 754 binary16, the "half" of Section 5.5's half-single format).  The
+ * narrow types carry one FP32 scale per slab A[i_0, ...] (a NULL scale array
+ * means 1); an element's value is scale[i_0] * decode(code), promoted to FP64
+ * before any arithmetic (the storage-only use of low precision of Section
+ * 5.5).
  *
  * Build: gcc -O2 -ffp-contract=off -fopenmp -shared -fPIC (IEEE semantics,
  * no fused multiply-add, no reassociation).
@@ -34,6 +36,7 @@
 #define OR_F32 1
 #define OR_BF16 2
 #define OR_E4M3 3
+#define OR_F16 4
 
 #define OR_OK 0
 #define OR_ERR_ARG 1
@@ -67,6 +70,25 @@ double oracle_decode_e4m3(uint8_t code) {
   return s ? -mag : mag;
 }
 
+/* IEEE 754 binary16: s.eeeee.mmmmmmmmmm, bias 15; e = 0 is subnormal
+ * (m/1024 * 2^-14); e = 31 is infinity (m = 0) or NaN; everything else
+ * (1 + m/1024) * 2^(e-15). */
+double oracle_decode_f16(uint16_t code) {
+  int s = (code >> 15) & 1;
+  int e = (code >> 10) & 31;
+  int m = code & 1023;
+  double mag;
+  if (e == 31) {
+    if (m != 0) return NAN;
+    mag = INFINITY;
+  } else if (e == 0) {
+    mag = ldexp((double)m / 1024.0, -14);
+  } else {
+    mag = ldexp(1.0 + (double)m / 1024.0, e - 15);
+  }
+  return s ? -mag : mag;
+}
+
 /* Value of element f of A, promoted to FP64.  slab = N / n_0. */
 static double elem(int dtype, const void* A, const float* scales, int64_t slab, int64_t f) {
   switch (dtype) {
@@ -74,6 +96,7 @@ static double elem(int dtype, const void* A, const float* scales, int64_t slab, 
     case OR_F32: return (double)((const float*)A)[f];
     case OR_BF16: return (double)scales[f / slab] * oracle_decode_bf16(((const uint16_t*)A)[f]);
     case OR_E4M3: return (double)scales[f / slab] * oracle_decode_e4m3(((const uint8_t*)A)[f]);
+    case OR_F16: return (scales ? (double)scales[f / slab] : 1.0) * oracle_decode_f16(((const uint16_t*)A)[f]);
   }
   return NAN;
 }
@@ -409,14 +432,52 @@ uint8_t oracle_e4m3_from_f32(float f) {
   return (uint8_t)(s | code);
 }
 
+/* binary32 -> binary16, round to nearest, ties to even (IEEE 754), by
+ * value: |f| >= 65520 (halfway between the largest finite half, 65504, and
+ * 2^16) becomes infinity; below 2^-14 the quantum is 2^-24 (subnormals);
+ * NaN stays NaN (quiet, sign kept). */
+uint16_t oracle_f16_from_f32(float f) {
+  uint16_t s = signbit(f) ? 0x8000 : 0;
+  double a = fabs((double)f);
+  if (isnan(f)) return (uint16_t)(s | 0x7E00);
+  if (a >= 65520.0) return (uint16_t)(s | 0x7C00);
+  if (a < ldexp(1.0, -14)) {
+    double q = nearbyint(a / ldexp(1.0, -24)); /* 0..1024; 1024 is the smallest normal */
+    return (uint16_t)(s | (uint16_t)q);
+  }
+  int ex;
+  frexp(a, &ex); /* a = fr * 2^ex, fr in [0.5, 1) */
+  int e = ex - 1;
+  double r = nearbyint(a / ldexp(1.0, e - 10)); /* 1024..2048 */
+  if (r >= 2048.0) {
+    e += 1;
+    r = 1024.0;
+  }
+  return (uint16_t)(s | ((e + 15) << 10) | ((int)r - 1024));
+}
+
 /* Per-slab quantisation of an FP32 tensor (slab = A[i_0, ...], N/n_0
  * elements).  E4M3: scale = amax(slab) / 448 in FP32 (1 when the slab is all
  * zero), code = E4M3(value / scale) with the FP32 quotient.  BF16: scale = 1,
- * code = BF16(value) (RNE, or truncation when truncate != 0). */
+ * code = BF16(value) (RNE, or truncation when truncate != 0).  F16: scale =
+ * 1, code = binary16(value) (RNE); every code is written and the status is
+ * OR_ERR_NONFINITE when some code is infinite or NaN (overflow or a
+ * non-finite source). */
 int oracle_quantise(int dtype, const float* src, int order, const int64_t* dims, void* codes,
                     float* scales, int truncate) {
   if (!valid_shape(order, dims)) return OR_ERR_ARG;
-  if (dtype != OR_BF16 && dtype != OR_E4M3) return OR_ERR_ARG;
+  if (dtype != OR_BF16 && dtype != OR_E4M3 && dtype != OR_F16) return OR_ERR_ARG;
+  if (dtype == OR_F16) {
+    int64_t n0 = dims[0], slab = prod(dims, 1, order);
+    int bad = 0;
+    for (int64_t i = 0; i < n0; i++) scales[i] = 1.0f;
+    for (int64_t f = 0; f < n0 * slab; f++) {
+      uint16_t c = oracle_f16_from_f32(src[f]);
+      ((uint16_t*)codes)[f] = c;
+      if ((c & 0x7C00) == 0x7C00) bad = 1;
+    }
+    return bad ? OR_ERR_NONFINITE : OR_OK;
+  }
   int64_t n0 = dims[0], slab = prod(dims, 1, order);
   for (int64_t i = 0; i < n0; i++) {
     const float* p = src + i * slab;

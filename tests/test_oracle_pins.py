@@ -350,3 +350,62 @@ def test_quantise_per_slab_scales():
     zero = np.zeros((2, 3), dtype=np.float32)
     c0, s0 = oracle.quantise(zero, oracle.E4M3)
     assert np.all(s0 == 1.0) and np.all(c0 == 0)
+
+
+# ----------------------------------------------------------- binary16 (F16)
+
+def test_f16_decode_matches_numpy_for_every_code():
+    codes = np.arange(65536, dtype=np.uint32).astype(np.uint16)
+    ref = codes.view(np.float16).astype(np.float64)
+    mine = np.array([oracle.decode_f16(c) for c in range(65536)])
+    nan = np.isnan(ref)
+    assert np.array_equal(np.isnan(mine), nan)
+    assert np.array_equal(mine[~nan], ref[~nan])
+    assert np.array_equal(np.signbit(mine[~nan]), np.signbit(ref[~nan]))
+    # IEEE 754 anchors: largest finite, smallest normal, smallest subnormal
+    assert oracle.decode_f16(0x7BFF) == 65504.0
+    assert oracle.decode_f16(0x0400) == 2.0 ** -14
+    assert oracle.decode_f16(0x0001) == 2.0 ** -24
+
+
+def test_f16_encode_matches_numpy_rne_with_ties_subnormals_and_overflow():
+    vals = np.concatenate([
+        synth.tensor("lognormal", 5, [20000]).astype(np.float32),
+        synth.tensor("u64", 6, [20000]).astype(np.float32) * 1e-5,  # subnormal range
+        np.array([0.0, -0.0, 65504.0, 65519.0, 65520.0, 65536.0, 1e6, -1e6, np.inf, -np.inf,
+                  2.0 ** -25, 3 * 2.0 ** -26, 2.0 ** -24, 2049.0, 2051.0, 1e-30], dtype=np.float32),
+    ]).astype(np.float32)
+    # every midpoint between neighbouring positive binary16 values (ties to even)
+    grid = np.arange(0x7C00, dtype=np.uint32).astype(np.uint16).view(np.float16).astype(np.float64)
+    mids = ((grid[:-1] + grid[1:]) / 2).astype(np.float32)
+    mids = mids[mids.astype(np.float64) == (grid[:-1] + grid[1:]) / 2]  # exactly representable in FP32
+    vals = np.concatenate([vals, mids, -mids])
+    ref = vals.astype(np.float16).view(np.uint16)
+    mine = np.array([oracle.f16_from_f32(v) for v in vals], dtype=np.uint16)
+    assert np.array_equal(mine, ref)
+    assert oracle.f16_from_f32(float("nan")) & 0x7E00 == 0x7E00
+
+
+def test_f16_quantise_unit_scales_and_overflow_status():
+    src = synth.tensor("lognormal", 7, (4, 30, 9)).astype(np.float32)
+    codes, scales = oracle.quantise(src, oracle.F16)
+    assert codes.dtype == np.float16 and np.all(scales == 1.0)
+    assert np.array_equal(codes.view(np.uint16), src.astype(np.float16).view(np.uint16))
+    big = src.copy()
+    big[2, 5, 3] = 1e5
+    with pytest.raises(oracle.OracleError):
+        oracle.quantise(big, oracle.F16)
+    codes, _ = oracle.quantise(big, oracle.F16, allow_nonfinite=True)
+    assert np.isinf(codes[2, 5, 3])
+
+
+def test_f16_tvc_is_the_tvc_of_the_decoded_values():
+    dims = (5, 6, 7)
+    src = synth.tensor("lognormal", 8, dims).astype(np.float32)
+    codes, scales = oracle.quantise(src, oracle.F16)
+    vals = codes.astype(np.float64)
+    for k in range(3):
+        x = synth.vector("u64", 1, synth.stream_x(k), dims[k])
+        ref = np.tensordot(vals, x, axes=([k], [0]))
+        assert np.allclose(oracle.tvc(codes, k, x, scales=scales), ref, rtol=1e-13, atol=0)
+        assert np.allclose(oracle.tvc(codes, k, x), ref, rtol=1e-13, atol=0)
