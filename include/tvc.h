@@ -20,7 +20,7 @@
  *   Tensors must be element-aligned; 16-byte alignment enables wider loads.
  * Types: tvc_dtype names the storage of A.  Vectors (x, y, gradients,
  *   prefix tensors) are FP64 for TVC_F64 and FP32 for every other type.
- *   TVC_BF16 and TVC_E4M3 carry one FP32 scale per slab A[i_0, ...]
+ *   TVC_BF16, TVC_E4M3 and TVC_F16 carry one FP32 scale per slab A[i_0, ...]
  *   (n_0 scales, device memory); an element's value is
  *   scale[i_0] * decode(code).  A NULL scale pointer means all scales are 1.
  * Streams: every call is stream-ordered on `stream` (NULL = legacy default
@@ -54,7 +54,8 @@ typedef enum {
   TVC_F64 = 0,  /* binary64 storage, FP64 results                        */
   TVC_F32 = 1,  /* binary32 storage, FP32 accumulation                   */
   TVC_BF16 = 2, /* upper half of binary32, per-slab FP32 scale           */
-  TVC_E4M3 = 3  /* OCP FP8 E4M3 (bias 7, max 448), per-slab FP32 scale   */
+  TVC_E4M3 = 3, /* OCP FP8 E4M3 (bias 7, max 448), per-slab FP32 scale   */
+  TVC_F16 = 4   /* IEEE binary16 (Section 5.5's half-single), FP32 math  */
 } tvc_dtype;
 
 typedef enum {
@@ -87,7 +88,7 @@ tvc_status tvc(const void* A, int order, const int64_t* dims, int mode, const vo
 /*
  * Y := alpha * (A x_mode x) + beta * Y  (the BLAS-like form of Eq. 1 for a
  * single process).  beta == 0 means y is not read (NaN in y is ignored).
- * slab_scales: n_0 FP32 scales for TVC_BF16 / TVC_E4M3, ignored otherwise.
+ * slab_scales: n_0 FP32 scales for TVC_BF16 / TVC_E4M3 / TVC_F16, ignored otherwise.
  * workspace: device memory of at least tvc_workspace_size(...) bytes; it
  * may be NULL when that size is 0.  Returns TVC_ERR_WORKSPACE if too small.
  */
@@ -156,10 +157,15 @@ size_t tvc_backward_workspace_size(int order, const int64_t* dims, int mode, tvc
  *   TVC_BF16: scale = 1, code = BF16(value) rounded to nearest even, or the
  *             upper half of the binary32 when truncate != 0 (the paper's
  *             truncating "brain" format).
- * src: N floats; codes: N bytes (E4M3) or N uint16 (BF16); scales: n_0
+ *   TVC_F16:  scale = 1, code = binary16(value) rounded to nearest even (the
+ *             paper's half-single storage; values of magnitude >= 65520
+ *             become infinity).
+ * src: N floats; codes: N bytes (E4M3) or N uint16 (BF16, F16); scales: n_0
  * floats; status_out: 1 device int, set to TVC_ERR_NONFINITE when an E4M3
- * slab holds NaN or Inf (its codes are then meaningless).  All device
- * pointers.  workspace: tvc_quantise_workspace_size(...) bytes.
+ * slab holds NaN or Inf (its codes are then meaningless) or when an F16 code
+ * is infinite or NaN (overflow or a non-finite source; every code is still
+ * written).  All device pointers.  workspace:
+ * tvc_quantise_workspace_size(...) bytes.
  */
 tvc_status tvc_quantise(const float* src, int order, const int64_t* dims, tvc_dtype dtype, void* codes,
                         float* scales, int truncate, int* status_out, void* workspace, size_t ws_bytes,

@@ -20,13 +20,13 @@ import threading
 import torch
 
 __all__ = [
-    "F64", "F32", "BF16", "E4M3", "TVCError", "load_library", "tvc", "tvc_workspace_size",
+    "F64", "F32", "BF16", "E4M3", "F16", "TVCError", "load_library", "tvc", "tvc_workspace_size",
     "dtype_code", "library_path", "kernel_launches", "hopm", "hopm_workspace_size", "HopmResult", "quantise", "tvc_backward", "TVCFunction", "tvc_autograd", "hopm_backward", "HOPMFunction", "hopm_autograd", "TVCBatch", "HOPMBatch", "BATCH_PREUPLOADED",
     "split_1d", "slab_extract", "slab_insert", "split_tensor", "dtvc", "dtvc_workspace_size", "dhopm",
     "dhopm_workspace_size",
 ]
 
-F64, F32, BF16, E4M3 = 0, 1, 2, 3
+F64, F32, BF16, E4M3, F16 = 0, 1, 2, 3, 4
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 library_path = os.path.join(_HERE, "_lib", "libtvc_gb300.so")
@@ -121,12 +121,13 @@ _TORCH_CODE = {
     torch.uint16: BF16,
     torch.float8_e4m3fn: E4M3,
     torch.uint8: E4M3,
+    torch.float16: F16,
 }
 
 
 def dtype_code(t: torch.Tensor) -> int:
     """Storage code of a tensor: float64, float32, bfloat16 (or raw uint16
-    codes), float8_e4m3fn (or raw uint8 codes)."""
+    codes), float8_e4m3fn (or raw uint8 codes), float16 (binary16 codes)."""
     try:
         return _TORCH_CODE[t.dtype]
     except KeyError:
@@ -274,17 +275,19 @@ def hopm(A: torch.Tensor, xs, iters: int, tol: float = 0.0, *, scales: torch.Ten
 
 
 def quantise(src: torch.Tensor, code: int, *, truncate: bool = False, stream=None):
-    """Per-slab quantisation of a float32 CUDA tensor to BF16 (uint16 codes)
-    or E4M3 (uint8 codes); returns (codes, scales, status) on the device."""
+    """Per-slab quantisation of a float32 CUDA tensor to BF16 (uint16 codes),
+    E4M3 (uint8 codes) or F16 (float16 codes); returns (codes, scales,
+    status) on the device."""
     lib = load_library()
     if src.dtype != torch.float32:
         raise ValueError("src must be float32")
-    if code not in (BF16, E4M3):
-        raise ValueError("code must be BF16 or E4M3")
+    if code not in (BF16, E4M3, F16):
+        raise ValueError("code must be BF16, E4M3 or F16")
     _check_cuda(src)
     shape = tuple(src.shape)
     dims = _dims_array(shape)
-    codes = torch.empty(shape, dtype=torch.uint8 if code == E4M3 else torch.uint16, device=src.device)
+    cdt = {E4M3: torch.uint8, BF16: torch.uint16, F16: torch.float16}[code]
+    codes = torch.empty(shape, dtype=cdt, device=src.device)
     scales = torch.empty(shape[0], dtype=torch.float32, device=src.device)
     status = torch.zeros(1, dtype=torch.int32, device=src.device)
     ws = torch.empty(max(1, lib.tvc_quantise_workspace_size(len(shape), dims)), dtype=torch.uint8, device=src.device)

@@ -42,7 +42,7 @@ tvc_status make_shape(int order, const int64_t* dims, int mode, Shape* s) {
   return TVC_OK;
 }
 
-bool valid_dtype(int dt) { return dt >= TVC_F64 && dt <= TVC_E4M3; }
+bool valid_dtype(int dt) { return dt >= TVC_F64 && dt <= TVC_F16; }
 
 size_t elem_size(tvc_dtype dt) {
   switch (dt) {
@@ -50,6 +50,7 @@ size_t elem_size(tvc_dtype dt) {
     case TVC_F32: return 4;
     case TVC_BF16: return 2;
     case TVC_E4M3: return 1;
+    case TVC_F16: return 2;
   }
   return 0;
 }

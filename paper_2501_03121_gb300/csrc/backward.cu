@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(kBT) tvc_gradx_kernel(const GradArgs<DT> a) {
       const float* gyp = static_cast<const float*>(a.gy) + o;
       float g[VEC];
       float sc = 1.0f;
-      if constexpr (DT == TVC_BF16 || DT == TVC_E4M3) {
+      if constexpr (kNarrow<DT>) {
         if (!a.mode0 && a.scales) sc = __ldg(a.scales + i / a.upi0);
       }
 #pragma unroll
@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(kBT) tvc_gradx_kernel(const GradArgs<DT> a) {
     double t = 0.0;
     for (int w = 0; w < kBW; w++) t += red[w][q];
     V val = (V)t;
-    if constexpr (DT == TVC_BF16 || DT == TVC_E4M3) {
+    if constexpr (kNarrow<DT>) {
       if (a.mode0 && a.scales) val = __fmul_rn(val, __ldg(a.scales + j0 + q));
     }
     static_cast<V*>(a.partial)[(int64_t)blockIdx.x * a.nk + j0 + q] = val;
@@ -230,7 +230,7 @@ GxPlan plan_gx(const Shape& s, tvc_dtype dt, const void* A) {
     g.ws_tvc = 0;
     for (uintptr_t al = elem_size(tdt); al <= 256; al *= 2)
       g.ws_tvc = std::max(g.ws_tvc, tvc_ws_bytes(g.view, tdt, reinterpret_cast<const void*>(al)));
-    if (dt == TVC_BF16 || dt == TVC_E4M3) g.ws_gy = align_up((size_t)s.u * 4, 256);
+    if (dt == TVC_BF16 || dt == TVC_E4M3 || dt == TVC_F16) g.ws_gy = align_up((size_t)s.u * 4, 256);
     g.total = align_up(g.ws_tvc, 256) + g.ws_gy;
     return g;
   }
@@ -292,7 +292,7 @@ tvc_status grad_x(const Shape& s, const void* A, const void* gy, void* gx, tvc_d
   if (g.via_tvc) {
     char* w = static_cast<char*>(ws);
     const void* gyv = gy;
-    if (dt == TVC_BF16 || dt == TVC_E4M3) {
+    if (dt == TVC_BF16 || dt == TVC_E4M3 || dt == TVC_F16) {
       float* gys = reinterpret_cast<float*>(w + align_up(g.ws_tvc, 256));
       const int blocks = (int)std::min<int64_t>(cdiv(s.u, 256), 4096);
       tvc_scale_gy_kernel<<<blocks, 256, 0, st>>>(static_cast<const float*>(gy), scales, gys, s.u,
@@ -308,6 +308,7 @@ tvc_status grad_x(const Shape& s, const void* A, const void* gy, void* gx, tvc_d
     case TVC_F32: return run_gx<TVC_F32>(g, s, A, gy, gx, scales, ws, st);
     case TVC_BF16: return run_gx<TVC_BF16>(g, s, A, gy, gx, scales, ws, st);
     case TVC_E4M3: return run_gx<TVC_E4M3>(g, s, A, gy, gx, scales, ws, st);
+    case TVC_F16: return run_gx<TVC_F16>(g, s, A, gy, gx, scales, ws, st);
   }
   return TVC_ERR_INVALID_ARG;
 }

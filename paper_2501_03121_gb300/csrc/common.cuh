@@ -190,6 +190,53 @@ struct Elem<TVC_BF16> {
   }
 };
 
+// FP16 (IEEE binary16): converted two at a time, f16x2 -> two FP32 (exact).
+template <>
+struct Elem<TVC_F16> {
+  using T = uint16_t;
+  using V = float;
+  using C = float;
+  static constexpr int kSize = 2;
+  __device__ __forceinline__ static void word2(uint32_t w, float& lo, float& hi) {
+    __half2_raw r;
+    r.x = (unsigned short)(w & 0xFFFFu);
+    r.y = (unsigned short)(w >> 16);
+    const float2 f = __half22float2(__half2(r));
+    lo = f.x;
+    hi = f.y;
+  }
+  __device__ __forceinline__ static void decode16(const uint4& w, float (&val)[8]) {
+    word2(w.x, val[0], val[1]);
+    word2(w.y, val[2], val[3]);
+    word2(w.z, val[4], val[5]);
+    word2(w.w, val[6], val[7]);
+  }
+  template <int VEC, bool PLAIN = false>
+  __device__ __forceinline__ static void load(const T* p, C (&val)[VEC]) {
+    if constexpr (VEC == 8) {
+      RawVec<16> r = ld_any<16, PLAIN>(p);
+      decode16(r.v, val);
+    } else if constexpr (VEC == 4) {
+      RawVec<8> r = ld_any<8, PLAIN>(p);
+      word2(r.v.x, val[0], val[1]);
+      word2(r.v.y, val[2], val[3]);
+    } else if constexpr (VEC == 2) {
+      word2(ld_any<4, PLAIN>(p).v, val[0], val[1]);
+    } else {
+#pragma unroll
+      for (int e = 0; e < VEC; e++) {
+        __half_raw h;
+        h.x = ld_any<2, PLAIN>(p + e).v;
+        val[e] = __half2float(__half(h));
+      }
+    }
+  }
+};
+
+// Storage types with per-slab scales (decoded to FP32 in registers).
+template <tvc_dtype DT>
+inline constexpr bool kNarrow = (DT == TVC_BF16 || DT == TVC_E4M3 || DT == TVC_F16);
+
 // FP8 E4M3 (OCP): decoded two at a time by the hardware e4m3x2 -> f16x2
 // conversion, then widened to FP32 (both exact).
 template <>

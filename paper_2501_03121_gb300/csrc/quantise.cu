@@ -6,6 +6,9 @@
 //   BF16: scale = 1; code = BF16(value), round to nearest even, or the upper
 //         half of the binary32 when truncation is asked for (the paper's
 //         "brain" conversion); NaN -> 0x7FC0 with the input's sign.
+//   F16:  scale = 1; code = binary16(value), round to nearest even (the
+//         paper's half-single storage), overflow to infinity; NaN -> 0x7E00
+//         with the input's sign; an infinite or NaN code sets the status.
 // The slab maximum is an order-independent reduction (integer max of the
 // non-negative binary32 bit patterns), so the codes are deterministic.
 #include "common.cuh"
@@ -44,11 +47,24 @@ __global__ void quant_scale_kernel(const unsigned* amax, float* scales, int64_t 
   }
 }
 
+enum QuantFmt { Q_BF16 = 0, Q_E4M3 = 1, Q_F16 = 2 };
+
 __global__ void quant_codes_kernel(const float* __restrict__ src, int64_t N, int64_t slab, const float* scales,
-                                   void* codes, int e4m3, int truncate) {
+                                   void* codes, int fmt, int truncate, int* status) {
+  int nonfinite = 0;
   for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < N; f += (int64_t)gridDim.x * blockDim.x) {
     const float v = src[f];
-    if (e4m3) {
+    if (fmt == Q_F16) {
+      uint16_t c;
+      if (isnan(v)) {
+        c = (uint16_t)(((__float_as_uint(v) >> 16) & 0x8000u) | 0x7E00u);
+      } else {
+        const __half h = __float2half_rn(v);
+        c = __half_as_ushort(h);
+      }
+      nonfinite |= ((c & 0x7C00u) == 0x7C00u);
+      static_cast<uint16_t*>(codes)[f] = c;
+    } else if (fmt == Q_E4M3) {
       const float q = __fdiv_rn(v, scales[f / slab]);
       static_cast<uint8_t*>(codes)[f] = (uint8_t)__nv_cvt_float_to_fp8(q, __NV_SATFINITE, __NV_E4M3);
     } else {
@@ -65,6 +81,7 @@ __global__ void quant_codes_kernel(const float* __restrict__ src, int64_t N, int
       static_cast<uint16_t*>(codes)[f] = c;
     }
   }
+  if (nonfinite) atomicExch(status, (int)TVC_ERR_NONFINITE);
 }
 
 }  // namespace tvcg
@@ -81,7 +98,8 @@ extern "C" tvc_status tvc_quantise(const float* src, int order, const int64_t* d
                                    tvc_stream_t stream) {
   int64_t N;
   if (check_dims(order, dims, &N) != TVC_OK) return TVC_ERR_INVALID_ARG;
-  if ((dtype != TVC_BF16 && dtype != TVC_E4M3) || !src || !codes || !scales || !status_out) return TVC_ERR_INVALID_ARG;
+  if ((dtype != TVC_BF16 && dtype != TVC_E4M3 && dtype != TVC_F16) || !src || !codes || !scales || !status_out)
+    return TVC_ERR_INVALID_ARG;
   if (!aligned(src, 4) || !aligned(scales, 4) || !aligned(codes, elem_size(dtype))) return TVC_ERR_INVALID_ARG;
   if (!workspace || ws_bytes < tvc_quantise_workspace_size(order, dims)) return TVC_ERR_WORKSPACE;
   cudaStream_t st = (cudaStream_t)stream;
@@ -100,7 +118,8 @@ extern "C" tvc_status tvc_quantise(const float* src, int order, const int64_t* d
   quant_scale_kernel<<<(unsigned)std::min<int64_t>((n0 + 255) / 256, 4096), 256, 0, st>>>(amax, scales, n0, e4m3,
                                                                                          status_out);
   const int blocks = (int)std::min<int64_t>((N + 255) / 256, (int64_t)device_sms() * 32);
-  quant_codes_kernel<<<blocks, 256, 0, st>>>(src, N, slab, scales, codes, e4m3, truncate);
+  const int fmt = e4m3 ? Q_E4M3 : (dtype == TVC_F16 ? Q_F16 : Q_BF16);
+  quant_codes_kernel<<<blocks, 256, 0, st>>>(src, N, slab, scales, codes, fmt, truncate, status_out);
   count_launches(launches + 2);
   return cuda_status(cudaGetLastError());
 }

@@ -68,7 +68,7 @@ __device__ __forceinline__ XSplit ldxs(const XSplit* p) {
 template <tvc_dtype DT>
 __device__ __forceinline__ float xval(const TvcArgs<DT>& a, int64_t j) {
   float xv = __ldg(static_cast<const float*>(a.x) + j);
-  if constexpr (DT == TVC_BF16 || DT == TVC_E4M3) {
+  if constexpr (kNarrow<DT>) {
     if (a.mode0 && a.scales) xv = __fmul_rn(xv, __ldg(a.scales + j));
   }
   return xv;
@@ -79,7 +79,7 @@ __device__ __forceinline__ float xval(const TvcArgs<DT>& a, int64_t j) {
 template <tvc_dtype DT, int VEC>
 __device__ __forceinline__ void xvec(const TvcArgs<DT>& a, int64_t j, float (&xq)[VEC]) {
   const float* x = static_cast<const float*>(a.x);
-  const bool fold = (DT == TVC_BF16 || DT == TVC_E4M3) && a.mode0 && a.scales;
+  const bool fold = kNarrow<DT> && a.mode0 && a.scales;
   if constexpr (VEC % 4 == 0) {
     if (!fold && ((reinterpret_cast<uintptr_t>(x) & 15) == 0)) {
 #pragma unroll
@@ -100,7 +100,7 @@ __device__ __forceinline__ void xvec(const TvcArgs<DT>& a, int64_t j, float (&xq
 // Scale of output row i (k > 0): all elements of an output share slab i / upi0.
 template <tvc_dtype DT>
 __device__ __forceinline__ float out_scale(const TvcArgs<DT>& a, int64_t i) {
-  if constexpr (DT == TVC_BF16 || DT == TVC_E4M3) {
+  if constexpr (kNarrow<DT>) {
     if (!a.mode0 && a.scales) return __ldg(a.scales + i / a.upi0);
   }
   return 1.0f;
@@ -1154,14 +1154,7 @@ __global__ void __launch_bounds__(kThreads) tvc_tile_kernel(const TvcArgs<DT> a,
     acc.init();
     for (int c = 0; c < nk; c++) {
       float val[1];
-      if constexpr (DT == TVC_F32) {
-        val[0] = row[(int64_t)jt * v];
-      } else if constexpr (DT == TVC_BF16) {
-        val[0] = __uint_as_float(((uint32_t)row[(int64_t)jt * v]) << 16);
-      } else {
-        __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)row[(int64_t)jt * v], __NV_E4M3);
-        val[0] = __half2float(*reinterpret_cast<__half*>(&h));
-      }
+      E::template load<1, true>(row + (int64_t)jt * v, val);
       acc.a[0] = __fmaf_rn(val[0], smx[jt], acc.a[0]);
       if (++jt == nk) jt = 0;
       if (++blk == kRB) {
@@ -1470,13 +1463,13 @@ static int env_choice(const char* name, int ok1, int ok2, int ok3) {
 static int slab_unroll(tvc_dtype dt) {
   static int v = env_choice("TVC_SLAB_UNR", 4, 8, 16);
   if (v) return v;
-  return (dt == TVC_BF16 || dt == TVC_E4M3) ? 16 : 8;  // measured best per type
+  return (dt == TVC_BF16 || dt == TVC_E4M3 || dt == TVC_F16) ? 16 : 8;  // measured best per type
 }
 
 static int rows_multi_rb(tvc_dtype dt) {
   static int v = env_choice("TVC_ROWS_RB", 2, 4, 8);
   if (v) return v;
-  return dt == TVC_E4M3 ? 8 : (dt == TVC_BF16 ? 2 : 4);
+  return dt == TVC_E4M3 ? 8 : ((dt == TVC_BF16 || dt == TVC_F16) ? 2 : 4);
 }
 
 static int rows_multi_unr(tvc_dtype dt) {
@@ -1672,7 +1665,7 @@ static void launch_rows(const Plan& p, const TvcArgs<DT>& a, cudaStream_t st) {
   } else if constexpr (DT == TVC_F32) {
     if (p.vec == 4) launch_rows_vec<DT, 4>(p, a, st);
     else launch_rows_vec<DT, 1>(p, a, st);
-  } else if constexpr (DT == TVC_BF16) {
+  } else if constexpr (sizeof(typename Elem<DT>::T) == 2) {  // BF16, F16
     if (p.vec == 8) launch_rows_vec<DT, 8>(p, a, st);
     else if (p.vec == 2) launch_rows_vec<DT, 2>(p, a, st);
     else launch_rows_vec<DT, 1>(p, a, st);
@@ -1794,7 +1787,7 @@ static void launch_main(const Plan& p, const TvcArgs<DT>& a, cudaStream_t st) {
       } else if constexpr (DT == TVC_F32) {
         if (p.vec == 4) tvc_cols_kernel<DT, 4, 0><<<p.grid, kThreads, 0, st>>>(a);
         else tvc_cols_kernel<DT, 1, 0><<<p.grid, kThreads, 0, st>>>(a);
-      } else if constexpr (DT == TVC_BF16) {
+      } else if constexpr (sizeof(typename Elem<DT>::T) == 2) {  // BF16, F16
         if (p.vec == 8) tvc_cols_async_kernel<DT, 8><<<p.grid, kThreads, 0, st>>>(a);
         else if (p.vec == 2) tvc_cols_kernel<DT, 2, 0><<<p.grid, kThreads, 0, st>>>(a);
         else tvc_cols_kernel<DT, 1, 0><<<p.grid, kThreads, 0, st>>>(a);
@@ -1890,6 +1883,7 @@ tvc_status tvc_launch(const void* A, const Shape& s, const void* x, void* y, tvc
     case TVC_F32: return run<TVC_F32>(A, s, x, y, nullptr, alpha, beta, ws, p, stream, done);
     case TVC_BF16: return run<TVC_BF16>(A, s, x, y, scales, alpha, beta, ws, p, stream, done);
     case TVC_E4M3: return run<TVC_E4M3>(A, s, x, y, scales, alpha, beta, ws, p, stream, done);
+    case TVC_F16: return run<TVC_F16>(A, s, x, y, scales, alpha, beta, ws, p, stream, done);
   }
   return TVC_ERR_INVALID_ARG;
 }

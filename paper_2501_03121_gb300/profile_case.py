@@ -25,7 +25,7 @@ def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--dims", type=int, nargs="+", required=True)
     ap.add_argument("--mode", type=int, default=0)
-    ap.add_argument("--dtype", default="f64", choices=["f64", "f32", "bf16", "e4m3"])
+    ap.add_argument("--dtype", default="f64", choices=["f64", "f32", "bf16", "e4m3", "f16"])
     ap.add_argument("--reps", type=int, default=3)
     a = ap.parse_args(argv)
     dt = torch.float64 if a.dtype == "f64" else torch.float32
@@ -34,8 +34,8 @@ def main(argv=None):
     A = torch.empty(N, dtype=dt, device="cuda")
     sd.fill(A, kind, 0, synth.STREAM_A)
     scales = None
-    if a.dtype in ("bf16", "e4m3"):
-        A, scales, _ = tg.quantise(A.view(a.dims), tg.BF16 if a.dtype == "bf16" else tg.E4M3)
+    if a.dtype in ("bf16", "e4m3", "f16"):
+        A, scales, _ = tg.quantise(A.view(a.dims), {"bf16": tg.BF16, "e4m3": tg.E4M3, "f16": tg.F16}[a.dtype])
         A = A.view(-1)
     x = torch.from_numpy(synth.vector(kind, 1, synth.stream_x(a.mode), a.dims[a.mode])).cuda()
     y = torch.empty(N // a.dims[a.mode], dtype=dt, device="cuda")

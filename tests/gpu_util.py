@@ -7,7 +7,7 @@ import synth
 
 DEV = torch.device("cuda:0") if torch.cuda.is_available() else None
 
-TOL = {oracle.F64: 1e-12, oracle.F32: 1e-5, oracle.BF16: 1e-5, oracle.E4M3: 1e-5}
+TOL = {oracle.F64: 1e-12, oracle.F32: 1e-5, oracle.BF16: 1e-5, oracle.E4M3: 1e-5, oracle.F16: 1e-5}
 
 
 def rel_l2(got, ref):
@@ -30,7 +30,7 @@ def to_dev(a):
 
 def inputs(dims, code, seed=0):
     """(A as stored for the GPU, A for the oracle, scales or None, x factory).
-    F64: uniform doubles; F32: uniform binary32; BF16/E4M3: N(0,1)exp(U[-3,3])
+    F64: uniform doubles; F32: uniform binary32; BF16/E4M3/F16: N(0,1)exp(U[-3,3])
     binary32 values quantised per slab by the oracle's quantiser."""
     if code == oracle.F64:
         A = synth.tensor("u64", seed, dims)

@@ -15,11 +15,11 @@ tg = pytest.importorskip("paper_2501_03121_gb300")
 
 SHAPES = [(7,), (5, 3), (4, 1), (3, 1, 5), (6, 5, 4, 3), (3, 50, 64), (5, 1000), (4, 100, 7), (300, 40),
           (50, 8, 8), (2000, 64), (9, 33, 130), (2, 3, 2, 3, 2, 3, 2), (257, 1, 3)]
-CODES = [oracle.F64, oracle.F32, oracle.BF16, oracle.E4M3]
+CODES = [oracle.F64, oracle.F32, oracle.BF16, oracle.E4M3, oracle.F16]
 
 
 @pytest.mark.parametrize("dims", SHAPES, ids=lambda d: "x".join(map(str, d)))
-@pytest.mark.parametrize("code", CODES, ids=["f64", "f32", "bf16", "e4m3"])
+@pytest.mark.parametrize("code", CODES, ids=["f64", "f32", "bf16", "e4m3", "f16"])
 def test_backward_matches_oracle(dims, code):
     A, Ao, scales = gu.inputs(dims, code)
     for k in range(len(dims)):

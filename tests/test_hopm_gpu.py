@@ -21,7 +21,7 @@ pytestmark = pytest.mark.gpu
 tg = pytest.importorskip("paper_2501_03121_gb300")
 
 VEC = {oracle.F64: torch.float64, oracle.F32: torch.float32, oracle.BF16: torch.float32,
-       oracle.E4M3: torch.float32}
+       oracle.E4M3: torch.float32, oracle.F16: torch.float32}
 
 
 def ones_start(dims, code):
@@ -56,7 +56,7 @@ SHAPES = [(9, 7), (5, 6, 7), (4, 5, 3, 6), (3, 4, 2, 3, 5), (2, 3, 2, 2, 3, 2), 
 
 
 @pytest.mark.parametrize("dims", SHAPES, ids=lambda d: "x".join(map(str, d)))
-@pytest.mark.parametrize("code", [oracle.F64, oracle.F32, oracle.BF16, oracle.E4M3], ids=["f64", "f32", "bf16", "e4m3"])
+@pytest.mark.parametrize("code", [oracle.F64, oracle.F32, oracle.BF16, oracle.E4M3, oracle.F16], ids=["f64", "f32", "bf16", "e4m3", "f16"])
 def test_hopm_matches_oracle(dims, code):
     A, Ao, scales = gu.inputs(dims, code)
     iters = 8
@@ -143,13 +143,16 @@ def test_hopm_deterministic():
 def test_quantise_bit_exact(dims):
     src = synth.tensor("lognormal", 3, dims).astype(np.float32)
     src.ravel()[::97] = 0.0
-    for code in (oracle.BF16, oracle.E4M3):
+    for code in (oracle.BF16, oracle.E4M3, oracle.F16):
         for trunc in ((False, True) if code == oracle.BF16 else (False,)):
             c_ref, s_ref = oracle.quantise(src, code, truncate=trunc)
             codes, scales, status = tg.quantise(gu.to_dev(src), code, truncate=trunc)
             assert int(status.item()) == 0
             assert np.array_equal(scales.cpu().numpy(), s_ref)
-            assert np.array_equal(codes.cpu().numpy(), c_ref)
+            got = codes.cpu().numpy()
+            if code == oracle.F16:  # compare the binary16 bits
+                got, c_ref = got.view(np.uint16), c_ref.view(np.uint16)
+            assert np.array_equal(got, c_ref)
 
 
 def test_quantise_nonfinite_status_and_zero_slab():
@@ -160,9 +163,18 @@ def test_quantise_nonfinite_status_and_zero_slab():
     src[2, 3, 3] = np.inf
     _, _, status = tg.quantise(gu.to_dev(src), tg.E4M3)
     assert int(status.item()) == 6
+    # binary16: overflow (and NaN) give non-finite codes and set the status;
+    # every code is still written and equals the oracle's
+    src = synth.tensor("lognormal", 1, (3, 8, 8)).astype(np.float32)
+    src[0, 1, 2] = 7e4
+    src[1, 2, 3] = np.nan
+    codes, scales, status = tg.quantise(gu.to_dev(src), tg.F16)
+    assert int(status.item()) == 6
+    ref, _ = oracle.quantise(src, oracle.F16, allow_nonfinite=True)
+    assert np.array_equal(codes.cpu().numpy().view(np.uint16), ref.view(np.uint16))
 
 
-@pytest.mark.parametrize("code", [oracle.BF16, oracle.E4M3], ids=["bf16", "e4m3"])
+@pytest.mark.parametrize("code", [oracle.BF16, oracle.E4M3, oracle.F16], ids=["bf16", "e4m3", "f16"])
 def test_low_precision_hopm_lambda_vs_fp64(code):
     """Mixed-precision recipe at reduced size (256^3): N(0,1)exp(U[-3,3])
     entries, stored narrow with per-slab scales, 30 sweeps; lambda against
@@ -174,8 +186,8 @@ def test_low_precision_hopm_lambda_vs_fp64(code):
     torch.cuda.synchronize()
     ref = oracle.hopm(src, ones_np(dims), 30)
     err = abs(r.lam.item() - ref["lam"]) / ref["lam"]
-    print(f"{'bf16' if code == oracle.BF16 else 'e4m3'} lambda rel err vs FP64 oracle: {err:.3e}")
-    if code == oracle.BF16:
+    print(f"{ {oracle.BF16: 'bf16', oracle.E4M3: 'e4m3', oracle.F16: 'f16'}[code]} lambda rel err vs FP64 oracle: {err:.3e}")
+    if code in (oracle.BF16, oracle.F16):
         assert err <= 1e-3
     else:
         assert err <= 2e-2

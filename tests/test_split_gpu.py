@@ -21,8 +21,8 @@ pytestmark = pytest.mark.gpu
 
 tg = pytest.importorskip("paper_2501_03121_gb300")
 
-CODES = [oracle.F64, oracle.F32, oracle.BF16, oracle.E4M3]
-IDS = ["f64", "f32", "bf16", "e4m3"]
+CODES = [oracle.F64, oracle.F32, oracle.BF16, oracle.E4M3, oracle.F16]
+IDS = ["f64", "f32", "bf16", "e4m3", "f16"]
 
 
 def _dev_codes(A):

@@ -28,11 +28,11 @@ SHAPES = [
     # counts, a single row, split-K, and mode 0 of an order-1 tensor
     (7, 3072), (19, 2, 1040), (1, 4096), (2048,), (3, 65536), (1001, 1536),
 ]
-CODES = [oracle.F64, oracle.F32, oracle.BF16, oracle.E4M3]
+CODES = [oracle.F64, oracle.F32, oracle.BF16, oracle.E4M3, oracle.F16]
 
 
 @pytest.mark.parametrize("dims", SHAPES, ids=lambda d: "x".join(map(str, d)))
-@pytest.mark.parametrize("code", CODES, ids=["f64", "f32", "bf16", "e4m3"])
+@pytest.mark.parametrize("code", CODES, ids=["f64", "f32", "bf16", "e4m3", "f16"])
 def test_tvc_every_mode(dims, code):
     A, Ao, scales = gu.inputs(dims, code)
     for k in range(len(dims)):
@@ -47,13 +47,13 @@ def test_tvc_every_mode(dims, code):
 @pytest.mark.parametrize("dims", [(3, 50, 64), (5, 1000), (4, 100, 7), (300, 40)])
 def test_narrow_storage_error_vs_source(dims):
     src = synth.tensor("lognormal", 0, dims).astype(np.float32)
-    for code, bound in ((oracle.BF16, 2e-2), (oracle.E4M3, None)):
+    for code, bound in ((oracle.BF16, 2e-2), (oracle.E4M3, None), (oracle.F16, 2e-3)):
         codes, scales = oracle.quantise(src, code)
         for k in range(len(dims)):
             x = gu.vec(code, dims[k], synth.stream_x(k))
             got = gu.gpu_tvc(tg, codes, k, x, scales)
             err_src = gu.rel_l2(got, oracle.tvc(src, k, x))
-            print(f"storage error {['f64','f32','bf16','e4m3'][code]} {dims} mode {k}: {err_src:.3e}")
+            print(f"storage error {['f64','f32','bf16','e4m3','f16'][code]} {dims} mode {k}: {err_src:.3e}")
             if bound is not None:
                 assert err_src <= bound
             else:
@@ -117,7 +117,7 @@ def test_alpha_beta(code):
         assert gu.rel_l2(yn.cpu().numpy(), 2.0 * oracle.tvc(Ao, k, x)) <= gu.TOL[code]
 
 
-@pytest.mark.parametrize("code", CODES, ids=["f64", "f32", "bf16", "e4m3"])
+@pytest.mark.parametrize("code", CODES, ids=["f64", "f32", "bf16", "e4m3", "f16"])
 def test_misaligned_base(code):
     dims = (6, 40, 48)
     A, Ao, scales = gu.inputs(dims, code)
