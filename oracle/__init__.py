@@ -25,7 +25,7 @@ import numpy as np
 __all__ = [
     "F64", "F32", "BF16", "E4M3", "F16", "build", "tvc", "tvc_grad_x", "tvc_grad_A",
     "hopm", "hopm3", "quantise", "decode_bf16", "decode_e4m3", "decode_f16",
-    "bf16_from_f32", "e4m3_from_f32", "f16_from_f32", "dequantise", "OracleError",
+    "bf16_from_f32", "e4m3_from_f32", "f16_from_f32", "dequantise", "OracleError", "dhopm_touched",
 ]
 
 F64, F32, BF16, E4M3, F16 = 0, 1, 2, 3, 4
@@ -84,6 +84,8 @@ def _load():
             lib.oracle_decode_f16.restype = D
             lib.oracle_f16_from_f32.argtypes = [ctypes.c_float]
             lib.oracle_f16_from_f32.restype = ctypes.c_uint16
+            lib.oracle_dhopm_touched.argtypes = [I, L, I, I, I, I]
+            lib.oracle_dhopm_touched.restype = L
             _lib = lib
     return _lib
 
@@ -251,3 +253,13 @@ def dequantise(codes, scales) -> np.ndarray:
     vals = table[codes]
     s = np.asarray(scales, dtype=np.float64).reshape((-1,) + (1,) * (codes.ndim - 1))
     return vals * s
+
+
+def dhopm_touched(d: int, n: int, p: int, s: int, j: int, three: bool = False) -> int:
+    """Touched elements of one process in external iteration j of the
+    distributed HOPM on n^d split along s over p processes (n % p == 0):
+    the canonical chain, or Algorithm 1's with three=True."""
+    r = int(_load().oracle_dhopm_touched(int(d), int(n), int(p), int(s), int(j), int(bool(three))))
+    if r < 0:
+        raise ValueError("invalid distributed-HOPM shape")
+    return r

@@ -432,6 +432,68 @@ uint8_t oracle_e4m3_from_f32(float f) {
   return (uint8_t)(s | code);
 }
 
+/* -------------------------------------------- distributed byte model */
+
+/* Touched elements of ONE process in external iteration j of the
+ * distributed HOPM (Section 4.2) on a hypersquare tensor n^d split along
+ * dimension s over p processes with n divisible by p, counted as in Eq. 3:
+ * a contraction touches its whole input, its whole output and the part of
+ * the vector it uses; the normalisation touches 3 x the length the process
+ * normalises (n/p for j = s, whose pieces are gathered afterwards; n for
+ * j != s, after the sum over processes).  Inter-process traffic is not
+ * counted (as in Eq. 4-7).  Sizes only: no arithmetic.
+ *   three = 0: the canonical chain (every other mode, ascending, from A);
+ *   three = 1: Algorithm 1's chain (the prefix W carried from iteration
+ *              j-1; iterations 0..j-1 are walked to rebuild it, only
+ *              iteration j is counted).
+ * Returns -1 for invalid arguments. */
+static int64_t dm_size(const int64_t* sz, int d) { return prod(sz, 0, d); }
+
+static void dm_contract(const int64_t* in, int d, int m, int64_t* out, int64_t* touched) {
+  int64_t isz = dm_size(in, d);
+  for (int q = 0; q < d; q++) out[q] = in[q];
+  out[m] = 1; /* the contracted mode keeps size one */
+  if (touched) *touched += isz + isz / in[m] + in[m];
+}
+
+int64_t oracle_dhopm_touched(int d, int64_t n, int p, int s, int j, int three) {
+  if (d < 2 || d > OR_MAXD || n < 1 || p < 1 || n % p != 0 || s < 0 || s >= d || j < 0 || j >= d) return -1;
+  int64_t base[OR_MAXD];
+  for (int q = 0; q < d; q++) base[q] = n;
+  base[s] = n / p;
+  int64_t t = 0;
+  const int64_t vec_len = (j == s) ? n / p : n;
+  if (!three) {
+    int64_t cur[OR_MAXD], nxt[OR_MAXD];
+    memcpy(cur, base, sizeof(int64_t) * (size_t)d);
+    for (int m = 0; m < d; m++) {
+      if (m == j) continue;
+      dm_contract(cur, d, m, nxt, &t);
+      memcpy(cur, nxt, sizeof(int64_t) * (size_t)d);
+    }
+    return t + 3 * vec_len;
+  }
+  int64_t W[OR_MAXD];
+  for (int jj = 0; jj <= j; jj++) {
+    int64_t* tc = (jj == j) ? &t : NULL;
+    int a = (jj > 0) ? 0 : 1;
+    int mu = (a > jj) ? a : jj;
+    int nu = (jj < d - 1) ? d - 1 : d - 2;
+    int64_t Y[OR_MAXD + 1][OR_MAXD];
+    int64_t Wj[OR_MAXD];
+    if (jj < 2)
+      dm_contract(base, d, a, Wj, tc);
+    else
+      dm_contract(W, d, mu - 1, Wj, tc);
+    int widx = (jj < 2) ? a : mu - 1;
+    memcpy(Y[widx], Wj, sizeof(int64_t) * (size_t)d);
+    if (mu + 1 <= d - 1) dm_contract(Y[mu + a - 1], d, mu + 1, Y[mu + 1], tc);
+    for (int k = mu + 2; k <= nu; k++) dm_contract(Y[k - 1], d, k, Y[k], tc);
+    memcpy(W, Wj, sizeof(int64_t) * (size_t)d);
+  }
+  return t + 3 * vec_len;
+}
+
 /* binary32 -> binary16, round to nearest, ties to even (IEEE 754), by
  * value: |f| >= 65520 (halfway between the largest finite half, 65504, and
  * 2^16) becomes infinity; below 2^-14 the quantum is 2^-24 (subnormals);

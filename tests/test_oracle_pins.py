@@ -409,3 +409,69 @@ def test_f16_tvc_is_the_tvc_of_the_decoded_values():
         ref = np.tensordot(vals, x, axes=([k], [0]))
         assert np.allclose(oracle.tvc(codes, k, x, scales=scales), ref, rtol=1e-13, atol=0)
         assert np.allclose(oracle.tvc(codes, k, x), ref, rtol=1e-13, atol=0)
+
+
+# ------------------------------------------- distributed byte model (Eq. 4-7)
+
+def _eq_terms(d, n, p):
+    """p * m_seq of Eq. 3 and helpers (integers: every term multiplied by p)."""
+    m_seq = n ** d + 2 * sum(n ** k for k in range(2, d)) + (d + 3) * n
+    return m_seq
+
+
+def _sum_pow(lo, hi, n):
+    return sum(n ** k for k in range(lo, hi + 1))
+
+
+@pytest.mark.parametrize("d,n", [(2, 6), (3, 6), (3, 12), (4, 6), (5, 4), (6, 4), (10, 4)])
+def test_dhopm_byte_model_equations_4_to_7(d, n):
+    for p in [q for q in range(1, n + 1) if n % q == 0]:
+        m_seq = _eq_terms(d, n, p)
+        M = {}
+        for s in range(d):
+            tot = 0
+            for j in range(d):
+                got = oracle.dhopm_touched(d, n, p, s, j)
+                tot += got
+                if j == s:  # Eq. 4 (regular division: the brackets are exact)
+                    want_p = n ** d + 2 * _sum_pow(2, d - 1, n) + 4 * n + (d - 1) * n * p
+                else:  # Eq. 5, l = 0 for j < s and 1 for j > s
+                    l = 0 if j < s else 1
+                    want_p = m_seq + (p - 1) * (2 * _sum_pow(2, d - s - l, n) + (d + 2) * n)
+                assert got * p == want_p, (d, n, p, s, j, got)
+            # Eq. 6: the process's total over the d external iterations
+            want_p = (d * m_seq + (p - 1) * (d - 1) * (d + 3) * n
+                      + (p - 1) * (s * 2 * _sum_pow(2, d - s, n) + (d - s - 1) * 2 * _sum_pow(2, d - s - 1, n)))
+            assert tot * p == want_p, (d, n, p, s)
+            M[s] = tot
+        for s in range(1, d):  # Eq. 7: the recursion over the split dimension
+            assert (M[s - 1] - M[s]) * p == (p - 1) * ((d - s - 1) * 2 * n ** (d - s) + (s - 1) * 2 * n ** (d - s + 1))
+
+
+@pytest.mark.parametrize("d,n", [(2, 5), (3, 4), (4, 3), (5, 3)])
+def test_dhopm_byte_model_one_process_is_the_oracles_own_count(d, n):
+    """p = 1: the size-only counter equals the touched counts of the oracle's
+    HOPM runs (canonical chain: Eq. 3; three-buffer chain: Algorithm 1)."""
+    dims = (n,) * d
+    A = rand_tensor(dims)
+    a = oracle.hopm(A, ones_start(dims), iters=1)
+    b = oracle.hopm3(A, ones_start(dims), iters=1)
+    assert sum(oracle.dhopm_touched(d, n, 1, 0, j) for j in range(d)) == a["touched"][0]
+    assert sum(oracle.dhopm_touched(d, n, 1, 0, j, three=True) for j in range(d)) == b["touched"][0]
+    assert a["touched"][0] == d * _eq_terms(d, n, 1)
+
+
+def test_dhopm3_saving_is_flat_in_processes_and_split():
+    for d_s, n_s, lo_p, hi_p, lo, hi in golden("dhopm_byte_model.txt"):
+        d, n, lo, hi = int(d_s), int(n_s), float(lo), float(hi)
+        ratios = []
+        for p in [q for q in range(1, n + 1) if n % q == 0 and float(lo_p) <= q / n <= float(hi_p)]:
+            for s in range(d):
+                a = sum(oracle.dhopm_touched(d, n, p, s, j) for j in range(d))
+                b = sum(oracle.dhopm_touched(d, n, p, s, j, three=True) for j in range(d))
+                ratios.append(a / b)
+        assert ratios and lo <= min(ratios) and max(ratios) <= hi, (d, min(ratios), max(ratios))
+    # the minimum of about 3.3x for d = 10 sits at p = n (one slab per process)
+    assert 3.2 <= min(sum(oracle.dhopm_touched(10, 8, 8, s, j) for j in range(10)) /
+                      sum(oracle.dhopm_touched(10, 8, 8, s, j, three=True) for j in range(10))
+                      for s in range(10)) <= 3.4
