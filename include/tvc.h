@@ -19,7 +19,9 @@
  *   of the batched calls are HOST pointers read before the call returns.
  *   Tensors must be element-aligned; 16-byte alignment enables wider loads.
  * Types: tvc_dtype names the storage of A.  Vectors (x, y, gradients,
- *   prefix tensors) are FP64 for TVC_F64 and FP32 for every other type.
+ *   prefix tensors) are FP64 for TVC_F64 and TVC_F32D and FP32 for every
+ *   other type.  TVC_F32D (Section 5.5's single-double) reads binary32
+ *   elements and computes in FP64 like TVC_F64.
  *   TVC_BF16, TVC_E4M3 and TVC_F16 carry one FP32 scale per slab A[i_0, ...]
  *   (n_0 scales, device memory); an element's value is
  *   scale[i_0] * decode(code).  A NULL scale pointer means all scales are 1.
@@ -55,7 +57,8 @@ typedef enum {
   TVC_F32 = 1,  /* binary32 storage, FP32 accumulation                   */
   TVC_BF16 = 2, /* upper half of binary32, per-slab FP32 scale           */
   TVC_E4M3 = 3, /* OCP FP8 E4M3 (bias 7, max 448), per-slab FP32 scale   */
-  TVC_F16 = 4   /* IEEE binary16 (Section 5.5's half-single), FP32 math  */
+  TVC_F16 = 4,  /* IEEE binary16 (Section 5.5's half-single), FP32 math  */
+  TVC_F32D = 5  /* binary32 storage, FP64 arithmetic (single-double)     */
 } tvc_dtype;
 
 typedef enum {

@@ -20,13 +20,13 @@ import threading
 import torch
 
 __all__ = [
-    "F64", "F32", "BF16", "E4M3", "F16", "TVCError", "load_library", "tvc", "tvc_workspace_size",
+    "F64", "F32", "BF16", "E4M3", "F16", "F32D", "TVCError", "load_library", "tvc", "tvc_workspace_size",
     "dtype_code", "library_path", "kernel_launches", "hopm", "hopm_workspace_size", "HopmResult", "quantise", "tvc_backward", "TVCFunction", "tvc_autograd", "hopm_backward", "HOPMFunction", "hopm_autograd", "TVCBatch", "HOPMBatch", "BATCH_PREUPLOADED",
     "split_1d", "slab_extract", "slab_insert", "split_tensor", "dtvc", "dtvc_workspace_size", "dhopm",
     "dhopm_workspace_size",
 ]
 
-F64, F32, BF16, E4M3, F16 = 0, 1, 2, 3, 4
+F64, F32, BF16, E4M3, F16, F32D = 0, 1, 2, 3, 4, 5
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 library_path = os.path.join(_HERE, "_lib", "libtvc_gb300.so")
@@ -135,7 +135,15 @@ def dtype_code(t: torch.Tensor) -> int:
 
 
 def vec_dtype(code: int) -> torch.dtype:
-    return torch.float64 if code == F64 else torch.float32
+    return torch.float64 if code in (F64, F32D) else torch.float32
+
+
+def _with_vectors(code: int, vec: torch.Tensor | None) -> int:
+    """FP32 storage with float64 vectors selects single-double (F32D: FP64
+    arithmetic on binary32 elements, Section 5.5)."""
+    if code == F32 and vec is not None and vec.dtype == torch.float64:
+        return F32D
+    return code
 
 
 def _dims_array(shape):
@@ -188,7 +196,7 @@ def tvc(A: torch.Tensor, mode: int, x: torch.Tensor, *, y: torch.Tensor | None =
     the library's own workspace is used.
     """
     lib = load_library()
-    code = dtype_code(A)
+    code = _with_vectors(dtype_code(A), x)
     shape = tuple(A.shape) if shape is None else tuple(int(n) for n in shape)
     if not 0 <= mode < len(shape):
         raise ValueError("mode out of range")
@@ -248,7 +256,7 @@ def hopm(A: torch.Tensor, xs, iters: int, tol: float = 0.0, *, scales: torch.Ten
     not read); unless ``inplace`` they are copied first.  Returns device
     tensors: x, lam, sweeps, status, lam_hist (lambda per completed sweep)."""
     lib = load_library()
-    code = dtype_code(A)
+    code = _with_vectors(dtype_code(A), xs[-1] if len(xs) else None)
     shape = tuple(A.shape) if shape is None else tuple(int(n) for n in shape)
     if len(shape) < 2 or len(xs) != len(shape):
         raise ValueError("hopm needs order >= 2 and one start vector per mode")
@@ -304,7 +312,7 @@ def tvc_backward(A: torch.Tensor | None, mode: int, x: torch.Tensor | None, gy: 
     gx = sum_{i,l} A[i,j,l] gy[i,l]; gA = gy (x) x along mode (+ beta_A gA)."""
     lib = load_library()
     if code is None:
-        code = dtype_code(A)
+        code = _with_vectors(dtype_code(A), gy)
     shape = tuple(A.shape) if shape is None else tuple(int(n) for n in shape)
     vt = vec_dtype(code)
     dev = gy.device
@@ -344,6 +352,8 @@ class TVCFunction(torch.autograd.Function):
         need_A = ctx.needs_input_grad[0] and A.is_floating_point() and A.dtype in (torch.float64, torch.float32)
         gy = gy.contiguous()
         gx, gA = tvc_backward(A, ctx.mode, x, gy, need_x=need_x, need_A=need_A, scales=scales)
+        if gA is not None and gA.dtype != A.dtype:  # single-double: FP64 gradient of FP32 storage
+            gA = gA.to(A.dtype)
         return gA, gx, None, None
 
 
@@ -358,7 +368,7 @@ def hopm_backward(A: torch.Tensor, x0, iters: int, gx_final=None, g_lambda: torc
     (gA, gstart) given upstream gradients of the final vectors (list,
     entries may be None) and of lambda (1-element float64 device tensor)."""
     lib = load_library()
-    code = dtype_code(A)
+    code = _with_vectors(dtype_code(A), x0[-1] if len(x0) else None)
     shape = tuple(A.shape) if shape is None else tuple(int(n) for n in shape)
     vt = vec_dtype(code)
     d = len(shape)
@@ -398,6 +408,8 @@ class HOPMFunction(torch.autograd.Function):
     def backward(ctx, g_lam, *gxs):
         A, *x0 = ctx.saved_tensors
         gA, gstart = hopm_backward(A, x0, ctx.iters, list(gxs), g_lam)
+        if gA.dtype != A.dtype:  # single-double: FP64 gradient of FP32 storage
+            gA = gA.to(A.dtype)
         return (gA, None) + tuple(gstart)
 
 
@@ -578,6 +590,7 @@ def dtvc(slabs, starts, shape, s: int, mode: int, x: torch.Tensor, *, y=None, sc
     lib = load_library()
     shape = tuple(int(n) for n in shape)
     parts, code, arr, ptrs = _split_args(slabs, starts, shape)
+    code = _with_vectors(code, x)
     vt = vec_dtype(code)
     if x.dtype != vt or x.numel() != shape[mode]:
         raise ValueError(f"x must be {vt} with {shape[mode]} entries")
@@ -626,6 +639,7 @@ def dhopm(slabs, starts, shape, s: int, xs, iters: int, tol: float = 0.0, *, sca
     if len(shape) < 2 or len(xs) != len(shape):
         raise ValueError("dhopm needs order >= 2 and one start vector per mode")
     parts, code, arr, ptrs = _split_args(slabs, starts, shape)
+    code = _with_vectors(code, xs[-1])
     vt = vec_dtype(code)
     xs = [v if inplace else v.clone() for v in xs]
     for m, v in enumerate(xs):

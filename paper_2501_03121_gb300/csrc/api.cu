@@ -42,7 +42,7 @@ tvc_status make_shape(int order, const int64_t* dims, int mode, Shape* s) {
   return TVC_OK;
 }
 
-bool valid_dtype(int dt) { return dt >= TVC_F64 && dt <= TVC_F16; }
+bool valid_dtype(int dt) { return dt >= TVC_F64 && dt <= TVC_F32D; }
 
 size_t elem_size(tvc_dtype dt) {
   switch (dt) {
@@ -51,11 +51,12 @@ size_t elem_size(tvc_dtype dt) {
     case TVC_BF16: return 2;
     case TVC_E4M3: return 1;
     case TVC_F16: return 2;
+    case TVC_F32D: return 4;
   }
   return 0;
 }
 
-size_t vec_size(tvc_dtype dt) { return dt == TVC_F64 ? 8 : 4; }
+size_t vec_size(tvc_dtype dt) { return (dt == TVC_F64 || dt == TVC_F32D) ? 8 : 4; }
 
 tvc_status cuda_status(cudaError_t e) { return e == cudaSuccess ? TVC_OK : TVC_ERR_CUDA; }
 

@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(kBT) tvc_gradx_kernel(const GradArgs<DT> a) {
   const int64_t ncol = a.uv / VEC;  // VEC divides v, hence uv
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   __shared__ double red[kBW][JC];
-  if constexpr (DT == TVC_F64) {
+  if constexpr (kF64Acc<DT>) {
     float s[JC], c[JC];
     double d[JC];
 #pragma unroll
@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(kBT) tvc_gradx_kernel(const GradArgs<DT> a) {
         gs[e] = split_x(gd[e]);
       }
       const T* p = a.A + (i * a.nk + j0) * a.v + l;
-      double r[JC][VEC];
+      typename E::C r[JC][VEC];
 #pragma unroll
       for (int q = 0; q < JC; q++)
         if (q < jn) E::template load<VEC>(p + (int64_t)q * a.v, r[q]);
@@ -238,7 +238,7 @@ GxPlan plan_gx(const Shape& s, tvc_dtype dt, const void* A) {
   const int cand = (dt == TVC_F64) ? 2 : ((dt == TVC_F32) ? 4 : 4);
   g.vec = 1;
   if (s.v % cand == 0 && aligned(A, (size_t)cand * es)) g.vec = cand;
-  g.jc = (dt == TVC_F64) ? 8 : 16;
+  g.jc = (dt == TVC_F64 || dt == TVC_F32D) ? 8 : 16;
   g.nchunks = cdiv(s.nk, g.jc);
   const int64_t cols = s.uv / g.vec;
   const int64_t want = std::max<int64_t>(1, (int64_t)device_sms() * 4 / std::max<int64_t>(1, g.nchunks));
@@ -251,7 +251,7 @@ GxPlan plan_gx(const Shape& s, tvc_dtype dt, const void* A) {
 template <tvc_dtype DT, int VEC>
 void launch_gx(const GxPlan& g, const GradArgs<DT>& a, cudaStream_t st) {
   dim3 grid((unsigned)g.nblk, (unsigned)g.nchunks);
-  if constexpr (DT == TVC_F64)
+  if constexpr (kF64Acc<DT>)
     tvc_gradx_kernel<DT, VEC, 8><<<grid, kBT, 0, st>>>(a);
   else
     tvc_gradx_kernel<DT, VEC, 16><<<grid, kBT, 0, st>>>(a);
@@ -305,6 +305,7 @@ tvc_status grad_x(const Shape& s, const void* A, const void* gy, void* gx, tvc_d
   }
   switch (dt) {
     case TVC_F64: return run_gx<TVC_F64>(g, s, A, gy, gx, scales, ws, st);
+    case TVC_F32D: return run_gx<TVC_F32D>(g, s, A, gy, gx, scales, ws, st);
     case TVC_F32: return run_gx<TVC_F32>(g, s, A, gy, gx, scales, ws, st);
     case TVC_BF16: return run_gx<TVC_BF16>(g, s, A, gy, gx, scales, ws, st);
     case TVC_E4M3: return run_gx<TVC_E4M3>(g, s, A, gy, gx, scales, ws, st);
@@ -365,7 +366,7 @@ extern "C" tvc_status tvc_backward(const void* A, int order, const int64_t* dims
     if (st != TVC_OK) return st;
   }
   if (gA) {
-    if (dtype == TVC_F64)
+    if (vs == 8)  // FP64 vectors: TVC_F64, TVC_F32D
       st = grad_A<double>(s, static_cast<const double*>(x), static_cast<const double*>(gy), static_cast<double*>(gA),
                           beta_A, cs);
     else

@@ -152,6 +152,25 @@ struct Elem<TVC_F32> {
   }
 };
 
+// FP32 storage with FP64 arithmetic and FP64 vectors (Section 5.5's
+// single-double): elements load as binary32 and enter the float-float
+// products without the hi/lo split a binary64 element needs.
+template <>
+struct Elem<TVC_F32D> {
+  using T = float;
+  using V = double;
+  using C = float;
+  static constexpr int kSize = 4;
+  template <int VEC, bool PLAIN = false>
+  __device__ __forceinline__ static void load(const T* p, C (&val)[VEC]) {
+    Elem<TVC_F32>::template load<VEC, PLAIN>(p, val);
+  }
+};
+
+// Storage types whose arithmetic and vectors are FP64.
+template <tvc_dtype DT>
+inline constexpr bool kF64Acc = (DT == TVC_F64 || DT == TVC_F32D);
+
 // BF16: the code is the upper half of a binary32, so decoding is a shift.
 template <>
 struct Elem<TVC_BF16> {
@@ -353,6 +372,39 @@ __device__ __forceinline__ void df_mac(float& s, float& c, double& d, double a, 
   }
 }
 
+// (s, c) += a * x for one binary32 element a (FP32 storage, FP64
+// arithmetic): a is exact as it stands, so only the TwoProduct against the
+// two pieces of x remains.  Window: |a| in [2^-64, 2^64) (biased exponent
+// 63 .. 190), zeros, subnormals and Inf/NaN take the exact DFMA.
+static __device__ __noinline__ double dfma_slow_f(float a, const double* xp, double d) {
+  return fma((double)a, *xp, d);
+}
+
+// Nonzero when the binary32 a is outside its window: with the sign shifted
+// out, exponent field - 63 wraps below the window, and 128 binades span
+// exactly 2^31, so bit 31 of the difference is the test.
+__device__ __forceinline__ uint32_t df_out_of_window(float a) {
+  return (((uint32_t)__float_as_uint(a) << 1) - (63u << 24)) >> 31;
+}
+
+__device__ __forceinline__ void df_mac_fast(float& s, float& c, float a, XSplit xs) {
+  const float p = __fmul_rn(a, xs.xh);
+  float e = __fmaf_rn(a, xs.xh, -p);
+  e = __fmaf_rn(a, xs.xl, e);
+  float t, err;
+  two_sum(s, p, t, err);
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(err, e));
+}
+
+__device__ __forceinline__ void df_mac(float& s, float& c, double& d, float a, const double* xp, XSplit xs) {
+  if (df_out_of_window(a) == 0 && xs.xh == xs.xh) {
+    df_mac_fast(s, c, a, xs);
+  } else {
+    d = dfma_slow_f(a, xp, d);
+  }
+}
+
 // df_mac without the window test, for elements already known to be in the
 // window (see df_out_of_window); x must be in its window too.
 __device__ __forceinline__ void df_mac_fast(float& s, float& c, double a, XSplit xs) {
@@ -385,6 +437,11 @@ __device__ __forceinline__ uint32_t df_out_of_window(double a) {
 }
 
 __device__ __forceinline__ void df_step(float& s, float& c, uint32_t& bad, double a, XSplit xs) {
+  bad |= df_out_of_window(a);
+  df_mac_fast(s, c, a, xs);
+}
+
+__device__ __forceinline__ void df_step(float& s, float& c, uint32_t& bad, float a, XSplit xs) {
   bad |= df_out_of_window(a);
   df_mac_fast(s, c, a, xs);
 }
@@ -427,17 +484,20 @@ struct AccF64 {
       d[e] = 0.0;
     }
   }
-  __device__ __forceinline__ void emul(const double (&a)[VEC], const double* xp, XSplit xs) {
+  template <class A>  // double (FP64 storage) or float (FP32 storage)
+  __device__ __forceinline__ void emul(const A (&a)[VEC], const double* xp, XSplit xs) {
 #pragma unroll
     for (int e = 0; e < VEC; e++) df_mac(s[e], c[e], d[e], a[e], xp, xs);
   }
   // One column, its own x entry (row-wise kernels).
-  __device__ __forceinline__ void emul1(int e, double a, const double* xp, XSplit xs) {
+  template <class A>
+  __device__ __forceinline__ void emul1(int e, A a, const double* xp, XSplit xs) {
     df_mac(s[e], c[e], d[e], a, xp, xs);
   }
-  __device__ __forceinline__ void dfma(const double (&a)[VEC], double x) {
+  template <class A>
+  __device__ __forceinline__ void dfma(const A (&a)[VEC], double x) {
 #pragma unroll
-    for (int e = 0; e < VEC; e++) d[e] = fma(a[e], x, d[e]);
+    for (int e = 0; e < VEC; e++) d[e] = fma((double)a[e], x, d[e]);
   }
   __device__ __forceinline__ void fold() {
 #pragma unroll

@@ -251,7 +251,7 @@ struct Ctx {
   void* wchain = nullptr;  // W_j of the running sweep
   void* wother = nullptr;
 
-  bool f64() const { return dt == TVC_F64; }
+  bool f64() const { return vdt == TVC_F64; }  // FP64 vectors (TVC_F64, TVC_F32D)
 
   void tvc(const void* X, const Shape& s, const void* xv, void* y, tvc_dtype t, const float* sc, double beta = 0.0) {
     if (rc != TVC_OK) return;
@@ -365,7 +365,7 @@ FwdLayout fwd_layout(int order, const int64_t* dims, tvc_dtype dt, size_t base) 
   c.d = order;
   for (int i = 0; i < order; i++) c.n[i] = dims[i];
   c.dt = dt;
-  c.vdt = (dt == TVC_F64) ? TVC_F64 : TVC_F32;
+  c.vdt = (dt == TVC_F64 || dt == TVC_F32D) ? TVC_F64 : TVC_F32;
   void* dummy[TVC_MAX_ORDER] = {};
   c.sweep(dummy, 0.0, nullptr, nullptr, nullptr, nullptr, nullptr);
   size_t off = base;
@@ -395,7 +395,7 @@ void bind(Ctx& c, const FwdLayout& L, void* ws, const void* A, int order, const 
   for (int i = 0; i < order; i++) c.n[i] = dims[i];
   c.N = prod_range(dims, 0, order);
   c.dt = dt;
-  c.vdt = (dt == TVC_F64) ? TVC_F64 : TVC_F32;
+  c.vdt = (dt == TVC_F64 || dt == TVC_F32D) ? TVC_F64 : TVC_F32;
   c.scales = scales;
   c.st = st;
   c.state = reinterpret_cast<HopmState*>(w + L.off_state);
@@ -482,7 +482,7 @@ tvc_status dhopm_launch(const void* const* slabs, int parts, const int64_t* star
   g.d = order;
   for (int i = 0; i < order; i++) g.n[i] = dims[i];
   g.dt = dt;
-  g.vdt = (dt == TVC_F64) ? TVC_F64 : TVC_F32;
+  g.vdt = (dt == TVC_F64 || dt == TVC_F32D) ? TVC_F64 : TVC_F32;
   g.st = st;
   g.state = reinterpret_cast<HopmState*>(w + D.off_state);
   g.done = &g.state->done;
@@ -604,7 +604,7 @@ BwdLayout bwd_layout(int order, const int64_t* dims, tvc_dtype dt, int iters) {
   c.d = order;
   for (int i = 0; i < order; i++) c.n[i] = dims[i];
   c.dt = dt;
-  c.vdt = (dt == TVC_F64) ? TVC_F64 : TVC_F32;
+  c.vdt = (dt == TVC_F64 || dt == TVC_F32D) ? TVC_F64 : TVC_F32;
   void* dummy[TVC_MAX_ORDER] = {};
   for (int j = 0; j < order; j++) {
     c.tvcA(j, nullptr, nullptr);

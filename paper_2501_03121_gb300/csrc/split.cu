@@ -264,7 +264,7 @@ extern "C" tvc_status dtvc(const void* const* slabs, int parts, const int64_t* s
   if (mode == s) {
     int64_t N = 1;
     for (int i = 0; i < order; i++) N *= dims[i];
-    return combine_parts(partial, parts, nullptr, N / dims[mode], y[0], dtype == TVC_F64 ? TVC_F64 : TVC_F32, 0,
+    return combine_parts(partial, parts, nullptr, N / dims[mode], y[0], vec_size(dtype) == 8 ? TVC_F64 : TVC_F32, 0,
                          alpha, beta, st, nullptr);
   }
   return TVC_OK;

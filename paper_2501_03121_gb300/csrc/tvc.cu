@@ -139,12 +139,12 @@ __global__ void __launch_bounds__(kThreads) tvc_cols_kernel(const TvcArgs<DT> a)
   const T* p = a.A + (i * a.nk + j0) * st + l;
   int64_t j = j0;
   int blk = 0;
-  if constexpr (DT == TVC_F64) {
+  if constexpr (kF64Acc<DT>) {
     const double* x = static_cast<const double*>(a.x);
     AccF64<VEC> acc;
     acc.init();
     for (; j + 8 <= j1; j += 8) {
-      double r[8][VEC];
+      typename E::C r[8][VEC];
 #pragma unroll
       for (int q = 0; q < 8; q++) E::template load<VEC>(p + q * st, r[q]);
 #pragma unroll
@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(kThreads) tvc_cols_kernel(const TvcArgs<DT> a)
       }
     }
     if (j < j1) {  // the last < 8 rows: all loads in flight at once
-      double r[7][VEC];
+      typename E::C r[7][VEC];
 #pragma unroll
       for (int q = 0; q < 7; q++)
         if (j + q < j1) E::template load<VEC>(p + q * st, r[q]);
@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(kThreads) tvc_rows_kernel(const TvcArgs<DT> a)
   const int64_t jt0 = j0 + ngroups * UNR * STEP;  // start of the ragged tail
   int64_t j = j0 + p * VEC;
   int blk = 0;
-  if constexpr (DT == TVC_F64) {
+  if constexpr (kF64Acc<DT>) {
     const double* x = static_cast<const double*>(a.x);
     AccF64<VEC> acc;
     acc.init();
@@ -313,7 +313,7 @@ __global__ void __launch_bounds__(kThreads) tvc_rows_kernel(const TvcArgs<DT> a)
     for (int64_t g0 = 0; g0 < ngroups; g0 += kGroupsPerFold) {
       const int64_t g1 = min(ngroups, g0 + kGroupsPerFold);
       for (int64_t g = g0; g < g1; g++, j += UNR * STEP) {
-        double r[UNR][VEC];
+        typename E::C r[UNR][VEC];
 #pragma unroll
         for (int q = 0; q < UNR; q++) E::template load<VEC>(rp + j + q * STEP, r[q]);
 #pragma unroll
@@ -338,7 +338,7 @@ __global__ void __launch_bounds__(kThreads) tvc_rows_kernel(const TvcArgs<DT> a)
     }
     if (active)
       for (int64_t jj = jt0 + p; jj < j1; jj += G) {
-        double r[1];
+        typename E::C r[1];
         E::template load<1>(rp + jj, r);
         acc.emul1(0, r[0], x + jj, ldxs(a.xs + jj));
       }
@@ -412,7 +412,7 @@ __global__ void __launch_bounds__(kThreads) tvc_rows_kernel(const TvcArgs<DT> a)
 // accumulators, folded into a compensated sum every 64 products.
 template <tvc_dtype DT, int VEC, int RB, int UNR>
 __global__ void __launch_bounds__(kThreads) tvc_rows_multi_kernel(const TvcArgs<DT> a) {
-  static_assert(DT != TVC_F64, "FP64 rows use the float-float kernels");
+  static_assert(!kF64Acc<DT>, "FP64 arithmetic rows use the float-float kernels");
   static_assert(VEC * sizeof(typename Elem<DT>::T) == 16, "16-byte pieces");
   if (skip(a.done)) return;
   using E = Elem<DT>;
@@ -498,10 +498,12 @@ __global__ void __launch_bounds__(kThreads) tvc_rows_multi_kernel(const TvcArgs<
 // with full-warp FP64 instructions.  The FP64 pipe takes a warp instruction
 // at the same cost whatever its active mask, so converting per pass would
 // spend it G times over.  Products and reductions stay on the FP32 pipe.
-template <int VEC, int G, int DQ>
-__global__ void __launch_bounds__(kThreads) tvc_rows_f64_slots_kernel(const TvcArgs<TVC_F64> a) {
+template <tvc_dtype DT, int VEC, int G, int DQ>
+__global__ void __launch_bounds__(kThreads) tvc_rows_f64_slots_kernel(const TvcArgs<DT> a) {
   if (skip(a.done)) return;
-  using E = Elem<TVC_F64>;
+  static_assert(kF64Acc<DT>, "FP64 arithmetic");
+  using E = Elem<DT>;
+  using T = typename E::T;
   constexpr int STEP = G * VEC;
   constexpr int GPW = kWarp / G;
   constexpr int UNR = (VEC == 1) ? 8 : 4;  // 8-byte loads: more of them in flight
@@ -518,7 +520,7 @@ __global__ void __launch_bounds__(kThreads) tvc_rows_f64_slots_kernel(const TvcA
   for (int it = 0; it < G; it++) {
     const int64_t row = wrow0 + it * GPW + gw;
     const bool active = row < a.u;
-    const double* rp = a.A + (active ? row : 0) * a.nk;
+    const T* rp = a.A + (active ? row : 0) * a.nk;
     float sacc = 0.0f, cacc = 0.0f;
     double d = 0.0;
     // 8-byte loads (VEC == 1): branch-free steps (df_step) with the window
@@ -533,7 +535,7 @@ __global__ void __launch_bounds__(kThreads) tvc_rows_f64_slots_kernel(const TvcA
       // odd rows of 63 .. 979 elements: 1.3-1.8x; with 16-byte loads the
       // unpredicated loop below measured faster.)
       for (int64_t jj = j0 + p * VEC; jj < j1; jj += UNR * STEP) {
-        double r[UNR][VEC];
+        typename E::C r[UNR][VEC];
 #pragma unroll
         for (int q = 0; q < UNR; q++)
           if (jj + q * STEP < j1) E::template load<VEC>(rp + jj + q * STEP, r[q]);
@@ -543,7 +545,7 @@ __global__ void __launch_bounds__(kThreads) tvc_rows_f64_slots_kernel(const TvcA
 #pragma unroll
           for (int e = 0; e < VEC; e++) {
             if (q < DQ)  // this share of the steps runs on the FP64 pipe
-              d = fma(r[q][e], __ldg(x + jj + q * STEP + e), d);
+              d = fma((double)r[q][e], __ldg(x + jj + q * STEP + e), d);
             else
               df_step(sacc, cacc, bad, r[q][e], ldxs(a.xs + jj + q * STEP + e));
           }
@@ -552,7 +554,7 @@ __global__ void __launch_bounds__(kThreads) tvc_rows_f64_slots_kernel(const TvcA
     } else if (active) {
       int64_t jj = j0 + p * VEC;
       for (; jj + (UNR - 1) * STEP + VEC <= j1; jj += UNR * STEP) {
-        double r[UNR][VEC];
+        typename E::C r[UNR][VEC];
 #pragma unroll
         for (int q = 0; q < UNR; q++) E::template load<VEC>(rp + jj + q * STEP, r[q]);
 #pragma unroll
@@ -560,13 +562,13 @@ __global__ void __launch_bounds__(kThreads) tvc_rows_f64_slots_kernel(const TvcA
 #pragma unroll
           for (int e = 0; e < VEC; e++) {
             if (q < DQ)
-              d = fma(r[q][e], __ldg(x + jj + q * STEP + e), d);
+              d = fma((double)r[q][e], __ldg(x + jj + q * STEP + e), d);
             else
               df_mac(sacc, cacc, d, r[q][e], x + jj + q * STEP + e, ldxs(a.xs + jj + q * STEP + e));
           }
       }
       for (; jj + VEC <= j1; jj += STEP) {
-        double r[VEC];
+        typename E::C r[VEC];
         E::template load<VEC>(rp + jj, r);
 #pragma unroll
         for (int e = 0; e < VEC; e++) df_mac(sacc, cacc, d, r[e], x + jj + e, ldxs(a.xs + jj + e));
@@ -579,7 +581,7 @@ __global__ void __launch_bounds__(kThreads) tvc_rows_f64_slots_kernel(const TvcA
       d = 0.0;
       for (int64_t jj = j0 + p * VEC; jj < j1; jj += STEP)
 #pragma unroll
-        for (int e = 0; e < VEC; e++) d = fma(rp[jj + e], x[jj + e], d);
+        for (int e = 0; e < VEC; e++) d = fma((double)rp[jj + e], x[jj + e], d);
     }
     if (DQ > 0 && df_out_of_window(d) == 0) {  // fold the DFMA share into the pair
       df_add_double(sacc, cacc, d);
@@ -645,7 +647,7 @@ __global__ void __launch_bounds__(kThreads) tvc_rows_short_kernel(const TvcArgs<
 #pragma unroll
     for (int e = 0; e < VEC; e++) {
       const int j = p * VEC + q * step + e;
-      if constexpr (DT == TVC_F64) {
+      if constexpr (kF64Acc<DT>) {
         XSplit t = (j < nk) ? ldxs(a.xs + j) : XSplit{0.0f, 0.0f};
         xh[q][e] = t.xh;
         xl[q][e] = t.xl;
@@ -672,7 +674,7 @@ __global__ void __launch_bounds__(kThreads) tvc_rows_short_kernel(const TvcArgs<
         }
       }
     }
-    if constexpr (DT == TVC_F64) {
+    if constexpr (kF64Acc<DT>) {
       const double* x = static_cast<const double*>(a.x);
       float sb[B], cb[B];
       double db[B];
@@ -840,7 +842,7 @@ __global__ void __launch_bounds__(kTmaThreads, 2) tvc_rows_tma_kernel(const TvcA
     for (int e = 0; e < VEC; e++) {
       const int j = p * VEC + q * step + e;
       const bool ok = q < prm.nst && j < nk;
-      if constexpr (DT == TVC_F64) {
+      if constexpr (kF64Acc<DT>) {
         XSplit t = ok ? ldxs(a.xs + j) : XSplit{0.0f, 0.0f};
         xh[q][e] = t.xh;
         xl[q][e] = t.xl;
@@ -860,7 +862,7 @@ __global__ void __launch_bounds__(kTmaThreads, 2) tvc_rows_tma_kernel(const TvcA
   int64_t slot_row = -1;
   int nslot = 0;
   auto flush = [&]() {
-    if constexpr (DT == TVC_F64) {
+    if constexpr (kF64Acc<DT>) {
       if (lane < nslot && slot_row >= 0) emit(a, 0, slot_row, (slot_d + (double)slot_s) + (double)slot_c);
       slot_row = -1;
       nslot = 0;
@@ -892,7 +894,7 @@ __global__ void __launch_bounds__(kTmaThreads, 2) tvc_rows_tma_kernel(const TvcA
           for (int e = 0; e < VEC; e++) v[q][e] = (Cm)0;
         }
       }
-      if constexpr (DT == TVC_F64) {
+      if constexpr (kF64Acc<DT>) {
         const double* x = static_cast<const double*>(a.x);
         float sacc = 0.0f, cacc = 0.0f;
         double d = 0.0;
@@ -913,7 +915,7 @@ __global__ void __launch_bounds__(kTmaThreads, 2) tvc_rows_tma_kernel(const TvcA
             if (active && q < prm.nst && p * VEC + q * step < nk) {
               if (q < prm.dq) {
 #pragma unroll
-                for (int e = 0; e < VEC; e++) d = fma(v[q][e], x[p * VEC + q * step + e], d);
+                for (int e = 0; e < VEC; e++) d = fma((double)v[q][e], x[p * VEC + q * step + e], d);
               } else {
 #pragma unroll
                 for (int e = 0; e < VEC; e++) df_mac_fast(sacc, cacc, v[q][e], XSplit{xh[q][e], xl[q][e]});
@@ -979,7 +981,7 @@ __global__ void __launch_bounds__(kTmaThreads, 2) tvc_rows_tma_kernel(const TvcA
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[st]);
-    if constexpr (DT != TVC_F64) {
+    if constexpr (!kF64Acc<DT>) {
       // One coalesced store per lane for the warp's rows.
       for (int lr = lane; lr < RW; lr += kWarp) {
         const int64_t row = row0 + warp * RW + lr;
@@ -1010,7 +1012,7 @@ __global__ void __launch_bounds__(kThreads) tvc_slab_kernel(const TvcArgs<DT> a,
   const int64_t st = (int64_t)G * a.v;
   const T* p = a.A + (slab * a.nk + j0 + jj) * a.v + l;
   V tot;
-  if constexpr (DT == TVC_F64) {
+  if constexpr (kF64Acc<DT>) {
     const double* x = static_cast<const double*>(a.x);
     AccF64<1> acc;
     acc.init();
@@ -1021,7 +1023,7 @@ __global__ void __launch_bounds__(kThreads) tvc_slab_kernel(const TvcArgs<DT> a,
       // every group).  The branch-free df_step measured slower here.
       while (j + (UNR - 1) * G < j1) {
         for (int g = 0; g < kRB / UNR && j + (UNR - 1) * G < j1; g++, j += UNR * G, p += UNR * st) {
-          double r[UNR][1];
+          typename E::C r[UNR][1];
 #pragma unroll
           for (int q = 0; q < UNR; q++) E::template load<1>(p + q * st, r[q]);
 #pragma unroll
@@ -1030,7 +1032,7 @@ __global__ void __launch_bounds__(kThreads) tvc_slab_kernel(const TvcArgs<DT> a,
         acc.fold();
       }
       for (; j < j1; j += G, p += st) {
-        double r[1];
+        typename E::C r[1];
         E::template load<1>(p, r);
         acc.emul1(0, r[0], x + j, ldxs(a.xs + j));
       }
@@ -1069,7 +1071,7 @@ __global__ void __launch_bounds__(kThreads) tvc_slab_kernel(const TvcArgs<DT> a,
     if (jj + k < G) tot += other;
   }
   if (jj == 0) {
-    if constexpr (DT == TVC_F64)
+    if constexpr (kF64Acc<DT>)
       emit(a, blockIdx.y, slab * a.v + l, tot);
     else
       emit(a, blockIdx.y, slab * a.v + l, __fmul_rn(tot, out_scale(a, slab)));
@@ -1097,7 +1099,7 @@ __global__ void __launch_bounds__(kThreads) tvc_tile_kernel(const TvcArgs<DT> a,
   const size_t tile_bytes = ((size_t)R * S * sizeof(T) + 15) / 16 * 16;
   const int t = threadIdx.x;
   // Stage x.
-  if constexpr (DT == TVC_F64) {
+  if constexpr (kF64Acc<DT>) {
     XSplit* smx = reinterpret_cast<XSplit*>(smraw + tile_bytes);
     for (int j = t; j < nk; j += kThreads) smx[j] = ldxs(a.xs + j);
   } else {
@@ -1134,7 +1136,7 @@ __global__ void __launch_bounds__(kThreads) tvc_tile_kernel(const TvcArgs<DT> a,
   const T* row = sm + (int64_t)r * S + l;
   int jt = rot;
   int blk = 0;
-  if constexpr (DT == TVC_F64) {
+  if constexpr (kF64Acc<DT>) {
     const double* x = static_cast<const double*>(a.x);
     const XSplit* smx = reinterpret_cast<const XSplit*>(smraw + tile_bytes);
     AccF64<1> acc;
@@ -1189,10 +1191,10 @@ __global__ void __launch_bounds__(kThreads) tvc_tile_async_kernel(const TvcArgs<
   const int nk = (int)a.nk, v = (int)a.v;
   const int t = threadIdx.x;
   if ((int64_t)blockIdx.x >= ntiles) return;
-  const int x_bytes = ((nk * (DT == TVC_F64 ? (int)sizeof(XSplit) : 4)) + 15) / 16 * 16;
+  const int x_bytes = ((nk * (kF64Acc<DT> ? (int)sizeof(XSplit) : 4)) + 15) / 16 * 16;
   unsigned char* const buf0 = smraw + x_bytes;  // buffer k at buf0 + k * tile_cap
   __shared__ int x_out;  // FP64: some x_j outside the exact window
-  if constexpr (DT == TVC_F64) {
+  if constexpr (kF64Acc<DT>) {
     XSplit* smx = reinterpret_cast<XSplit*>(smraw);
     if (t == 0) x_out = 0;
     __syncthreads();
@@ -1244,7 +1246,7 @@ __global__ void __launch_bounds__(kThreads) tvc_tile_async_kernel(const TvcArgs<
     if (t < reff * v) {
       const int r = t / v, l = t - (t / v) * v;
       const T* row = reinterpret_cast<const T*>(buf0 + k * tile_cap + (k ? head1 : head0)) + (int64_t)r * S + l;
-      if constexpr (DT == TVC_F64) {
+      if constexpr (kF64Acc<DT>) {
         const double* x = static_cast<const double*>(a.x);
         const XSplit* smx = reinterpret_cast<const XSplit*>(smraw);
         // Branch-free float-float products with the window bits ORed
@@ -1258,7 +1260,7 @@ __global__ void __launch_bounds__(kThreads) tvc_tile_async_kernel(const TvcArgs<
           const int je = min(nk, jb + kRB);
           float sf = 0.0f, cf = 0.0f;
           for (int j = jb; j < je; j++) {
-            const double aj = reinterpret_cast<const double*>(row)[j * v];
+            const auto aj = row[j * v];  // binary64, or binary32 promoted in the product
             bad |= df_out_of_window(aj);
             df_mac_fast(sf, cf, aj, smx[j]);
           }
@@ -1267,7 +1269,7 @@ __global__ void __launch_bounds__(kThreads) tvc_tile_async_kernel(const TvcArgs<
         }
         if (bad) {
           d = 0.0;
-          for (int j = 0; j < nk; j++) d = fma(reinterpret_cast<const double*>(row)[j * v], x[j], d);
+          for (int j = 0; j < nk; j++) d = fma((double)row[j * v], x[j], d);
         }
         emit(a, 0, (i0 + r) * a.v + l, d);
       } else {
@@ -1500,6 +1502,7 @@ static Plan make_plan(const Shape& s, tvc_dtype dt, const void* A) { return make
 
 static Plan make_plan_impl(const Shape& s, tvc_dtype dt, const void* A, bool allow_staged) {
   Plan p;
+  const bool f64acc = (dt == TVC_F64 || dt == TVC_F32D);  // FP64 arithmetic (float-float kernels)
   const int sms = device_sms();
   const int64_t target_threads = (int64_t)sms * 2048;
   const int64_t S = s.nk * s.v;
@@ -1513,7 +1516,8 @@ static Plan make_plan_impl(const Shape& s, tvc_dtype dt, const void* A, bool all
     p.chunk = ceil_div(ceil_div(s.nk, splits), 8) * 8;
     p.splits = ceil_div(s.nk, p.chunk);
     p.grid = dim3((unsigned)ceil_div(threads, kThreads), (unsigned)p.splits);
-  } else if (s.v == 1 && (dt != TVC_F64 || f64_staged_rows(s.nk, A)) && allow_staged && staged_rows_enabled() &&
+  } else if (s.v == 1 && (!f64acc || (dt == TVC_F64 && f64_staged_rows(s.nk, A))) && allow_staged &&
+             staged_rows_enabled() &&
              aligned(A, 16) &&
              s.nk <= 8 * 32 * (int64_t)pick_vec(dt, s.nk, A, 4) && s.u >= 8) {
     // Staged short rows: tiles of R = 8*RW whole rows through shared memory.
@@ -1545,7 +1549,7 @@ static Plan make_plan_impl(const Shape& s, tvc_dtype dt, const void* A, bool all
     p.splits = 1;
     p.chunk = s.nk;
     p.grid = dim3((unsigned)std::max<int64_t>(1, std::min<int64_t>(p.ntiles, (int64_t)sms * 2)), 1);
-  } else if (s.v == 1 && dt != TVC_F64 && s.nk <= 8 * 32 * (int64_t)pick_vec(dt, s.nk, A, 4)) {
+  } else if (s.v == 1 && !f64acc && s.nk <= 8 * 32 * (int64_t)pick_vec(dt, s.nk, A, 4)) {
     // (FP64 rows, short or long, measured fastest with the grouped-row
     // kernel below; the staged kernel serves the narrow types.)
     // Short rows: the smallest group whose 4 steps cover the row (8 steps
@@ -1564,7 +1568,7 @@ static Plan make_plan_impl(const Shape& s, tvc_dtype dt, const void* A, bool all
     p.splits = 1;
     p.chunk = s.nk;
     p.grid = dim3((unsigned)std::max<int64_t>(1, blocks), 1);
-  } else if (s.v == 1 && dt != TVC_F64 && rows_multi_enabled() && pick_vec(dt, s.nk, A) * (int)es == 16) {
+  } else if (s.v == 1 && !f64acc && rows_multi_enabled() && pick_vec(dt, s.nk, A) * (int)es == 16) {
     // Long rows of the narrow types: RB rows per warp share each x piece.
     p.kind = K_ROWS_MULTI;
     p.vec = pick_vec(dt, s.nk, A);
@@ -1586,12 +1590,12 @@ static Plan make_plan_impl(const Shape& s, tvc_dtype dt, const void* A, bool all
     // go down to 1 lane, so that rows of 8 .. 15 elements fill one unrolled
     // pass of the slots kernel).
     int G = 32;
-    const int gmin = (dt == TVC_F64) ? 1 : 2;
+    const int gmin = f64acc ? 1 : 2;
     while (G > gmin && (int64_t)G * p.vec * 4 > s.nk) G >>= 1;
     p.G = G;
     const int64_t group = 4 * (int64_t)G * p.vec;  // one unrolled step of a group
     int64_t rows_per_block = (int64_t)kWarpsPerBlock * (kWarp / G);
-    if (dt == TVC_F64 && (G < 32 || (p.vec == 1 && s.nk <= f64_slots_max_nk()))) {
+    if (f64acc && (G < 32 || (p.vec == 1 && s.nk <= f64_slots_max_nk()))) {
       p.kind = K_ROWS_F64S;  // 32 rows per warp, results converted in slots
       rows_per_block = (int64_t)kWarpsPerBlock * kWarp;
     }
@@ -1619,7 +1623,7 @@ static Plan make_plan_impl(const Shape& s, tvc_dtype dt, const void* A, bool all
     p.R = (int)R;
     p.ntiles = ceil_div(s.u, R);
     p.vec16 = (int)(align_up((size_t)R * S * es, 16) + 32);  // tile capacity in bytes
-    const size_t x_bytes = align_up((size_t)s.nk * (dt == TVC_F64 ? sizeof(XSplit) : 4), 16);
+    const size_t x_bytes = align_up((size_t)s.nk * (f64acc ? sizeof(XSplit) : 4), 16);
     p.smem = x_bytes + 2 * (size_t)p.vec16;
     const int bps = (int)std::max<size_t>(1, std::min<size_t>(8, (size_t)(220 * 1024) / p.smem));
     p.splits = 1;
@@ -1638,7 +1642,7 @@ static Plan make_plan_impl(const Shape& s, tvc_dtype dt, const void* A, bool all
     p.chunk = s.nk;
     p.grid = dim3((unsigned)ceil_div(s.u, R), 1);
   }
-  if (dt == TVC_F64) p.ws_xs = align_up((size_t)s.nk * sizeof(XSplit), 256);
+  if (f64acc) p.ws_xs = align_up((size_t)s.nk * sizeof(XSplit), 256);
   if (p.splits > 1) p.ws_partial = align_up((size_t)p.splits * s.uv * vec_size(dt), 256);
   p.ws_total = p.ws_xs + p.ws_partial;
   return p;
@@ -1662,7 +1666,7 @@ static void launch_rows(const Plan& p, const TvcArgs<DT>& a, cudaStream_t st) {
   if constexpr (DT == TVC_F64) {
     if (p.vec == 2) launch_rows_vec<DT, 2>(p, a, st);
     else launch_rows_vec<DT, 1>(p, a, st);
-  } else if constexpr (DT == TVC_F32) {
+  } else if constexpr (DT == TVC_F32 || DT == TVC_F32D) {
     if (p.vec == 4) launch_rows_vec<DT, 4>(p, a, st);
     else launch_rows_vec<DT, 1>(p, a, st);
   } else if constexpr (sizeof(typename Elem<DT>::T) == 2) {  // BF16, F16
@@ -1684,7 +1688,7 @@ static void launch_rows_multi_rb(const Plan& p, const TvcArgs<DT>& a, cudaStream
 
 template <tvc_dtype DT>
 static void launch_rows_multi(const Plan& p, const TvcArgs<DT>& a, cudaStream_t st) {
-  if constexpr (DT != TVC_F64) {
+  if constexpr (!kF64Acc<DT>) {
     constexpr int VEC = 16 / (int)sizeof(typename Elem<DT>::T);
     if (p.rb == 2) launch_rows_multi_rb<DT, VEC, 2>(p, a, st);
     else if (p.rb == 8) launch_rows_multi_rb<DT, VEC, 8>(p, a, st);
@@ -1738,15 +1742,15 @@ static void launch_rows_tma(const Plan& p, const TvcArgs<DT>& a, cudaStream_t st
   }
 }
 
-template <int VEC, int DQ>
-static void launch_rows_f64s_dq(const Plan& p, const TvcArgs<TVC_F64>& a, cudaStream_t st) {
+template <tvc_dtype DT, int VEC, int DQ>
+static void launch_rows_f64s_dq(const Plan& p, const TvcArgs<DT>& a, cudaStream_t st) {
   switch (p.G) {
-    case 1: tvc_rows_f64_slots_kernel<VEC, 1, DQ><<<p.grid, kThreads, 0, st>>>(a); break;
-    case 2: tvc_rows_f64_slots_kernel<VEC, 2, DQ><<<p.grid, kThreads, 0, st>>>(a); break;
-    case 4: tvc_rows_f64_slots_kernel<VEC, 4, DQ><<<p.grid, kThreads, 0, st>>>(a); break;
-    case 8: tvc_rows_f64_slots_kernel<VEC, 8, DQ><<<p.grid, kThreads, 0, st>>>(a); break;
-    case 16: tvc_rows_f64_slots_kernel<VEC, 16, DQ><<<p.grid, kThreads, 0, st>>>(a); break;
-    default: tvc_rows_f64_slots_kernel<VEC, 32, DQ><<<p.grid, kThreads, 0, st>>>(a); break;
+    case 1: tvc_rows_f64_slots_kernel<DT, VEC, 1, DQ><<<p.grid, kThreads, 0, st>>>(a); break;
+    case 2: tvc_rows_f64_slots_kernel<DT, VEC, 2, DQ><<<p.grid, kThreads, 0, st>>>(a); break;
+    case 4: tvc_rows_f64_slots_kernel<DT, VEC, 4, DQ><<<p.grid, kThreads, 0, st>>>(a); break;
+    case 8: tvc_rows_f64_slots_kernel<DT, VEC, 8, DQ><<<p.grid, kThreads, 0, st>>>(a); break;
+    case 16: tvc_rows_f64_slots_kernel<DT, VEC, 16, DQ><<<p.grid, kThreads, 0, st>>>(a); break;
+    default: tvc_rows_f64_slots_kernel<DT, VEC, 32, DQ><<<p.grid, kThreads, 0, st>>>(a); break;
   }
 }
 
@@ -1762,12 +1766,12 @@ static int slots_dfma_steps() {
   return v;
 }
 
-template <int VEC>
-static void launch_rows_f64s_vec(const Plan& p, const TvcArgs<TVC_F64>& a, cudaStream_t st) {
-  const int dq = slots_dfma_steps();
-  if (dq == 0) launch_rows_f64s_dq<VEC, 0>(p, a, st);
-  else if (dq == 1) launch_rows_f64s_dq<VEC, 1>(p, a, st);
-  else launch_rows_f64s_dq<VEC, 2>(p, a, st);
+template <tvc_dtype DT, int VEC>
+static void launch_rows_f64s_vec(const Plan& p, const TvcArgs<DT>& a, cudaStream_t st) {
+  const int dq = (DT == TVC_F64) ? slots_dfma_steps() : 0;
+  if (dq == 0) launch_rows_f64s_dq<DT, VEC, 0>(p, a, st);
+  else if (dq == 1) launch_rows_f64s_dq<DT, VEC, 1>(p, a, st);
+  else launch_rows_f64s_dq<DT, VEC, 2>(p, a, st);
 }
 
 template <tvc_dtype DT>
@@ -1784,7 +1788,7 @@ static void launch_main(const Plan& p, const TvcArgs<DT>& a, cudaStream_t st) {
         } else {
           tvc_cols_kernel<DT, 1, 0><<<p.grid, kThreads, 0, st>>>(a);
         }
-      } else if constexpr (DT == TVC_F32) {
+      } else if constexpr (DT == TVC_F32 || DT == TVC_F32D) {
         if (p.vec == 4) tvc_cols_kernel<DT, 4, 0><<<p.grid, kThreads, 0, st>>>(a);
         else tvc_cols_kernel<DT, 1, 0><<<p.grid, kThreads, 0, st>>>(a);
       } else if constexpr (sizeof(typename Elem<DT>::T) == 2) {  // BF16, F16
@@ -1812,8 +1816,11 @@ static void launch_main(const Plan& p, const TvcArgs<DT>& a, cudaStream_t st) {
       break;
     case K_ROWS_F64S:
       if constexpr (DT == TVC_F64) {
-        if (p.vec == 2) launch_rows_f64s_vec<2>(p, a, st);
-        else launch_rows_f64s_vec<1>(p, a, st);
+        if (p.vec == 2) launch_rows_f64s_vec<DT, 2>(p, a, st);
+        else launch_rows_f64s_vec<DT, 1>(p, a, st);
+      } else if constexpr (DT == TVC_F32D) {
+        if (p.vec == 4) launch_rows_f64s_vec<DT, 4>(p, a, st);
+        else launch_rows_f64s_vec<DT, 1>(p, a, st);
       }
       break;
     case K_SLAB:
@@ -1857,14 +1864,14 @@ static tvc_status run(const void* A, const Shape& s, const void* x, void* y, con
   a.beta = beta;
   a.done = done;
   char* w = static_cast<char*>(ws);
-  if (DT == TVC_F64) {
+  if (kF64Acc<DT>) {
     a.xs = reinterpret_cast<const XSplit*>(w);
     const int blocks = (int)std::min<int64_t>(ceil_div(s.nk, 256), 4096);
     tvc_split_x_kernel<<<blocks, 256, 0, st>>>(static_cast<const double*>(x), reinterpret_cast<XSplit*>(w), s.nk, done);
   }
   if (p.splits > 1) a.partial = w + p.ws_xs;
   launch_main<DT>(p, a, st);
-  count_launches((DT == TVC_F64 ? 1 : 0) + 1 + (p.splits > 1 ? 1 : 0));
+  count_launches((kF64Acc<DT> ? 1 : 0) + 1 + (p.splits > 1 ? 1 : 0));
   if (p.splits > 1) {
     using V = typename Elem<DT>::V;
     const int blocks = (int)std::min<int64_t>(ceil_div(s.uv, 256), 8192);
@@ -1884,6 +1891,7 @@ tvc_status tvc_launch(const void* A, const Shape& s, const void* x, void* y, tvc
     case TVC_BF16: return run<TVC_BF16>(A, s, x, y, scales, alpha, beta, ws, p, stream, done);
     case TVC_E4M3: return run<TVC_E4M3>(A, s, x, y, scales, alpha, beta, ws, p, stream, done);
     case TVC_F16: return run<TVC_F16>(A, s, x, y, scales, alpha, beta, ws, p, stream, done);
+    case TVC_F32D: return run<TVC_F32D>(A, s, x, y, scales, alpha, beta, ws, p, stream, done);
   }
   return TVC_ERR_INVALID_ARG;
 }

@@ -25,7 +25,7 @@ def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--dims", type=int, nargs="+", required=True)
     ap.add_argument("--mode", type=int, default=0)
-    ap.add_argument("--dtype", default="f64", choices=["f64", "f32", "bf16", "e4m3", "f16"])
+    ap.add_argument("--dtype", default="f64", choices=["f64", "f32", "bf16", "e4m3", "f16", "f32d"])
     ap.add_argument("--reps", type=int, default=3)
     a = ap.parse_args(argv)
     dt = torch.float64 if a.dtype == "f64" else torch.float32
@@ -37,9 +37,11 @@ def main(argv=None):
     if a.dtype in ("bf16", "e4m3", "f16"):
         A, scales, _ = tg.quantise(A.view(a.dims), {"bf16": tg.BF16, "e4m3": tg.E4M3, "f16": tg.F16}[a.dtype])
         A = A.view(-1)
-    x = torch.from_numpy(synth.vector(kind, 1, synth.stream_x(a.mode), a.dims[a.mode])).cuda()
-    y = torch.empty(N // a.dims[a.mode], dtype=dt, device="cuda")
-    ws = torch.empty(max(1, tg.tvc_workspace_size(a.dims, a.mode, tg.dtype_code(A))), dtype=torch.uint8, device="cuda")
+    xkind = "u64" if a.dtype == "f32d" else kind  # single-double: FP32 storage, FP64 vectors
+    x = torch.from_numpy(synth.vector(xkind, 1, synth.stream_x(a.mode), a.dims[a.mode])).cuda()
+    y = torch.empty(N // a.dims[a.mode], dtype=x.dtype, device="cuda")
+    code = tg.F32D if a.dtype == "f32d" else tg.dtype_code(A)
+    ws = torch.empty(max(1, tg.tvc_workspace_size(a.dims, a.mode, code)), dtype=torch.uint8, device="cuda")
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ms = 0.0
     for _ in range(a.reps):

@@ -88,3 +88,17 @@ def test_backward_deterministic():
     a, _ = tg.tvc_backward(A, 1, x, gy, need_A=False)
     b, _ = tg.tvc_backward(A, 1, x, gy, need_A=False)
     assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("dims", SHAPES, ids=lambda d: "x".join(map(str, d)))
+def test_backward_single_double(dims):
+    """binary32 storage, FP64 vectors and arithmetic (single-double)."""
+    A = synth.tensor("u32", 2, dims)
+    for k in range(len(dims)):
+        x = synth.vector("u64", 1, synth.stream_x(k), dims[k])
+        gyshape = [n for i, n in enumerate(dims) if i != k]
+        gy = synth.vector("u64", 3, 40 + k, int(np.prod(gyshape, dtype=np.int64))).reshape(gyshape)
+        gx, gA = tg.tvc_backward(gu.to_dev(A), k, gu.to_dev(x), gu.to_dev(gy), shape=dims)
+        assert gx.dtype == torch.float64 and gA.dtype == torch.float64
+        assert gu.rel_l2(gx.cpu().numpy(), oracle.tvc_grad_x(A, k, gy)) <= 1e-12, (dims, k)
+        assert gu.rel_l2(gA.cpu().numpy(), oracle.tvc_grad_A(dims, k, x, gy)) <= 1e-12, (dims, k)

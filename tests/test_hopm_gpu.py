@@ -194,3 +194,15 @@ def test_low_precision_hopm_lambda_vs_fp64(code):
     # kernel error: the oracle on the same stored codes
     ref_q = oracle.hopm(codes.cpu().numpy(), ones_np(dims), 30, scales=scales.cpu().numpy())
     assert abs(r.lam.item() - ref_q["lam"]) <= 1e-5 * ref_q["lam"]
+
+
+@pytest.mark.parametrize("dims", SHAPES, ids=lambda d: "x".join(map(str, d)))
+def test_hopm_single_double(dims):
+    """binary32 storage with FP64 vectors: the FP64 tolerances of the oracle's
+    FP32 path (which promotes every element to FP64)."""
+    A = synth.tensor("u32", 0, dims)
+    ref = oracle.hopm(A, ones_np(dims), 8)
+    r = tg.hopm(gu.to_dev(A), ones_start(dims, oracle.F64), 8, shape=dims)
+    torch.cuda.synchronize()
+    assert int(r.status.item()) == 0
+    check_against(r, ref, oracle.F64)

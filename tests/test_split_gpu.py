@@ -207,3 +207,25 @@ def test_split_bad_arguments_raise():
         tg.dtvc(slabs, [0, 2, 4], (4, 6), 2, 1, x)
     with pytest.raises(ValueError):
         tg.split_1d(0, 2)
+
+
+def test_split_single_double():
+    dims = (7, 3, 5, 2)
+    A = synth.tensor("u32", 1, dims)
+    At = gu.to_dev(A)
+    for s in range(len(dims)):
+        starts = tg.split_1d(dims[s], 3)
+        slabs = tg.split_tensor(At, s, starts)
+        for k in range(len(dims)):
+            x = synth.vector("u64", 1, synth.stream_x(k), dims[k])
+            ref = oracle.tvc(A, k, x)
+            got = tg.dtvc(slabs, starts, dims, s, k, gu.to_dev(x))
+            if k == s:
+                assert gu.rel_l2(got.cpu().numpy(), ref) <= 1e-12
+            else:
+                so = s if s < k else s - 1
+                assert gu.rel_l2(np.concatenate([g.cpu().numpy() for g in got], axis=so), ref) <= 1e-12
+        r = tg.dhopm(slabs, starts, dims, s, _ones(dims, oracle.F64), 5)
+        ref = oracle.hopm(A, [np.ones(n) / math.sqrt(n) for n in dims], 5)
+        torch.cuda.synchronize()
+        np.testing.assert_allclose(r.lam_hist.cpu().numpy()[:5], ref["lam_hist"], rtol=1e-12)

@@ -235,3 +235,45 @@ def test_staged_kernel_waits_never_time_out():
         assert gu.rel_l2(got, oracle.tvc(A, 1, x)) <= 1e-5
     torch.cuda.synchronize()
     assert lib.tvc_device_error(ctypes.byref(code), 0) == 0 and code.value == 0
+
+
+# ----------------------------------------------------- single-double (F32D)
+# binary32 storage with FP64 vectors and FP64 arithmetic (Section 5.5): the
+# oracle's FP32 path computes exactly that (elements promoted to FP64), so
+# the FP64 tolerance applies.
+
+@pytest.mark.parametrize("dims", SHAPES, ids=lambda d: "x".join(map(str, d)))
+def test_single_double_every_mode(dims):
+    A = synth.tensor("u32", 0, dims)
+    for k in range(len(dims)):
+        x = synth.vector("u64", 1, synth.stream_x(k), dims[k])
+        got = gu.gpu_tvc(tg, A, k, x)
+        assert got.dtype == np.float64
+        assert gu.rel_l2(got, oracle.tvc(A, k, x)) <= 1e-12, (dims, k)
+
+
+@pytest.mark.parametrize("dims", WINDOW_SHAPES, ids=lambda d: "x".join(map(str, d)))
+def test_single_double_outside_the_window(dims):
+    A = synth.tensor("u32", 4, dims)
+    flat = A.ravel()
+    rng = np.random.default_rng(6)
+    pos = rng.choice(flat.size, size=500, replace=False)
+    flat[pos[:100]] = 0.0
+    flat[pos[100:200]] = np.float32(1e38)
+    flat[pos[200:300]] = np.float32(1e-40)  # subnormal
+    flat[pos[300:400]] *= np.float32(2.0 ** 70)
+    flat[pos[400:]] *= np.float32(2.0 ** -70)
+    for k in range(len(dims)):
+        x = synth.vector("u64", 1, 1 + k, dims[k])
+        x[::5] *= 1e-20
+        x[1::7] = 0.0
+        assert gu.rel_l2(gu.gpu_tvc(tg, A, k, x), oracle.tvc(A, k, x)) <= 1e-12, (dims, k)
+
+
+@pytest.mark.parametrize("dims", [(6, 70, 33), (5, 1000), (4, 100, 7), (3000, 13), (500, 19, 19)])
+def test_single_double_integer_inputs_bit_exact(dims):
+    rng = np.random.default_rng(12)
+    A = rng.integers(-1000, 1000, size=dims).astype(np.float32)
+    for k in range(len(dims)):
+        x = rng.integers(-1000, 1000, size=dims[k]).astype(np.float64)
+        assert np.array_equal(gu.gpu_tvc(tg, A, k, x), oracle.tvc(A, k, x)), (dims, k)
