@@ -24,7 +24,7 @@ import numpy as np
 
 __all__ = [
     "F64", "F32", "BF16", "E4M3", "F16", "build", "tvc", "tvc_grad_x", "tvc_grad_A",
-    "hopm", "hopm3", "quantise", "decode_bf16", "decode_e4m3", "decode_f16",
+    "hopm", "hopm3", "hopm_jacobi", "quantise", "decode_bf16", "decode_e4m3", "decode_f16",
     "bf16_from_f32", "e4m3_from_f32", "f16_from_f32", "dequantise", "OracleError", "dhopm_touched",
 ]
 
@@ -71,6 +71,7 @@ def _load():
             lib.oracle_tvc_grad_A.argtypes = [I, P, I, P, P, P]
             for f in (lib.oracle_hopm, lib.oracle_hopm3):
                 f.argtypes = [I, P, P, I, P, P, I, D, P, P, P, P, P]
+            lib.oracle_hopm_jacobi.argtypes = [I, P, P, I, P, P, I, D, P, P, P]
             lib.oracle_quantise.argtypes = [I, P, I, P, P, P, I]
             lib.oracle_decode_bf16.argtypes = [ctypes.c_uint16]
             lib.oracle_decode_bf16.restype = D
@@ -195,6 +196,27 @@ def hopm(A, xs, iters: int, tol: float = 0.0, *, dims=None, scales=None) -> dict
 def hopm3(A, xs, iters: int, tol: float = 0.0, *, dims=None, scales=None) -> dict:
     """Three-buffer HOPM of Algorithm 1 (p = 1); same outputs as :func:`hopm`."""
     return _hopm(_load().oracle_hopm3, A, xs, iters, tol, dims, scales)
+
+
+def hopm_jacobi(A, xs, iters: int, tol: float = 0.0, *, dims=None, scales=None) -> dict:
+    """Jacobi HOPM: every z_j of a sweep from the previous sweep's vectors
+    (status, x, lam, sweeps, lam_hist as for :func:`hopm`)."""
+    A, d, dt = _tensor(A, dims)
+    s = _scales(dt, scales, int(d[0]))
+    if len(xs) != d.size:
+        raise ValueError("one start vector per mode")
+    x = np.ascontiguousarray(np.concatenate([np.asarray(v, dtype=np.float64).ravel() for v in xs]))
+    if x.size != int(d.sum()):
+        raise ValueError("start vector lengths do not match dims")
+    lam = np.zeros(1)
+    sweeps = np.zeros(1, dtype=np.int32)
+    hist = np.zeros(max(iters, 1))
+    st = _load().oracle_hopm_jacobi(dt, _p(A), _p(s), int(d.size), _p(d), _p(x), int(iters), float(tol),
+                                    _p(lam), _p(sweeps), _p(hist))
+    offs = np.concatenate([[0], np.cumsum(d)])
+    n = int(sweeps[0])
+    return dict(status=int(st), x=[x[offs[m]:offs[m + 1]].copy() for m in range(d.size)], lam=float(lam[0]),
+                sweeps=n, lam_hist=hist[:n].copy())
 
 
 def quantise(src, fmt: int, *, truncate: bool = False, allow_nonfinite: bool = False):

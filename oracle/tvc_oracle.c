@@ -307,6 +307,57 @@ int oracle_hopm(int dtype, const void* A, const float* scales, int order, const 
   return status;
 }
 
+/* Jacobi HOPM (a variant of the power method, not the paper's Algorithm 1):
+ * in each sweep every z_j = A x_{m != j} x_m is formed from the vectors of
+ * the PREVIOUS sweep (canonical chain, every other mode ascending), then
+ * every x_j <- z_j / ||z_j||.  lambda_t = ||z_{d-1}|| of sweep t (as for the
+ * Gauss-Seidel method); same stopping rule, outputs and status.  All d
+ * updates read the same vectors, so one pass over A can serve a sweep. */
+int oracle_hopm_jacobi(int dtype, const void* A, const float* scales, int order, const int64_t* dims,
+                       double* x, int iters, double tol, double* lambda_out, int* sweeps_out,
+                       double* lambda_hist) {
+  if (!valid_shape(order, dims) || order < 2 || iters < 0) return OR_ERR_ARG;
+  int64_t off[OR_MAXD + 1];
+  off[0] = 0;
+  for (int m = 0; m < order; m++) off[m + 1] = off[m] + dims[m];
+  double* z = (double*)malloc(sizeof(double) * (size_t)off[order]);
+  if (!z) return OR_ERR_ARG;
+  double lam = 0.0, prev = 0.0;
+  int status = OR_OK, t;
+  for (t = 1; t <= iters; t++) {
+    for (int j = 0; j < order && status == OR_OK; j++) {
+      otensor cur;
+      base_tensor(&cur, dtype, A, scales, order, dims);
+      for (int m = 0; m < order; m++) {
+        if (m == j) continue;
+        otensor nxt;
+        status = ocontract(&cur, m, x + off[m], &nxt, NULL);
+        ofree(&cur);
+        cur = nxt;
+        if (status != OR_OK) break;
+      }
+      if (status == OR_OK) memcpy(z + off[j], cur.data, sizeof(double) * (size_t)dims[j]);
+      ofree(&cur);
+    }
+    for (int j = 0; j < order && status == OR_OK; j++) {
+      double sigma;
+      status = onormalise(z + off[j], dims[j], x + off[j], &sigma, NULL);
+      if (j == order - 1 && status == OR_OK) lam = sigma;
+    }
+    if (status != OR_OK) break;
+    if (lambda_hist) lambda_hist[t - 1] = lam;
+    if (converged(lam, prev, t, tol)) {
+      prev = lam;
+      break;
+    }
+    prev = lam;
+  }
+  free(z);
+  if (lambda_out) *lambda_out = lam;
+  if (sweeps_out) *sweeps_out = (t > iters) ? iters : t;
+  return status;
+}
+
 /* Three-buffer HOPM of Algorithm 1 for one process (p = 1): the external
  * iteration j reuses the prefix W_{j-1} = A x_0 x_0 ... x_{j-2} x_{j-2}
  * (ORIGINAL mode ids throughout).  Per iteration j, with

@@ -475,3 +475,42 @@ def test_dhopm3_saving_is_flat_in_processes_and_split():
     assert 3.2 <= min(sum(oracle.dhopm_touched(10, 8, 8, s, j) for j in range(10)) /
                       sum(oracle.dhopm_touched(10, 8, 8, s, j, three=True) for j in range(10))
                       for s in range(10)) <= 3.4
+
+
+# ------------------------------------------------------------ Jacobi HOPM
+
+def test_jacobi_first_sweep_is_the_einsum_contractions():
+    dims = (5, 6, 4)
+    A = rand_tensor(dims, sid=3)
+    xs = [synth.vector("u64", 9, 30 + m, n) for m, n in enumerate(dims)]
+    r = oracle.hopm_jacobi(A, xs, 1)
+    zs = [np.einsum("ijk,j,k->i", A, xs[1], xs[2]), np.einsum("ijk,i,k->j", A, xs[0], xs[2]),
+          np.einsum("ijk,i,j->k", A, xs[0], xs[1])]
+    for got, z in zip(r["x"], zs):
+        np.testing.assert_allclose(got, z / np.linalg.norm(z), rtol=1e-13, atol=1e-15)
+    assert abs(r["lam"] - np.linalg.norm(zs[2])) <= 1e-13 * np.linalg.norm(zs[2])
+
+
+def test_jacobi_rank1_in_one_sweep_and_svd_for_order_2():
+    us = [synth.vector("u64", 4, 50 + j, n) for j, n in enumerate((6, 5, 7))]
+    A = np.einsum("i,j,k->ijk", *us)
+    # one sweep aligns every vector with its factor; lambda, formed from the
+    # previous sweep's vectors, reaches ||A|| = prod ||u_j|| in the second
+    r = oracle.hopm_jacobi(A, ones_start(A.shape), 1)
+    for xg, u in zip(r["x"], us):
+        assert abs(abs(np.dot(xg, u / np.linalg.norm(u))) - 1) <= 1e-13
+    r = oracle.hopm_jacobi(A, ones_start(A.shape), 2)
+    assert abs(r["lam"] - np.prod([np.linalg.norm(u) for u in us])) <= 1e-13 * r["lam"]
+    M = rand_tensor((9, 7), sid=4)
+    r = oracle.hopm_jacobi(M, ones_start(M.shape), 400, 1e-15)
+    assert abs(r["lam"] - np.linalg.svd(M, compute_uv=False)[0]) <= 1e-10 * r["lam"]
+
+
+def test_jacobi_leaves_a_converged_point_fixed():
+    dims = (6, 7, 5)
+    A = rand_tensor(dims, sid=5)
+    gs = oracle.hopm(A, ones_start(dims), 300, 1e-15)
+    r = oracle.hopm_jacobi(A, gs["x"], 1)
+    assert abs(r["lam"] - gs["lam"]) <= 1e-10 * gs["lam"]
+    for a, b in zip(r["x"], gs["x"]):
+        assert np.max(np.abs(a - b)) <= 1e-8
