@@ -510,7 +510,10 @@ def test_jacobi_leaves_a_converged_point_fixed():
     dims = (6, 7, 5)
     A = rand_tensor(dims, sid=5)
     gs = oracle.hopm(A, ones_start(dims), 300, 1e-15)
+    # near the fixed point both maps move the vectors by the same order as
+    # the remaining residual (lambda converges as its square)
+    step = max(np.max(np.abs(a - b)) for a, b in zip(oracle.hopm(A, gs["x"], 1)["x"], gs["x"]))
     r = oracle.hopm_jacobi(A, gs["x"], 1)
     assert abs(r["lam"] - gs["lam"]) <= 1e-10 * gs["lam"]
     for a, b in zip(r["x"], gs["x"]):
-        assert np.max(np.abs(a - b)) <= 1e-8
+        assert np.max(np.abs(a - b)) <= 4 * step + 1e-13
