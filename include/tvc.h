@@ -205,6 +205,21 @@ tvc_status hopm(const void* A, int order, const int64_t* dims, void* const* x, i
 size_t hopm_workspace_size(int order, const int64_t* dims, tvc_dtype dtype);
 
 /*
+ * Jacobi HOPM (a variant of the power method, not the paper's Algorithm 1):
+ * every z_j = A x_{m != j} x_m of a sweep is formed from the vectors of the
+ * previous sweep, then every x_j <- z_j / ||z_j||; lambda = ||z_{d-1}|| of
+ * the sweep.  Results differ from hopm() (Gauss-Seidel) except at a fixed
+ * point.  A is read through two views per sweep: T = A x_{d-1} x_{d-1} and
+ * z_{d-1} = A^T (x_0 (x) ... (x) x_{d-2}); every other z_j comes from the
+ * small T.  Arguments, outputs, stopping rule and status as for hopm().
+ * Workspace: hopm_jacobi_workspace_size(order, dims, dtype) bytes.
+ */
+tvc_status hopm_jacobi(const void* A, int order, const int64_t* dims, void* const* x, int iters, double tol,
+                       double* lambda_out, int* sweeps_out, int* status_out, double* lambda_hist, tvc_dtype dtype,
+                       const float* slab_scales, void* workspace, size_t ws_bytes, tvc_stream_t stream);
+size_t hopm_jacobi_workspace_size(int order, const int64_t* dims, tvc_dtype dtype);
+
+/*
  * Reverse-mode gradient of `iters` HOPM sweeps (fixed count: the run this
  * differentiates used tol = 0, or pass the sweep count it reported) started
  * from x0[m] (device, not modified).  Upstream gradients: gx_final[m]

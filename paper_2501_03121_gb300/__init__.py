@@ -23,7 +23,7 @@ __all__ = [
     "F64", "F32", "BF16", "E4M3", "F16", "F32D", "TVCError", "load_library", "tvc", "tvc_workspace_size",
     "dtype_code", "library_path", "kernel_launches", "hopm", "hopm_workspace_size", "HopmResult", "quantise", "tvc_backward", "TVCFunction", "tvc_autograd", "hopm_backward", "HOPMFunction", "hopm_autograd", "TVCBatch", "HOPMBatch", "BATCH_PREUPLOADED",
     "split_1d", "slab_extract", "slab_insert", "split_tensor", "dtvc", "dtvc_workspace_size", "dhopm",
-    "dhopm_workspace_size",
+    "dhopm_workspace_size", "hopm_jacobi",
 ]
 
 F64, F32, BF16, E4M3, F16, F32D = 0, 1, 2, 3, 4, 5
@@ -74,6 +74,10 @@ def load_library():
         lib.hopm.restype = I
         lib.hopm_workspace_size.argtypes = [I, P, I]
         lib.hopm_workspace_size.restype = Z
+        lib.hopm_jacobi.argtypes = [P, I, P, P, I, D, P, P, P, P, I, P, P, Z, P]
+        lib.hopm_jacobi.restype = I
+        lib.hopm_jacobi_workspace_size.argtypes = [I, P, I]
+        lib.hopm_jacobi_workspace_size.restype = Z
         lib.tvc_quantise.argtypes = [P, I, P, I, P, P, I, P, P, Z, P]
         lib.tvc_quantise.restype = I
         lib.tvc_quantise_workspace_size.argtypes = [I, P]
@@ -279,6 +283,38 @@ def hopm(A: torch.Tensor, xs, iters: int, tol: float = 0.0, *, scales: torch.Ten
     st = lib.hopm(_ptr(A), len(shape), dims, ptrs, int(iters), float(tol), _ptr(lam), _ptr(sweeps), _ptr(status),
                   _ptr(hist), code, _ptr(scales), _ptr(workspace), workspace.numel(), _stream(stream))
     _check(st, "hopm")
+    return HopmResult(xs, lam, sweeps, status, hist)
+
+
+def hopm_jacobi(A: torch.Tensor, xs, iters: int, tol: float = 0.0, *, scales: torch.Tensor | None = None,
+                workspace: torch.Tensor | None = None, stream=None, shape=None, inplace: bool = False) -> HopmResult:
+    """Jacobi HOPM on the GPU: every update of a sweep from the previous
+    sweep's vectors (see include/tvc.h); outputs as for :func:`hopm`."""
+    lib = load_library()
+    code = _with_vectors(dtype_code(A), xs[-1] if len(xs) else None)
+    shape = tuple(A.shape) if shape is None else tuple(int(n) for n in shape)
+    if len(shape) < 2 or len(xs) != len(shape):
+        raise ValueError("hopm_jacobi needs order >= 2 and one start vector per mode")
+    vt = vec_dtype(code)
+    xs = [v if inplace else v.clone() for v in xs]
+    for m, v in enumerate(xs):
+        if v.dtype != vt or v.numel() != shape[m]:
+            raise ValueError(f"x[{m}] must be {vt} with {shape[m]} entries")
+    _check_cuda(A, scales, workspace, *xs)
+    dev = A.device
+    lam = torch.zeros(1, dtype=torch.float64, device=dev)
+    sweeps = torch.zeros(1, dtype=torch.int32, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    hist = torch.zeros(max(1, iters), dtype=torch.float64, device=dev)
+    dims = _dims_array(shape)
+    if workspace is None:
+        need = lib.hopm_jacobi_workspace_size(len(shape), dims, code)
+        workspace = torch.empty(max(1, need), dtype=torch.uint8, device=dev)
+    ptrs = (ctypes.c_void_p * len(xs))(*[v.data_ptr() for v in xs])
+    st = lib.hopm_jacobi(_ptr(A), len(shape), dims, ptrs, int(iters), float(tol), _ptr(lam), _ptr(sweeps),
+                         _ptr(status), _ptr(hist), code, _ptr(scales), _ptr(workspace), workspace.numel(),
+                         _stream(stream))
+    _check(st, "hopm_jacobi")
     return HopmResult(xs, lam, sweeps, status, hist)
 
 

@@ -56,6 +56,7 @@ struct OuterArgs {
   int nm;
   int64_t dims[TVC_MAX_ORDER];
   const void* xs[TVC_MAX_ORDER];
+  const float* scale0;  // nullable: the first factor times scale0[its index] (slab scales)
 };
 
 template <class V>
@@ -69,6 +70,7 @@ __global__ void hopm_outer_kernel(V* __restrict__ w, int64_t n, OuterArgs oa, co
       rem /= oa.dims[m];
     }
     V acc = static_cast<const V*>(oa.xs[0])[dig[0]];
+    if (oa.scale0) acc *= (V)oa.scale0[dig[0]];
     for (int m = 1; m < oa.nm; m++) acc *= static_cast<const V*>(oa.xs[m])[dig[m]];
     w[c] = acc;
   }
@@ -524,6 +526,188 @@ tvc_status dhopm_launch(const void* const* slabs, int parts, const int64_t* star
   return cuda_status(cudaGetLastError());
 }
 
+// ------------------------------------------------------------ Jacobi
+
+namespace {
+
+// Jacobi HOPM (not the paper's Algorithm 1): every z_j of a sweep from the
+// previous sweep's vectors.  With C = n_{d-1} and R = N / C:
+//   w       = x_0 (x) ... (x) x_{d-2}           (R entries; slab scales of
+//                                                narrow storage folded in)
+//   T       = A x_{d-1} x_{d-1}                 (R entries)
+//   z_{d-1} = A^T w over the R x C view          (C entries)
+//   z_j     = T contracted with x_m, m != j, m < d-1   (j < d-1; T is small)
+// then every x_j <- z_j / ||z_j||, lambda = ||z_{d-1}|| (FP64 norms).
+struct JacobiCtx {
+  bool dry = true;
+  const void* A = nullptr;
+  int d = 0;
+  int64_t n[TVC_MAX_ORDER] = {};
+  int64_t R = 0, C = 0;
+  tvc_dtype dt = TVC_F64, vdt = TVC_F64;
+  const float* scales = nullptr;
+  cudaStream_t st = nullptr;
+  HopmState* state = nullptr;
+  void *T = nullptr, *T1 = nullptr, *wv = nullptr, *tws = nullptr;
+  void* z[TVC_MAX_ORDER] = {};
+  size_t tws_bytes = 0, tvc_need = 0;
+  tvc_status rc = TVC_OK;
+  int launches = 0;
+
+  bool f64() const { return vdt == TVC_F64; }
+  void tvc(const void* X, const Shape& s, const void* xv, void* y, tvc_dtype t, const float* sc) {
+    if (rc != TVC_OK) return;
+    if (dry) {
+      for (uintptr_t al = elem_size(t); al <= 256; al *= 2)
+        tvc_need = std::max(tvc_need, tvc_ws_bytes(s, t, reinterpret_cast<const void*>(al)));
+      return;
+    }
+    rc = tvc_launch(X, s, xv, y, t, sc, 1.0, 0.0, tws, tws_bytes, st, &state->done);
+  }
+  // out = x_lo (x) ... (x) x_{hi-1} (the first factor times scale0 when given)
+  void outer(int lo, int hi, void* const* xs, void* out, const float* scale0) {
+    if (dry || rc != TVC_OK) return;
+    OuterArgs oa{};
+    oa.nm = hi - lo;
+    for (int m = lo; m < hi; m++) {
+      oa.dims[m - lo] = n[m];
+      oa.xs[m - lo] = xs[m];
+    }
+    oa.scale0 = scale0;
+    const int64_t len = prod_range(n, lo, hi);
+    if (f64())
+      hopm_outer_kernel<double><<<grid_for(len), 256, 0, st>>>(static_cast<double*>(out), len, oa, state);
+    else
+      hopm_outer_kernel<float><<<grid_for(len), 256, 0, st>>>(static_cast<float*>(out), len, oa, state);
+    launches++;
+  }
+  void normalize(int j, void* xj, double tol, double* lam_out, int* sweeps_out, int* status_out, double* lam_hist) {
+    if (dry || rc != TVC_OK) return;
+    const int last = (j == d - 1);
+    if (f64())
+      hopm_normalize_kernel<double><<<1, kNormThreads, 0, st>>>(static_cast<const double*>(z[j]), static_cast<double*>(xj),
+                                                                n[j], last, tol, state, lam_out, sweeps_out, status_out,
+                                                                lam_hist, nullptr);
+    else
+      hopm_normalize_kernel<float><<<1, kNormThreads, 0, st>>>(static_cast<const float*>(z[j]), static_cast<float*>(xj),
+                                                               n[j], last, tol, state, lam_out, sweeps_out, status_out,
+                                                               lam_hist, nullptr);
+    launches++;
+  }
+  void sweep(void* const* xs, double tol, double* lam_out, int* sweeps_out, int* status_out, double* lam_hist) {
+    const bool narrow = (dt == TVC_BF16 || dt == TVC_E4M3 || dt == TVC_F16) && scales != nullptr;
+    // w (slab scales folded into the x_0 factor), then the two views of A
+    const void* w = xs[0];
+    if (d > 2 || narrow) {
+      outer(0, d - 1, xs, wv, narrow ? scales : nullptr);
+      w = wv;
+    }
+    Shape s;
+    make_shape(d, n, d - 1, &s);
+    tvc(A, s, xs[d - 1], T, dt, scales);           // T = A x_{d-1} x_{d-1}
+    tvc(A, shape2(R, C, 0), w, z[d - 1], dt, nullptr);  // z_{d-1} = A^T w
+    // z_j, j < d-1, from T (order d-1: n_0 .. n_{d-2}): contract the modes
+    // after j, then those before j, each group against its outer product
+    // (modes of size one included: their x entry is a factor too)
+    for (int j = 0; j < d - 1 && rc == TVC_OK; j++) {
+      const int64_t u = prod_range(n, 0, j), v = prod_range(n, j + 1, d - 1);
+      const bool has_pre = j > 0, has_post = j + 1 < d - 1;
+      const void* src = T;
+      if (has_post) {
+        outer(j + 1, d - 1, xs, wv, nullptr);
+        void* dst = has_pre ? T1 : z[j];
+        tvc(T, shape2(u * n[j], v, 1), wv, dst, vdt, nullptr);
+        src = dst;
+      }
+      if (has_pre) {
+        outer(0, j, xs, wv, nullptr);
+        tvc(src, shape2(u, n[j], 0), wv, z[j], vdt, nullptr);
+      }
+      // neither: d = 2, where T is z_0 itself (see the launch)
+    }
+    for (int j = 0; j < d && rc == TVC_OK; j++) normalize(j, xs[j], tol, lam_out, sweeps_out, status_out, lam_hist);
+  }
+};
+
+struct JLayout {
+  size_t off_state = 0, off_T = 0, off_T1 = 0, off_w = 0, off_tvc = 0, total = 0, tvc = 0;
+  size_t off_z[TVC_MAX_ORDER] = {};
+};
+
+JLayout jacobi_layout(int order, const int64_t* dims, tvc_dtype dt) {
+  JLayout L;
+  const size_t vs = vec_size(dt);
+  const int64_t N = prod_range(dims, 0, order);
+  const int64_t R = N / dims[order - 1];
+  JacobiCtx c;
+  c.dry = true;
+  c.d = order;
+  for (int i = 0; i < order; i++) c.n[i] = dims[i];
+  c.R = R;
+  c.C = dims[order - 1];
+  c.dt = dt;
+  c.vdt = (dt == TVC_F64 || dt == TVC_F32D) ? TVC_F64 : TVC_F32;
+  void* dummy[TVC_MAX_ORDER] = {};
+  c.sweep(dummy, 0.0, nullptr, nullptr, nullptr, nullptr);
+  size_t off = 0;
+  L.off_state = off;
+  off += align_up(sizeof(HopmState), 256);
+  L.off_T = off;
+  off += align_up((size_t)R * vs, 256);
+  L.off_T1 = off;
+  off += align_up((size_t)R * vs, 256);
+  L.off_w = off;
+  off += align_up((size_t)R * vs, 256);
+  for (int j = 0; j < order; j++) {
+    L.off_z[j] = off;
+    off += align_up((size_t)dims[j] * vs, 256);
+  }
+  L.off_tvc = off;
+  L.tvc = c.tvc_need;
+  off += align_up(c.tvc_need, 256);
+  L.total = off;
+  return L;
+}
+
+}  // namespace
+
+size_t hopm_jacobi_ws_bytes(int order, const int64_t* dims, tvc_dtype dt) {
+  return jacobi_layout(order, dims, dt).total;
+}
+
+tvc_status hopm_jacobi_launch(const void* A, int order, const int64_t* dims, void* const* x, int iters, double tol,
+                              double* lam_out, int* sweeps_out, int* status_out, double* lam_hist, tvc_dtype dt,
+                              const float* scales, void* ws, size_t ws_bytes, cudaStream_t st) {
+  const JLayout L = jacobi_layout(order, dims, dt);
+  if (ws == nullptr || ws_bytes < L.total) return TVC_ERR_WORKSPACE;
+  char* w = static_cast<char*>(ws);
+  JacobiCtx c;
+  c.dry = false;
+  c.A = A;
+  c.d = order;
+  for (int i = 0; i < order; i++) c.n[i] = dims[i];
+  c.C = dims[order - 1];
+  c.R = prod_range(dims, 0, order) / c.C;
+  c.dt = dt;
+  c.vdt = (dt == TVC_F64 || dt == TVC_F32D) ? TVC_F64 : TVC_F32;
+  c.scales = scales;
+  c.st = st;
+  c.state = reinterpret_cast<HopmState*>(w + L.off_state);
+  c.T = w + L.off_T;
+  c.T1 = w + L.off_T1;
+  c.wv = w + L.off_w;
+  for (int j = 0; j < order; j++) c.z[j] = w + L.off_z[j];
+  if (order == 2) c.T = c.z[0];  // T = A x_1 x_1 is z_0
+  c.tws = w + L.off_tvc;
+  c.tws_bytes = L.tvc;
+  hopm_init_kernel<<<1, 1, 0, st>>>(c.state);
+  c.launches++;
+  for (int it = 0; it < iters && c.rc == TVC_OK; it++) c.sweep(x, tol, lam_out, sweeps_out, status_out, lam_hist);
+  count_launches(c.launches);
+  if (c.rc != TVC_OK) return c.rc;
+  return cuda_status(cudaGetLastError());
+}
+
 // ---------------------------------------------------------------- backward
 
 namespace {
@@ -803,6 +987,25 @@ extern "C" tvc_status dhopm(const void* const* slabs, int parts, const int64_t* 
     if (!x[m] || !aligned(x[m], vs)) return TVC_ERR_INVALID_ARG;
   return dhopm_launch(slabs, parts, starts, order, dims, s, x, iters, tol, lambda_out, sweeps_out, status_out,
                       lambda_hist, dtype, slab_scales, workspace, ws_bytes, (cudaStream_t)stream);
+}
+
+extern "C" size_t hopm_jacobi_workspace_size(int order, const int64_t* dims, tvc_dtype dtype) {
+  if (!valid_dtype(dtype) || order < 2 || check_dims(order, dims, nullptr) != TVC_OK) return 0;
+  return hopm_jacobi_ws_bytes(order, dims, dtype);
+}
+
+extern "C" tvc_status hopm_jacobi(const void* A, int order, const int64_t* dims, void* const* x, int iters, double tol,
+                                  double* lambda_out, int* sweeps_out, int* status_out, double* lambda_hist,
+                                  tvc_dtype dtype, const float* slab_scales, void* workspace, size_t ws_bytes,
+                                  tvc_stream_t stream) {
+  if (!valid_dtype(dtype) || order < 2 || !A || !x || iters < 0 || !(tol >= 0.0)) return TVC_ERR_INVALID_ARG;
+  if (check_dims(order, dims, nullptr) != TVC_OK) return TVC_ERR_INVALID_ARG;
+  const size_t vs = vec_size(dtype);
+  if (!aligned(A, elem_size(dtype))) return TVC_ERR_INVALID_ARG;
+  for (int m = 0; m < order; m++)
+    if (!x[m] || !aligned(x[m], vs)) return TVC_ERR_INVALID_ARG;
+  return hopm_jacobi_launch(A, order, dims, x, iters, tol, lambda_out, sweeps_out, status_out, lambda_hist, dtype,
+                            slab_scales, workspace, ws_bytes, (cudaStream_t)stream);
 }
 
 extern "C" size_t hopm_backward_workspace_size(int order, const int64_t* dims, tvc_dtype dtype, int iters) {

@@ -206,3 +206,39 @@ def test_hopm_single_double(dims):
     torch.cuda.synchronize()
     assert int(r.status.item()) == 0
     check_against(r, ref, oracle.F64)
+
+
+# ------------------------------------------------------------ Jacobi HOPM
+
+@pytest.mark.parametrize("dims", SHAPES, ids=lambda d: "x".join(map(str, d)))
+@pytest.mark.parametrize("code", [oracle.F64, oracle.F32, oracle.BF16, oracle.E4M3, oracle.F16],
+                         ids=["f64", "f32", "bf16", "e4m3", "f16"])
+def test_hopm_jacobi_matches_oracle(dims, code):
+    """Sweep by sweep: from the GPU's own vectors after sweep t-1, one GPU
+    sweep against one oracle sweep (a Jacobi iteration need not contract,
+    so differences of rounding may grow over many sweeps; the map itself
+    is what must agree)."""
+    A, Ao, scales = gu.inputs(dims, code)
+    st = gu.to_dev(scales) if scales is not None else None
+    xs = ones_start(dims, code)
+    for t in range(5):
+        ref = oracle.hopm_jacobi(Ao, [v.cpu().numpy().astype(np.float64) for v in xs], 1, scales=scales)
+        assert ref["status"] == 0
+        r = tg.hopm_jacobi(gu.to_dev(A), xs, 1, scales=st, shape=dims)
+        torch.cuda.synchronize()
+        assert int(r.status.item()) == 0
+        check_against(r, ref, code)
+        xs = r.x
+
+
+def test_hopm_jacobi_single_double_and_stopping_rule():
+    # a dominant rank-1 term (the planted workload's structure), where the
+    # Jacobi iteration converges; binary32 storage with FP64 vectors
+    dims = (9, 8, 7)
+    us = [synth.unit_gaussian(0, synth.stream_u(j), n) for j, n in enumerate(dims)]
+    A = synth.tensor("planted", 0, dims, us=us).astype(np.float32)
+    ref = oracle.hopm_jacobi(A, ones_np(dims), 200, 1e-10)
+    r = tg.hopm_jacobi(gu.to_dev(A), ones_start(dims, oracle.F64), 200, 1e-10, shape=dims)
+    torch.cuda.synchronize()
+    check_against(r, ref, oracle.F64)
+    assert int(r.sweeps.item()) == ref["sweeps"] < 200
