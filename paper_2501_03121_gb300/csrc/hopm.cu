@@ -602,10 +602,21 @@ struct JacobiCtx {
       outer(0, d - 1, xs, wv, narrow ? scales : nullptr);
       w = wv;
     }
-    Shape s;
-    make_shape(d, n, d - 1, &s);
-    tvc(A, s, xs[d - 1], T, dt, scales);           // T = A x_{d-1} x_{d-1}
-    tvc(A, shape2(R, C, 0), w, z[d - 1], dt, nullptr);  // z_{d-1} = A^T w
+    if (dual_supported(R, C, dt, dry ? reinterpret_cast<const void*>(256) : A)) {
+      // both products from ONE pass over A (FP32 / BF16 / F16 / E4M3)
+      if (dry) {
+        tvc_need = std::max(tvc_need, dual_ws_bytes(R, C, dt, nullptr));
+      } else if (rc == TVC_OK) {
+        rc = dual_launch(A, R, C, dt, static_cast<const float*>(xs[d - 1]), static_cast<const float*>(w),
+                         narrow ? scales : nullptr, R / n[0], static_cast<float*>(T), static_cast<float*>(z[d - 1]),
+                         tws, tws_bytes, st, &state->done);
+      }
+    } else {
+      Shape s;
+      make_shape(d, n, d - 1, &s);
+      tvc(A, s, xs[d - 1], T, dt, scales);               // T = A x_{d-1} x_{d-1}
+      tvc(A, shape2(R, C, 0), w, z[d - 1], dt, nullptr);  // z_{d-1} = A^T w
+    }
     // z_j, j < d-1, from T (order d-1: n_0 .. n_{d-2}): contract the modes
     // after j, then those before j, each group against its outer product
     // (modes of size one included: their x entry is a factor too)

@@ -63,4 +63,14 @@ tvc_status combine_parts(const void* const* parts, int nparts, const int64_t* of
                          tvc_dtype vdt, int gather, double alpha, double beta, cudaStream_t st,
                          const int* done);
 
+// One pass over an R x C row-major matrix M (FP32, BF16, F16 or E4M3
+// storage) for T = M x (scaled per slab: T[r] *= scales[r / upi0] when
+// scales is given) and z = M^T w (dual.cu).  dual_supported says whether
+// the shape and alignment fit; dual_ws_bytes covers every 16-byte aligned M.
+bool dual_supported(int64_t R, int64_t C, tvc_dtype dt, const void* M);
+size_t dual_ws_bytes(int64_t R, int64_t C, tvc_dtype dt, const void* M);
+tvc_status dual_launch(const void* M, int64_t R, int64_t C, tvc_dtype dt, const float* x, const float* w,
+                       const float* scales, int64_t upi0, float* T, float* z, void* ws, size_t ws_bytes,
+                       cudaStream_t st, const int* done);
+
 }  // namespace tvcg

@@ -242,3 +242,26 @@ def test_hopm_jacobi_single_double_and_stopping_rule():
     torch.cuda.synchronize()
     check_against(r, ref, oracle.F64)
     assert int(r.sweeps.item()) == ref["sweeps"] < 200
+
+
+# last dimensions that are multiples of 32 x (16 bytes of codes): the
+# single-pass kernel (T = A x_{d-1} x_{d-1} and z_{d-1} = A^T w from one read
+# of A) with 1, 2, 4 and 8 warps per row, slab scales applied in the kernel
+# (one warp per row) or after it, a single row, and ragged row counts
+SINGLE_PASS_SHAPES = [(6, 5, 256), (7, 3, 512), (3, 1024), (2, 3, 2048), (1, 4096), (5, 4, 3, 128)]
+
+
+@pytest.mark.parametrize("dims", SINGLE_PASS_SHAPES, ids=lambda d: "x".join(map(str, d)))
+@pytest.mark.parametrize("code", [oracle.F32, oracle.BF16, oracle.E4M3, oracle.F16],
+                         ids=["f32", "bf16", "e4m3", "f16"])
+def test_hopm_jacobi_single_pass_kernel(dims, code):
+    A, Ao, scales = gu.inputs(dims, code)
+    st = gu.to_dev(scales) if scales is not None else None
+    xs = ones_start(dims, code)
+    for t in range(3):
+        ref = oracle.hopm_jacobi(Ao, [v.cpu().numpy().astype(np.float64) for v in xs], 1, scales=scales)
+        r = tg.hopm_jacobi(gu.to_dev(A), xs, 1, scales=st, shape=dims)
+        torch.cuda.synchronize()
+        assert int(r.status.item()) == 0
+        check_against(r, ref, code)
+        xs = r.x
