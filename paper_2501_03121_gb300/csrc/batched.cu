@@ -58,24 +58,78 @@ struct HItem {
 // y[o] = sum_j A[(i*nk + j)*v + l] x[j], o = i*v + l < u*v; G lanes per output.
 __device__ void blk_tvc(const float* __restrict__ A, int64_t u, int64_t nk, int64_t v, const float* __restrict__ x,
                         float* __restrict__ y, int G, int64_t o_begin = 0, int64_t o_end = -1) {
+  const int64_t uv = (o_end < 0) ? u * v : o_end;
+  if (v >= 2) {
+    // One thread per output o = (i, l): the pair is found by one division
+    // and then advanced by the block stride; sixteen rows of n_k in flight
+    // through pointer increments (one block streams at the rate its bytes in
+    // flight allow), only the last (< 8) rows predicated.
+    int64_t o = o_begin + threadIdx.x;
+    if (o >= uv) return;
+    int64_t i = o / v, l = o - i * v;
+    const int64_t stride = kBBT;
+    const int64_t di = stride / v, dl = stride - di * v;
+    for (; o < uv; o += stride) {
+      const float* p = A + i * nk * v + l;
+      float acc0 = 0.0f, acc1 = 0.0f;
+      int64_t jj = 0;
+      for (; jj + 16 <= nk; jj += 16, p += 16 * v) {  // 16 rows in flight (64 B per thread)
+        float av[16];
+#pragma unroll
+        for (int q = 0; q < 16; q++) av[q] = __ldcs(p + q * v);
+#pragma unroll
+        for (int q = 0; q < 16; q += 2) {
+          acc0 = __fmaf_rn(av[q], __ldg(x + jj + q), acc0);
+          acc1 = __fmaf_rn(av[q + 1], __ldg(x + jj + q + 1), acc1);
+        }
+      }
+      if (jj + 8 <= nk) {
+        float av[8];
+#pragma unroll
+        for (int q = 0; q < 8; q++) av[q] = __ldcs(p + q * v);
+#pragma unroll
+        for (int q = 0; q < 8; q += 2) {
+          acc0 = __fmaf_rn(av[q], __ldg(x + jj + q), acc0);
+          acc1 = __fmaf_rn(av[q + 1], __ldg(x + jj + q + 1), acc1);
+        }
+        jj += 8;
+        p += 8 * v;
+      }
+      if (jj < nk) {
+        float av[7];
+#pragma unroll
+        for (int q = 0; q < 7; q++) av[q] = (jj + q < nk) ? __ldcs(p + q * v) : 0.0f;
+#pragma unroll
+        for (int q = 0; q < 7; q++)
+          if (jj + q < nk) acc0 = __fmaf_rn(av[q], __ldg(x + jj + q), acc0);
+      }
+      y[o] = acc0 + acc1;
+      i += di;
+      l += dl;
+      if (l >= v) {
+        l -= v;
+        i++;
+      }
+    }
+    return;
+  }
+  // v == 1 (rows): a group of G lanes per row, eight predicated loads in
+  // flight per lane (short rows too), shuffle reduction.
   const int lane = threadIdx.x & 31;
   const int p = lane & (G - 1);
   const int gw = 32 / G;  // groups per warp
-  const int64_t uv = (o_end < 0) ? u * v : o_end;
   const int64_t ngroups = (int64_t)(kBBT / 32) * gw;
   for (int64_t base = o_begin + (int64_t)(threadIdx.x >> 5) * gw; base < uv; base += ngroups) {
     const int64_t o = base + lane / G;
     float acc = 0.0f;
     if (o < uv) {
-      const int64_t i = o / v, l = o - i * v;
-      const float* row = A + i * nk * v + l;
-      // eight (predicated) loads in flight per lane, also for short rows
+      const float* row = A + o * nk;
       for (int64_t j = p; j < nk; j += 8 * G) {
         float av[8], xv[8];
 #pragma unroll
         for (int q = 0; q < 8; q++) {
           const bool ok = j + q * G < nk;
-          av[q] = ok ? __ldcs(row + (j + q * G) * v) : 0.0f;
+          av[q] = ok ? __ldcs(row + j + q * G) : 0.0f;
           xv[q] = ok ? __ldg(x + j + q * G) : 0.0f;
         }
 #pragma unroll
