@@ -285,9 +285,10 @@ tvc_status tvc_batched(const tvc_batch_desc* descs, int count, int flags, void* 
                        tvc_stream_t stream);
 size_t tvc_batched_workspace_size(const tvc_batch_desc* descs, int count);
 
-/* Times the candidate block mappings (lanes per output) on one tensor of
- * each shape class of the batch and keeps the fastest for later calls of
- * tvc_batched / hopm_batched in this process; synchronises the stream.
+/* Times the candidate block mappings (lanes per output) of the forward
+ * contraction of rows v == 1 on the tensors of each such shape class of the
+ * batch and keeps the fastest for later calls of tvc_batched / hopm_batched
+ * in this process; synchronises the stream.
  * workspace: tvc_batched_workspace_size(descs, count) bytes; a batch
  * uploaded on it before must be uploaded again (call without
  * TVC_BATCH_PREUPLOADED). */

@@ -3,20 +3,22 @@
 // launch (the GPU counterpart of the paper's task-based execution, Section
 // 4.3, where many TVCs overlap instead of joining after each one).
 //
-// The host uploads one descriptor per tensor (largest first) into the
-// workspace; a persistent kernel of a few blocks per SM then pulls tensors
-// from an atomic work counter, and one block runs all the work of its
-// tensor (forward TVC, gx, gA; or every sweep of a HOPM) with block-level
-// routines.  With TVC_BATCH_PREUPLOADED the descriptors of a previous call
-// are reused and a call issues only a memset and one kernel, so it can be
-// captured in a CUDA graph and replayed.
+// Contraction and adjoints: the host cuts every tensor (largest first) into
+// work items of about 2^20 elements (output ranges of the forward
+// contraction, slab x row rectangles of gx and gA) and uploads the
+// descriptors and items into the workspace; a persistent kernel of a few
+// blocks per SM pulls items from an atomic work counter.  gx items of one
+// tensor leave partial sums that the tensor's last item adds in a fixed
+// order.  Power methods: one block runs every sweep of one tensor.  With
+// TVC_BATCH_PREUPLOADED the descriptors of a previous call are reused and a
+// call issues only a memset and one kernel, so it can be captured in a CUDA
+// graph and replayed.
 //
-// Block-level contraction: a group of G lanes (G a power of two <= 32)
-// computes one output, its lanes splitting the contracted index; G = 1 is
-// one thread per output (coalesced when v is large), G = 32 a warp per
-// output (coalesced along rows when v == 1).  The autotuner picks G per
-// shape class (v and n_k rounded to powers of two) by timing the
-// candidates; untuned classes use a fixed rule.
+// Forward contraction of rows v == 1: a group of G lanes (G a power of two
+// <= 32) computes one output, its lanes splitting the row; the autotuner
+// picks G per shape class (n_k rounded to a power of two) by timing the
+// candidates, untuned classes use a fixed rule.  For v >= 2 one thread
+// computes one output, coalesced along l.
 #include <algorithm>
 #include <map>
 #include <mutex>
@@ -40,7 +42,9 @@ struct BItem {
   float* gx;
   float* gA;
   int64_t u, nk, v;
-  int gf, gb;  // lanes per output: forward contraction, gx
+  int gf;         // lanes per output of the forward contraction
+  int gxk;        // gx items (slab ranges) of this tensor
+  int64_t gxp;    // their partials: floats [gxp, gxp + gxk * nk) of the partial area (gxk > 1)
 };
 
 struct HItem {
@@ -141,111 +145,6 @@ __device__ void blk_tvc(const float* __restrict__ A, int64_t u, int64_t nk, int6
   }
 }
 
-// gx[j] = sum_{i,l} A[(i*nk + j)*v + l] gy[i*v + l]; a group of G lanes per j.
-// Compensated FP32 sums (the reduction can be long).
-__device__ void blk_gx(const float* __restrict__ A, int64_t u, int64_t nk, int64_t v, const float* __restrict__ gy,
-                       float* __restrict__ gx, int G, int64_t j_begin = 0, int64_t j_end = -1) {
-  const int lane = threadIdx.x & 31;
-  const int p = lane & (G - 1);
-  const int gw = 32 / G;
-  const int64_t je = (j_end < 0) ? nk : j_end;
-  const int64_t ngroups = (int64_t)(kBBT / 32) * gw;
-  for (int64_t base = j_begin + (int64_t)(threadIdx.x >> 5) * gw; base < je; base += ngroups) {
-    const int64_t j = base + lane / G;
-    KahanF32 acc;
-    if (j < je) {
-      if (v >= G) {
-        for (int64_t i = 0; i < u; i++) {
-          const float* a = A + (i * nk + j) * v;
-          const float* g = gy + i * v;
-          float part = 0.0f;
-          for (int64_t l = p; l < v; l += 8 * G) {  // eight predicated loads in flight
-            float av[8], gv[8];
-#pragma unroll
-            for (int q = 0; q < 8; q++) {
-              const bool ok = l + q * G < v;
-              av[q] = ok ? __ldcs(a + l + q * G) : 0.0f;
-              gv[q] = ok ? __ldg(g + l + q * G) : 0.0f;
-            }
-#pragma unroll
-            for (int q = 0; q < 8; q++) part = __fmaf_rn(av[q], gv[q], part);
-          }
-          acc.add(part);
-        }
-      } else {
-        // v < G: lanes split the slabs i, eight slabs in flight per lane
-        for (int64_t i = p; i < u; i += 8 * G) {
-          for (int64_t l = 0; l < v; l++) {
-            float av[8], gv[8];
-#pragma unroll
-            for (int q = 0; q < 8; q++) {
-              const int64_t ii = i + q * G;
-              const bool ok = ii < u;
-              av[q] = ok ? __ldcs(A + (ii * nk + j) * v + l) : 0.0f;
-              gv[q] = ok ? __ldg(gy + ii * v + l) : 0.0f;
-            }
-            float part = 0.0f;
-#pragma unroll
-            for (int q = 0; q < 8; q++) part = __fmaf_rn(av[q], gv[q], part);
-            acc.add(part);
-          }
-        }
-      }
-    }
-    float t = acc.value();
-    for (int off = G / 2; off > 0; off >>= 1) t += __shfl_xor_sync(0xFFFFFFFFu, t, off);
-    if (j < je && p == 0) gx[j] = t;
-  }
-}
-
-// gx[j] for a few j (<= 8) with all 256 threads: a team of T = 256/J
-// threads (whole warps) per j splits the (i, l) space (lane t: l = t % v'
-// and i = t / v' with v' = min(v, T), stepping by T / v'), compensated sums,
-// then warp shuffles and a fixed-order sum of the team's warps.
-__device__ void blk_gx_teams(const float* __restrict__ A, int64_t u, int64_t nk, int64_t v,
-                             const float* __restrict__ gy, float* __restrict__ gx, int64_t j_begin, int64_t j_end,
-                             float* red /* shared, kBBT/32 floats */) {
-  const int J = (int)(j_end - j_begin);
-  int T = 256;
-  while (T > 32 && T * J > 256) T >>= 1;
-  const int team = threadIdx.x / T, t = threadIdx.x % T;
-  const int64_t j = j_begin + team;
-  const int64_t vv = v < T ? v : T;
-  const int lanes = (int)((T / vv) * vv);
-  KahanF32 acc;
-  if (team < J && t < lanes) {
-    const int64_t l0 = t % vv, i0 = t / vv, istep = T / vv;
-    for (int64_t i = i0; i < u; i += istep) {
-      const float* a = A + (i * nk + j) * v;
-      const float* g = gy + i * v;
-      float part = 0.0f;
-      for (int64_t l = l0; l < v; l += 8 * vv) {
-        float av[8], gv[8];
-#pragma unroll
-        for (int q = 0; q < 8; q++) {
-          const bool ok = l + q * vv < v;
-          av[q] = ok ? __ldcs(a + l + q * vv) : 0.0f;
-          gv[q] = ok ? __ldg(g + l + q * vv) : 0.0f;
-        }
-#pragma unroll
-        for (int q = 0; q < 8; q++) part = __fmaf_rn(av[q], gv[q], part);
-      }
-      acc.add(part);
-    }
-  }
-  float s = acc.value();
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, off);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (t == 0 && team < J) {
-    float tot = 0.0f;
-    for (int w = 0; w < T / 32; w++) tot += red[team * (T / 32) + w];
-    gx[j] = tot;
-  }
-  __syncthreads();
-}
-
 // gA[(i*nk + j)*v + l] = gy[i*v + l] * x[j] over slabs i in [i0, i1) and
 // rows j in [j0, j1), with coalesced stores: threads own columns l (v >= 32)
 // or positions q = j*v + l of the slab (v < 32, whole slabs).
@@ -314,27 +213,172 @@ __device__ int grab(int* counter, int* slot) {
 // ------------------------------------------------------------ the kernels
 
 // A unit of work: kind 0 = outputs [a0, a1) of the forward contraction,
-// 1 = gx[j] for j in [a0, a1), 2 = gA over slabs [a0, a1) and rows [c0, c1).
+// 1 = gx over slabs [a0, a1) and rows j in [c0, c1) (slab range e0 of the
+// tensor's gxk, e1 gx items in all), 2 = gA over slabs [a0, a1) and rows
+// [c0, c1).
 struct WItem {
   int b, kind;
   int64_t a0, a1, c0, c1;
+  int e0, e1;
 };
 
+// gx over a rectangle of one tensor: slabs [i0, i1) x rows j in [j0, j1)
+// (item ks of the tensor's gxk slab ranges):
+//   part[j] = sum_{i in [i0,i1), l < v} A[(i*nk + j)*v + l] gy[i*v + l].
+// Rows of v >= 32 go to warps: warp w takes the slabs i = i0 + w (mod 8) of
+// every j (or, when the item has fewer than 8 slabs, the w-th 32-aligned
+// segment of every row), lanes stride over l; each warp's sum for j (FP32
+// folded every 64 products into a compensated pair, then a fixed xor tree) goes
+// to red[w][j - j0] and the 8 warp sums are added in w order (j1 - j0 <=
+// kGxJ).  Rows of v < 32 go to columns: the item's columns c = j*v + l
+// (contiguous in every slab) are taken in chunks of at most kBBT; a chunk
+// narrower than the block gives the spare threads alternate slabs (phases).
+// Each thread streams its column down its slabs (eight in flight, folded
+// every 64 slabs), the phases of a column are added in phase order and the
+// columns of a j in l order.  With gxk > 1 the slab ranges write partials
+// [ks][j] and the tensor's last item to finish (counted per tensor) sums them
+// in slab-range order into gx and resets the counter: deterministic, no
+// waiting.
+constexpr int64_t kGxWarpRows = 32;  // v at or above which rows go to warps
+constexpr int64_t kGxJ = 256;        // rows j per warp-mapped item
+
+__device__ void blk_gx_rect(const BItem& it, int64_t i0, int64_t i1, int64_t j0, int64_t j1, int ks, int items,
+                            int* cnt, float* partials, float* red, int* flag) {
+  const int64_t S = it.nk * it.v, v = it.v;
+  float* dst = (it.gxk > 1) ? partials + it.gxp + (int64_t)ks * it.nk : it.gx;
+  const int t = threadIdx.x;
+  if (v >= kGxWarpRows) {
+    const int w = t >> 5, lane = t & 31;
+    const bool phase = i1 - i0 >= 8;
+    const int64_t seg = phase ? v : ((v + 8 * 32 - 1) / (8 * 32)) * 32;
+    const int64_t ls = phase ? 0 : min((int64_t)w * seg, v);
+    const int64_t L = min(seg, v - ls);
+    const int64_t ib = phase ? i0 + w : i0, di = phase ? 8 : 1;
+    for (int64_t j = j0; j < j1; j++) {
+      KahanF32 tot;
+      int64_t i = ib;
+      const float* a = it.A + (i * it.nk + j) * v + ls;
+      const float* g = it.gy + i * v + ls;
+      // folded every 16 lane passes (at most 64 products per partial sum)
+      for (; i + 3 * di < i1; i += 4 * di, a += 4 * di * S, g += 4 * di * v)
+        for (int64_t lb = 0; lb < L; lb += 16 * 32) {
+          const int64_t le = min(lb + 16 * 32, L);
+          float acc = 0.0f;
+          for (int64_t l = lb + lane; l < le; l += 32) {
+            const float x0 = __ldcs(a + l), x1 = __ldcs(a + di * S + l);
+            const float x2 = __ldcs(a + 2 * di * S + l), x3 = __ldcs(a + 3 * di * S + l);
+            const float y0 = __ldg(g + l), y1 = __ldg(g + di * v + l);
+            const float y2 = __ldg(g + 2 * di * v + l), y3 = __ldg(g + 3 * di * v + l);
+            acc = __fmaf_rn(x0, y0, acc);
+            acc = __fmaf_rn(x1, y1, acc);
+            acc = __fmaf_rn(x2, y2, acc);
+            acc = __fmaf_rn(x3, y3, acc);
+          }
+          tot.add(acc);
+        }
+      for (; i < i1; i += di, a += di * S, g += di * v)
+        for (int64_t lb = 0; lb < L; lb += 64 * 32) {
+          const int64_t le = min(lb + 64 * 32, L);
+          float acc = 0.0f;
+          for (int64_t l = lb + lane; l < le; l += 32) acc = __fmaf_rn(__ldcs(a + l), __ldg(g + l), acc);
+          tot.add(acc);
+        }
+      float sw = tot.value();
+      for (int off = 16; off > 0; off >>= 1) sw = __fadd_rn(sw, __shfl_xor_sync(0xffffffffu, sw, off));
+      if (lane == 0) red[w * kGxJ + (j - j0)] = sw;
+    }
+    __syncthreads();
+    for (int64_t j = j0 + t; j < j1; j += kBBT) {
+      float sj = red[j - j0];
+      for (int q = 1; q < kBBT / 32; q++) sj = __fadd_rn(sj, red[q * kGxJ + (j - j0)]);
+      dst[j] = sj;
+    }
+    __syncthreads();
+  } else {
+    const int64_t C = (j1 - j0) * v;  // the item's columns in one slab
+    const int CW = (int)min(C, (int64_t)kBBT);
+    const int P = kBBT / CW;  // slab phases
+    const int ph = t / CW, cc = t - (t / CW) * CW;
+    for (int64_t cb = 0; cb < C; cb += CW) {
+      const int64_t c = j0 * v + cb + cc;  // column within the slab
+      float acc = 0.0f;
+      KahanF32 tot;
+      if (ph < P && cb + cc < C) {
+        const int64_t l = c - (c / v) * v;
+        const int64_t di = P;
+        const float* a = it.A + (i0 + ph) * S + c;
+        const float* g = it.gy + (i0 + ph) * v + l;
+        int64_t i = i0 + ph;
+        int blk = 0;
+        for (; i + 7 * di < i1; i += 8 * di, a += 8 * di * S, g += 8 * di * v) {
+          float av[8], gv[8];
+#pragma unroll
+          for (int q = 0; q < 8; q++) {
+            av[q] = __ldcs(a + q * di * S);
+            gv[q] = __ldg(g + q * di * v);
+          }
+#pragma unroll
+          for (int q = 0; q < 8; q++) acc = __fmaf_rn(av[q], gv[q], acc);
+          if (++blk == 8) {
+            tot.add(acc);
+            acc = 0.0f;
+            blk = 0;
+          }
+        }
+        for (; i < i1; i += di, a += di * S, g += di * v) acc = __fmaf_rn(__ldcs(a), __ldg(g), acc);
+        tot.add(acc);
+      }
+      red[t] = (ph < P && cb + cc < C) ? tot.value() : 0.0f;
+      __syncthreads();
+      if (t < CW && P > 1) {  // the phases of column cc, in phase order
+        float sc = red[t];
+        for (int q = 1; q < P; q++) sc = __fadd_rn(sc, red[q * CW + t]);
+        red[t] = sc;
+      }
+      __syncthreads();
+      // per j of the chunk: its columns in l order, added in chunk order
+      const int64_t c0 = j0 * v + cb, c1 = min(c0 + CW, j1 * v);
+      for (int64_t j = c0 / v + t; j * v < c1; j += kBBT) {
+        const int64_t a0 = max(j * v, c0), a1 = min((j + 1) * v, c1);
+        float sj = 0.0f;
+        for (int64_t q = a0; q < a1; q++) sj = __fadd_rn(sj, red[q - c0]);
+        dst[j] = (a0 == j * v) ? sj : __fadd_rn(dst[j], sj);  // the chunk holding l = 0 starts j
+      }
+      __syncthreads();
+    }
+  }
+  if (it.gxk > 1) {
+    __threadfence();
+    __syncthreads();
+    if (t == 0) *flag = (atomicAdd(cnt, 1) == items - 1);
+    __syncthreads();
+    if (*flag) {
+      __threadfence();
+      const float* Pp = partials + it.gxp;
+      for (int64_t j = t; j < it.nk; j += kBBT) {
+        KahanF32 sum;
+        for (int q = 0; q < it.gxk; q++) sum.add(__ldcg(Pp + (int64_t)q * it.nk + j));
+        it.gx[j] = sum.value();
+      }
+      if (t == 0) *cnt = 0;  // ready for the next launch
+    }
+    __syncthreads();
+  }
+}
+
 __global__ void __launch_bounds__(kBBT, 6) tvc_batched_kernel(const BItem* __restrict__ items,
-                                                           const WItem* __restrict__ work, int nwork, int* counter) {
+                                                           const WItem* __restrict__ work, int nwork, int* counter,
+                                                           int* gx_counters, float* gx_partials) {
   __shared__ int slot;
-  __shared__ float red[kBBT / 32];
+  __shared__ float red[(kBBT / 32) * kGxJ];
+  __shared__ int last_flag;
   for (int w = grab(counter, &slot); w < nwork; w = grab(counter, &slot)) {
     const WItem wi = work[w];
     const BItem it = items[wi.b];
     if (wi.kind == 0)
       blk_tvc(it.A, it.u, it.nk, it.v, it.x, it.y, it.gf, wi.a0, wi.a1);
-    else if (wi.kind == 1) {
-      if (wi.a1 - wi.a0 <= 8)
-        blk_gx_teams(it.A, it.u, it.nk, it.v, it.gy, it.gx, wi.a0, wi.a1, red);
-      else
-        blk_gx(it.A, it.u, it.nk, it.v, it.gy, it.gx, it.gb, wi.a0, wi.a1);
-    }
+    else if (wi.kind == 1)
+      blk_gx_rect(it, wi.a0, wi.a1, wi.c0, wi.c1, wi.e0, wi.e1, gx_counters + wi.b, gx_partials, red, &last_flag);
     else
       blk_gA(it.gy, it.x, it.gA, it.nk, it.v, wi.a0, wi.a1, wi.c0, wi.c1);
   }
@@ -429,29 +473,25 @@ int64_t clog2(int64_t x) {
   return r;
 }
 
-// Autotuner cache: (kind, log2 v, log2 n_k) -> G.
+// Autotuner cache of the forward contraction: (log2 v, log2 n_k) -> G.
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int>, int> g_tune;
+std::map<std::pair<int, int>, int> g_tune;
 std::map<void*, int> g_nwork;  // work items uploaded per workspace
 
-int rule_G(int kind, int64_t nk, int64_t v) {
-  if (kind == 0) {  // forward: lanes split n_k
-    if (v >= 32) return 1;
-    if (v >= 8) return 4;
-    return nk >= 64 ? 32 : 8;
-  }
-  // gx: lanes split the (i, l) columns (for v < 8 the slabs i)
-  return v >= 32 ? 32 : 8;
+int rule_G(int64_t nk, int64_t v) {  // lanes splitting n_k per forward output
+  if (v >= 32) return 1;
+  if (v >= 8) return 4;
+  return nk >= 64 ? 32 : 8;
 }
 
-int pick_G(int kind, int64_t nk, int64_t v) {
+int pick_G(int64_t nk, int64_t v) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  auto it = g_tune.find({kind, (int)clog2(v), (int)clog2(nk)});
-  return it != g_tune.end() ? it->second : rule_G(kind, nk, v);
+  auto it = g_tune.find({(int)clog2(v), (int)clog2(nk)});
+  return it != g_tune.end() ? it->second : rule_G(nk, v);
 }
 
 struct BLayout {
-  size_t off_counter = 0, off_items = 0, off_scratch = 0, total = 0;
+  size_t off_counter = 0, off_items = 0, off_scratch = 0, off_gxcnt = 0, off_gxpart = 0, total = 0;
   int64_t slen = 0, zlen = 0;
   int blocks = 0;
 };
@@ -462,18 +502,40 @@ constexpr int64_t kItemElems = 1 << 20;
 
 int64_t cdiv64(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
-void make_work(const std::vector<BItem>& items, std::vector<WItem>* work) {
+int64_t assign_gx(std::vector<BItem>* items);
+
+// Rectangle of a gx item: jr rows j by sr slabs, about kItemElems elements.
+// Warp-mapped rows (v >= 32) take every slab of a j before cutting the slabs
+// and keep 8 slabs (one per warp) where the tensor has them; column-mapped
+// rows take whole slab widths.
+void gx_rect(const BItem& it, int64_t* jr, int64_t* sr) {
+  const int64_t v = std::max<int64_t>(1, it.v);
+  if (v >= kGxWarpRows)  // whole slab ranges per j first; at most kGxJ rows, 8 slabs when there are
+    *jr = std::max<int64_t>(1, std::min<int64_t>(std::min(it.nk, kGxJ), kItemElems / std::max<int64_t>(1, it.u * v)));
+  else  // whole slab widths first (coalesced columns)
+    *jr = std::max<int64_t>(1, std::min<int64_t>(it.nk, kItemElems / v));
+  *sr = std::max<int64_t>(1, std::min<int64_t>(it.u, kItemElems / (*jr * v)));
+  if (v >= kGxWarpRows) *sr = std::max(*sr, std::min<int64_t>(it.u, 8));
+}
+
+void make_work(std::vector<BItem>& items, std::vector<WItem>* work) {
+  assign_gx(&items);
   work->clear();
   for (int b = 0; b < (int)items.size(); b++) {
     const BItem& it = items[b];
-    const int64_t uv = it.u * it.v, N = uv * it.nk;
+    const int64_t uv = it.u * it.v;
     if (it.y) {
       const int64_t per = std::max<int64_t>(256, cdiv64(kItemElems, it.nk) / 256 * 256);
-      for (int64_t o = 0; o < uv; o += per) work->push_back({b, 0, o, std::min(uv, o + per), 0, 0});
+      for (int64_t o = 0; o < uv; o += per) work->push_back({b, 0, o, std::min(uv, o + per), 0, 0, 0, 0});
     }
-    if (it.gx) {
-      const int64_t per = std::max<int64_t>(1, kItemElems / std::max<int64_t>(1, uv));
-      for (int64_t j = 0; j < it.nk; j += per) work->push_back({b, 1, j, std::min(it.nk, j + per), 0, 0});
+    if (it.gx) {  // rectangles (see assign_gx), partials summed by the tensor's last item
+      int64_t jr, sr;
+      gx_rect(it, &jr, &sr);
+      const int nitems = (int)(cdiv64(it.u, sr) * cdiv64(it.nk, jr));
+      int ks = 0;
+      for (int64_t i = 0; i < it.u; i += sr, ks++)
+        for (int64_t j = 0; j < it.nk; j += jr)
+          work->push_back({b, 1, i, std::min(it.u, i + sr), j, std::min(it.nk, j + jr), ks, nitems});
     }
     if (it.gA) {
       const int64_t S = it.nk * it.v;
@@ -483,13 +545,13 @@ void make_work(const std::vector<BItem>& items, std::vector<WItem>* work) {
         const int64_t slabs = std::max<int64_t>(1, kItemElems / (rows * it.v));
         for (int64_t i = 0; i < it.u; i += slabs)
           for (int64_t j = 0; j < it.nk; j += rows)
-            work->push_back({b, 2, i, std::min(it.u, i + slabs), j, std::min(it.nk, j + rows)});
+            work->push_back({b, 2, i, std::min(it.u, i + slabs), j, std::min(it.nk, j + rows), 0, 0});
       } else {
         const int64_t slabs = std::max<int64_t>(1, kItemElems / S);
-        for (int64_t i = 0; i < it.u; i += slabs) work->push_back({b, 2, i, std::min(it.u, i + slabs), 0, it.nk});
+        for (int64_t i = 0; i < it.u; i += slabs)
+          work->push_back({b, 2, i, std::min(it.u, i + slabs), 0, it.nk, 0, 0});
       }
     }
-    (void)N;
   }
 }
 
@@ -497,12 +559,36 @@ void make_work(const std::vector<BItem>& items, std::vector<WItem>* work) {
 // count, from the same construction the call uses).
 tvc_status check_tvc_descs(const tvc_batch_desc* d, int count, std::vector<BItem>* items);
 
+// gx items per tensor (slab ranges of about kItemElems elements) and the
+// offsets of their partials; called on every item list before make_work.
+int64_t assign_gx(std::vector<BItem>* items) {
+  int64_t off = 0;
+  for (BItem& it : *items) {
+    it.gxk = 0;
+    it.gxp = 0;
+    if (!it.gx) continue;
+    int64_t jr, sr;
+    gx_rect(it, &jr, &sr);
+    it.gxk = (int)cdiv64(it.u, sr);
+    if (it.gxk > 1) {
+      it.gxp = off;
+      off += (int64_t)it.gxk * it.nk;
+    }
+  }
+  return off;
+}
+
 BLayout layout_tvc_items(const std::vector<BItem>& items, size_t nwork) {
   BLayout L;
   L.off_counter = 0;
   L.off_items = 256;
   L.off_scratch = L.off_items + align_up(items.size() * sizeof(BItem), 256);
-  L.total = L.off_scratch + align_up(nwork * sizeof(WItem), 256);
+  L.off_gxcnt = L.off_scratch + align_up(nwork * sizeof(WItem), 256);
+  int64_t nparts = 0;
+  for (const BItem& it : items)
+    if (it.gxk > 1) nparts = std::max<int64_t>(nparts, it.gxp + (int64_t)it.gxk * it.nk);
+  L.off_gxpart = L.off_gxcnt + align_up(items.size() * sizeof(int), 256);
+  L.total = L.off_gxpart + align_up((size_t)std::max<int64_t>(1, nparts) * sizeof(float), 256);
   L.blocks = device_sms() * kBBlocksPerSM;
   return L;
 }
@@ -557,8 +643,9 @@ tvc_status check_tvc_descs(const tvc_batch_desc* d, int count, std::vector<BItem
       it.u = s.u;
       it.nk = s.nk;
       it.v = s.v;
-      it.gf = pick_G(0, s.nk, s.v);
-      it.gb = pick_G(1, s.nk, s.v);
+      it.gf = pick_G(s.nk, s.v);
+      it.gxk = 0;
+      it.gxp = 0;
       items->push_back(it);
     }
   }
@@ -599,7 +686,9 @@ extern "C" tvc_status tvc_batched(const tvc_batch_desc* descs, int count, int fl
             cudaSuccess ||
         cudaMemcpyAsync(w + L.off_scratch, work.data(), work.size() * sizeof(WItem), cudaMemcpyHostToDevice, st) !=
             cudaSuccess ||
-        cudaMemcpyAsync(hdr + 1, &nwork, sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        cudaMemcpyAsync(hdr + 1, &nwork, sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        // per-tensor gx counters: zero now; the last item of a tensor resets its own
+        cudaMemsetAsync(w + L.off_gxcnt, 0, items.size() * sizeof(int), st) != cudaSuccess)
       return TVC_ERR_CUDA;
     // The host vectors die here: wait for the copies (pageable sources).
     if (cudaStreamSynchronize(st) != cudaSuccess) return TVC_ERR_CUDA;
@@ -615,15 +704,17 @@ extern "C" tvc_status tvc_batched(const tvc_batch_desc* descs, int count, int fl
   }
   cudaMemsetAsync(hdr, 0, sizeof(int), st);
   tvc_batched_kernel<<<L.blocks, kBBT, 0, st>>>(reinterpret_cast<const BItem*>(w + L.off_items),
-                                               reinterpret_cast<const WItem*>(w + L.off_scratch), nwork, hdr);
+                                               reinterpret_cast<const WItem*>(w + L.off_scratch), nwork, hdr,
+                                               reinterpret_cast<int*>(w + L.off_gxcnt),
+                                               reinterpret_cast<float*>(w + L.off_gxpart));
   count_launches(1);
   return cuda_status(cudaGetLastError());
 }
 
 extern "C" tvc_status tvc_batched_autotune(const tvc_batch_desc* descs, int count, void* workspace, size_t ws_bytes,
                                            tvc_stream_t stream) {
-  // Times the candidate lane counts on one tensor of every shape class
-  // (forward contraction and gx) and records the fastest; synchronises.
+  // Times the candidate lane counts of the forward contraction on the
+  // tensors of every shape class and records the fastest; synchronises.
   if (count <= 0 || !descs) return TVC_ERR_INVALID_ARG;
   std::vector<BItem> items;
   tvc_status rc = check_tvc_descs(descs, count, &items);
@@ -634,30 +725,27 @@ extern "C" tvc_status tvc_batched_autotune(const tvc_batch_desc* descs, int coun
   if (!workspace || ws_bytes < L.total) return TVC_ERR_WORKSPACE;
   cudaStream_t st = (cudaStream_t)stream;
   char* w = static_cast<char*>(workspace);
-  // every shape class with the tensors that belong to it (forward, gx)
-  std::map<std::tuple<int, int, int>, std::vector<BItem>> classes;
-  for (const BItem& it : items)
-    for (int kind = 0; kind < 2; kind++) {
-      if (kind == 0 && !it.y) continue;
-      if (kind == 1 && !it.gx) continue;
-      BItem one = it;
-      one.y = kind == 0 ? it.y : nullptr;
-      one.gx = kind == 1 ? it.gx : nullptr;
-      one.gA = nullptr;
-      classes[std::make_tuple(kind, (int)clog2(it.v), (int)clog2(it.nk))].push_back(one);
-    }
+  // every shape class of forward rows (v == 1, where lanes split a row)
+  // with the tensors that belong to it
+  std::map<std::pair<int, int>, std::vector<BItem>> classes;
+  for (const BItem& it : items) {
+    if (!it.y || it.v != 1) continue;
+    BItem one = it;
+    one.gx = nullptr;
+    one.gA = nullptr;
+    classes[{(int)clog2(it.v), (int)clog2(it.nk)}].push_back(one);
+  }
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   const int cands[5] = {1, 4, 8, 16, 32};
   for (auto& kv : classes) {
-    const int kind = std::get<0>(kv.first);
     std::vector<BItem> sub = kv.second;  // at most 256 tensors of the class
     if (sub.size() > 256) sub.resize(256);
     float best = 1e30f;
-    int bestG = rule_G(kind, sub[0].nk, sub[0].v);
+    int bestG = rule_G(sub[0].nk, sub[0].v);
     for (int G : cands) {
-      for (BItem& it : sub) (kind == 0 ? it.gf : it.gb) = G;
+      for (BItem& it : sub) it.gf = G;
       std::vector<WItem> wk;
       make_work(sub, &wk);
       cudaMemcpy(w + L.off_items, sub.data(), sub.size() * sizeof(BItem), cudaMemcpyHostToDevice);
@@ -668,7 +756,9 @@ extern "C" tvc_status tvc_batched_autotune(const tvc_batch_desc* descs, int coun
         cudaEventRecord(e0, st);
         tvc_batched_kernel<<<L.blocks, kBBT, 0, st>>>(reinterpret_cast<const BItem*>(w + L.off_items),
                                                      reinterpret_cast<const WItem*>(w + L.off_scratch),
-                                                     (int)wk.size(), reinterpret_cast<int*>(w + L.off_counter));
+                                                     (int)wk.size(), reinterpret_cast<int*>(w + L.off_counter),
+                                                     reinterpret_cast<int*>(w + L.off_gxcnt),
+                                                     reinterpret_cast<float*>(w + L.off_gxpart));
         cudaEventRecord(e1, st);
         cudaEventSynchronize(e1);
         float ms = 0.0f;
@@ -735,8 +825,8 @@ extern "C" tvc_status hopm_batched(const hopm_batch_desc* descs, int count, int 
       // lanes per output of the two big contractions (A x_1 x_1, A x_0 x_0)
       int64_t N = 1;
       for (int m = 0; m < e.order; m++) N *= e.dims[m];
-      it.gsel[0] = pick_G(0, e.dims[0], N / e.dims[0]);
-      it.gsel[1] = pick_G(0, e.dims[1], N / (e.dims[0] * e.dims[1]));
+      it.gsel[0] = pick_G(e.dims[0], N / e.dims[0]);
+      it.gsel[1] = pick_G(e.dims[1], N / (e.dims[0] * e.dims[1]));
       it.lam = e.lambda_out;
       it.status = e.status_out;
       items.push_back(it);

@@ -60,6 +60,25 @@ def test_batched_tvc_and_adjoints():
     check_items(items, host, spec)
 
 
+# gx work items are rectangles (slab range x rows j): these shapes give
+# several slab ranges summed by the tensor's last item (column-mapped rows
+# v < 32 and warp-mapped rows v >= 32), several row ranges, the per-warp
+# row segments of items with fewer than 8 slabs, and rows longer than an item.
+GX_RECT_SPEC = [((40000, 30), 1), ((3000, 50, 10), 1), ((266, 8, 4000), 1), ((5, 600, 64), 1),
+                ((8, 300000), 0), ((9, 5, 31), 0), ((2, 3, 40), 0), ((20, 700, 40), 1), ((1100, 1000), 1)]
+
+
+def test_batched_gx_rectangles_twice():
+    items, host = make_items(GX_RECT_SPEC, 30)
+    batch = tg.TVCBatch(items)
+    for rep in range(2):  # the per-tensor counters are reset by the last item
+        for it in items:
+            it["gx"].zero_()
+        batch.run()
+        torch.cuda.synchronize()
+        check_items(items, host, GX_RECT_SPEC)
+
+
 def test_batched_graph_replay_and_autotune():
     spec = random_batch(60, 1)
     items, host = make_items(spec, 20)
