@@ -67,6 +67,7 @@ def _load():
             lib = ctypes.CDLL(build())
             P, I, D, L = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64
             lib.oracle_tvc.argtypes = [I, P, P, I, P, I, P, P, D, D]
+            lib.oracle_tmc.argtypes = [I, P, P, I, P, I, P, L, P, D, D]
             lib.oracle_tvc_grad_x.argtypes = [I, P, P, I, P, I, P, P]
             lib.oracle_tvc_grad_A.argtypes = [I, P, I, P, P, P]
             for f in (lib.oracle_hopm, lib.oracle_hopm3):
@@ -137,6 +138,25 @@ def tvc(A, mode: int, x, *, dims=None, scales=None, y=None, alpha=1.0, beta=0.0)
                             float(alpha), float(beta))
     if st:
         raise OracleError(st, "tvc")
+    return out
+
+
+def tmc(A, mode: int, X, *, dims=None, scales=None, Y=None, alpha=1.0, beta=0.0) -> np.ndarray:
+    """Y = alpha * (A x_mode X) + beta * Y in FP64 for an R x n_mode matrix X
+    (shape: dims with n_mode replaced by R)."""
+    A, d, dt = _tensor(A, dims)
+    s = _scales(dt, scales, int(d[0]))
+    X = np.ascontiguousarray(np.asarray(X, dtype=np.float64))
+    if X.ndim != 2 or not 0 <= mode < d.size or X.shape[1] != d[mode] or X.shape[0] < 1:
+        raise ValueError("bad mode or matrix shape")
+    R = int(X.shape[0])
+    out_shape = tuple(R if i == mode else int(n) for i, n in enumerate(d))
+    out = (np.zeros(out_shape) if Y is None else
+           np.ascontiguousarray(np.asarray(Y, dtype=np.float64)).reshape(out_shape).copy())
+    st = _load().oracle_tmc(dt, _p(A), _p(s), int(d.size), _p(d), int(mode), _p(X), R, _p(out),
+                            float(alpha), float(beta))
+    if st:
+        raise OracleError(st, "tmc")
     return out
 
 

@@ -135,6 +135,29 @@ int oracle_tvc(int dtype, const void* A, const float* scales, int order, const i
   return OR_OK;
 }
 
+/* -------------------------------------------------------------------- TMC */
+
+/* Tensor-matrix contraction in mode k (the TMC of Section 1, the mode-k
+ * product with a matrix): X is an R x n_k matrix in row-major order and
+ *     Y[i][r][l] = alpha * sum_{j<n_k} A[i][j][l] X[r][j] + beta * Y[i][r][l],
+ * i.e. Y has the shape of A with n_k replaced by R, row-major.  Row r of X
+ * gives the mode-k TVC with that row.  beta == 0 means Y is not read. */
+int oracle_tmc(int dtype, const void* A, const float* scales, int order, const int64_t* dims, int mode,
+               const double* X, int64_t R, double* Y, double alpha, double beta) {
+  if (!valid_shape(order, dims) || mode < 0 || mode >= order || R < 1) return OR_ERR_ARG;
+  int64_t u = prod(dims, 0, mode), nk = dims[mode], v = prod(dims, mode + 1, order);
+  int64_t slab = prod(dims, 1, order);
+  int64_t nout = u * R * v;
+#pragma omp parallel for schedule(static)
+  for (int64_t o = 0; o < nout; o++) {
+    int64_t i = o / (R * v), r = (o / v) % R, l = o % v;
+    double s = 0.0;
+    for (int64_t j = 0; j < nk; j++) s += elem(dtype, A, scales, slab, (i * nk + j) * v + l) * X[r * nk + j];
+    Y[o] = (beta != 0.0) ? alpha * s + beta * Y[o] : alpha * s;
+  }
+  return OR_OK;
+}
+
 /* ---------------------------------------------------------- TVC gradients */
 
 /* Gradient of L(Y) with Y = A x_k x, with respect to x:

@@ -159,6 +159,88 @@ def test_tvc_bad_arguments():
         oracle.tvc(A, 0, np.ones(3))
 
 
+# ------------------------------------------------------------------ TMC ----
+
+def _tmc_ref(A, k, X):
+    """Mode-k product with a matrix through numpy's tensordot: contract the
+    n_k axis of A with the columns of X, then move the new R axis to k."""
+    return np.moveaxis(np.tensordot(A, X, axes=([k], [1])), -1, k)
+
+
+@pytest.mark.parametrize("dims", SHAPES)
+def test_tmc_matches_tensordot_every_mode(dims):
+    A = rand_tensor(dims)
+    for k, n in enumerate(dims):
+        for R in (1, 3, 8):
+            X = synth.tensor("u64", 2, (R, n), synth.stream_x(k))
+            got = oracle.tmc(A, k, X)
+            want = _tmc_ref(A, k, X)
+            assert got.shape == want.shape == tuple(R if i == k else m for i, m in enumerate(dims))
+            np.testing.assert_allclose(got, want, rtol=1e-13, atol=1e-13)
+
+
+def test_tmc_selection_matrices_gather_slices_exactly():
+    """A 0/1 matrix whose row r selects index pi(r) of mode k makes the
+    product a gather of slices: exact, and a transposed use of X fails."""
+    dims = (3, 5, 4, 2)
+    A = rand_tensor(dims, sid=4)
+    for k, n in enumerate(dims):
+        rng = np.random.default_rng(10 + k)
+        for R in (n, 2 * n + 1, 1):
+            pi = rng.integers(0, n, size=R) if R != n else rng.permutation(n)
+            X = np.zeros((R, n))
+            X[np.arange(R), pi] = 1.0
+            assert np.array_equal(oracle.tmc(A, k, X), np.take(A, pi, axis=k))
+
+
+def test_tmc_rank1_closed_form():
+    dims = (4, 5, 6, 3)
+    us = [synth.vector("u64", 5, 30 + j, n) for j, n in enumerate(dims)]
+    A = np.einsum("i,j,k,l->ijkl", *us)
+    for k in range(4):
+        X = synth.tensor("u64", 6, (5, dims[k]), synth.stream_x(k))
+        factors = [X @ us[k] if j == k else us[j] for j in range(4)]
+        want = np.einsum("i,j,k,l->ijkl", *factors)
+        np.testing.assert_allclose(oracle.tmc(A, k, X), want, rtol=1e-13, atol=1e-15)
+
+
+def test_tmc_matrix_and_vector_cases():
+    A = rand_tensor((9, 13))
+    X1 = synth.tensor("u64", 1, (4, 13), 1)
+    X0 = synth.tensor("u64", 1, (6, 9), 2)
+    np.testing.assert_allclose(oracle.tmc(A, 1, X1), A @ X1.T, rtol=1e-13)
+    np.testing.assert_allclose(oracle.tmc(A, 0, X0), X0 @ A, rtol=1e-13)
+    a = synth.vector("u64", 3, 3, 11)
+    Xa = synth.tensor("u64", 3, (5, 11), 4)
+    np.testing.assert_allclose(oracle.tmc(a, 0, Xa), Xa @ a, rtol=1e-13)
+
+
+def test_tmc_rows_are_tvcs_alpha_beta_and_narrow_types():
+    dims = (3, 4, 5)
+    src = synth.tensor("lognormal", 0, dims).astype(np.float32)
+    for k in range(3):
+        X = synth.tensor("u64", 7, (3, dims[k]), synth.stream_x(k))
+        Y0 = synth.tensor("u64", 8, tuple(3 if i == k else n for i, n in enumerate(dims)))
+        for fmt in (oracle.BF16, oracle.E4M3, oracle.F16):
+            codes, scales = oracle.quantise(src, fmt)
+            deq = oracle.dequantise(codes, scales)
+            got = oracle.tmc(codes, k, X, scales=scales, Y=Y0, alpha=-0.5, beta=2.0)
+            np.testing.assert_allclose(got, -0.5 * _tmc_ref(deq, k, X) + 2.0 * Y0, rtol=1e-13, atol=1e-13)
+            for r in range(3):
+                np.testing.assert_array_equal(np.take(oracle.tmc(codes, k, X, scales=scales), r, axis=k),
+                                              oracle.tvc(codes, k, X[r], scales=scales))
+
+
+def test_tmc_bad_arguments():
+    A = rand_tensor((2, 3))
+    with pytest.raises(ValueError):
+        oracle.tmc(A, 1, np.ones((2, 2)))
+    with pytest.raises(ValueError):
+        oracle.tmc(A, 2, np.ones((2, 3)))
+    with pytest.raises(ValueError):
+        oracle.tmc(A, 0, np.ones(2))
+
+
 # ------------------------------------------------------------ gradients ----
 
 @pytest.mark.parametrize("dims", [(4, 5, 3), (6, 7), (2, 3, 2, 3)])
