@@ -104,6 +104,29 @@ tvc_status tvc_ex(const void* A, int order, const int64_t* dims, int mode, const
 size_t tvc_workspace_size(int order, const int64_t* dims, int mode, tvc_dtype dtype);
 
 /*
+ * Mode-k tensor-matrix contraction (TMC, Section 1; the mode-k product with
+ * a matrix that the higher-order orthogonal iteration for the Tucker
+ * decomposition and CP alternating least squares are built from):
+ *     Y[i][r][l] := alpha * sum_{j < n_mode} A[i][j][l] X[r][j] + beta * Y[i][r][l]
+ * with A read as u x n_mode x v (Section 3).  X: R x n_mode matrix, row-major,
+ * FP64 for TVC_F64 / TVC_F32D and FP32 otherwise.  Y: the dims of A with
+ * n_mode replaced by R, row-major, same type as X; beta == 0 means Y is not
+ * read.  Row r of Y (along mode) is the TVC of A with row r of X.  A is read
+ * once per pass of up to 16 rows of X (8 for FP64 vectors; R <= 4 and R <= 8
+ * use one pass of 4 or 8).  FP32 accumulation for FP32 and the narrow
+ * types, FP64 multiply-adds for FP64 and single-double storage.
+ * slab_scales: as for tvc_ex.  workspace: tmc_workspace_size(...) bytes (0
+ * when the output columns fill the GPU without splitting n_mode).
+ * Errors: TVC_ERR_INVALID_ARG for a bad shape, mode, dtype, R < 1, a NULL
+ * pointer or a misaligned A, X or Y; TVC_ERR_WORKSPACE when the workspace is
+ * too small; nothing is launched then.
+ */
+tvc_status tmc(const void* A, int order, const int64_t* dims, int mode, const void* X, int64_t R, void* Y,
+               tvc_dtype dtype, const float* slab_scales, double alpha, double beta, void* workspace,
+               size_t ws_bytes, tvc_stream_t stream);
+size_t tmc_workspace_size(int order, const int64_t* dims, int mode, int64_t R, tvc_dtype dtype);
+
+/*
  * tvc_noalloc: the same contraction as tvc_ex() with alpha = 1, beta = 0,
  * for callers that cannot allocate device memory (code run from a host
  * callback queued with cudaLaunchHostFunc, where CUDA API calls are not

@@ -70,6 +70,10 @@ def load_library():
         lib.tvc_ex.restype = I
         lib.tvc_workspace_size.argtypes = [I, P, I, I]
         lib.tvc_workspace_size.restype = Z
+        lib.tmc.argtypes = [P, I, P, I, P, L, P, I, P, D, D, P, Z, P]
+        lib.tmc.restype = I
+        lib.tmc_workspace_size.argtypes = [I, P, I, L, I]
+        lib.tmc_workspace_size.restype = Z
         lib.hopm.argtypes = [P, I, P, P, I, D, P, P, P, P, I, P, P, Z, P]
         lib.hopm.restype = I
         lib.hopm_workspace_size.argtypes = [I, P, I]
@@ -229,6 +233,49 @@ def tvc(A: torch.Tensor, mode: int, x: torch.Tensor, *, y: torch.Tensor | None =
                             float(alpha), float(beta), _ptr(workspace), workspace.numel(), st)
     _check(status, "tvc")
     return y
+
+
+def tmc_workspace_size(shape, mode: int, R: int, code: int) -> int:
+    """Bytes of workspace tmc(..., workspace=...) needs for this shape and R."""
+    lib = load_library()
+    return int(lib.tmc_workspace_size(len(shape), _dims_array(shape), int(mode), int(R), int(code)))
+
+
+def tmc(A: torch.Tensor, mode: int, X: torch.Tensor, *, Y: torch.Tensor | None = None,
+        scales: torch.Tensor | None = None, alpha: float = 1.0, beta: float = 0.0,
+        workspace: torch.Tensor | None = None, stream=None, shape=None) -> torch.Tensor:
+    """Y = alpha * (A x_mode X) + beta * Y on the GPU for an R x n_mode matrix X
+    (float64 for float64 storage, float32 otherwise; float64 with float32
+    storage selects single-double).  Y has the shape of A with n_mode
+    replaced by R."""
+    lib = load_library()
+    code = _with_vectors(dtype_code(A), X)
+    shape = tuple(A.shape) if shape is None else tuple(int(n) for n in shape)
+    if not 0 <= mode < len(shape):
+        raise ValueError("mode out of range")
+    vt = vec_dtype(code)
+    if X.dtype != vt or X.dim() != 2 or X.shape[1] != shape[mode] or X.shape[0] < 1 or not X.is_contiguous():
+        raise ValueError(f"X must be a contiguous {vt} matrix with {shape[mode]} columns")
+    R = int(X.shape[0])
+    out_shape = tuple(R if i == mode else n for i, n in enumerate(shape))
+    if Y is None:
+        if beta != 0.0:
+            raise ValueError("beta != 0 needs Y")
+        Y = torch.empty(out_shape, dtype=vt, device=A.device)
+    elif Y.dtype != vt or Y.numel() != math.prod(out_shape) or not Y.is_contiguous():
+        raise ValueError("Y has the wrong dtype or size")
+    if scales is not None and scales.dtype != torch.float32:
+        raise ValueError("scales must be float32")
+    _check_cuda(A, X, Y, scales, workspace)
+    dims = _dims_array(shape)
+    if workspace is None:
+        need = lib.tmc_workspace_size(len(shape), dims, int(mode), R, code)
+        if need:
+            workspace = torch.empty(need, dtype=torch.uint8, device=A.device)
+    status = lib.tmc(_ptr(A), len(shape), dims, int(mode), _ptr(X), R, _ptr(Y), code, _ptr(scales), float(alpha),
+                     float(beta), _ptr(workspace), 0 if workspace is None else workspace.numel(), _stream(stream))
+    _check(status, "tmc")
+    return Y
 
 
 class HopmResult:

@@ -1,0 +1,553 @@
+// Mode-k tensor-matrix contraction (the TMC of Section 1, the building
+// block of the higher-order orthogonal iteration for the Tucker
+// decomposition and of CP alternating least squares):
+//     Y[i][r][l] = alpha * sum_{j < n_k} A[i][j][l] X[r][j] + beta * Y[i][r][l]
+// for an R x n_k matrix X, with A read as u x n_k x v (Section 3) and Y of
+// the shape of A with n_k replaced by R (row-major).
+//
+// Like the TVC it streams A once in its own order whatever k is: one thread
+// owns one output column (i, l) for a block of RP rows of X and walks the
+// n_k entries A[i][j][l], 16 (or 8) rows in flight (a warp reads 32
+// consecutive l of a row when v >= 32; for v == 1 each thread streams its
+// own row with 16-byte loads).  The rows of X are staged in shared memory as Xs[j][r] (the whole
+// n_k range of the block when it fits in 48 KB, else in chunks), so each
+// element of A costs RP multiply-adds against broadcast shared-memory
+// reads, with one block barrier per chunk.  X with more than RP rows is done in
+// passes over A (blockIdx.z); few outputs split n_k over blockIdx.y and a
+// second kernel adds the partial sums in a fixed order (deterministic).
+// FP32 accumulation (two levels: 64 products, then the running sum) for
+// FP32 and the narrow types; FP64 multiply-adds for FP64 and single-double.
+#include <algorithm>
+#include <type_traits>
+
+#include "common.cuh"
+#include "internal.h"
+#include "tma.cuh"
+
+namespace tvcg {
+namespace {
+
+constexpr int kTmcThreads = 256;
+constexpr int kXsBytes = 16 * 1024;  // shared memory for the staged rows of X
+
+template <tvc_dtype DT>
+using TmcW = std::conditional_t<kF64Acc<DT>, double, float>;  // vectors and accumulators
+
+template <tvc_dtype DT>
+struct TmcArgs {
+  const typename Elem<DT>::T* A;
+  const TmcW<DT>* X;    // R x nk
+  const float* scales;  // narrow types, nullable
+  TmcW<DT>* Y;          // u x R x v
+  TmcW<DT>* partial;    // splits x (u R v) when splits > 1
+  int64_t u, nk, v, uv, R, upi0, chunk, uRv;
+  int mode0, splits, jc;  // jc: entries j of X staged at a time (a multiple of 16)
+  double alpha, beta;
+};
+
+// U entries of one output column: rows j .. j+U-1 at stride v (streaming
+// loads), or (VJ) the contiguous run p[0..U-1] of a row (v == 1, U-element
+// aligned) with L1-cached 16-byte loads, so that the 32-byte sector a
+// thread's row piece shares with nothing else stays in L1 between its loads.
+template <tvc_dtype DT, bool VJ, int U>
+__device__ __forceinline__ void loadU(const typename Elem<DT>::T* p, int64_t v, typename Elem<DT>::C (&r)[U]) {
+  using E = Elem<DT>;
+  if constexpr (VJ) {
+    constexpr int P = 16 / E::kSize;  // elements per 16-byte piece
+    static_assert(U % P == 0, "U must be a multiple of the 16-byte piece");
+#pragma unroll
+    for (int h = 0; h < U / P; h++) {
+      typename E::C t[P];
+      E::template load<P, true>(p + P * h, t);
+#pragma unroll
+      for (int e = 0; e < P; e++) r[P * h + e] = t[e];
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < U; q++) {
+      typename E::C t[1];
+      E::template load<1>(p + q * v, t);
+      r[q] = t[0];
+    }
+  }
+}
+
+// acc[r] += a * Xs[j][r] for r < RP, Xs read in 16-byte pieces.
+template <int RP, class W, class C>
+__device__ __forceinline__ void mac_row(W (&acc)[RP], C a, const W* xs) {
+  if constexpr (sizeof(W) == 4) {
+#pragma unroll
+    for (int r = 0; r < RP; r += 4) {
+      const float4 xv = *reinterpret_cast<const float4*>(xs + r);
+      acc[r] = __fmaf_rn(a, xv.x, acc[r]);
+      acc[r + 1] = __fmaf_rn(a, xv.y, acc[r + 1]);
+      acc[r + 2] = __fmaf_rn(a, xv.z, acc[r + 2]);
+      acc[r + 3] = __fmaf_rn(a, xv.w, acc[r + 3]);
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < RP; r += 2) {
+      const double2 xv = *reinterpret_cast<const double2*>(xs + r);
+      acc[r] = fma((double)a, xv.x, acc[r]);
+      acc[r + 1] = fma((double)a, xv.y, acc[r + 1]);
+    }
+  }
+}
+
+// Rows of A in flight per thread: 16 when the accumulators leave room.
+template <tvc_dtype DT, int RP>
+inline constexpr int kTmcU = (RP * sizeof(TmcW<DT>) <= 32) ? 16 : 8;
+
+template <tvc_dtype DT, int RP, bool VJ>
+__global__ void __launch_bounds__(kTmcThreads) tmc_kernel(const TmcArgs<DT> a) {
+  using E = Elem<DT>;
+  using T = typename E::T;
+  using C = typename E::C;
+  using W = TmcW<DT>;
+  constexpr bool kF32 = sizeof(W) == 4;
+  extern __shared__ __align__(16) unsigned char xs_raw[];
+  W* Xs = reinterpret_cast<W*>(xs_raw);  // [jc][RP]
+  const int64_t o = (int64_t)blockIdx.x * kTmcThreads + threadIdx.x;  // output column (i, l)
+  const bool act = o < a.uv;
+  const int64_t i = act ? o / a.v : 0;
+  const int64_t l = act ? o - i * a.v : 0;
+  const int64_t r0 = (int64_t)blockIdx.z * RP;
+  const int64_t j0 = (int64_t)blockIdx.y * a.chunk;
+  const int64_t j1 = min(a.nk, j0 + a.chunk);
+  const T* p = a.A + (i * a.nk + j0) * a.v + l;
+  W acc[RP], sum[RP];
+#pragma unroll
+  for (int r = 0; r < RP; r++) {
+    acc[r] = 0;
+    sum[r] = 0;
+  }
+  const bool fold_scale = kNarrow<DT> && a.mode0 && a.scales;
+  int blk = 0;
+  for (int64_t jc = j0; jc < j1; jc += a.jc) {
+    const int jn = (int)min((int64_t)a.jc, j1 - jc);
+    __syncthreads();  // the previous chunk is consumed
+    for (int t = threadIdx.x; t < jn * RP; t += kTmcThreads) {
+      const int jl = t / RP, r = t - (t / RP) * RP;
+      W xv = 0;
+      if (r0 + r < a.R) {
+        xv = a.X[(r0 + r) * a.nk + jc + jl];
+        if (fold_scale) xv *= (W)__ldg(a.scales + jc + jl);  // k = 0: row j lies in slab j
+      }
+      Xs[t] = xv;
+    }
+    __syncthreads();
+    if (act) {
+      constexpr int P16 = 16 / Elem<DT>::kSize;
+      constexpr int U = (VJ && kTmcU<DT, RP> < P16) ? P16 : kTmcU<DT, RP>;
+      int jl = 0;
+      for (; jl + U <= jn; jl += U) {
+        C vu[U];
+        loadU<DT, VJ, U>(p, a.v, vu);
+#pragma unroll
+        for (int q = 0; q < U; q++) mac_row<RP>(acc, vu[q], Xs + (jl + q) * RP);
+        p += U * a.v;
+        if constexpr (kF32) {
+          if (++blk == 64 / U) {  // 64 products per partial sum
+#pragma unroll
+            for (int r = 0; r < RP; r++) {
+              sum[r] += acc[r];
+              acc[r] = 0;
+            }
+            blk = 0;
+          }
+        }
+      }
+      for (; jl < jn; jl++, p += a.v) {
+        C v1[1];
+        E::template load<1>(p, v1);
+        mac_row<RP>(acc, v1[0], Xs + jl * RP);
+      }
+    }
+  }
+  if (!act) return;
+  W sc = 1;
+  if constexpr (kNarrow<DT>) {
+    if (!a.mode0 && a.scales) sc = (W)__ldg(a.scales + i / a.upi0);
+  }
+#pragma unroll
+  for (int r = 0; r < RP; r++) {
+    if (r0 + r < a.R) {
+      const W val = (sum[r] + acc[r]) * sc;
+      const int64_t y = (i * a.R + r0 + r) * a.v + l;
+      if (a.splits > 1) {
+        a.partial[blockIdx.y * a.uRv + y] = val;
+      } else {
+        W out = (W)a.alpha * val;
+        if (a.beta != 0.0) out += (W)a.beta * a.Y[y];
+        a.Y[y] = out;
+      }
+    }
+  }
+}
+
+// FP32 storage, v % VEC == 0: each thread owns VEC = 16 / RP consecutive
+// output columns (i, l..l+VEC-1) and keeps the next D rows of that piece
+// (4 * VEC bytes) in flight with cp.async into its own shared-memory slots,
+// consuming row j while row j + D is fetched (it waits only for its own
+// copies).  VEC x RP accumulators (two levels), X staged as in tmc_kernel.
+__device__ __forceinline__ void cp_async_piece(void* smem, const void* gmem, int bytes) {
+  if (bytes == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
+  else if (bytes == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_group() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+template <int RP>
+struct TmcAsync {
+  static constexpr int VEC = 16 / RP;               // 4, 2, 1 floats per piece
+  static constexpr int D = VEC == 4 ? 8 : 16;       // rows in flight per thread
+  static constexpr int kStageBytes = D * kTmcThreads * VEC * 4;
+};
+
+template <int RP>
+__global__ void __launch_bounds__(kTmcThreads) tmc_cols_async_kernel(const TmcArgs<TVC_F32> a) {
+  using Q = TmcAsync<RP>;
+  constexpr int VEC = Q::VEC, D = Q::D;
+  __shared__ __align__(16) float stage[D][kTmcThreads * VEC];
+  extern __shared__ __align__(16) unsigned char xs_raw[];
+  float* Xs = reinterpret_cast<float*>(xs_raw);  // [jc][RP]
+  const int t = threadIdx.x;
+  const int64_t o = ((int64_t)blockIdx.x * kTmcThreads + t) * VEC;
+  const bool act = o < a.uv;
+  const int64_t oo = act ? o : 0;
+  const int64_t i = oo / a.v;
+  const int64_t l = oo - i * a.v;
+  const int64_t r0 = (int64_t)blockIdx.z * RP;
+  const int64_t j0 = (int64_t)blockIdx.y * a.chunk;
+  const int64_t j1 = min(a.nk, j0 + a.chunk);
+  const float* p = a.A + (i * a.nk + j0) * a.v + l;
+  const int64_t n = act ? j1 - j0 : 0;
+#pragma unroll
+  for (int d = 0; d < D; d++) {
+    if (d < n) cp_async_piece(&stage[d][t * VEC], p + d * a.v, VEC * 4);
+    cp_async_commit_group();
+  }
+  float acc[VEC][RP], sum[VEC][RP];
+#pragma unroll
+  for (int e = 0; e < VEC; e++)
+#pragma unroll
+    for (int r = 0; r < RP; r++) {
+      acc[e][r] = 0.0f;
+      sum[e][r] = 0.0f;
+    }
+  int slot = 0, blk = 0;
+  int64_t row = 0;
+  for (int64_t jc = j0; jc < j1; jc += a.jc) {
+    const int jn = (int)min((int64_t)a.jc, j1 - jc);
+    __syncthreads();  // the previous chunk of X is consumed
+    for (int q = t; q < jn * RP; q += kTmcThreads) {
+      const int jl = q / RP, r = q - (q / RP) * RP;
+      Xs[q] = (r0 + r < a.R) ? a.X[(r0 + r) * a.nk + jc + jl] : 0.0f;
+    }
+    __syncthreads();
+    if (act) {
+      for (int jl = 0; jl < jn; jl++, row++) {
+        cp_async_wait_group<D - 1>();
+        float v[VEC];
+        if constexpr (VEC == 4) {
+          const float4 f = *reinterpret_cast<const float4*>(&stage[slot][t * 4]);
+          v[0] = f.x;
+          v[1] = f.y;
+          v[2] = f.z;
+          v[3] = f.w;
+        } else if constexpr (VEC == 2) {
+          const float2 f = *reinterpret_cast<const float2*>(&stage[slot][t * 2]);
+          v[0] = f.x;
+          v[1] = f.y;
+        } else {
+          v[0] = stage[slot][t];
+        }
+        // the slot is free again: fetch row + D into it
+        if (row + D < n) cp_async_piece(&stage[slot][t * VEC], p + (row + D) * a.v, VEC * 4);
+        cp_async_commit_group();
+#pragma unroll
+        for (int e = 0; e < VEC; e++) mac_row<RP>(acc[e], v[e], Xs + jl * RP);
+        if (++slot == D) slot = 0;
+        if (++blk == 64) {
+#pragma unroll
+          for (int e = 0; e < VEC; e++)
+#pragma unroll
+            for (int r = 0; r < RP; r++) {
+              sum[e][r] += acc[e][r];
+              acc[e][r] = 0.0f;
+            }
+          blk = 0;
+        }
+      }
+    }
+  }
+  cp_async_wait_group<0>();
+  if (!act) return;
+#pragma unroll
+  for (int r = 0; r < RP; r++) {
+    if (r0 + r < a.R) {
+#pragma unroll
+      for (int e = 0; e < VEC; e++) {
+        const float val = sum[e][r] + acc[e][r];
+        const int64_t y = (i * a.R + r0 + r) * a.v + l + e;
+        if (a.splits > 1) {
+          a.partial[blockIdx.y * a.uRv + y] = val;
+        } else {
+          float out = (float)a.alpha * val;
+          if (a.beta != 0.0) out += (float)a.beta * a.Y[y];
+          a.Y[y] = out;
+        }
+      }
+    }
+  }
+}
+
+// FP32 storage, v == 1 (rows), n_k % 8 == 0: each thread owns one row i and
+// keeps its next D pieces of 8 entries (a whole 32-byte sector, two 16-byte
+// cp.async) in flight in its own shared-memory slots; X is read by broadcast
+// as in tmc_kernel.  RP accumulators (two levels).
+constexpr int kRowsD = 4;
+
+template <int RP>
+__global__ void __launch_bounds__(kTmcThreads) tmc_rows_async_kernel(const TmcArgs<TVC_F32> a) {
+  __shared__ __align__(16) float stage[kRowsD][kTmcThreads * 8];
+  extern __shared__ __align__(16) unsigned char xs_raw[];
+  float* Xs = reinterpret_cast<float*>(xs_raw);  // [jc][RP]
+  const int t = threadIdx.x;
+  const int64_t i = (int64_t)blockIdx.x * kTmcThreads + t;
+  const bool act = i < a.uv;
+  const int64_t r0 = (int64_t)blockIdx.z * RP;
+  const int64_t j0 = (int64_t)blockIdx.y * a.chunk;
+  const int64_t j1 = min(a.nk, j0 + a.chunk);
+  const float* p = a.A + (act ? i : 0) * a.nk + j0;
+  const int64_t n = act ? (j1 - j0) / 8 : 0;  // pieces
+#pragma unroll
+  for (int d = 0; d < kRowsD; d++) {
+    if (d < n) {
+      cp_async_piece(&stage[d][t * 8], p + 8 * d, 16);
+      cp_async_piece(&stage[d][t * 8 + 4], p + 8 * d + 4, 16);
+    }
+    cp_async_commit_group();
+  }
+  float acc[RP], sum[RP];
+#pragma unroll
+  for (int r = 0; r < RP; r++) {
+    acc[r] = 0.0f;
+    sum[r] = 0.0f;
+  }
+  int slot = 0, blk = 0;
+  int64_t piece = 0;
+  for (int64_t jc = j0; jc < j1; jc += a.jc) {
+    const int jn = (int)min((int64_t)a.jc, j1 - jc);
+    __syncthreads();  // the previous chunk of X is consumed
+    for (int q = t; q < jn * RP; q += kTmcThreads) {
+      const int jl = q / RP, r = q - (q / RP) * RP;
+      Xs[q] = (r0 + r < a.R) ? a.X[(r0 + r) * a.nk + jc + jl] : 0.0f;
+    }
+    __syncthreads();
+    if (act) {
+      for (int jl = 0; jl < jn; jl += 8, piece++) {
+        cp_async_wait_group<kRowsD - 1>();
+        const float4 f0 = *reinterpret_cast<const float4*>(&stage[slot][t * 8]);
+        const float4 f1 = *reinterpret_cast<const float4*>(&stage[slot][t * 8 + 4]);
+        // the slot is free again: fetch piece + D into it
+        if (piece + kRowsD < n) {
+          cp_async_piece(&stage[slot][t * 8], p + 8 * (piece + kRowsD), 16);
+          cp_async_piece(&stage[slot][t * 8 + 4], p + 8 * (piece + kRowsD) + 4, 16);
+        }
+        cp_async_commit_group();
+        const float v[8] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w};
+#pragma unroll
+        for (int q = 0; q < 8; q++) mac_row<RP>(acc, v[q], Xs + (jl + q) * RP);
+        if (++slot == kRowsD) slot = 0;
+        if (++blk == 8) {  // 64 products per partial sum
+#pragma unroll
+          for (int r = 0; r < RP; r++) {
+            sum[r] += acc[r];
+            acc[r] = 0.0f;
+          }
+          blk = 0;
+        }
+      }
+    }
+  }
+  cp_async_wait_group<0>();
+  if (!act) return;
+#pragma unroll
+  for (int r = 0; r < RP; r++) {
+    if (r0 + r < a.R) {
+      const float val = sum[r] + acc[r];
+      const int64_t y = i * a.R + r0 + r;
+      if (a.splits > 1) {
+        a.partial[blockIdx.y * a.uRv + y] = val;
+      } else {
+        float out = (float)a.alpha * val;
+        if (a.beta != 0.0) out += (float)a.beta * a.Y[y];
+        a.Y[y] = out;
+      }
+    }
+  }
+}
+
+// Y[o] = alpha * sum_s partial[s][o] + beta * Y[o], s ascending.
+template <class W>
+__global__ void tmc_reduce_kernel(const W* __restrict__ partial, W* __restrict__ Y, int64_t n, int splits,
+                                  double alpha, double beta) {
+  for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (int64_t)gridDim.x * blockDim.x) {
+    W s = 0;
+    for (int k = 0; k < splits; k++) s += partial[(int64_t)k * n + o];
+    W r = (W)alpha * s;
+    if (beta != 0.0) r += (W)beta * Y[o];
+    Y[o] = r;
+  }
+}
+
+// Launch plan: rows of X per pass, passes, split of n_k.
+struct TmcPlan {
+  int rp = 8, passes = 1, splits = 1, jc = 8, vec = 1;
+  bool async = false;       // FP32 column pieces through the cp.async pipeline
+  bool rows_async = false;  // FP32 rows (v == 1) through the cp.async pipeline
+  int64_t chunk = 0, blocks_x = 0;
+  bool vj = false;
+  size_t ws = 0;
+};
+
+int tmc_rp(tvc_dtype dt, int64_t R) {
+  const bool f64 = vec_size(dt) == 8;
+  if (R <= 4) return 4;
+  if (R <= 8 || f64) return 8;
+  return 16;
+}
+
+// A == nullptr (the workspace query) plans for a 16-byte aligned A; the
+// query reports the larger workspace of the aligned and unaligned plans.
+TmcPlan tmc_plan(const Shape& s, int64_t R, tvc_dtype dt, const void* A, bool a16 = false) {
+  TmcPlan p;
+  p.rp = tmc_rp(dt, R);
+  p.passes = (int)((R + p.rp - 1) / p.rp);
+  const int avec = 16 / p.rp;
+  const bool f32 = dt == TVC_F32 && p.rp <= 8;
+  p.async = f32 && s.v > 1 && s.v % avec == 0 && (A == nullptr ? a16 : aligned(A, 4 * avec));
+  p.rows_async = f32 && p.rp == 8 && s.v == 1 && s.nk % 8 == 0 && (A == nullptr ? a16 : aligned(A, 16));
+  p.vec = p.async ? avec : 1;
+  p.blocks_x = (s.uv / p.vec + kTmcThreads - 1) / kTmcThreads;
+  const int64_t want = 4LL * device_sms();  // blocks for a full GPU
+  int64_t have = p.blocks_x * p.passes;
+  int64_t splits = 1;
+  if (have < want) splits = std::min<int64_t>((want + have - 1) / have, std::max<int64_t>(1, s.nk / 256));
+  p.chunk = ((s.nk + splits - 1) / splits + 15) / 16 * 16;
+  p.splits = (int)((s.nk + p.chunk - 1) / p.chunk);
+  p.vj = s.v == 1 && s.nk % 16 == 0 && aligned(A, 16);
+  const int jmax = kXsBytes / (p.rp * (int)vec_size(dt)) / 16 * 16;
+  p.jc = (int)std::min<int64_t>(jmax, p.chunk);
+  p.ws = p.splits > 1 ? (size_t)p.splits * (size_t)(s.uv * R) * vec_size(dt) : 0;
+  return p;
+}
+
+template <tvc_dtype DT, int RP>
+void launch_rp(const TmcArgs<DT>& a, const TmcPlan& p, cudaStream_t st) {
+  dim3 grid((unsigned)p.blocks_x, (unsigned)p.splits, (unsigned)p.passes);
+  const size_t smem = (size_t)p.jc * RP * sizeof(TmcW<DT>);
+  if constexpr (DT == TVC_F32) {
+    if constexpr (RP <= 8) {
+      if (p.async) {
+        tmc_cols_async_kernel<RP><<<grid, kTmcThreads, smem, st>>>(a);
+        return;
+      }
+      if (p.rows_async) {
+        tmc_rows_async_kernel<RP><<<grid, kTmcThreads, smem, st>>>(a);
+        return;
+      }
+    }
+  }
+  if (p.vj)
+    tmc_kernel<DT, RP, true><<<grid, kTmcThreads, smem, st>>>(a);
+  else
+    tmc_kernel<DT, RP, false><<<grid, kTmcThreads, smem, st>>>(a);
+}
+
+template <tvc_dtype DT>
+tvc_status run(const void* A, const Shape& s, const void* X, int64_t R, void* Y, const float* scales, double alpha,
+               double beta, void* ws, const TmcPlan& p, cudaStream_t st) {
+  using W = TmcW<DT>;
+  TmcArgs<DT> a;
+  a.A = static_cast<const typename Elem<DT>::T*>(A);
+  a.X = static_cast<const W*>(X);
+  a.scales = scales;
+  a.Y = static_cast<W*>(Y);
+  a.partial = static_cast<W*>(ws);
+  a.u = s.u;
+  a.nk = s.nk;
+  a.v = s.v;
+  a.uv = s.uv;
+  a.R = R;
+  a.upi0 = s.upi0;
+  a.chunk = p.chunk;
+  a.uRv = s.uv * R;
+  a.mode0 = s.mode == 0;
+  a.splits = p.splits;
+  a.jc = p.jc;
+  a.alpha = alpha;
+  a.beta = beta;
+  if (p.blocks_x > 0x7FFFFFFF || p.passes > 65535) return TVC_ERR_UNSUPPORTED;
+  switch (p.rp) {
+    case 4: launch_rp<DT, 4>(a, p, st); break;
+    case 8: launch_rp<DT, 8>(a, p, st); break;
+    default:
+      if constexpr (!kF64Acc<DT>) launch_rp<DT, 16>(a, p, st);
+      break;
+  }
+  int launches = 1;
+  if (p.splits > 1) {
+    const int64_t n = s.uv * R;
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 8LL * device_sms());
+    tmc_reduce_kernel<W><<<blocks, 256, 0, st>>>(static_cast<const W*>(ws), static_cast<W*>(Y), n, p.splits, alpha,
+                                                 beta);
+    launches++;
+  }
+  count_launches(launches);
+  return cuda_status(cudaGetLastError());
+}
+
+}  // namespace
+}  // namespace tvcg
+
+using namespace tvcg;
+
+extern "C" size_t tmc_workspace_size(int order, const int64_t* dims, int mode, int64_t R, tvc_dtype dtype) {
+  Shape s;
+  if (!valid_dtype(dtype) || R < 1 || make_shape(order, dims, mode, &s) != TVC_OK) return 0;
+  return std::max(tmc_plan(s, R, dtype, nullptr, true).ws, tmc_plan(s, R, dtype, nullptr, false).ws);
+}
+
+extern "C" tvc_status tmc(const void* A, int order, const int64_t* dims, int mode, const void* X, int64_t R, void* Y,
+                          tvc_dtype dtype, const float* slab_scales, double alpha, double beta, void* workspace,
+                          size_t ws_bytes, tvc_stream_t stream) {
+  if (!valid_dtype(dtype) || !A || !X || !Y || R < 1) return TVC_ERR_INVALID_ARG;
+  Shape s;
+  tvc_status rc = make_shape(order, dims, mode, &s);
+  if (rc != TVC_OK) return rc;
+  int64_t uRv;
+  if (__builtin_mul_overflow(s.uv, R, &uRv) || uRv >= ((int64_t)1 << 62)) return TVC_ERR_INVALID_ARG;
+  if (!aligned(A, elem_size(dtype)) || !aligned(X, vec_size(dtype)) || !aligned(Y, vec_size(dtype)))
+    return TVC_ERR_INVALID_ARG;
+  const TmcPlan p = tmc_plan(s, R, dtype, A);
+  if (p.ws > 0 && (!workspace || ws_bytes < p.ws)) return TVC_ERR_WORKSPACE;
+  cudaStream_t st = (cudaStream_t)stream;
+  switch (dtype) {
+    case TVC_F64: return run<TVC_F64>(A, s, X, R, Y, slab_scales, alpha, beta, workspace, p, st);
+    case TVC_F32: return run<TVC_F32>(A, s, X, R, Y, slab_scales, alpha, beta, workspace, p, st);
+    case TVC_BF16: return run<TVC_BF16>(A, s, X, R, Y, slab_scales, alpha, beta, workspace, p, st);
+    case TVC_E4M3: return run<TVC_E4M3>(A, s, X, R, Y, slab_scales, alpha, beta, workspace, p, st);
+    case TVC_F16: return run<TVC_F16>(A, s, X, R, Y, slab_scales, alpha, beta, workspace, p, st);
+    case TVC_F32D: return run<TVC_F32D>(A, s, X, R, Y, slab_scales, alpha, beta, workspace, p, st);
+  }
+  return TVC_ERR_INVALID_ARG;
+}

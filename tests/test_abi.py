@@ -79,3 +79,26 @@ def test_workspace_size_query(lib):
     assert lib.tvc_workspace_size(2, dims, 1, 1) == 0 or lib.tvc_workspace_size(2, dims, 1, 1) > 0
     bad = (ctypes.c_int64 * 2)(0, 3)
     assert lib.tvc_workspace_size(2, bad, 0, 0) == 0
+
+
+def test_tmc_validation_without_gpu(lib):
+    P, I, D, Z, L = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t, ctypes.c_int64
+    lib.tmc.argtypes = [P, I, P, I, P, L, P, I, P, D, D, P, Z, P]
+    lib.tmc.restype = I
+    lib.tmc_workspace_size.argtypes = [I, P, I, L, I]
+    lib.tmc_workspace_size.restype = Z
+    dims = (ctypes.c_int64 * 3)(4, 5, 6)
+    fake = ctypes.c_void_p(1 << 20)
+    args = lambda A=fake, X=fake, Y=fake, R=3, dt=0, mode=1, d=dims: (A, 3, d, mode, X, R, Y, dt, None, 1.0, 0.0,
+                                                                        None, 0, None)
+    assert lib.tmc(*args(R=0)) == 1                                  # R < 1
+    assert lib.tmc(*args(A=None)) == 1                               # null A
+    assert lib.tmc(*args(X=None)) == 1                               # null X
+    assert lib.tmc(*args(mode=3)) == 1                               # mode out of range
+    assert lib.tmc(*args(dt=9)) == 1                                 # dtype
+    assert lib.tmc(*args(Y=ctypes.c_void_p((1 << 20) + 4))) == 1     # Y not 8-byte aligned (FP64 vectors)
+    long = (ctypes.c_int64 * 2)(2, 1 << 20)
+    need = lib.tmc_workspace_size(2, long, 1, 8, 1)                  # two outputs per row of X: split n_k
+    assert need > 0
+    assert lib.tmc(fake, 2, long, 1, fake, 8, fake, 1, None, 1.0, 0.0, None, 0, None) == 3   # workspace
+    assert lib.tmc_workspace_size(2, long, 1, 0, 1) == 0
