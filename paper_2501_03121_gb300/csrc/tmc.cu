@@ -243,7 +243,8 @@ __global__ void __launch_bounds__(kTmcThreads) tmc_cols_async_kernel(const TmcAr
       sum[e][r] = 0.0f;
     }
   int slot = 0, blk = 0;
-  int64_t row = 0;
+  int64_t left = n - D;           // rows still to fetch after the prologue
+  const float* pf = p + D * a.v;  // next row to fetch
   for (int64_t jc = j0; jc < j1; jc += a.jc) {
     const int jn = (int)min((int64_t)a.jc, j1 - jc);
     __syncthreads();  // the previous chunk of X is consumed
@@ -253,7 +254,7 @@ __global__ void __launch_bounds__(kTmcThreads) tmc_cols_async_kernel(const TmcAr
     }
     __syncthreads();
     if (act) {
-      for (int jl = 0; jl < jn; jl++, row++) {
+      for (int jl = 0; jl < jn; jl++) {
         cp_async_wait_group<D - 1>();
         float v[VEC];
         if constexpr (VEC == 4) {
@@ -269,9 +270,11 @@ __global__ void __launch_bounds__(kTmcThreads) tmc_cols_async_kernel(const TmcAr
         } else {
           v[0] = stage[slot][t];
         }
-        // the slot is free again: fetch row + D into it
-        if (row + D < n) cp_async_piece(&stage[slot][t * VEC], p + (row + D) * a.v, VEC * 4);
+        // the slot is free again: fetch the row D ahead into it
+        if (left > 0) cp_async_piece(&stage[slot][t * VEC], pf, VEC * 4);
         cp_async_commit_group();
+        left--;
+        pf += a.v;
 #pragma unroll
         for (int e = 0; e < VEC; e++) mac_row<RP>(acc[e], v[e], Xs + jl * RP);
         if (++slot == D) slot = 0;
@@ -309,65 +312,128 @@ __global__ void __launch_bounds__(kTmcThreads) tmc_cols_async_kernel(const TmcAr
   }
 }
 
-// FP32 storage, v == 1 (rows), n_k % 8 == 0: each thread owns one row i and
-// keeps its next D pieces of 8 entries (a whole 32-byte sector, two 16-byte
-// cp.async) in flight in its own shared-memory slots; X is read by broadcast
-// as in tmc_kernel.  RP accumulators (two levels).
-constexpr int kRowsD = 4;
+// Rows (v == 1) by lane groups: G lanes (2, 4 or 8) share one row, lane g
+// reading the 16-byte pieces g, g + G, ... (P entries each), so a warp
+// reads 32 / G rows as contiguous runs.  X is staged transposed, Xt[r][j],
+// so a lane's P entries of row r of X are 16-byte shared-memory reads that
+// the 32 / G rows of the warp share (few lanes per row keep the shared-
+// memory traffic per element of A low).  Each lane keeps its next 8 pieces
+// in flight with cp.async into its own shared-memory slots.  Each lane
+// accumulates RP partial sums (two levels); at the end the group reduces
+// them by a butterfly that halves the values a lane keeps at every level
+// (RP - 1 + log2(G / RP) exchanges instead of RP log2 G), a fixed order.
+// A block owns 8 * 32 / G rows for its whole n_k range (chunks of X staged
+// in turn); when X fits in one chunk the block loops over further rows.
+template <int G, int K>
+__device__ __forceinline__ void group_reduce(float (&v)[K], int gl, int& base, bool& writer) {
+  int kk = K;
+  base = 0;
+  writer = true;
+#pragma unroll
+  for (int off = G / 2; off >= 1; off >>= 1) {
+    const bool hi = (gl & off) != 0;
+    if (kk > 1) {
+      const int half = kk / 2;
+#pragma unroll
+      for (int m = 0; m < K / 2; m++) {
+        if (m < half) {
+          const float send = hi ? v[m] : v[m + half];
+          const float keep = hi ? v[m + half] : v[m];
+          v[m] = __fadd_rn(keep, __shfl_xor_sync(0xFFFFFFFFu, send, off));
+        }
+      }
+      if (hi) base += half;
+      kk = half;
+    } else {
+      v[0] = __fadd_rn(v[0], __shfl_xor_sync(0xFFFFFFFFu, v[0], off));
+      writer = writer && !hi;
+    }
+  }
+}
+
+constexpr int kGroupD = 8;  // 16-byte pieces in flight per lane (cp.async)
 
 template <int RP>
-__global__ void __launch_bounds__(kTmcThreads) tmc_rows_async_kernel(const TmcArgs<TVC_F32> a) {
-  __shared__ __align__(16) float stage[kRowsD][kTmcThreads * 8];
+inline constexpr int kGroupJC = kXsBytes / (RP * 4);  // row stride of the transposed X (entries)
+
+template <tvc_dtype DT, int RP, int G>
+__global__ void __launch_bounds__(kTmcThreads) tmc_rows_group_kernel(const TmcArgs<DT> a, int loop_rows) {
+  using E = Elem<DT>;
+  using T = typename E::T;
+  constexpr int P = 16 / E::kSize;                    // entries per 16-byte piece
+  constexpr int RPB = (kTmcThreads / 32) * (32 / G);  // rows per block
+  constexpr int JT = kGroupJC<RP>;                    // a.jc <= JT
+  __shared__ __align__(16) uint4 stage[kGroupD][kTmcThreads];
   extern __shared__ __align__(16) unsigned char xs_raw[];
-  float* Xs = reinterpret_cast<float*>(xs_raw);  // [jc][RP]
-  const int t = threadIdx.x;
-  const int64_t i = (int64_t)blockIdx.x * kTmcThreads + t;
-  const bool act = i < a.uv;
+  float* Xt = reinterpret_cast<float*>(xs_raw);  // [RP][JT]
+  const int t = threadIdx.x, lane = t & 31, gl = lane & (G - 1);
+  const int row_in_block = (t >> 5) * (32 / G) + (lane / G);
   const int64_t r0 = (int64_t)blockIdx.z * RP;
   const int64_t j0 = (int64_t)blockIdx.y * a.chunk;
   const int64_t j1 = min(a.nk, j0 + a.chunk);
-  const float* p = a.A + (act ? i : 0) * a.nk + j0;
-  const int64_t n = act ? (j1 - j0) / 8 : 0;  // pieces
+  const int64_t pieces = (j1 - j0) / P;  // of the row in [j0, j1)
+  const bool fold_scale = kNarrow<DT> && a.mode0 && a.scales;
+  bool staged = false;
+  for (int64_t rb = blockIdx.x; rb * RPB < a.u; rb += gridDim.x) {
+    const int64_t i = rb * RPB + row_in_block;
+    const bool act = i < a.u;
+    const T* prow = a.A + (act ? i : 0) * a.nk + j0;
+    const int64_t n = act ? (pieces > gl ? (pieces - gl + G - 1) / G : 0) : 0;  // this lane's pieces
 #pragma unroll
-  for (int d = 0; d < kRowsD; d++) {
-    if (d < n) {
-      cp_async_piece(&stage[d][t * 8], p + 8 * d, 16);
-      cp_async_piece(&stage[d][t * 8 + 4], p + 8 * d + 4, 16);
+    for (int d = 0; d < kGroupD; d++) {
+      if (d < n) cp_async_piece(&stage[d][t], prow + (gl + (int64_t)d * G) * P, 16);
+      cp_async_commit_group();
     }
-    cp_async_commit_group();
-  }
-  float acc[RP], sum[RP];
+    float acc[RP], sum[RP];
 #pragma unroll
-  for (int r = 0; r < RP; r++) {
-    acc[r] = 0.0f;
-    sum[r] = 0.0f;
-  }
-  int slot = 0, blk = 0;
-  int64_t piece = 0;
-  for (int64_t jc = j0; jc < j1; jc += a.jc) {
-    const int jn = (int)min((int64_t)a.jc, j1 - jc);
-    __syncthreads();  // the previous chunk of X is consumed
-    for (int q = t; q < jn * RP; q += kTmcThreads) {
-      const int jl = q / RP, r = q - (q / RP) * RP;
-      Xs[q] = (r0 + r < a.R) ? a.X[(r0 + r) * a.nk + jc + jl] : 0.0f;
+    for (int r = 0; r < RP; r++) {
+      acc[r] = 0.0f;
+      sum[r] = 0.0f;
     }
-    __syncthreads();
-    if (act) {
-      for (int jl = 0; jl < jn; jl += 8, piece++) {
-        cp_async_wait_group<kRowsD - 1>();
-        const float4 f0 = *reinterpret_cast<const float4*>(&stage[slot][t * 8]);
-        const float4 f1 = *reinterpret_cast<const float4*>(&stage[slot][t * 8 + 4]);
-        // the slot is free again: fetch piece + D into it
-        if (piece + kRowsD < n) {
-          cp_async_piece(&stage[slot][t * 8], p + 8 * (piece + kRowsD), 16);
-          cp_async_piece(&stage[slot][t * 8 + 4], p + 8 * (piece + kRowsD) + 4, 16);
+    int blk = 0, slot = 0;
+    int64_t k = 0;                                      // next piece of this lane
+    int64_t left = n - kGroupD;                         // pieces still to fetch after the prologue
+    const T* pf = prow + (gl + (int64_t)kGroupD * G) * P;  // next piece to fetch
+    for (int64_t jc = j0; jc < j1; jc += a.jc) {
+      const int jn = (int)min((int64_t)a.jc, j1 - jc);
+      if (!(loop_rows && staged)) {
+        __syncthreads();  // the previous chunk of X is consumed
+        for (int q = t; q < RP * JT; q += kTmcThreads) {
+          const int r = q / JT, jl = q - (q / JT) * JT;
+          float xv = 0.0f;
+          if (jl < jn && r0 + r < a.R) {
+            xv = a.X[(r0 + r) * a.nk + jc + jl];
+            if (fold_scale) xv *= __ldg(a.scales + jc + jl);  // order 1: entry j lies in slab j
+          }
+          Xt[q] = xv;
         }
+        __syncthreads();
+        staged = true;
+      }
+      // this lane's pieces whose entries lie in [jc, jc + jn)
+      for (int jl = (int)((gl + k * G) * P - (jc - j0)); k < n && jl < jn; k++, jl += G * P) {
+        cp_async_wait_group<kGroupD - 1>();
+        float v[P];
+        E::template load<P, true>(reinterpret_cast<const T*>(&stage[slot][t]), v);
+        if (left > 0) cp_async_piece(&stage[slot][t], pf, 16);
         cp_async_commit_group();
-        const float v[8] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w};
+        left--;
+        pf += G * P;
+        if (++slot == kGroupD) slot = 0;
+        const float* xj = Xt + jl;
 #pragma unroll
-        for (int q = 0; q < 8; q++) mac_row<RP>(acc, v[q], Xs + (jl + q) * RP);
-        if (++slot == kRowsD) slot = 0;
-        if (++blk == 8) {  // 64 products per partial sum
+        for (int r = 0; r < RP; r++) {
+          const float* xr = xj + r * JT;
+#pragma unroll
+          for (int q = 0; q < P; q += 4) {
+            const float4 xv = *reinterpret_cast<const float4*>(xr + q);
+            acc[r] = __fmaf_rn(v[q], xv.x, acc[r]);
+            acc[r] = __fmaf_rn(v[q + 1], xv.y, acc[r]);
+            acc[r] = __fmaf_rn(v[q + 2], xv.z, acc[r]);
+            acc[r] = __fmaf_rn(v[q + 3], xv.w, acc[r]);
+          }
+        }
+        if (++blk == (64 + P - 1) / P) {  // about 64 products per partial sum
 #pragma unroll
           for (int r = 0; r < RP; r++) {
             sum[r] += acc[r];
@@ -377,22 +443,35 @@ __global__ void __launch_bounds__(kTmcThreads) tmc_rows_async_kernel(const TmcAr
         }
       }
     }
-  }
-  cp_async_wait_group<0>();
-  if (!act) return;
+    cp_async_wait_group<0>();
+    float tot[RP];
 #pragma unroll
-  for (int r = 0; r < RP; r++) {
-    if (r0 + r < a.R) {
-      const float val = sum[r] + acc[r];
-      const int64_t y = i * a.R + r0 + r;
-      if (a.splits > 1) {
-        a.partial[blockIdx.y * a.uRv + y] = val;
-      } else {
-        float out = (float)a.alpha * val;
-        if (a.beta != 0.0) out += (float)a.beta * a.Y[y];
-        a.Y[y] = out;
+    for (int r = 0; r < RP; r++) tot[r] = sum[r] + acc[r];
+    int base;
+    bool writer;
+    group_reduce<G, RP>(tot, gl, base, writer);
+    constexpr int KF = (RP / G) > 1 ? RP / G : 1;
+    if (act && writer) {
+      float sc = 1.0f;
+      if constexpr (kNarrow<DT>) {
+        if (!a.mode0 && a.scales) sc = __ldg(a.scales + i / a.upi0);
+      }
+#pragma unroll
+      for (int m = 0; m < KF; m++) {
+        if (r0 + base + m < a.R) {
+          const float val = tot[m] * sc;
+          const int64_t y = i * a.R + r0 + base + m;
+          if (a.splits > 1) {
+            a.partial[blockIdx.y * a.uRv + y] = val;
+          } else {
+            float out = (float)a.alpha * val;
+            if (a.beta != 0.0) out += (float)a.beta * a.Y[y];
+            a.Y[y] = out;
+          }
+        }
       }
     }
+    if (!loop_rows) break;
   }
 }
 
@@ -413,7 +492,8 @@ __global__ void tmc_reduce_kernel(const W* __restrict__ partial, W* __restrict__
 struct TmcPlan {
   int rp = 8, passes = 1, splits = 1, jc = 8, vec = 1;
   bool async = false;       // FP32 column pieces through the cp.async pipeline
-  bool rows_async = false;  // FP32 rows (v == 1) through the cp.async pipeline
+  int group = 0;            // lanes per row of the lane-group rows kernel (0: not used)
+  bool loop_rows = false;   // X staged once, the block loops over row groups
   int64_t chunk = 0, blocks_x = 0;
   bool vj = false;
   size_t ws = 0;
@@ -435,9 +515,20 @@ TmcPlan tmc_plan(const Shape& s, int64_t R, tvc_dtype dt, const void* A, bool a1
   const int avec = 16 / p.rp;
   const bool f32 = dt == TVC_F32 && p.rp <= 8;
   p.async = f32 && s.v > 1 && s.v % avec == 0 && (A == nullptr ? a16 : aligned(A, 4 * avec));
-  p.rows_async = f32 && p.rp == 8 && s.v == 1 && s.nk % 8 == 0 && (A == nullptr ? a16 : aligned(A, 16));
   p.vec = p.async ? avec : 1;
   p.blocks_x = (s.uv / p.vec + kTmcThreads - 1) / kTmcThreads;
+  // rows by lane groups: FP32-accumulated types, 16-byte pieces along rows
+  const int piece = 16 / (int)elem_size(dt);
+  if (vec_size(dt) == 4 && p.rp <= 8 && s.v == 1 && s.nk % piece == 0 && s.nk / piece >= 2 &&
+      (A == nullptr ? a16 : aligned(A, 16))) {
+    // G lanes per row: 128 contiguous bytes per row for FP32; fewer lanes
+    // for the narrow types so that more rows of a warp share each read of X
+    int g = elem_size(dt) == 4 ? 8 : elem_size(dt) == 2 ? 4 : 2;
+    while (g > 2 && g * piece > s.nk) g /= 2;
+    p.group = g;
+    const int64_t rpb = (kTmcThreads / 32) * (32 / g);
+    p.blocks_x = (s.u + rpb - 1) / rpb;
+  }
   const int64_t want = 4LL * device_sms();  // blocks for a full GPU
   int64_t have = p.blocks_x * p.passes;
   int64_t splits = 1;
@@ -447,6 +538,10 @@ TmcPlan tmc_plan(const Shape& s, int64_t R, tvc_dtype dt, const void* A, bool a1
   p.vj = s.v == 1 && s.nk % 16 == 0 && aligned(A, 16);
   const int jmax = kXsBytes / (p.rp * (int)vec_size(dt)) / 16 * 16;
   p.jc = (int)std::min<int64_t>(jmax, p.chunk);
+  if (p.group && p.splits == 1 && p.chunk <= p.jc) {
+    p.loop_rows = true;
+    p.blocks_x = std::min<int64_t>(p.blocks_x, 8LL * device_sms());
+  }
   p.ws = p.splits > 1 ? (size_t)p.splits * (size_t)(s.uv * R) * vec_size(dt) : 0;
   return p;
 }
@@ -455,14 +550,22 @@ template <tvc_dtype DT, int RP>
 void launch_rp(const TmcArgs<DT>& a, const TmcPlan& p, cudaStream_t st) {
   dim3 grid((unsigned)p.blocks_x, (unsigned)p.splits, (unsigned)p.passes);
   const size_t smem = (size_t)p.jc * RP * sizeof(TmcW<DT>);
+  if constexpr (!kF64Acc<DT> && RP <= 8) {
+    if (p.group) {
+      const size_t gsmem = (size_t)kGroupJC<RP> * RP * sizeof(float);
+      const int lr = p.loop_rows ? 1 : 0;
+      switch (p.group) {
+        case 2: tmc_rows_group_kernel<DT, RP, 2><<<grid, kTmcThreads, gsmem, st>>>(a, lr); break;
+        case 4: tmc_rows_group_kernel<DT, RP, 4><<<grid, kTmcThreads, gsmem, st>>>(a, lr); break;
+        default: tmc_rows_group_kernel<DT, RP, 8><<<grid, kTmcThreads, gsmem, st>>>(a, lr); break;
+      }
+      return;
+    }
+  }
   if constexpr (DT == TVC_F32) {
     if constexpr (RP <= 8) {
       if (p.async) {
         tmc_cols_async_kernel<RP><<<grid, kTmcThreads, smem, st>>>(a);
-        return;
-      }
-      if (p.rows_async) {
-        tmc_rows_async_kernel<RP><<<grid, kTmcThreads, smem, st>>>(a);
         return;
       }
     }

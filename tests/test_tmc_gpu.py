@@ -18,8 +18,13 @@ pytestmark = pytest.mark.gpu
 
 tg = pytest.importorskip("paper_2501_03121_gb300")
 
-SHAPES = [(7,), (100003,), (5, 3), (4, 1), (3, 1, 5), (6, 5, 4, 3), (3, 50, 64), (5, 1000), (3, 4099),
-          (4, 100, 7), (300, 40), (9, 33, 130), (7, 3072), (1001, 1536), (2, 3, 2, 3, 2, 3, 2), (3, 65536)]
+# Reaching every kernel: column pieces (v > 1), rows by lane groups of 4 to
+# 32 lanes (v == 1, rows of whole 16-byte pieces, an order-1 tensor with its
+# per-entry slab scales), the generic kernel (ragged rows, FP64), split n_k
+# (few outputs), several passes over A (R > 16) and ragged tails.
+SHAPES = [(7,), (64,), (100003,), (5, 3), (4, 1), (3, 1, 5), (6, 5, 4, 3), (3, 50, 64), (5, 1000), (3, 4099),
+          (4, 100, 7), (300, 40), (9, 33, 130), (7, 3072), (1001, 1536), (2, 3, 2, 3, 2, 3, 2), (3, 65536),
+          (50, 256), (17, 48), (3, 7, 128), (2, 4096)]
 CODES = [oracle.F64, oracle.F32, oracle.BF16, oracle.E4M3, oracle.F16]
 RS = [1, 3, 8, 13, 21]
 
