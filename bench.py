@@ -353,7 +353,7 @@ def hopm_bytes(dims, es, vs):
 
 
 def secondary(dev):
-    """HOPM and batched figures (other workloads; not part of `value`)."""
+    """HOPM, batched and TMC figures (other workloads; not part of `value`)."""
     import numpy as np
     import torch
     import synth
@@ -480,6 +480,24 @@ def secondary(dev):
                            "hopm10_ms": hms, "hopm10_GB/s": hbytes / (hms / 1e3) / 1e9,
                            "note": "one persistent launch each; effective GB/s (part of the data is L2-resident)"}
     del pool, gApool, items, hitems, batch, hb
+    torch.cuda.empty_cache()
+    # tensor-matrix contraction (Section 1's TMC, the HOOI / CP-ALS building
+    # block): 1024^3 FP32, R = 4 and 8 rows of X, every mode; algorithmic bytes
+    dims = (1024, 1024, 1024)
+    N = math.prod(dims)
+    A = torch.empty(N, dtype=torch.float32, device=dev)
+    sd.fill(A, "u32", 0, synth.STREAM_A)
+    res = {}
+    for R in (4, 8):
+        for k in range(3):
+            X = torch.from_numpy(synth.tensor("u32", 1, (R, dims[k]), synth.stream_x(k))).to(dev)
+            Y = torch.empty(N // dims[k] * R, dtype=torch.float32, device=dev)
+            ws = torch.empty(max(1, tg.tmc_workspace_size(dims, k, R, tg.F32)), dtype=torch.uint8, device=dev)
+            ms = _timed(lambda: tg.tmc(A, k, X, Y=Y, shape=dims, workspace=ws), 5)
+            res[f"R{R}_mode{k}_GB/s"] = (N * 4 + X.numel() * 4 + Y.numel() * 4) / (ms / 1e3) / 1e9
+            del X, Y, ws
+    out["tmc_1024^3_f32"] = res
+    del A
     torch.cuda.empty_cache()
     return out
 
