@@ -424,6 +424,18 @@ __device__ __forceinline__ void df_mac_fast(float& s, float& c, double a, XSplit
   c = __fadd_rn(c, __fadd_rn(err, e));
 }
 
+// The float-float split a = ah + al of an in-window double (the split of
+// df_mac_fast on its own, for kernels that reuse one element's pieces
+// against several x).
+__device__ __forceinline__ void df_split(double a, float& ah, float& al) {
+  const uint32_t lo = (uint32_t)__double2loint(a);
+  const uint32_t hi = (uint32_t)__double2hiint(a);
+  const uint32_t hb = __funnelshift_l(lo, hi - 0x38000000u, 3) | (hi & 0x80000000u);
+  ah = __uint_as_float(hb);
+  const float sc = __uint_as_float((hb & 0xFF800000u) - 0x1A000000u);
+  al = __fmul_rn(__uint2float_rn(lo & 0x1FFFFFFFu), sc);
+}
+
 // df_mac_fast with the window bit of a ORed into `bad`: kernels run every
 // element through it and redo the (rare) results that met an element
 // outside the window with DFMA.  An x outside its window needs no test: its

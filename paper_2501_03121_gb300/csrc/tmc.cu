@@ -16,7 +16,8 @@
 // passes over A (blockIdx.z); few outputs split n_k over blockIdx.y and a
 // second kernel adds the partial sums in a fixed order (deterministic).
 // FP32 accumulation (two levels: 64 products, then the running sum) for
-// FP32 and the narrow types; FP64 multiply-adds for FP64 and single-double.
+// FP32 and the narrow types; float-float products with FP64 totals for FP64
+// and single-double.
 #include <algorithm>
 #include <type_traits>
 
@@ -185,6 +186,155 @@ __global__ void __launch_bounds__(kTmcThreads) tmc_kernel(const TmcArgs<DT> a) {
   }
 }
 
+// FP64 and single-double storage: the products on the FP32 pipe in
+// float-float arithmetic, as in the TVC's FP64 kernels (one DFMA per
+// product would leave an FP64 TMC at a fraction of the bandwidth: the
+// FP64 pipe runs about two multiply-adds per SM per clock).  Each element
+// a is split once into ah + al (exact in the window 2^-64 <= |a| < 2^64);
+// each row r of X was split into xh + xl when staged; the product's error
+// terms go into a compensated pair (s_r, c_r), folded into an FP64 total
+// every 64 products.  Nonzero elements or entries of X outside their
+// windows (NaN pieces for X) flag the thread, which then recomputes its
+// outputs with FP64 multiply-adds: exact-window results are FP64-accurate,
+// the rest are the plain FP64 dot products.
+template <int RP>
+__device__ __forceinline__ void df_row(float (&s)[RP], float (&c)[RP], float ah, float al, const float2* xs) {
+#pragma unroll
+  for (int r = 0; r < RP; r += 2) {
+    const float4 x2 = *reinterpret_cast<const float4*>(xs + r);  // (xh, xl) of rows r, r + 1
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+      const float xh = h ? x2.z : x2.x, xl = h ? x2.w : x2.y;
+      const float pr = __fmul_rn(ah, xh);
+      float e = __fmaf_rn(ah, xh, -pr);
+      e = __fmaf_rn(ah, xl, e);
+      e = __fmaf_rn(al, xh, e);
+      float t, err;
+      two_sum(s[r + h], pr, t, err);
+      s[r + h] = t;
+      c[r + h] = __fadd_rn(c[r + h], __fadd_rn(err, e));
+    }
+  }
+}
+
+// Pieces of one element; zeros are exact (0 + 0), other elements outside
+// the window set `bad`.
+__device__ __forceinline__ void split_elem(double v, float& ah, float& al, uint32_t& bad) {
+  const bool z = v == 0.0;
+  bad |= (df_out_of_window(v) != 0u && !z) ? 1u : 0u;
+  df_split(v, ah, al);
+  ah = z ? 0.0f : ah;
+  al = z ? 0.0f : al;
+}
+__device__ __forceinline__ void split_elem(float v, float& ah, float& al, uint32_t& bad) {
+  bad |= (df_out_of_window(v) != 0u && v != 0.0f) ? 1u : 0u;
+  ah = v;
+  al = 0.0f;
+}
+
+template <tvc_dtype DT, int RP, bool VJ>
+__global__ void __launch_bounds__(kTmcThreads) tmc_f64_kernel(const TmcArgs<DT> a) {
+  using E = Elem<DT>;
+  using T = typename E::T;
+  using C = typename E::C;  // double (FP64) or float (single-double)
+  extern __shared__ __align__(16) unsigned char xs_raw[];
+  float2* Xs = reinterpret_cast<float2*>(xs_raw);  // [jc][RP] split entries of X
+  const int64_t o = (int64_t)blockIdx.x * kTmcThreads + threadIdx.x;  // output column (i, l)
+  const bool act = o < a.uv;
+  const int64_t i = act ? o / a.v : 0;
+  const int64_t l = act ? o - i * a.v : 0;
+  const int64_t r0 = (int64_t)blockIdx.z * RP;
+  const int64_t j0 = (int64_t)blockIdx.y * a.chunk;
+  const int64_t j1 = min(a.nk, j0 + a.chunk);
+  const T* p = a.A + (i * a.nk + j0) * a.v + l;
+  float s[RP], c[RP];
+  double d[RP];
+#pragma unroll
+  for (int r = 0; r < RP; r++) {
+    s[r] = 0.0f;
+    c[r] = 0.0f;
+    d[r] = 0.0;
+  }
+  uint32_t bad = 0;
+  constexpr int U = 8;
+  int blk = 0;
+  for (int64_t jc = j0; jc < j1; jc += a.jc) {
+    const int jn = (int)min((int64_t)a.jc, j1 - jc);
+    __syncthreads();  // the previous chunk is consumed
+    for (int t = threadIdx.x; t < jn * RP; t += kTmcThreads) {
+      const int jl = t / RP, r = t - (t / RP) * RP;
+      XSplit xsp{0.0f, 0.0f};
+      if (r0 + r < a.R) xsp = split_x(a.X[(r0 + r) * a.nk + jc + jl]);
+      Xs[t] = make_float2(xsp.xh, xsp.xl);
+    }
+    __syncthreads();
+    if (act) {
+      int jl = 0;
+      for (; jl + U <= jn; jl += U) {
+        C vu[U];
+        loadU<DT, VJ, U>(p, a.v, vu);
+#pragma unroll
+        for (int q = 0; q < U; q++) {
+          float ah, al;
+          split_elem(vu[q], ah, al, bad);
+          df_row<RP>(s, c, ah, al, Xs + (jl + q) * RP);
+        }
+        p += U * a.v;
+        if (++blk == 64 / U) {  // 64 products per compensated pair
+#pragma unroll
+          for (int r = 0; r < RP; r++) {
+            d[r] += (double)s[r];
+            d[r] += (double)c[r];
+            s[r] = 0.0f;
+            c[r] = 0.0f;
+          }
+          blk = 0;
+        }
+      }
+      for (; jl < jn; jl++, p += a.v) {
+        C v1[1];
+        E::template load<1>(p, v1);
+        float ah, al;
+        split_elem(v1[0], ah, al, bad);
+        df_row<RP>(s, c, ah, al, Xs + jl * RP);
+      }
+    }
+  }
+  if (!act) return;
+  bool redo = bad != 0;
+#pragma unroll
+  for (int r = 0; r < RP; r++) {
+    d[r] += (double)s[r];
+    d[r] += (double)c[r];
+    redo = redo || !isfinite(d[r]);
+  }
+  if (redo) {  // rare: plain FP64 multiply-adds over this thread's range
+#pragma unroll
+    for (int r = 0; r < RP; r++) d[r] = 0.0;
+    const T* q = a.A + (i * a.nk + j0) * a.v + l;
+    for (int64_t j = j0; j < j1; j++, q += a.v) {
+      C v1[1];
+      E::template load<1>(q, v1);
+#pragma unroll
+      for (int r = 0; r < RP; r++)
+        if (r0 + r < a.R) d[r] = fma((double)v1[0], a.X[(r0 + r) * a.nk + j], d[r]);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < RP; r++) {
+    if (r0 + r < a.R) {
+      const int64_t y = (i * a.R + r0 + r) * a.v + l;
+      if (a.splits > 1) {
+        a.partial[blockIdx.y * a.uRv + y] = d[r];
+      } else {
+        double out = a.alpha * d[r];
+        if (a.beta != 0.0) out += a.beta * a.Y[y];
+        a.Y[y] = out;
+      }
+    }
+  }
+}
+
 // FP32 storage, v % VEC == 0: each thread owns VEC = 16 / RP consecutive
 // output columns (i, l..l+VEC-1) and keeps the next D rows of that piece
 // (4 * VEC bytes) in flight with cp.async into its own shared-memory slots,
@@ -208,7 +358,6 @@ template <int RP>
 struct TmcAsync {
   static constexpr int VEC = 16 / RP;               // 4, 2, 1 floats per piece
   static constexpr int D = VEC == 4 ? 8 : 16;       // rows in flight per thread
-  static constexpr int kStageBytes = D * kTmcThreads * VEC * 4;
 };
 
 template <int RP>
@@ -569,6 +718,13 @@ void launch_rp(const TmcArgs<DT>& a, const TmcPlan& p, cudaStream_t st) {
         return;
       }
     }
+  }
+  if constexpr (kF64Acc<DT>) {
+    if (p.vj)
+      tmc_f64_kernel<DT, RP, true><<<grid, kTmcThreads, smem, st>>>(a);
+    else
+      tmc_f64_kernel<DT, RP, false><<<grid, kTmcThreads, smem, st>>>(a);
+    return;
   }
   if (p.vj)
     tmc_kernel<DT, RP, true><<<grid, kTmcThreads, smem, st>>>(a);

@@ -4,6 +4,8 @@ against the FP64 oracle: every mode and storage type, X with 1 to 21 rows
 ragged tails, alpha/beta, exact gathers by selection matrices, integer
 inputs bit for bit, and the 1024^3 workload sampled at full size.
 
+FP64 values outside the float-float window are covered too.
+
 Tolerances (relative l2 over the output): FP64 and single-double 1e-12,
 FP32 and the narrow types (against the oracle on the same codes) 1e-5."""
 import numpy as np
@@ -84,7 +86,9 @@ def test_tmc_alpha_beta(code):
 @pytest.mark.parametrize("code", CODES, ids=["f64", "f32", "bf16", "e4m3", "f16"])
 def test_tmc_selection_matrix_gathers_exactly(code):
     """Rows of X that pick one index of mode k: every output is one stored
-    value (times its slab scale), exact in every storage type."""
+    value (times its slab scale), exact for FP32 and the narrow types; FP64
+    runs through the float-float split, whose low piece keeps 24 of the 29
+    remaining bits, so each output is within 2^-47 of the value."""
     dims = (5, 24, 40)
     A, Ao, scales = gu.inputs(dims, code)
     deq = oracle.dequantise(Ao, scales) if scales is not None else Ao.astype(np.float64)
@@ -96,7 +100,11 @@ def test_tmc_selection_matrix_gathers_exactly(code):
             X = np.zeros((R, dims[k]), dtype=vt)
             X[np.arange(R), pi] = 1.0
             got = gpu_tmc(A, k, X, scales)
-            assert np.array_equal(got, np.take(deq, pi, axis=k).astype(vt)), (k, R)
+            want = np.take(deq, pi, axis=k).astype(vt)
+            if code == oracle.F64:
+                assert np.all(np.abs(got - want) <= 2.0 ** -47 * np.abs(want)), (k, R)
+            else:
+                assert np.array_equal(got, want), (k, R)
 
 
 @pytest.mark.parametrize("dims", [(7, 3072), (3, 65536), (9, 33, 130), (100003,)], ids=lambda d: "x".join(map(str, d)))
@@ -106,6 +114,39 @@ def test_tmc_integer_inputs_bit_exact_f64(dims):
     for k in range(len(dims)):
         X = rng.integers(-8, 9, size=(10, dims[k])).astype(np.float64)
         assert np.array_equal(gpu_tmc(A, k, X), oracle.tmc(A, k, X)), k
+
+
+@pytest.mark.parametrize("dims", [(9, 33, 130), (1001, 1536), (3, 65536), (40, 41, 5)],
+                         ids=lambda d: "x".join(map(str, d)))
+def test_tmc_fp64_values_outside_the_emulation_window(dims):
+    """FP64 products run in float-float pieces on the FP32 pipe; zeros are
+    exact and other elements or entries of X outside the pieces' window
+    (huge, tiny, subnormal) send the thread to FP64 multiply-adds."""
+    A = synth.tensor("u64", 4, dims)
+    flat = A.ravel()
+    rng = np.random.default_rng(6)
+    pos = rng.choice(flat.size, size=min(600, flat.size), replace=False)
+    flat[pos[:100]] = 0.0
+    flat[pos[100:200]] *= 1e300
+    flat[pos[200:300]] *= 1e-300
+    flat[pos[300:400]] = 5e-324
+    flat[pos[400:500]] *= 2.0 ** 70
+    flat[pos[500:]] *= 2.0 ** -70
+    for k in range(len(dims)):
+        X = synth.tensor("u64", 1, (5, dims[k]), 1 + k)
+        X[:, ::5] *= 1e-20
+        X[:, 1::7] = 0.0
+        assert gu.rel_l2(gpu_tmc(A, k, X), oracle.tmc(A, k, X)) <= 1e-12, (dims, k)
+        X = synth.tensor("u64", 1, (5, dims[k]), 1 + k)
+        assert gu.rel_l2(gpu_tmc(A, k, X), oracle.tmc(A, k, X)) <= 1e-12, (dims, k)
+    A32 = synth.tensor("u32", 4, dims)
+    f32 = A32.ravel()
+    f32[pos[:100]] = 0.0
+    f32[pos[100:200]] *= np.float32(1e30)
+    f32[pos[200:300]] = np.float32(1e-42)
+    for k in range(len(dims)):
+        X = synth.tensor("u64", 1, (3, dims[k]), 1 + k)
+        assert gu.rel_l2(gpu_tmc(A32, k, X), oracle.tmc(A32, k, X)) <= 1e-12, (dims, k)
 
 
 def test_tmc_split_deterministic():
