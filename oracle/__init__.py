@@ -68,6 +68,8 @@ def _load():
             P, I, D, L = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64
             lib.oracle_tvc.argtypes = [I, P, P, I, P, I, P, P, D, D]
             lib.oracle_tmc.argtypes = [I, P, P, I, P, I, P, L, P, D, D]
+            lib.oracle_khatri_rao.argtypes = [P, I, P, L, P]
+            lib.oracle_mttkrp.argtypes = [I, P, P, I, P, I, P, L, P]
             lib.oracle_tvc_grad_x.argtypes = [I, P, P, I, P, I, P, P]
             lib.oracle_tvc_grad_A.argtypes = [I, P, I, P, P, P]
             for f in (lib.oracle_hopm, lib.oracle_hopm3):
@@ -158,6 +160,53 @@ def tmc(A, mode: int, X, *, dims=None, scales=None, Y=None, alpha=1.0, beta=0.0)
     if st:
         raise OracleError(st, "tmc")
     return out
+
+
+def khatri_rao(mats) -> np.ndarray:
+    """Columnwise Kronecker product of matrices U_m (rows_m x R): row
+    (i_0, ..., i_{c-1}) (i_0 most significant) holds prod_m U_m[i_m, :]."""
+    mats = [np.ascontiguousarray(np.asarray(U, dtype=np.float64)) for U in mats]
+    if not mats:
+        raise ValueError("need at least one matrix (R is their column count)")
+    R = mats[0].shape[1]
+    if any(U.ndim != 2 or U.shape[1] != R for U in mats) or R < 1:
+        raise ValueError("matrices must be 2-D with the same column count")
+    rows = np.array([U.shape[0] for U in mats], dtype=np.int64)
+    ptrs = (ctypes.c_void_p * len(mats))(*[U.ctypes.data for U in mats])
+    out = np.empty((int(np.prod(rows)), R))
+    st = _load().oracle_khatri_rao(ptrs, len(mats), _p(rows), R, _p(out))
+    if st:
+        raise OracleError(st, "khatri_rao")
+    return out
+
+
+def mttkrp(A, mode: int, factors, *, R=None, dims=None, scales=None) -> np.ndarray:
+    """M[i_mode, r] = sum of A times prod_{m != mode} factors[m][i_m, r]
+    (factors[m]: n_m x R; factors[mode] is ignored and may be None; R is
+    needed only when no other factor gives it, as for an order-1 tensor)."""
+    A, d, dt = _tensor(A, dims)
+    s = _scales(dt, scales, int(d[0]))
+    if not 0 <= mode < d.size or len(factors) != d.size:
+        raise ValueError("bad mode or factor count")
+    mats = []
+    for m in range(d.size):
+        if m == mode:
+            mats.append(None)
+            continue
+        U = np.ascontiguousarray(np.asarray(factors[m], dtype=np.float64))
+        if U.ndim != 2 or U.shape[0] != d[m] or (R is not None and U.shape[1] != R):
+            raise ValueError("factor m must be n_m x R")
+        R = U.shape[1]
+        mats.append(U)
+    if R is None:
+        raise ValueError("R is needed when no factor other than factors[mode] is given")
+    R = int(R)
+    ptrs = (ctypes.c_void_p * d.size)(*[0 if U is None else U.ctypes.data for U in mats])
+    M = np.empty((int(d[mode]), R))
+    st = _load().oracle_mttkrp(dt, _p(A), _p(s), int(d.size), _p(d), int(mode), ptrs, R, _p(M))
+    if st:
+        raise OracleError(st, "mttkrp")
+    return M
 
 
 def tvc_grad_x(A, mode: int, gy, *, dims=None, scales=None) -> np.ndarray:

@@ -158,6 +158,66 @@ int oracle_tmc(int dtype, const void* A, const float* scales, int order, const i
   return OR_OK;
 }
 
+/* ------------------------------------------------- Khatri-Rao and MTTKRP */
+
+/* Khatri-Rao product (Section 1) of `count` matrices U_m (rows[m] x R,
+ * row-major): the columnwise Kronecker product, out[(i_0, ..., i_{c-1})][r] =
+ * prod_m U_m[i_m][r] with i_0 the most significant index of the row
+ * (rows = prod rows[m]; count == 0 gives one row of ones). */
+int oracle_khatri_rao(const double* const* U, int count, const int64_t* rows, int64_t R, double* out) {
+  if (count < 0 || R < 1) return OR_ERR_ARG;
+  int64_t n = 1;
+  for (int m = 0; m < count; m++) {
+    if (rows[m] < 1) return OR_ERR_ARG;
+    n *= rows[m];
+  }
+  for (int64_t row = 0; row < n; row++) {
+    for (int64_t r = 0; r < R; r++) out[row * R + r] = 1.0;
+    int64_t rem = row;
+    for (int m = count - 1; m >= 0; m--) {
+      int64_t im = rem % rows[m];
+      rem /= rows[m];
+      for (int64_t r = 0; r < R; r++) out[row * R + r] *= U[m][im * R + r];
+    }
+  }
+  return OR_OK;
+}
+
+/* Matricized tensor times Khatri-Rao product for mode k (the core of CP
+ * alternating least squares, Section 1): with factor matrices X_m (n_m x R,
+ * row-major) for every m != k,
+ *     M[i_k][r] = sum over all other indices of A[i_0..i_{d-1}] prod_{m != k} X_m[i_m][r].
+ * factors[k] is not read.  M is n_k x R, row-major.  Straight from the
+ * definition: one pass over the elements, each weighted by its row of the
+ * Khatri-Rao product of the other factors. */
+int oracle_mttkrp(int dtype, const void* A, const float* scales, int order, const int64_t* dims, int mode,
+                  const double* const* factors, int64_t R, double* M) {
+  if (!valid_shape(order, dims) || mode < 0 || mode >= order || R < 1) return OR_ERR_ARG;
+  for (int m = 0; m < order; m++)
+    if (m != mode && !factors[m]) return OR_ERR_ARG;
+  int64_t N = prod(dims, 0, order), slab = prod(dims, 1, order);
+  for (int64_t q = 0; q < dims[mode] * R; q++) M[q] = 0.0;
+  double* w = (double*)malloc(sizeof(double) * (size_t)R);
+  if (!w) return OR_ERR_ARG;
+  for (int64_t f = 0; f < N; f++) {
+    double a = elem(dtype, A, scales, slab, f);
+    int64_t rem = f, ik = 0;
+    for (int64_t r = 0; r < R; r++) w[r] = 1.0;
+    for (int m = order - 1; m >= 0; m--) {
+      int64_t im = rem % dims[m];
+      rem /= dims[m];
+      if (m == mode) {
+        ik = im;
+        continue;
+      }
+      for (int64_t r = 0; r < R; r++) w[r] *= factors[m][im * R + r];
+    }
+    for (int64_t r = 0; r < R; r++) M[ik * R + r] += a * w[r];
+  }
+  free(w);
+  return OR_OK;
+}
+
 /* ---------------------------------------------------------- TVC gradients */
 
 /* Gradient of L(Y) with Y = A x_k x, with respect to x:

@@ -241,6 +241,70 @@ def test_tmc_bad_arguments():
         oracle.tmc(A, 0, np.ones(2))
 
 
+# -------------------------------------------------- Khatri-Rao, MTTKRP ----
+
+def test_khatri_rao_columns_are_kronecker_products_and_gram_identity():
+    U = synth.tensor("u64", 1, (3, 4), 1)
+    V = synth.tensor("u64", 1, (5, 4), 2)
+    W = synth.tensor("u64", 1, (2, 4), 3)
+    K = oracle.khatri_rao([U, V])
+    assert K.shape == (15, 4)
+    for r in range(4):
+        np.testing.assert_array_equal(K[:, r], np.kron(U[:, r], V[:, r]))
+    # (U (.) V)^T (U (.) V) = (U^T U) * (V^T V), Hadamard product of the Grams
+    np.testing.assert_allclose(K.T @ K, (U.T @ U) * (V.T @ V), rtol=1e-13)
+    # associativity, and a single matrix is itself
+    np.testing.assert_allclose(oracle.khatri_rao([U, V, W]), oracle.khatri_rao([K, W]), rtol=1e-15)
+    np.testing.assert_array_equal(oracle.khatri_rao([W]), W)
+
+
+@pytest.mark.parametrize("dims", [(7,), (5, 6), (3, 4, 5), (2, 3, 4, 3), (3, 1, 2, 2, 3)])
+def test_mttkrp_matches_einsum_every_mode(dims):
+    A = rand_tensor(dims, sid=5)
+    d = len(dims)
+    letters = "abcdefgh"[:d]
+    for k in range(d):
+        for R in (1, 3):
+            X = [synth.tensor("u64", 2, (n, R), 10 + m) for m, n in enumerate(dims)]
+            spec = letters + "," + ",".join(f"{letters[m]}z" for m in range(d) if m != k) + "->" + letters[k] + "z"
+            want = np.einsum(spec, A, *[X[m] for m in range(d) if m != k]) if d > 1 else A[:, None] * np.ones((1, R))
+            got = oracle.mttkrp(A, k, [None if m == k else X[m] for m in range(d)], R=R)
+            np.testing.assert_allclose(got, want, rtol=1e-13, atol=1e-13)
+
+
+def test_mttkrp_one_column_is_the_all_but_one_contraction():
+    """R = 1: the contraction of every mode but k with the factor columns,
+    done as successive TVCs (highest mode first)."""
+    dims = (4, 3, 5, 2)
+    A = rand_tensor(dims, sid=6)
+    xs = [synth.vector("u64", 3, 20 + m, n) for m, n in enumerate(dims)]
+    for k in range(4):
+        T = A
+        for m in reversed(range(4)):
+            if m != k:
+                T = oracle.tvc(T, m, xs[m])
+        got = oracle.mttkrp(A, k, [x[:, None] for x in xs])
+        np.testing.assert_allclose(got[:, 0], T, rtol=1e-13)
+
+
+def test_mttkrp_rank1_closed_form_and_matrix_case():
+    dims = (4, 5, 6)
+    us = [synth.vector("u64", 5, 30 + j, n) for j, n in enumerate(dims)]
+    A = np.einsum("i,j,k->ijk", *us)
+    X = [synth.tensor("u64", 4, (n, 3), 40 + m) for m, n in enumerate(dims)]
+    for k in range(3):
+        w = np.ones(3)
+        for m in range(3):
+            if m != k:
+                w = w * (us[m] @ X[m])
+        np.testing.assert_allclose(oracle.mttkrp(A, k, X), np.outer(us[k], w), rtol=1e-13)
+    B = rand_tensor((7, 9), sid=7)
+    Y0 = synth.tensor("u64", 6, (7, 2), 1)
+    Y1 = synth.tensor("u64", 6, (9, 2), 2)
+    np.testing.assert_allclose(oracle.mttkrp(B, 0, [None, Y1]), B @ Y1, rtol=1e-13)
+    np.testing.assert_allclose(oracle.mttkrp(B, 1, [Y0, None]), B.T @ Y0, rtol=1e-13)
+
+
 # ------------------------------------------------------------ gradients ----
 
 @pytest.mark.parametrize("dims", [(4, 5, 3), (6, 7), (2, 3, 2, 3)])
