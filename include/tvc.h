@@ -127,6 +127,41 @@ tvc_status tmc(const void* A, int order, const int64_t* dims, int mode, const vo
 size_t tmc_workspace_size(int order, const int64_t* dims, int mode, int64_t R, tvc_dtype dtype);
 
 /*
+ * Khatri-Rao product (Section 1): out = U_0 (.) U_1 (.) ... (.) U_{count-1},
+ * the columnwise Kronecker product of `count` matrices U_m (rows[m] x R,
+ * row-major, device), out[(i_0, ..., i_{count-1})][r] = prod_m U_m[i_m][r]
+ * with i_0 the most significant index of the row (prod rows[m] rows, R
+ * columns, row-major).  vdtype: TVC_F64 or TVC_F32 for all matrices.
+ * Errors: TVC_ERR_INVALID_ARG (count outside 1..TVC_MAX_ORDER, R < 1, a
+ * NULL or misaligned pointer, sizes too large); nothing is launched then.
+ */
+tvc_status khatri_rao(const void* const* mats, int count, const int64_t* rows, int64_t R, void* out,
+                      tvc_dtype vdtype, tvc_stream_t stream);
+
+/*
+ * Matricized tensor times Khatri-Rao product for mode k (the core of CP
+ * alternating least squares, Section 1):
+ *     M[i_k][r] = sum over all other indices of A[i_0..i_{d-1}] prod_{m != k} X_m[i_m][r].
+ * factors: host array of `order` device pointers; factors[m] (m != mode) is
+ * the n_m x R factor matrix X_m, row-major, FP64 for TVC_F64 / TVC_F32D and
+ * FP32 otherwise; factors[mode] is not read (may be NULL; for order 1 the
+ * array may be NULL).  M: n_mode x R, row-major, same type.  A is read
+ * once: the larger side of mode k (the modes before it, or after it) is
+ * contracted first by one tensor-matrix contraction (tmc) with the
+ * transposed Khatri-Rao product of its factors, then the small result with
+ * the other side's Khatri-Rao rows, in a fixed order.  slab_scales: as for
+ * tvc_ex (folded into the Khatri-Rao rows).  workspace:
+ * mttkrp_workspace_size(...) bytes, 256-byte aligned (it holds the two
+ * Khatri-Rao products, the R x n_k x (smaller side) intermediate and the
+ * contraction's own workspace).  Errors as for tmc; TVC_ERR_WORKSPACE when
+ * the workspace is missing or too small.
+ */
+tvc_status mttkrp(const void* A, int order, const int64_t* dims, int mode, const void* const* factors, int64_t R,
+                  void* M, tvc_dtype dtype, const float* slab_scales, void* workspace, size_t ws_bytes,
+                  tvc_stream_t stream);
+size_t mttkrp_workspace_size(int order, const int64_t* dims, int mode, int64_t R, tvc_dtype dtype);
+
+/*
  * tvc_noalloc: the same contraction as tvc_ex() with alpha = 1, beta = 0,
  * for callers that cannot allocate device memory (code run from a host
  * callback queued with cudaLaunchHostFunc, where CUDA API calls are not

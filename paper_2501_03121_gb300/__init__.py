@@ -74,6 +74,12 @@ def load_library():
         lib.tmc.restype = I
         lib.tmc_workspace_size.argtypes = [I, P, I, L, I]
         lib.tmc_workspace_size.restype = Z
+        lib.khatri_rao.argtypes = [P, I, P, L, P, I, P]
+        lib.khatri_rao.restype = I
+        lib.mttkrp.argtypes = [P, I, P, I, P, L, P, I, P, P, Z, P]
+        lib.mttkrp.restype = I
+        lib.mttkrp_workspace_size.argtypes = [I, P, I, L, I]
+        lib.mttkrp_workspace_size.restype = Z
         lib.hopm.argtypes = [P, I, P, P, I, D, P, P, P, P, I, P, P, Z, P]
         lib.hopm.restype = I
         lib.hopm_workspace_size.argtypes = [I, P, I]
@@ -276,6 +282,75 @@ def tmc(A: torch.Tensor, mode: int, X: torch.Tensor, *, Y: torch.Tensor | None =
                      float(beta), _ptr(workspace), 0 if workspace is None else workspace.numel(), _stream(stream))
     _check(status, "tmc")
     return Y
+
+
+def khatri_rao(mats, *, stream=None) -> torch.Tensor:
+    """Columnwise Kronecker product U_0 (.) U_1 (.) ... of CUDA matrices
+    (rows_m x R, all float64 or all float32): row (i_0, ..., i_{c-1}), i_0
+    most significant, holds prod_m U_m[i_m, :]."""
+    lib = load_library()
+    mats = list(mats)
+    if not mats:
+        raise ValueError("need at least one matrix")
+    dt = mats[0].dtype
+    R = int(mats[0].shape[1]) if mats[0].dim() == 2 else -1
+    if dt not in (torch.float64, torch.float32) or any(
+            U.dtype != dt or U.dim() != 2 or U.shape[1] != R or not U.is_contiguous() for U in mats):
+        raise ValueError("matrices must be contiguous 2-D float64 or float32 with one column count")
+    _check_cuda(*mats)
+    rows = (ctypes.c_int64 * len(mats))(*[int(U.shape[0]) for U in mats])
+    ptrs = (ctypes.c_void_p * len(mats))(*[U.data_ptr() for U in mats])
+    out = torch.empty((math.prod(int(U.shape[0]) for U in mats), R), dtype=dt, device=mats[0].device)
+    _check(lib.khatri_rao(ptrs, len(mats), rows, R, _ptr(out), F64 if dt == torch.float64 else F32,
+                          _stream(stream)), "khatri_rao")
+    return out
+
+
+def mttkrp_workspace_size(shape, mode: int, R: int, code: int) -> int:
+    """Bytes of workspace mttkrp(..., workspace=...) needs."""
+    lib = load_library()
+    return int(lib.mttkrp_workspace_size(len(shape), _dims_array(shape), int(mode), int(R), int(code)))
+
+
+def mttkrp(A: torch.Tensor, mode: int, factors, *, R: int | None = None, scales: torch.Tensor | None = None,
+           workspace: torch.Tensor | None = None, stream=None, shape=None) -> torch.Tensor:
+    """Matricized tensor times Khatri-Rao product on the GPU:
+    M[i_mode, r] = sum of A times prod_{m != mode} factors[m][i_m, r].
+    factors: one n_m x R CUDA matrix per mode (factors[mode] ignored, may be
+    None); float64 for float64 storage, float32 otherwise (float64 with
+    float32 storage selects single-double).  Returns M (n_mode x R)."""
+    lib = load_library()
+    shape = tuple(A.shape) if shape is None else tuple(int(n) for n in shape)
+    d = len(shape)
+    if not 0 <= mode < d or len(factors) != d:
+        raise ValueError("bad mode or factor count")
+    others = [factors[m] for m in range(d) if m != mode]
+    vref = others[0] if others else None
+    code = _with_vectors(dtype_code(A), vref)
+    vt = vec_dtype(code)
+    if others:
+        R = int(others[0].shape[1])
+    elif R is None:
+        raise ValueError("R is needed when no factor other than factors[mode] is given")
+    for m in range(d):
+        if m == mode:
+            continue
+        U = factors[m]
+        if U.dtype != vt or U.dim() != 2 or tuple(U.shape) != (shape[m], R) or not U.is_contiguous():
+            raise ValueError(f"factor {m} must be a contiguous {vt} matrix of shape ({shape[m]}, {R})")
+    if scales is not None and scales.dtype != torch.float32:
+        raise ValueError("scales must be float32")
+    _check_cuda(A, scales, workspace, *others)
+    dims = _dims_array(shape)
+    if workspace is None:
+        need = lib.mttkrp_workspace_size(d, dims, int(mode), R, code)
+        workspace = torch.empty(max(1, need), dtype=torch.uint8, device=A.device)
+    M = torch.empty((shape[mode], R), dtype=vt, device=A.device)
+    ptrs = (ctypes.c_void_p * d)(*[0 if (m == mode or factors[m] is None) else factors[m].data_ptr()
+                                   for m in range(d)])
+    _check(lib.mttkrp(_ptr(A), d, dims, int(mode), ptrs, R, _ptr(M), code, _ptr(scales), _ptr(workspace),
+                      workspace.numel(), _stream(stream)), "mttkrp")
+    return M
 
 
 class HopmResult:

@@ -102,3 +102,27 @@ def test_tmc_validation_without_gpu(lib):
     assert need > 0
     assert lib.tmc(fake, 2, long, 1, fake, 8, fake, 1, None, 1.0, 0.0, None, 0, None) == 3   # workspace
     assert lib.tmc_workspace_size(2, long, 1, 0, 1) == 0
+
+
+def test_cpals_validation_without_gpu(lib):
+    P, I, Z, L = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t, ctypes.c_int64
+    lib.khatri_rao.argtypes = [P, I, P, L, P, I, P]
+    lib.khatri_rao.restype = I
+    lib.mttkrp.argtypes = [P, I, P, I, P, L, P, I, P, P, Z, P]
+    lib.mttkrp.restype = I
+    lib.mttkrp_workspace_size.argtypes = [I, P, I, L, I]
+    lib.mttkrp_workspace_size.restype = Z
+    fake = ctypes.c_void_p(1 << 20)
+    mats = (ctypes.c_void_p * 2)(1 << 20, 1 << 21)
+    rows = (ctypes.c_int64 * 2)(3, 4)
+    assert lib.khatri_rao(mats, 0, rows, 2, fake, 0, None) == 1        # no matrices
+    assert lib.khatri_rao(mats, 2, rows, 0, fake, 0, None) == 1        # R < 1
+    assert lib.khatri_rao(mats, 2, rows, 2, fake, 2, None) == 1        # matrices are FP64 or FP32
+    dims = (ctypes.c_int64 * 3)(4, 5, 6)
+    facs = (ctypes.c_void_p * 3)(1 << 20, 0, 1 << 21)
+    assert lib.mttkrp(fake, 3, dims, 1, facs, 0, fake, 1, None, fake, 1 << 30, None) == 1   # R < 1
+    assert lib.mttkrp(fake, 3, dims, 0, facs, 2, fake, 1, None, fake, 1 << 30, None) == 1   # factor 1 missing
+    assert lib.mttkrp(fake, 3, dims, 1, facs, 2, fake, 1, None, None, 0, None) == 3         # no workspace
+    need = lib.mttkrp_workspace_size(3, dims, 1, 2, 1)
+    assert need >= (2 * 6 + 2 * 4 + 2 * 5 * 4) * 4                      # Khatri-Rao rows and the intermediate
+    assert lib.mttkrp_workspace_size(3, dims, 3, 2, 1) == 0              # bad mode
