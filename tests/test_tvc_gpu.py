@@ -150,6 +150,27 @@ def test_empty_like_degenerate_sizes():
             assert np.all(got == 6.0)
 
 
+@pytest.mark.parametrize("dims", [(64, 2048), (8, 33, 512), (300, 4, 96)], ids=lambda d: "x".join(map(str, d)))
+def test_e4m3_columns_with_large_and_nonfinite_x(dims):
+    """E4M3 columns with x entries far from unit size (up to 2.5e6) give the
+    oracle's values, and an infinite entry of x gives non-finite outputs
+    exactly where the oracle's are."""
+    src = synth.tensor("lognormal", 3, dims).astype(np.float32)
+    codes, scales = oracle.quantise(src, oracle.E4M3)
+    for k in range(len(dims)):
+        x = gu.vec(oracle.E4M3, dims[k], synth.stream_x(k))
+        x[::7] *= 300.0
+        x[1] = -2.5e6
+        x[2] = 255.99
+        ref = oracle.tvc(codes, k, x, scales=scales)
+        got = gu.gpu_tvc(tg, codes, k, x, scales)
+        assert gu.rel_l2(got, ref) <= 1e-5, (dims, k)
+        x[3] = np.inf
+        got = gu.gpu_tvc(tg, codes, k, x, scales)
+        ref = oracle.tvc(codes, k, x, scales=scales)
+        assert np.array_equal(np.isfinite(got), np.isfinite(ref)), (dims, k)
+
+
 def test_bad_arguments_raise():
     A = gu.to_dev(np.zeros((3, 4)))
     with pytest.raises(ValueError):
