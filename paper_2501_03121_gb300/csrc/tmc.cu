@@ -5,19 +5,24 @@
 // for an R x n_k matrix X, with A read as u x n_k x v (Section 3) and Y of
 // the shape of A with n_k replaced by R (row-major).
 //
-// Like the TVC it streams A once in its own order whatever k is: one thread
-// owns one output column (i, l) for a block of RP rows of X and walks the
-// n_k entries A[i][j][l], 16 (or 8) rows in flight (a warp reads 32
-// consecutive l of a row when v >= 32; for v == 1 each thread streams its
-// own row with 16-byte loads).  The rows of X are staged in shared memory as Xs[j][r] (the whole
-// n_k range of the block when it fits in 48 KB, else in chunks), so each
-// element of A costs RP multiply-adds against broadcast shared-memory
-// reads, with one block barrier per chunk.  X with more than RP rows is done in
-// passes over A (blockIdx.z); few outputs split n_k over blockIdx.y and a
-// second kernel adds the partial sums in a fixed order (deterministic).
-// FP32 accumulation (two levels: 64 products, then the running sum) for
-// FP32 and the narrow types; float-float products with FP64 totals for FP64
-// and single-double.
+// Like the TVC it streams A once in its own order whatever k is; RP rows of
+// X (4, 8 or 16) are applied per pass over A (blockIdx.z), and the rows of X
+// are staged in shared memory (16 KB chunks of the n_k range, one block
+// barrier per chunk), read by broadcast or shared by a warp's rows.  The
+// kernels:
+//   * tmc_cols_async_kernel (FP32, v > 1): a thread owns 16/RP output
+//     columns (i, l..) and keeps the next rows of that piece in flight with
+//     cp.async into its own shared-memory slots;
+//   * tmc_rows_group_kernel (v == 1, FP32 and narrow storage): a few lanes
+//     per row read 16-byte pieces along it with a cp.async pipeline, and
+//     the RP partial sums are reduced over the lanes by a butterfly;
+//   * tmc_f64_kernel (FP64, single-double): float-float products on the
+//     FP32 pipe, FP64 totals;
+//   * tmc_kernel: every other case, one output column per thread, 16 (8)
+//     rows in flight.
+// Few outputs split n_k over blockIdx.y; tmc_reduce_kernel adds the partial
+// sums in a fixed order (deterministic).  FP32 accumulation is two-level
+// (64 products, then the running sum).
 #include <algorithm>
 #include <type_traits>
 
