@@ -1293,29 +1293,31 @@ __global__ void __launch_bounds__(kThreads) tvc_tile_async_kernel(const TvcArgs<
   cp_async_wait<0>();
 }
 
-// Large slabs (1 < v < 32) of E4M3 codes: one block per slab (and
+// Large slabs (1 < v < 32) of the narrow types: one block per slab (and
 // split of n_k) streams its rows in tiles of about 8 KB, copied from the
 // 16-byte boundary below the tile with cp.async into two shared-memory
 // buffers (the next tile in flight while the current one is used); thread
-// (ph, l) of P = floor(256 / v) phases sums the rows j = ph (mod P) of its
-// column l from shared memory, and the P partial sums of each column are
-// added in phase order at the end.  The per-warp slab kernel reads 1-byte
-// codes straight from global memory, 32 bytes per warp load; here every
-// global access is a 16-byte piece.
+// (ph, c) of P = floor(256 / (v / W)) phases sums the rows j = ph (mod P)
+// of its W columns c*W .. c*W + W-1 from shared memory (one load and one x
+// entry per W elements), and the P partial sums of each column are added
+// in phase order at the end.  The per-warp slab kernel reads 1- or 2-byte
+// elements straight from global memory; here every global access is a
+// 16-byte piece.
 constexpr int kSlabTile = 8192;  // bytes of A per tile
 
-template <tvc_dtype DT>
+template <tvc_dtype DT, int W>
 __global__ void __launch_bounds__(kThreads) tvc_slab_async_kernel(const TvcArgs<DT> a) {
   if (skip(a.done)) return;
   using E = Elem<DT>;
   using T = typename E::T;
   constexpr int es = (int)sizeof(T);
   __shared__ __align__(16) unsigned char buf[2][kSlabTile + 32];
-  __shared__ float red[kThreads];
+  __shared__ float red[kThreads * W];
   const int v = (int)a.v;
-  const int P = kThreads / v;
+  const int C = v / W;       // threads per row, W consecutive columns each
+  const int P = kThreads / C;
   const int t = threadIdx.x;
-  const int ph = t / v, l = t - (t / v) * v;
+  const int ph = t / C, l = (t - (t / C) * C) * W;
   const bool act = ph < P;
   const int64_t i = blockIdx.x;
   const int64_t j0 = (int64_t)blockIdx.y * a.chunk;
@@ -1340,7 +1342,7 @@ __global__ void __launch_bounds__(kThreads) tvc_slab_async_kernel(const TvcArgs<
     }
     return (int)(gs - c0);
   };
-  AccF32<1> acc;
+  AccF32<W> acc;
   acc.init();
   int head[2] = {0, 0};
   head[0] = issue(j0, (int)min((int64_t)J, j1 - j0), buf[0]);
@@ -1355,9 +1357,9 @@ __global__ void __launch_bounds__(kThreads) tvc_slab_async_kernel(const TvcArgs<
     if (act) {
       const T* tile = reinterpret_cast<const T*>(buf[k] + head[k]);
       for (int jl = ph; jl < n; jl += P) {
-        float val[1];
-        E::template load<1, true>(tile + jl * v + l, val);
-        acc.a[0] = __fmaf_rn(val[0], xval(a, jt + jl), acc.a[0]);
+        float val[W];
+        E::template load<W, true>(tile + jl * v + l, val);  // W * es bytes, aligned (see the planner)
+        acc.mac(val, xval(a, jt + jl));
         if (++blk == kRB) {
           acc.fold();
           blk = 0;
@@ -1368,7 +1370,8 @@ __global__ void __launch_bounds__(kThreads) tvc_slab_async_kernel(const TvcArgs<
   }
   cp_async_wait<0>();
   acc.fold();
-  red[t] = act ? acc.result(0) : 0.0f;
+#pragma unroll
+  for (int e = 0; e < W; e++) red[ph * v + l + e] = act ? acc.result(e) : 0.0f;  // (ph, column)
   __syncthreads();
   if (t < v) {
     float sum = red[t];
@@ -1698,11 +1701,16 @@ static Plan make_plan_impl(const Shape& s, tvc_dtype dt, const void* A, bool all
     p.chunk = ceil_div(ceil_div(s.nk, splits), group) * group;
     p.splits = ceil_div(s.nk, p.chunk);
     p.grid = dim3((unsigned)ceil_div(s.u, rows_per_block), (unsigned)p.splits);
-  } else if (S > 512 && dt == TVC_E4M3 && aligned(A, 16) && slab_async_enabled()) {
-    // Large slabs of 1-byte elements: staged 16-byte pieces (see the kernel;
-    // measured 1.6x the per-warp slab kernel for E4M3 on 4096x4096x16, but
-    // 0.73x for BF16 and F16, which keep the per-warp kernel).
+  } else if (S > 512 && (dt == TVC_E4M3 || ((dt == TVC_BF16 || dt == TVC_F16) && s.v % 2 == 0)) &&
+             aligned(A, 16) && slab_async_enabled()) {
+    // Large slabs of 1- and 2-byte elements: staged 16-byte pieces (see the
+    // kernel).  Measured on 4096x4096x16 mode 1: BF16 3.5 TB/s, E4M3 2.1
+    // (the per-warp slab kernel: 2.2 and 0.54); 2-byte types with odd v
+    // (one column per thread) measured below the per-warp kernel and keep it.
     p.kind = K_SLAB_ASYNC;
+    // columns per thread: W elements from one shared-memory load (a tile
+    // starts at element (i n_k + j) v, so v % W == 0 keeps the load aligned)
+    p.vec = (s.v % 4 == 0) ? 4 : (s.v % 2 == 0) ? 2 : 1;
     const int64_t J = kSlabTile / (s.v * (int64_t)es);
     const int64_t target_blocks = (int64_t)sms * 4;
     int64_t splits = 1;
@@ -1935,7 +1943,11 @@ static void launch_main(const Plan& p, const TvcArgs<DT>& a, cudaStream_t st) {
       else tvc_slab_kernel<DT, 8><<<p.grid, kThreads, 0, st>>>(a, p.g, p.G);
       break;
     case K_SLAB_ASYNC:
-      if constexpr (DT == TVC_E4M3) tvc_slab_async_kernel<DT><<<p.grid, kThreads, 0, st>>>(a);
+      if constexpr (kNarrow<DT>) {
+        if (p.vec == 4) tvc_slab_async_kernel<DT, 4><<<p.grid, kThreads, 0, st>>>(a);
+        else if (p.vec == 2) tvc_slab_async_kernel<DT, 2><<<p.grid, kThreads, 0, st>>>(a);
+        else tvc_slab_async_kernel<DT, 1><<<p.grid, kThreads, 0, st>>>(a);
+      }
       break;
     case K_TILE_ASYNC: {
       opt_in_smem(reinterpret_cast<const void*>(tvc_tile_async_kernel<DT>), 200 * 1024);
