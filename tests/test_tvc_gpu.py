@@ -28,8 +28,9 @@ SHAPES = [
     # counts, a single row, split-K, and mode 0 of an order-1 tensor
     (7, 3072), (19, 2, 1040), (1, 4096), (2048,), (3, 65536), (1001, 1536),
     # large slabs with 1 < v < 32 (staged 16-byte tiles for the narrow
-    # types): v = 7, 31 and 2, ragged n_k, split n_k
-    (5, 3000, 7), (3, 700, 31), (6, 4099, 2),
+    # types, 4, 2 or 1 columns per thread): v = 16, 12, 7, 31 and 2, ragged
+    # n_k, split n_k
+    (3, 600, 16), (2, 300, 12), (5, 3000, 7), (3, 700, 31), (6, 4099, 2),
 ]
 CODES = [oracle.F64, oracle.F32, oracle.BF16, oracle.E4M3, oracle.F16]
 
