@@ -52,7 +52,7 @@ __global__ void khatri_rao_kernel(KrArgs a, V* __restrict__ out) {
   }
 }
 
-// M[i_k][r] = s(i_k) * sum_{q < K} T[q*sq + i_k*sk + r*sr] * W[q*R + r];
+// M[i_k][r] = s(i_k) * sum_{q < K} T[(q / K2)*sq + (q % K2)*sq2 + i_k*sk + r*sr] * W[q*R + r];
 // s(i_k) = scales[i_k] when given.  A block owns 32 consecutive outputs
 // (e = i_k*R + r, one per lane) and its 8 warps split q (warp w takes
 // q = w, w + 8, ...); the warps' sums are added in warp order (FP64, or
@@ -63,7 +63,8 @@ template <class V>
 __global__ void __launch_bounds__(kFinWarps * 32) mttkrp_finish_kernel(const V* __restrict__ T,
                                                                        const V* __restrict__ W, V* __restrict__ M,
                                                                        int64_t nk, int64_t R, int64_t K, int64_t sq,
-                                                                       int64_t sk, int64_t sr, const float* scales) {
+                                                                       int64_t sk, int64_t sr, const float* scales,
+                                                                       int64_t K2, int64_t sq2) {
   __shared__ V part[kFinWarps][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t n = nk * R;
@@ -73,18 +74,33 @@ __global__ void __launch_bounds__(kFinWarps * 32) mttkrp_finish_kernel(const V* 
   const V* t = T + ik * sk + r * sr;
   V val = 0;
   if (act) {
+    // q = q1 K2 + q2, advanced by kFinWarps without division
+    int64_t q1 = w / K2, q2 = w - (w / K2) * K2;
+    const int64_t d1 = kFinWarps / K2, d2 = kFinWarps - (kFinWarps / K2) * K2;
     if constexpr (sizeof(V) == 8) {
       double s = 0.0;
-#pragma unroll 8
-      for (int64_t q = w; q < K; q += kFinWarps) s = fma(t[q * sq], W[q * R + r], s);
+      for (int64_t q = w; q < K; q += kFinWarps) {
+        s = fma(t[q1 * sq + q2 * sq2], W[q * R + r], s);
+        q1 += d1;
+        q2 += d2;
+        if (q2 >= K2) {
+          q2 -= K2;
+          q1++;
+        }
+      }
       val = s;
     } else {
       KahanF32 s;
       float blk = 0.0f;
       int c = 0;
-#pragma unroll 8
       for (int64_t q = w; q < K; q += kFinWarps) {
-        blk = __fmaf_rn(t[q * sq], W[q * R + r], blk);
+        blk = __fmaf_rn(t[q1 * sq + q2 * sq2], W[q * R + r], blk);
+        q1 += d1;
+        q2 += d2;
+        if (q2 >= K2) {
+          q2 -= K2;
+          q1++;
+        }
         if (++c == 64) {
           s.add(blk);
           blk = 0.0f;
@@ -106,9 +122,13 @@ __global__ void __launch_bounds__(kFinWarps * 32) mttkrp_finish_kernel(const V* 
 }
 
 // Workspace plan of one MTTKRP.
+constexpr size_t kKrL2Bytes = 16u << 20;  // contracted Khatri-Rao rows kept L2-sized
+
 struct MkPlan {
   bool right = true;    // contract the modes after k first
   int64_t u = 1, nk = 1, v = 1, R = 1;
+  int msplit = 0;       // right side: modes [msplit, d) are contracted by the pass over A
+  int64_t va = 1, vb = 1;  // right side: v = va * vb (modes (k, msplit) and [msplit, d))
   size_t vs = 4;        // bytes per vector entry
   size_t off_kt = 0, off_kw = 0, off_t = 0, off_tmc = 0, total = 0;
   int vorder = 0;       // view of A handed to the tensor-matrix contraction
@@ -127,20 +147,32 @@ MkPlan mk_plan(const Shape& s, int64_t R, tvc_dtype dt) {
   p.vs = vec_size(dt);
   p.right = s.v >= s.u;
   if (p.right) {
-    // A as (n_0, u n_k / n_0, v) (or (n_k, v) for k = 0), contracted over v
+    // The pass over A contracts the trailing modes [msplit, d): all of the
+    // modes after k when their transposed Khatri-Rao rows (R x v) fit the
+    // L2-sized budget, else the longest suffix that does (at least the last
+    // mode), so that the rows re-read by every block of rows stay in L2;
+    // the middle modes (k, msplit) are left to the finishing contraction.
+    p.msplit = s.mode + 1;
+    p.vb = s.v;
+    while (p.msplit < s.order - 1 && (size_t)R * (size_t)p.vb * p.vs > kKrL2Bytes) {
+      p.vb /= s.dims[p.msplit];
+      p.msplit++;
+    }
+    p.va = s.v / p.vb;
+    // A as (n_0, u n_k va / n_0, vb) (or (n_k va, vb) for k = 0), contracted over vb
     if (s.mode == 0) {
       p.vorder = 2;
-      p.vdims[0] = s.nk;
-      p.vdims[1] = s.v;
+      p.vdims[0] = s.nk * p.va;
+      p.vdims[1] = p.vb;
       p.vmode = 1;
     } else {
       p.vorder = 3;
       p.vdims[0] = s.n0;
-      p.vdims[1] = s.u * s.nk / s.n0;
-      p.vdims[2] = s.v;
+      p.vdims[1] = s.u * s.nk * p.va / s.n0;
+      p.vdims[2] = p.vb;
       p.vmode = 2;
     }
-    p.t_is_m = s.mode == 0;  // no modes before k: the contraction's output is M
+    p.t_is_m = s.mode == 0 && p.va == 1;  // nothing left to contract: the pass writes M
   } else {
     // A as (u, n_k v), contracted over u
     p.vorder = 2;
@@ -148,9 +180,9 @@ MkPlan mk_plan(const Shape& s, int64_t R, tvc_dtype dt) {
     p.vdims[1] = s.nk * s.v;
     p.vmode = 0;
   }
-  const int64_t kt = R * (p.right ? s.v : s.u);  // transposed Khatri-Rao rows of the contracted side
-  const int64_t kw = R * (p.right ? s.u : s.v);  // Khatri-Rao rows of the other side
-  const int64_t t = p.t_is_m ? 0 : R * s.nk * (p.right ? s.u : s.v);
+  const int64_t kt = R * (p.right ? p.vb : s.u);         // transposed Khatri-Rao rows of the contracted side
+  const int64_t kw = R * (p.right ? s.u * p.va : s.v);  // Khatri-Rao rows of what is left
+  const int64_t t = p.t_is_m ? 0 : R * s.nk * (p.right ? s.u * p.va : s.v);
   p.tmc_ws = tmc_workspace_size(p.vorder, p.vdims, p.vmode, R, dt);
   p.off_kt = 0;
   p.off_kw = align_up(p.off_kt + (size_t)kt * p.vs, 256);
@@ -205,12 +237,18 @@ tvc_status mttkrp_run(const void* A, const Shape& s, const void* const* factors,
     lo_m[nlo] = factors[m];
     lo_r[nlo++] = s.dims[m];
   }
-  for (int m = k + 1; m < s.order; m++) {
+  const int mfirst = p.right ? p.msplit : k + 1;  // right side: the middle modes go with the lower ones
+  for (int m = k + 1; m < mfirst; m++) {
+    lo_m[nlo] = factors[m];
+    lo_r[nlo++] = s.dims[m];
+  }
+  for (int m = mfirst; m < s.order; m++) {
     hi_m[nhi] = factors[m];
     hi_r[nhi++] = s.dims[m];
   }
   const float* lo_scales = (narrow && k > 0) ? scales : nullptr;
-  const int64_t per_slab = k > 0 ? s.u / s.n0 : 1;
+  // rows of the lower Khatri-Rao product: (i, ia) with i in u; i lies in slab i / (u / n_0)
+  const int64_t per_slab = k > 0 ? (s.u / s.n0) * (p.right ? p.va : 1) : 1;
   if (p.right) {
     rc = kr_launch<V>(hi_m, hi_r, nhi, R, 1, nullptr, 1, KT, st);
     if (rc != TVC_OK) return rc;
@@ -236,17 +274,18 @@ tvc_status mttkrp_run(const void* A, const Shape& s, const void* const* factors,
       // k = 0: M[i_0][r] = scale[i_0] * T[i_0][r] in place (one term of weight 1)
       rc = kr_launch<V>(nullptr, nullptr, 0, R, 0, nullptr, 1, KW, st);  // one row of ones
       if (rc != TVC_OK) return rc;
-      mttkrp_finish_kernel<V><<<fin_blocks(p.nk * R), kFinWarps * 32, 0, st>>>(Tv, Wv, static_cast<V*>(M), p.nk, R, 1, 0, R, 1,
-                                                                  out_scales);
+      mttkrp_finish_kernel<V><<<fin_blocks(p.nk * R), kFinWarps * 32, 0, st>>>(
+          Tv, Wv, static_cast<V*>(M), p.nk, R, 1, 0, R, 1, out_scales, 1, 0);
     } else {
-      // T: (u n_k) x R, T[(i n_k + i_k) R + r]; sum over i with KL[i][r]
-      mttkrp_finish_kernel<V><<<fin_blocks(p.nk * R), kFinWarps * 32, 0, st>>>(Tv, Wv, static_cast<V*>(M), p.nk, R, p.u,
-                                                                  p.nk * R, R, 1, out_scales);
+      // T: (u n_k va) x R, T[((i n_k + i_k) va + ia) R + r]; sum over q = (i, ia)
+      // with the lower Khatri-Rao rows W[(i va + ia)][r]
+      mttkrp_finish_kernel<V><<<fin_blocks(p.nk * R), kFinWarps * 32, 0, st>>>(
+          Tv, Wv, static_cast<V*>(M), p.nk, R, p.u * p.va, p.nk * p.va * R, p.va * R, 1, out_scales, p.va, R);
     }
   } else {
     // T: R x (n_k v), T[r (n_k v) + i_k v + l]; sum over l with KR[l][r]
-    mttkrp_finish_kernel<V><<<fin_blocks(p.nk * R), kFinWarps * 32, 0, st>>>(Tv, Wv, static_cast<V*>(M), p.nk, R, p.v, 1, p.v,
-                                                                p.nk * p.v, out_scales);
+    mttkrp_finish_kernel<V><<<fin_blocks(p.nk * R), kFinWarps * 32, 0, st>>>(
+        Tv, Wv, static_cast<V*>(M), p.nk, R, p.v, p.v, p.v, p.nk * p.v, out_scales, p.v, 1);
   }
   count_launches(1);
   return cuda_status(cudaGetLastError());

@@ -79,6 +79,24 @@ def test_mttkrp_one_column_is_hopms_all_but_one_contraction():
         assert gu.rel_l2(got[:, 0], T) <= 1e-12, k
 
 
+@pytest.mark.parametrize("case", [((4, 96, 96, 96), 0), ((4, 96, 96, 96), 1), ((2, 5, 128, 8192), 1)],
+                         ids=["4x96^3-k0", "4x96^3-k1", "2x5x128x8192-k1"])
+@pytest.mark.parametrize("code", [oracle.F64, oracle.F32, oracle.BF16], ids=["f64", "f32", "bf16"])
+def test_mttkrp_long_trailing_block(case, code):
+    """Trailing modes whose transposed Khatri-Rao rows exceed the L2-sized
+    budget: the pass over A contracts only a suffix of them and the rest
+    goes to the finishing contraction with the lower factors."""
+    dims, k = case
+    A, Ao, scales = gu.inputs(dims, code)
+    vt = np.float64 if code == oracle.F64 else np.float32
+    R = 8
+    X = factors_for(dims, R, vt)
+    ref = oracle.mttkrp(Ao, k, X, R=R, scales=scales)
+    got = tg.mttkrp(gu.to_dev(A), k, [None if m == k else gu.to_dev(X[m]) for m in range(len(dims))],
+                    scales=gu.to_dev(scales) if scales is not None else None, shape=dims).cpu().numpy()
+    assert gu.rel_l2(got, ref) <= gu.TOL[code], (dims, k)
+
+
 def test_mttkrp_bad_arguments():
     A = gu.to_dev(np.zeros((3, 4)))
     with pytest.raises(ValueError):
