@@ -353,7 +353,7 @@ def hopm_bytes(dims, es, vs):
 
 
 def secondary(dev):
-    """HOPM, batched and TMC figures (other workloads; not part of `value`)."""
+    """HOPM, batched, TMC and MTTKRP figures (other workloads; not part of `value`)."""
     import numpy as np
     import torch
     import synth
@@ -497,6 +497,17 @@ def secondary(dev):
             res[f"R{R}_mode{k}_GB/s"] = (N * 4 + X.numel() * 4 + Y.numel() * 4) / (ms / 1e3) / 1e9
             del X, Y, ws
     out["tmc_1024^3_f32"] = res
+    # MTTKRP (CP-ALS building block) on the same tensor: R = 8 factor columns, every mode
+    res = {}
+    for k in range(3):
+        facs = [None if m == k else torch.from_numpy(synth.tensor("u32", 1, (n, 8), 20 + m)).to(dev)
+                for m, n in enumerate(dims)]
+        ws = torch.empty(max(1, tg.mttkrp_workspace_size(dims, k, 8, tg.F32)), dtype=torch.uint8, device=dev)
+        ms = _timed(lambda: tg.mttkrp(A, k, facs, workspace=ws, shape=dims), 5)
+        nbytes = N * 4 + sum(f.numel() * 4 for f in facs if f is not None) + dims[k] * 8 * 4
+        res[f"R8_mode{k}_GB/s"] = nbytes / (ms / 1e3) / 1e9
+        del facs, ws
+    out["mttkrp_1024^3_f32"] = res
     del A
     torch.cuda.empty_cache()
     return out
