@@ -1,5 +1,5 @@
-// Bulk asynchronous copies (the TMA engine, cp.async.bulk) and mbarriers,
-// written as inline PTX for sm_90 and later.  Every wait is bounded in
+// Bulk asynchronous copies (the TMA engine, cp.async.bulk), mbarriers and
+// per-thread cp.async copies, written as inline PTX for sm_90 and later.  Every wait is bounded in
 // time: a wait that gives up records an error code in a device word and
 // returns false, so a lost arrival can never hang the GPU.
 #pragma once
@@ -61,6 +61,24 @@ __device__ __forceinline__ void tma_load_1d(void* dst_smem, const void* src, uin
           smem_u32(dst_smem)),
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
+}
+
+// Per-thread asynchronous copies global -> shared (cp.async): 16 bytes
+// bypassing L1, or 8 / 4 bytes through it; each thread commits its copies in
+// groups and waits for its own groups only.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
 // Barrier over `count` threads (a multiple of 32) on hardware barrier `id`.

@@ -373,18 +373,15 @@ __global__ void __launch_bounds__(kTmcThreads) tmc_f64_kernel(const TmcArgs<DT> 
 // (4 * VEC bytes) in flight with cp.async into its own shared-memory slots,
 // consuming row j while row j + D is fetched (it waits only for its own
 // copies).  VEC x RP accumulators (two levels), X staged as in tmc_kernel.
-__device__ __forceinline__ void cp_async_piece(void* smem, const void* gmem, int bytes) {
-  if (bytes == 16)
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
-  else if (bytes == 8)
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
+// A column piece of 4, 8 or 16 bytes.
+template <int BYTES>
+__device__ __forceinline__ void cp_async_piece(void* smem, const void* gmem) {
+  if constexpr (BYTES == 16)
+    cp_async16(smem, gmem);
+  else if constexpr (BYTES == 8)
+    cp_async8(smem, gmem);
   else
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit_group() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait_group() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+    cp_async4(smem, gmem);
 }
 
 template <int RP>
@@ -413,8 +410,8 @@ __global__ void __launch_bounds__(kTmcThreads) tmc_cols_async_kernel(const TmcAr
   const int64_t n = act ? j1 - j0 : 0;
 #pragma unroll
   for (int d = 0; d < D; d++) {
-    if (d < n) cp_async_piece(&stage[d][t * VEC], p + d * a.v, VEC * 4);
-    cp_async_commit_group();
+    if (d < n) cp_async_piece<VEC * 4>(&stage[d][t * VEC], p + d * a.v);
+    cp_async_commit();
   }
   float acc[VEC][RP], sum[VEC][RP];
 #pragma unroll
@@ -437,7 +434,7 @@ __global__ void __launch_bounds__(kTmcThreads) tmc_cols_async_kernel(const TmcAr
     __syncthreads();
     if (act) {
       for (int jl = 0; jl < jn; jl++) {
-        cp_async_wait_group<D - 1>();
+        cp_async_wait<D - 1>();
         float v[VEC];
         if constexpr (VEC == 4) {
           const float4 f = *reinterpret_cast<const float4*>(&stage[slot][t * 4]);
@@ -453,8 +450,8 @@ __global__ void __launch_bounds__(kTmcThreads) tmc_cols_async_kernel(const TmcAr
           v[0] = stage[slot][t];
         }
         // the slot is free again: fetch the row D ahead into it
-        if (left > 0) cp_async_piece(&stage[slot][t * VEC], pf, VEC * 4);
-        cp_async_commit_group();
+        if (left > 0) cp_async_piece<VEC * 4>(&stage[slot][t * VEC], pf);
+        cp_async_commit();
         left--;
         pf += a.v;
 #pragma unroll
@@ -473,7 +470,7 @@ __global__ void __launch_bounds__(kTmcThreads) tmc_cols_async_kernel(const TmcAr
       }
     }
   }
-  cp_async_wait_group<0>();
+  cp_async_wait<0>();
   if (!act) return;
 #pragma unroll
   for (int r = 0; r < RP; r++) {
@@ -563,8 +560,8 @@ __global__ void __launch_bounds__(kTmcThreads) tmc_rows_group_kernel(const TmcAr
     const int64_t n = act ? (pieces > gl ? (pieces - gl + G - 1) / G : 0) : 0;  // this lane's pieces
 #pragma unroll
     for (int d = 0; d < kGroupD; d++) {
-      if (d < n) cp_async_piece(&stage[d][t], prow + (gl + (int64_t)d * G) * P, 16);
-      cp_async_commit_group();
+      if (d < n) cp_async16(&stage[d][t], prow + (gl + (int64_t)d * G) * P);
+      cp_async_commit();
     }
     float acc[RP], sum[RP];
 #pragma unroll
@@ -594,11 +591,11 @@ __global__ void __launch_bounds__(kTmcThreads) tmc_rows_group_kernel(const TmcAr
       }
       // this lane's pieces whose entries lie in [jc, jc + jn)
       for (int jl = (int)((gl + k * G) * P - (jc - j0)); k < n && jl < jn; k++, jl += G * P) {
-        cp_async_wait_group<kGroupD - 1>();
+        cp_async_wait<kGroupD - 1>();
         float v[P];
         E::template load<P, true>(reinterpret_cast<const T*>(&stage[slot][t]), v);
-        if (left > 0) cp_async_piece(&stage[slot][t], pf, 16);
-        cp_async_commit_group();
+        if (left > 0) cp_async16(&stage[slot][t], pf);
+        cp_async_commit();
         left--;
         pf += G * P;
         if (++slot == kGroupD) slot = 0;
@@ -625,7 +622,7 @@ __global__ void __launch_bounds__(kTmcThreads) tmc_rows_group_kernel(const TmcAr
         }
       }
     }
-    cp_async_wait_group<0>();
+    cp_async_wait<0>();
     float tot[RP];
 #pragma unroll
     for (int r = 0; r < RP; r++) tot[r] = sum[r] + acc[r];

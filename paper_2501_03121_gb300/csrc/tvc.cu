@@ -208,14 +208,6 @@ __global__ void __launch_bounds__(kThreads) tvc_cols_kernel(const TvcArgs<DT> a)
 // column kernel cannot for 8- or 16-element vectors.
 constexpr int kAsyncDepth = 12;
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
 
 template <tvc_dtype DT, int VEC>
 __global__ void __launch_bounds__(kThreads) tvc_cols_async_kernel(const TvcArgs<DT> a) {
@@ -791,8 +783,7 @@ __global__ void __launch_bounds__(kTmaThreads, 2) tvc_rows_tma_kernel(const TvcA
   size_t off = (size_t)S * prm.tile_bytes;
   float2* wres = reinterpret_cast<float2*>(smraw + off);  // [warps][RW]
   off += (size_t)kTmaConsumerWarps * RW * sizeof(float2);
-  double* wd = reinterpret_cast<double*>(smraw + off);  // [warps][RW]
-  off += (size_t)kTmaConsumerWarps * RW * sizeof(double);
+  off += (size_t)kTmaConsumerWarps * RW * sizeof(double);  // [warps][RW] doubles, part of the host's layout
   uint64_t* full = reinterpret_cast<uint64_t*>(smraw + off);
   uint64_t* empty = full + S;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
