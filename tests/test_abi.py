@@ -126,3 +126,49 @@ def test_cpals_validation_without_gpu(lib):
     need = lib.mttkrp_workspace_size(3, dims, 1, 2, 1)
     assert need >= (2 * 6 + 2 * 4 + 2 * 5 * 4) * 4                      # Khatri-Rao rows and the intermediate
     assert lib.mttkrp_workspace_size(3, dims, 3, 2, 1) == 0              # bad mode
+
+
+def _mttkrp_ws_expected(lib, dims, k, R, code):
+    """The MTTKRP workspace from the plan's rules: the larger side of mode k
+    is contracted by the pass over A; for the modes after k, only the
+    longest trailing block whose transposed Khatri-Rao rows fit 16 MB."""
+    import math
+    vs = 8 if code in (0, 5) else 4
+    d = len(dims)
+    u, nk, v, n0 = math.prod(dims[:k]), dims[k], math.prod(dims[k + 1:]), dims[0]
+    right = v >= u
+    va = vb = 1
+    if right:
+        msplit, vb = k + 1, v
+        while msplit < d - 1 and R * vb * vs > (16 << 20):
+            vb //= dims[msplit]
+            msplit += 1
+        va = v // vb
+        view, mode = ((nk * va, vb), 1) if k == 0 else ((n0, u * nk * va // n0, vb), 2)
+        t_is_m = k == 0 and va == 1
+    else:
+        view, mode, t_is_m = (u, nk * v), 0, False
+    kt = R * (vb if right else u)
+    kw = R * (u * va if right else v)
+    t = 0 if t_is_m else R * nk * (u * va if right else v)
+    vd = (ctypes.c_int64 * len(view))(*view)
+    tmc_ws = lib.tmc_workspace_size(len(view), vd, mode, R, code)
+    up = lambda x: (x + 255) // 256 * 256  # noqa: E731
+    off_kw = up(kt * vs)
+    off_t = up(off_kw + kw * vs)
+    off_tmc = up(off_t + t * vs)
+    return off_tmc + tmc_ws
+
+
+def test_mttkrp_plan_workspace_without_gpu(lib):
+    lib.mttkrp_workspace_size.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_int]
+    lib.mttkrp_workspace_size.restype = ctypes.c_size_t
+    lib.tmc_workspace_size.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_int]
+    lib.tmc_workspace_size.restype = ctypes.c_size_t
+    cases = [((3, 4, 5), 1, 3, 1), ((40, 3, 6), 2, 8, 0), ((6, 3, 40), 0, 8, 2), ((4, 96, 96, 96), 0, 8, 1),
+             ((4, 96, 96, 96), 1, 8, 0), ((2, 5, 128, 8192), 1, 8, 1), ((1024, 1024, 1024), 2, 16, 1),
+             ((256, 256, 256, 256), 0, 8, 1), ((7,), 0, 4, 1)]
+    for dims, k, R, code in cases:
+        arr = (ctypes.c_int64 * len(dims))(*dims)
+        got = lib.mttkrp_workspace_size(len(dims), arr, k, R, code)
+        assert got == _mttkrp_ws_expected(lib, dims, k, R, code), (dims, k, R, code)
