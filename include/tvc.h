@@ -64,7 +64,7 @@ typedef enum {
 typedef enum {
   TVC_OK = 0,
   TVC_ERR_INVALID_ARG = 1, /* bad pointer, order, size, mode or dtype         */
-  TVC_ERR_UNSUPPORTED = 2, /* valid but not supported by this build           */
+  TVC_ERR_UNSUPPORTED = 2, /* valid but not supported by this library         */
   TVC_ERR_WORKSPACE = 3,   /* workspace smaller than the *_workspace_size     */
   TVC_ERR_CUDA = 4,        /* a CUDA launch or runtime call failed            */
   TVC_ERR_ZERO_NORM = 5,   /* device status: a HOPM update had zero norm      */

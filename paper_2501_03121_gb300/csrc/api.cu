@@ -120,7 +120,7 @@ extern "C" const char* tvc_status_string(tvc_status s) {
   switch (s) {
     case TVC_OK: return "TVC_OK";
     case TVC_ERR_INVALID_ARG: return "TVC_ERR_INVALID_ARG: bad pointer, order, size, mode or dtype";
-    case TVC_ERR_UNSUPPORTED: return "TVC_ERR_UNSUPPORTED: not supported by this build";
+    case TVC_ERR_UNSUPPORTED: return "TVC_ERR_UNSUPPORTED: not supported by this library";
     case TVC_ERR_WORKSPACE: return "TVC_ERR_WORKSPACE: workspace too small";
     case TVC_ERR_CUDA: return "TVC_ERR_CUDA: a CUDA call failed";
     case TVC_ERR_ZERO_NORM: return "TVC_ERR_ZERO_NORM: an update vector had zero norm";
