@@ -6,7 +6,16 @@
  * (arXiv 2501.03121).  This library is the single-GPU hot path of that
  * method: the mode-oblivious dense tensor-vector contraction (TVC) and the
  * higher-order power method (HOPM) built on it, with low-precision storage,
- * adjoints and batching.
+ * adjoints and batching; the 1D split over virtual ranks (Eq. 1/2,
+ * Algorithm 1); and the building blocks that Section 1 names next to the
+ * TVC: the tensor-matrix contraction, the Khatri-Rao product and the MTTKRP
+ * of CP alternating least squares.
+ *
+ * Entry points: tvc, tvc_ex, tvc_noalloc; tvc_quantise; tvc_backward;
+ * hopm, hopm_jacobi, hopm_backward; tvc_batched, tvc_batched_autotune,
+ * hopm_batched; tvc_split_1d, tvc_slab_copy, dtvc, dhopm; tmc, khatri_rao,
+ * mttkrp; each with its *_workspace_size query where it takes a workspace;
+ * diagnostics tvc_status_string, tvc_kernel_launches, tvc_device_error.
  *
  * Conventions shared by every entry point
  * ---------------------------------------
