@@ -15,7 +15,8 @@
  * hopm, hopm_jacobi, hopm_backward; tvc_batched, tvc_batched_autotune,
  * hopm_batched; tvc_split_1d, tvc_slab_copy, dtvc, dhopm; tmc, khatri_rao,
  * mttkrp; each with its *_workspace_size query where it takes a workspace;
- * diagnostics tvc_status_string, tvc_kernel_launches, tvc_device_error.
+ * diagnostics tvc_read_status, tvc_status_string, tvc_kernel_launches,
+ * tvc_device_error.
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -448,6 +449,15 @@ size_t dhopm_workspace_size(int parts, const int64_t* starts, int order, const i
  * results are then invalid.  Synchronises the device; returns
  * TVC_ERR_TIMEOUT when a code is set (and clears it when clear != 0). */
 tvc_status tvc_device_error(int* code_out, int clear);
+
+/* Reads a device status word (the status_out / status argument of hopm,
+ * hopm_jacobi, hopm_backward, tvc_quantise and the batched power methods):
+ * waits for the work queued on `stream` before it (a stream-ordered copy,
+ * then a synchronisation of that stream) and stores the word's value, a
+ * tvc_status code, in *host_out.  Returns TVC_ERR_INVALID_ARG for a NULL
+ * pointer, TVC_ERR_CUDA if the copy fails, else TVC_OK (whatever the word
+ * holds). */
+tvc_status tvc_read_status(const int* dev_status, int* host_out, tvc_stream_t stream);
 
 /* Number of CUDA kernels this library has launched in this process (all
  * devices, all entry points).  Host-side counter, incremented per launch;

@@ -122,6 +122,8 @@ def load_library():
         lib.dhopm.restype = I
         lib.dhopm_workspace_size.argtypes = [I, P, I, P, I, I]
         lib.dhopm_workspace_size.restype = Z
+        lib.tvc_read_status.argtypes = [P, P, P]
+        lib.tvc_read_status.restype = I
         lib.tvc_kernel_launches.argtypes = []
         lib.tvc_kernel_launches.restype = ctypes.c_uint64
         _lib = lib
@@ -184,6 +186,18 @@ def _check_cuda(*ts):
     for t in ts:
         if t is not None and (not t.is_cuda or not t.is_contiguous()):
             raise ValueError("tensors must be contiguous CUDA tensors")
+
+
+def read_status(status: torch.Tensor, *, stream=None) -> int:
+    """Value of a device status word (one int32 on the GPU) once the work
+    queued before it on `stream` has finished: a tvc_status code."""
+    lib = load_library()
+    if status.dtype != torch.int32 or status.numel() < 1:
+        raise ValueError("status must be a CUDA int32 tensor")
+    _check_cuda(status)
+    out = ctypes.c_int(0)
+    _check(lib.tvc_read_status(_ptr(status), ctypes.byref(out), _stream(stream)), "tvc_read_status")
+    return int(out.value)
 
 
 def kernel_launches() -> int:

@@ -129,3 +129,14 @@ extern "C" const char* tvc_status_string(tvc_status s) {
   }
   return "unknown tvc_status";
 }
+
+extern "C" tvc_status tvc_read_status(const int* dev_status, int* host_out, tvc_stream_t stream) {
+  if (!dev_status || !host_out) return TVC_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  int v = 0;
+  if (cudaMemcpyAsync(&v, dev_status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return TVC_ERR_CUDA;
+  *host_out = v;
+  return TVC_OK;
+}

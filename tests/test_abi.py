@@ -172,3 +172,11 @@ def test_mttkrp_plan_workspace_without_gpu(lib):
         arr = (ctypes.c_int64 * len(dims))(*dims)
         got = lib.mttkrp_workspace_size(len(dims), arr, k, R, code)
         assert got == _mttkrp_ws_expected(lib, dims, k, R, code), (dims, k, R, code)
+
+
+def test_read_status_validation_without_gpu(lib):
+    lib.tvc_read_status.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    lib.tvc_read_status.restype = ctypes.c_int
+    out = ctypes.c_int(0)
+    assert lib.tvc_read_status(None, ctypes.byref(out), None) == 1
+    assert lib.tvc_read_status(ctypes.c_void_p(1 << 20), None, None) == 1

@@ -265,3 +265,15 @@ def test_hopm_jacobi_single_pass_kernel(dims, code):
         assert int(r.status.item()) == 0
         check_against(r, ref, code)
         xs = r.x
+
+
+def test_read_status_after_a_zero_tensor():
+    """The status word of a power method on a zero tensor, read through the
+    C ABI once the queued work is done: TVC_ERR_ZERO_NORM."""
+    dims = (3, 4, 5)
+    A = torch.zeros(dims, dtype=torch.float64, device=gu.DEV)
+    xs = [torch.full((n,), 1.0 / math.sqrt(n), dtype=torch.float64, device=gu.DEV) for n in dims]
+    r = tg.hopm(A, xs, 3)
+    assert tg.read_status(r.status) == 5
+    ok = torch.zeros(1, dtype=torch.int32, device=gu.DEV)
+    assert tg.read_status(ok) == 0
