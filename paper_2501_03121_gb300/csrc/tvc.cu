@@ -1284,7 +1284,7 @@ __global__ void __launch_bounds__(kThreads) tvc_tile_async_kernel(const TvcArgs<
   cp_async_wait<0>();
 }
 
-// Large slabs (1 < v < 32) of the narrow types: one block per slab (and
+// Large slabs (1 < v < 32) of the narrow types and FP32: one block per slab (and
 // split of n_k) streams its rows in tiles of about 8 KB, copied from the
 // 16-byte boundary below the tile with cp.async into two shared-memory
 // buffers (the next tile in flight while the current one is used); thread
@@ -1517,6 +1517,14 @@ static bool slab_async_enabled() {
   return v;
 }
 
+static bool slab_async_f32() {
+  static bool v = [] {
+    const char* e = std::getenv("TVC_SLAB_ASYNC_F32");
+    return !(e && std::atoi(e) == 0);
+  }();
+  return v;
+}
+
 static bool tile_async_enabled() {
   static bool v = [] {
     const char* e = std::getenv("TVC_TILE_ASYNC");
@@ -1692,12 +1700,15 @@ static Plan make_plan_impl(const Shape& s, tvc_dtype dt, const void* A, bool all
     p.chunk = ceil_div(ceil_div(s.nk, splits), group) * group;
     p.splits = ceil_div(s.nk, p.chunk);
     p.grid = dim3((unsigned)ceil_div(s.u, rows_per_block), (unsigned)p.splits);
-  } else if (S > 512 && (dt == TVC_E4M3 || ((dt == TVC_BF16 || dt == TVC_F16) && s.v % 2 == 0)) &&
+  } else if (S > 512 &&
+             (dt == TVC_E4M3 || ((dt == TVC_BF16 || dt == TVC_F16) && s.v % 2 == 0) ||
+              (dt == TVC_F32 && s.v % 4 == 0 && slab_async_f32())) &&
              aligned(A, 16) && slab_async_enabled()) {
-    // Large slabs of 1- and 2-byte elements: staged 16-byte pieces (see the
-    // kernel).  Measured on 4096x4096x16 mode 1: BF16 3.5 TB/s, E4M3 2.1
-    // (the per-warp slab kernel: 2.2 and 0.54); 2-byte types with odd v
-    // (one column per thread) measured below the per-warp kernel and keep it.
+    // Large slabs: staged 16-byte pieces (see the kernel).  Measured on
+    // 4096x4096x16 mode 1: BF16 3.5 TB/s, E4M3 2.1, FP32 5.0 (the per-warp
+    // slab kernel: 2.2, 0.54 and 4.9; FP32 on 16384x8192x8: 5.5 against
+    // 5.0); 2-byte types with odd v (one column per thread) measured below
+    // the per-warp kernel and keep it, as do FP32 with v % 4 != 0 and FP64.
     p.kind = K_SLAB_ASYNC;
     // columns per thread: W elements from one shared-memory load (a tile
     // starts at element (i n_k + j) v, so v % W == 0 keeps the load aligned)
@@ -1934,7 +1945,9 @@ static void launch_main(const Plan& p, const TvcArgs<DT>& a, cudaStream_t st) {
       else tvc_slab_kernel<DT, 8><<<p.grid, kThreads, 0, st>>>(a, p.g, p.G);
       break;
     case K_SLAB_ASYNC:
-      if constexpr (kNarrow<DT>) {
+      if constexpr (DT == TVC_F32) {
+        tvc_slab_async_kernel<DT, 4><<<p.grid, kThreads, 0, st>>>(a);
+      } else if constexpr (kNarrow<DT>) {
         if (p.vec == 4) tvc_slab_async_kernel<DT, 4><<<p.grid, kThreads, 0, st>>>(a);
         else if (p.vec == 2) tvc_slab_async_kernel<DT, 2><<<p.grid, kThreads, 0, st>>>(a);
         else tvc_slab_async_kernel<DT, 1><<<p.grid, kThreads, 0, st>>>(a);
