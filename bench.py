@@ -12,6 +12,7 @@ Every input is far larger than the 129 MB L2 (the smallest is 1.07 GB), so
 no flush is needed between timed iterations.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+    python bench.py --case tvc|batched ...   (one case, for profiling)
 """
 from __future__ import annotations
 
@@ -443,15 +444,7 @@ def secondary(dev):
     del src
     torch.cuda.empty_cache()
     # batched: 4096 FP32 tensors (order 3/4, dims U[8,192], <= 2^24 elements)
-    rng = np.random.default_rng(0)
-    spec = []
-    for b in range(4096):
-        d = 3 if rng.random() < 0.5 else 4
-        while True:
-            dd = tuple(int(n) for n in rng.integers(8, 193, size=d))
-            if math.prod(dd) <= (1 << 24):
-                break
-        spec.append((dd, int(rng.integers(0, d))))
+    spec = batched_spec(4096)
     total = sum(math.prod(dd) for dd, _ in spec)
     pool = torch.empty(total, dtype=torch.float32, device=dev)
     sd.fill(pool, "u32", 0, synth.STREAM_A)
@@ -513,9 +506,148 @@ def secondary(dev):
     return out
 
 
+# --------------------------------------------------- single cases (profiling)
+
+def batched_spec(count, seed=0):
+    """The batched workload's tensors: order 3 or 4 (seeded coin), dims
+    U[8,192], redrawn above 2^24 elements, a random contraction mode."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    spec = []
+    for _ in range(count):
+        d = 3 if rng.random() < 0.5 else 4
+        while True:
+            dd = tuple(int(n) for n in rng.integers(8, 193, size=d))
+            if math.prod(dd) <= (1 << 24):
+                break
+        spec.append((dd, int(rng.integers(0, d))))
+    return spec
+
+
+def run_case(argv):
+    """One contraction case, repeated, for profiling (ncu) and quick timing:
+
+        python bench.py --case tvc --dims 512 1024 1024 --mode 1 --dtype f64 --reps 3
+        python bench.py --case tvc --dims 1024 1024 1024 --mode 0 --dtype f32 --tmc 4
+        python bench.py --case batched --count 128 --what tvc --reps 3
+
+    tvc: fills A (uniform [-1, 1), seed 0) on the device, runs `reps`
+    contractions (--tmc R: the tensor-matrix contraction with an R-row
+    matrix; --mttkrp R: the MTTKRP with R-column factors) and prints the
+    CUDA-event time and the GB/s of the last one.  batched: the batched
+    workload at --count tensors; --what tvc (forward), fwdbwd (forward + gx
+    + rank-1 gA), gx, ga (one adjoint), hopm (10 sweeps per tensor)."""
+    import torch
+    import synth
+    import synth.device as sd
+    import paper_2501_03121_gb300 as tg
+
+    ap = argparse.ArgumentParser(prog="bench.py --case")
+    ap.add_argument("case", choices=["tvc", "batched"])
+    ap.add_argument("--dims", type=int, nargs="+")
+    ap.add_argument("--mode", type=int, default=0)
+    ap.add_argument("--dtype", default="f64", choices=["f64", "f32", "bf16", "e4m3", "f16", "f32d"])
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--tmc", type=int, default=0, help="rows of X (tensor-matrix contraction); 0: TVC")
+    ap.add_argument("--mttkrp", type=int, default=0, help="columns of the factor matrices (MTTKRP); 0: TVC")
+    ap.add_argument("--count", type=int, default=128)
+    ap.add_argument("--what", default="tvc", choices=["tvc", "fwdbwd", "gx", "ga", "hopm"])
+    a = ap.parse_args(argv)
+    dev = torch.device("cuda", 0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed_last(fn):
+        ms = 0.0
+        for _ in range(a.reps):
+            e0.record()
+            out = fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+        return ms, out
+
+    if a.case == "batched":
+        spec = batched_spec(a.count)
+        total = sum(math.prod(dd) for dd, _ in spec)
+        pool = torch.empty(total, dtype=torch.float32, device=dev)
+        sd.fill(pool, "u32", 0, synth.STREAM_A)
+        items, off, nbytes = [], 0, 0
+        f32 = dict(dtype=torch.float32, device=dev)
+        for dd, mode in spec:
+            N = math.prod(dd)
+            A = pool[off:off + N]
+            off += N
+            if a.what == "hopm":
+                items.append(dict(A=A, shape=dd, x=[torch.full((n,), 1 / math.sqrt(n), **f32) for n in dd]))
+                nbytes += 10 * (2 * N * 4)
+                continue
+            x = torch.full((dd[mode],), 0.5, **f32)
+            gy = torch.full((N // dd[mode],), 0.25, **f32)
+            it = dict(A=A, shape=dd, mode=mode, x=x)
+            nbytes += N * 4 + (N // dd[mode]) * 4
+            if a.what == "gx":
+                it.update(gy=gy, gx=torch.empty(dd[mode], **f32))
+            elif a.what == "ga":
+                it.update(gy=gy, gA=torch.empty(N, **f32))
+            else:
+                it.update(y=torch.empty(N // dd[mode], **f32))
+                if a.what == "fwdbwd":
+                    it.update(gy=gy, gx=torch.empty(dd[mode], **f32), gA=torch.empty(N, **f32))
+                    nbytes += N * 4 + (N // dd[mode]) * 4 + N * 4
+            items.append(it)
+        batch = tg.HOPMBatch(items, 10) if a.what == "hopm" else tg.TVCBatch(items)
+        ms, _ = timed_last(batch.run)
+        print(f"{a.count} tensors ({total / 1e9:.2f}e9 elements) {a.what}: {ms:.3f} ms  {nbytes / ms / 1e6:.1f} GB/s")
+        return 0
+
+    if not a.dims:
+        ap.error("--dims is required for --case tvc")
+    dt = torch.float64 if a.dtype == "f64" else torch.float32
+    kind = "u64" if a.dtype == "f64" else "u32"
+    N = math.prod(a.dims)
+    A = torch.empty(N, dtype=dt, device=dev)
+    sd.fill(A, kind, 0, synth.STREAM_A)
+    scales = None
+    if a.dtype in ("bf16", "e4m3", "f16"):
+        A, scales, _ = tg.quantise(A.view(a.dims), {"bf16": tg.BF16, "e4m3": tg.E4M3, "f16": tg.F16}[a.dtype])
+        A = A.view(-1)
+    xkind = "u64" if a.dtype == "f32d" else kind  # single-double: FP32 storage, FP64 vectors
+    code = tg.F32D if a.dtype == "f32d" else tg.dtype_code(A)
+    nk = a.dims[a.mode]
+    if a.mttkrp:
+        R = a.mttkrp
+        facs = [None if m == a.mode else torch.from_numpy(synth.tensor(xkind, 1, (n, R), 20 + m)).to(dev)
+                for m, n in enumerate(a.dims)]
+        ws = torch.empty(max(1, tg.mttkrp_workspace_size(a.dims, a.mode, R, code)), dtype=torch.uint8, device=dev)
+        ms, M = timed_last(lambda: tg.mttkrp(A, a.mode, facs, scales=scales, workspace=ws, shape=a.dims))
+        nbytes = N * A.element_size() + sum(f.numel() * f.element_size() for f in facs if f is not None) \
+            + M.numel() * M.element_size()
+        print(f"dims={a.dims} mode={a.mode} {a.dtype} mttkrp R={R}: {ms:.3f} ms  {nbytes / ms / 1e6:.1f} GB/s")
+        return 0
+    R = max(1, a.tmc)
+    if a.tmc:
+        x = torch.from_numpy(synth.tensor(xkind, 1, (R, nk), synth.stream_x(a.mode))).to(dev)
+        y = torch.empty(N // nk * R, dtype=x.dtype, device=dev)
+        ws = torch.empty(max(1, tg.tmc_workspace_size(a.dims, a.mode, R, code)), dtype=torch.uint8, device=dev)
+        fn = lambda: tg.tmc(A, a.mode, x, Y=y, shape=a.dims, scales=scales, workspace=ws)  # noqa: E731
+    else:
+        x = torch.from_numpy(synth.vector(xkind, 1, synth.stream_x(a.mode), nk)).to(dev)
+        y = torch.empty(N // nk, dtype=x.dtype, device=dev)
+        ws = torch.empty(max(1, tg.tvc_workspace_size(a.dims, a.mode, code)), dtype=torch.uint8, device=dev)
+        fn = lambda: tg.tvc(A, a.mode, x, y=y, shape=a.dims, scales=scales, workspace=ws)  # noqa: E731
+    ms, _ = timed_last(fn)
+    nbytes = N * A.element_size() + x.numel() * x.element_size() + y.numel() * y.element_size()
+    what = f"tmc R={R}" if a.tmc else "tvc"
+    print(f"dims={a.dims} mode={a.mode} {a.dtype} {what}: {ms:.3f} ms  {nbytes / ms / 1e6:.1f} GB/s")
+    return 0
+
+
 # ------------------------------------------------------------------- main
 
 def main(argv=None):
+    argv = sys.argv[1:] if argv is None else list(argv)
+    if argv and argv[0] == "--case":
+        return run_case(argv[1:])
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)

@@ -45,7 +45,8 @@
  *   indexing is 64-bit.
  * Aliasing: outputs must not overlap inputs.
  * Threading: calls on different streams may run concurrently when they use
- *   different workspaces.
+ *   different workspaces (tvc() takes its own per call; tvc_noalloc shares
+ *   one array per device and must be ordered).
  */
 #ifndef TVC_GB300_H
 #define TVC_GB300_H
@@ -92,8 +93,20 @@ const char* tvc_status_string(tvc_status s);
  *     y[i*v + l] = sum_{j < n_k} A[(i*n_k + j)*v + l] * x[j]
  * x: n_mode entries; y: N / n_mode entries, the remaining modes in
  * row-major order (the contracted mode behaves as a mode of size one).
- * Uses a workspace the library allocates once per device when the shape
- * needs one (see tvc_ex to pass your own).  Narrow types use unit scales.
+ * Narrow types use unit scales.
+ * Scratch: shapes that need a workspace (FP64 always: the split pieces of
+ * x; any type when n_mode is split over several blocks) take it for the
+ * duration of the call from a library-owned memory pool of the current
+ * device, stream-ordered: cudaMallocFromPoolAsync on `stream` before the
+ * kernels and cudaFreeAsync on `stream` after them.  So calls on different
+ * streams never share scratch and may run concurrently; no call
+ * synchronises the device or the stream.  The pool is created by the
+ * first call on a device that needs scratch (make that call before any
+ * stream capture); it keeps the memory it has handed out reserved for
+ * later calls until the process exits.  Under stream capture the
+ * allocation and the free become the graph's own memory nodes, so the call
+ * can be captured in a CUDA graph.  tvc_ex with a caller-owned workspace
+ * allocates nothing.
  */
 tvc_status tvc(const void* A, int order, const int64_t* dims, int mode, const void* x, void* y,
                tvc_dtype dtype, tvc_stream_t stream);
@@ -173,12 +186,14 @@ size_t mttkrp_workspace_size(int order, const int64_t* dims, int mode, int64_t R
 
 /*
  * tvc_noalloc: the same contraction as tvc_ex() with alpha = 1, beta = 0,
- * for callers that cannot allocate device memory (code run from a host
- * callback queued with cudaLaunchHostFunc, where CUDA API calls are not
- * allowed; plug-ins whose host framework owns every device allocation;
+ * for callers that cannot allocate device memory: plug-ins whose host
+ * framework owns every device allocation through its own pool, and
  * real-time or certified deployments that forbid device allocation after
- * start-up).  The paper has no counterpart: this is an interface of this
- * library only.
+ * start-up.  The paper has no counterpart: this is an interface of this
+ * library only.  The call still makes ordinary CUDA runtime calls (device
+ * query, kernel launches, and on the first call a symbol lookup), so it
+ * cannot be used where CUDA calls are not allowed at all (for instance
+ * inside a host function queued on a stream).
  * It allocates nothing and needs no workspace: its scratch (the split
  * pieces of x for FP64 and the split-K partial sums) is a fixed array of
  * TVC_NOALLOC_SCRATCH_BYTES that is part of the library's device image, so
@@ -454,9 +469,11 @@ tvc_status tvc_device_error(int* code_out, int clear);
  * hopm_jacobi, hopm_backward, tvc_quantise and the batched power methods):
  * waits for the work queued on `stream` before it (a stream-ordered copy,
  * then a synchronisation of that stream) and stores the word's value, a
- * tvc_status code, in *host_out.  Returns TVC_ERR_INVALID_ARG for a NULL
- * pointer, TVC_ERR_CUDA if the copy fails, else TVC_OK (whatever the word
- * holds). */
+ * tvc_status code, in *host_out.  It synchronises, so it must not be
+ * called on a stream that is being captured: it then returns
+ * TVC_ERR_INVALID_ARG without touching the stream (the capture stays
+ * valid).  Returns TVC_ERR_INVALID_ARG for a NULL pointer, TVC_ERR_CUDA if
+ * the copy fails, else TVC_OK (whatever the word holds). */
 tvc_status tvc_read_status(const int* dev_status, int* host_out, tvc_stream_t stream);
 
 /* Number of CUDA kernels this library has launched in this process (all

@@ -1,5 +1,5 @@
 // Host utilities of the C ABI: status strings, shape validation, the
-// library-owned per-device workspace.
+// library-owned stream-ordered memory pool of tvc().
 #include <atomic>
 #include <mutex>
 #include <vector>
@@ -65,38 +65,58 @@ void count_launches(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order
 
 namespace {
 std::mutex g_ws_mu;
-std::vector<std::pair<void*, size_t>> g_ws;  // per device id
+std::vector<cudaMemPool_t> g_pools;  // per device id
 std::vector<int> g_sms;
 }  // namespace
 
-void* library_workspace(size_t bytes, tvc_status* st) {
-  *st = TVC_OK;
-  if (bytes == 0) return nullptr;
+// The library's stream-ordered memory pool on the current device, created on
+// first use.  Its release threshold is "never", so memory freed back to it
+// stays reserved and later allocations of the same size cost no driver
+// mapping.
+static tvc_status device_pool(cudaMemPool_t* out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
-    *st = TVC_ERR_CUDA;
-    return nullptr;
+    cudaGetLastError();
+    return TVC_ERR_CUDA;
   }
   std::lock_guard<std::mutex> lk(g_ws_mu);
-  if ((int)g_ws.size() <= dev) g_ws.resize(dev + 1, {nullptr, 0});
-  auto& slot = g_ws[dev];
-  if (slot.second < bytes) {
-    if (slot.first) {
-      // The old buffer may still be used by queued work on any stream.
-      cudaDeviceSynchronize();
-      cudaFree(slot.first);
-      slot = {nullptr, 0};
-    }
-    size_t want = align_up(bytes, (size_t)1 << 20);
-    void* p = nullptr;
-    if (cudaMalloc(&p, want) != cudaSuccess) {
+  if ((int)g_pools.size() <= dev) g_pools.resize(dev + 1, nullptr);
+  if (g_pools[dev] == nullptr) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
       cudaGetLastError();
-      *st = TVC_ERR_CUDA;
-      return nullptr;
+      return TVC_ERR_CUDA;
     }
-    slot = {p, want};
+    uint64_t keep = ~(uint64_t)0;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    g_pools[dev] = pool;
   }
-  return slot.first;
+  *out = g_pools[dev];
+  return TVC_OK;
+}
+
+tvc_status stream_scratch_alloc(size_t bytes, cudaStream_t st, void** out) {
+  *out = nullptr;
+  if (bytes == 0) return TVC_OK;
+  cudaMemPool_t pool = nullptr;
+  tvc_status s = device_pool(&pool);
+  if (s != TVC_OK) return s;
+  if (cudaMallocFromPoolAsync(out, bytes, pool, st) != cudaSuccess) {
+    cudaGetLastError();
+    *out = nullptr;
+    return TVC_ERR_CUDA;
+  }
+  return TVC_OK;
+}
+
+tvc_status stream_scratch_free(void* p, cudaStream_t st) {
+  if (p == nullptr) return TVC_OK;
+  return cuda_status(cudaFreeAsync(p, st));
 }
 
 int device_sms() {
@@ -133,6 +153,14 @@ extern "C" const char* tvc_status_string(tvc_status s) {
 extern "C" tvc_status tvc_read_status(const int* dev_status, int* host_out, tvc_stream_t stream) {
   if (!dev_status || !host_out) return TVC_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
+  // The read waits for the stream, which a stream being captured cannot do:
+  // refuse before touching it, so that the capture stays valid.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    return TVC_ERR_CUDA;
+  }
+  if (cap != cudaStreamCaptureStatusNone) return TVC_ERR_INVALID_ARG;
   int v = 0;
   if (cudaMemcpyAsync(&v, dev_status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)

@@ -15,7 +15,6 @@
 // in row-group order in shared memory and written per block; a third kernel
 // sums the blocks in order.  Every result is deterministic.
 #include <algorithm>
-#include <cstdlib>
 
 #include "common.cuh"
 #include "internal.h"
@@ -175,28 +174,12 @@ __global__ void dual_cols_kernel(const float* __restrict__ P, float* __restrict_
   }
 }
 
-// Largest warps per row (TVC_DUAL_WG: 8, 4 or 2) and rows in flight per warp
-// (TVC_DUAL_UR: 2 or 4) of the single-pass kernel.  Measured on 2048^3 and
-// 256^4: at most 4 warps per row; 4 rows in flight, 2 when a lane holds 16
-// FP32 columns (155 registers with 4).
-int dual_wg_max() {
-  static int v = [] {
-    const char* e = std::getenv("TVC_DUAL_WG");
-    const int r = e ? std::atoi(e) : 4;
-    return (r == 2 || r == 4 || r == 8) ? r : 4;
-  }();
-  return v;
-}
+// Largest warps per row and rows in flight per warp of the single-pass
+// kernel, as measured on 2048^3 and 256^4: at most 4 warps per row; 4 rows in
+// flight, 2 when a lane holds 16 FP32 columns (155 registers with 4).
+int dual_wg_max() { return 4; }
 
-int dual_ur(int K, int vec) {
-  static int v = [] {
-    const char* e = std::getenv("TVC_DUAL_UR");
-    const int r = e ? std::atoi(e) : 0;
-    return (r == 2 || r == 4) ? r : 0;
-  }();
-  if (v) return v;
-  return (vec == 4 && K * vec >= 16) ? 2 : 4;
-}
+int dual_ur(int K, int vec) { return (vec == 4 && K * vec >= 16) ? 2 : 4; }
 
 struct DualPlan {
   bool ok = false;

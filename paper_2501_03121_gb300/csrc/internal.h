@@ -30,10 +30,14 @@ bool valid_dtype(int dt);
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 inline bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
-// A per-device, grow-only workspace owned by the library, for the entry
-// points that do not take one.  Serialised by a mutex; the buffer is kept
-// until process exit.  Returns NULL (and sets *st) if cudaMalloc fails.
-void* library_workspace(size_t bytes, tvc_status* st);
+// Stream-ordered scratch for the entry points that do not take a workspace:
+// cudaMallocFromPoolAsync on `st` from a library-owned pool of the current
+// device (created on first use, memory kept reserved once freed), released
+// with cudaFreeAsync on the same stream after the work that uses it.  Calls
+// on different streams get different memory; under stream capture the pair
+// becomes the graph's own allocation and free nodes.  bytes == 0 gives NULL.
+tvc_status stream_scratch_alloc(size_t bytes, cudaStream_t st, void** out);
+tvc_status stream_scratch_free(void* p, cudaStream_t st);
 
 // Number of SMs of the current device (cached per device).
 int device_sms();

@@ -1,12 +1,15 @@
 // tvc_noalloc: the contraction of tvc()/tvc_ex() for callers that must not
-// allocate device memory.  Some callers cannot call cudaMalloc: code run
-// from a host callback queued with cudaLaunchHostFunc (where CUDA API calls
-// are not allowed), plug-ins whose host framework owns every device
-// allocation through its own pool, and real-time or certified deployments
-// that forbid device allocation once start-up is over.  tvc() would allocate
-// its workspace on first use and tvc_ex() needs one from the caller, so this
+// allocate device memory.  Two kinds of caller cannot call cudaMalloc:
+// plug-ins whose host framework owns every device allocation through its own
+// pool (an allocation behind its back is invisible to its accounting and can
+// push it out of memory), and real-time or certified deployments that forbid
+// device allocation once start-up is over (an allocation can block on the
+// driver and its failure mode is hard to bound).  tvc() allocates its
+// scratch per call and tvc_ex() needs a workspace from the caller, so this
 // entry point instead uses a fixed scratch array that is part of the
-// library's device image.
+// library's device image.  It still makes ordinary CUDA runtime calls
+// (device query, symbol lookup on first use, kernel launches), so it is no
+// use where CUDA calls are forbidden altogether.
 #include <mutex>
 
 #include "internal.h"

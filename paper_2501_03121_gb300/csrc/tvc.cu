@@ -20,7 +20,6 @@
 // ("split-K"); the partial results go to the workspace and a second kernel
 // adds them in a fixed order (deterministic).
 #include <algorithm>
-#include <cstdlib>
 #include <mutex>
 #include <set>
 
@@ -1444,136 +1443,27 @@ static void opt_in_smem(const void* kern, int bytes) {
   }
 }
 
-// Steps per lane of the staged rows kernel (4: fewer registers; 8: fewer
-// lanes per row and shorter reductions).  TVC_STAGED_STEPS overrides.
-static int staged_steps_target() {
-  static int v = [] {
-    const char* e = std::getenv("TVC_STAGED_STEPS");
-    const int r = e ? std::atoi(e) : 4;
-    return (r == 4 || r == 8) ? r : 4;
-  }();
-  return v;
-}
+// Measured defaults of the planner (one choice per case; no run-time
+// switches).  Staged (TMA) rows kernel: 4 steps per lane (fewer registers
+// than 8).  FP64 rows with 8-byte loads (odd n_k) of up to 4096 elements go
+// to the slots kernel with G = 32 (below that the per-row FP64 epilogue of
+// one row per warp occupies the FP64 pipe; 979-element rows 4.0 -> 5.3
+// TB/s).
+constexpr int kStagedSteps = 4;
+constexpr int64_t kF64SlotsMaxNk = 4096;
 
-// Steps per lane of FP64 staged rows sent to the DFMA pipe: about a third
-// of them by default (TVC_STAGED_DFMA = steps overrides, -1 = default).
-static int staged_dfma_steps(int nst) {
-  static int v = [] {
-    const char* e = std::getenv("TVC_STAGED_DFMA");
-    return e ? std::atoi(e) : -1;
-  }();
-  if (v >= 0) return v;
-  return nst / 3;
-}
-
-// Staged (TMA) rows kernel on by default; TVC_STAGED_ROWS=0 turns it off.
-static bool staged_rows_enabled() {
-  static bool v = [] {
-    const char* e = std::getenv("TVC_STAGED_ROWS");
-    return !(e && std::atoi(e) == 0);
-  }();
-  return v;
-}
-
-static int dfma_rows_option() {
-  static int v = [] {
-    const char* e = std::getenv("TVC_F64_DFMA_ROWS");
-    int r = e ? std::atoi(e) : 0;
-    return (r == 0 || r == 2 || r == 3 || r == 4) ? r : 0;
-  }();
-  return v;
-}
-
-// FP64 short rows through the staged (TMA) kernel: only where the register
-// kernels are left with 8-byte loads (odd n_k); TVC_F64_STAGED=0 turns it
-// off, 1 (default 0 until measured) turns it on.
-static bool f64_staged_rows(int64_t nk, const void* A) {
-  static int v = [] {
-    const char* e = std::getenv("TVC_F64_STAGED");
-    return e ? std::atoi(e) : 0;
-  }();
-  return v == 1 && (nk % 2 == 1 || !aligned(A, 16));
-}
-
-// Longest FP64 rows with 8-byte loads (odd n_k) served by the slots kernel
-// with G = 32 (below it the per-row FP64 epilogue of one row per warp
-// occupies the FP64 pipe; 979-element rows 4.0 -> 5.3 TB/s);
-// TVC_F64_SLOTS_MAX overrides (0: only G < 32).
-static int64_t f64_slots_max_nk() {
-  static int64_t v = [] {
-    const char* e = std::getenv("TVC_F64_SLOTS_MAX");
-    return e ? (int64_t)std::atoll(e) : (int64_t)4096;
-  }();
-  return v;
-}
-
-// Persistent double-buffered small-slab kernel on by default;
-// TVC_TILE_ASYNC=0 returns to one tile per block.
-static bool slab_async_enabled() {
-  static bool v = [] {
-    const char* e = std::getenv("TVC_SLAB_ASYNC");
-    return !(e && std::atoi(e) == 0);
-  }();
-  return v;
-}
-
-static bool slab_async_f32() {
-  static bool v = [] {
-    const char* e = std::getenv("TVC_SLAB_ASYNC_F32");
-    return !(e && std::atoi(e) == 0);
-  }();
-  return v;
-}
-
-static bool tile_async_enabled() {
-  static bool v = [] {
-    const char* e = std::getenv("TVC_TILE_ASYNC");
-    return !(e && std::atoi(e) == 0);
-  }();
-  return v;
-}
-
-// Narrow long-row kernel on by default; TVC_ROWS_MULTI=0 returns those rows
-// to the one-row-per-group kernel.
-static bool rows_multi_enabled() {
-  static bool v = [] {
-    const char* e = std::getenv("TVC_ROWS_MULTI");
-    return !(e && std::atoi(e) == 0);
-  }();
-  return v;
-}
+// Rows in flight per lane of the slab kernel: 8 for FP64/FP32, 16 for the
+// narrow types (measured at v = 3 .. 20).
+static int slab_unroll(tvc_dtype dt) { return (dt == TVC_BF16 || dt == TVC_E4M3 || dt == TVC_F16) ? 16 : 8; }
 
 // Rows per warp (2, 4 or 8) and unrolled steps (1 or 2) of the narrow
 // long-row kernel, per storage type as measured on rows of 16384 to 1048576
 // elements: E4M3 8 x 1 (x traffic 0.5x that of A, 128 registers), BF16 2 x 2,
-// FP32 4 x 2.  TVC_ROWS_RB and TVC_ROWS_UNR override.
-// Value of an integer environment switch if it is one of the allowed values, else 0.
-static int env_choice(const char* name, int ok1, int ok2, int ok3) {
-  const char* e = std::getenv(name);
-  if (!e) return 0;
-  const int r = std::atoi(e);
-  return (r == ok1 || r == ok2 || r == ok3) ? r : 0;
-}
-
-// Rows in flight per lane of the slab kernel (4, 8 or 16): 8 for FP64/FP32,
-// 16 for the narrow types (as measured at v = 3 .. 20); TVC_SLAB_UNR overrides.
-static int slab_unroll(tvc_dtype dt) {
-  static int v = env_choice("TVC_SLAB_UNR", 4, 8, 16);
-  if (v) return v;
-  return (dt == TVC_BF16 || dt == TVC_E4M3 || dt == TVC_F16) ? 16 : 8;  // measured best per type
-}
-
+// FP32 4 x 2.
 static int rows_multi_rb(tvc_dtype dt) {
-  static int v = env_choice("TVC_ROWS_RB", 2, 4, 8);
-  if (v) return v;
   return dt == TVC_E4M3 ? 8 : ((dt == TVC_BF16 || dt == TVC_F16) ? 2 : 4);
 }
-
-static int rows_multi_unr(tvc_dtype dt) {
-  static int v = env_choice("TVC_ROWS_UNR", 1, 2, 1);
-  if (v) return v;
-  return dt == TVC_E4M3 ? 1 : 2;
-}
+static int rows_multi_unr(tvc_dtype dt) { return dt == TVC_E4M3 ? 1 : 2; }
 
 // Largest vector width (elements per load) the alignment and v allow.
 static int pick_vec(tvc_dtype dt, int64_t stride_elems, const void* A, int max_vec = 16) {
@@ -1611,18 +1501,16 @@ static Plan make_plan_impl(const Shape& s, tvc_dtype dt, const void* A, bool all
     p.chunk = ceil_div(ceil_div(s.nk, splits), 8) * 8;
     p.splits = ceil_div(s.nk, p.chunk);
     p.grid = dim3((unsigned)ceil_div(threads, kThreads), (unsigned)p.splits);
-  } else if (s.v == 1 && (!f64acc || (dt == TVC_F64 && f64_staged_rows(s.nk, A))) && allow_staged &&
-             staged_rows_enabled() &&
-             aligned(A, 16) &&
+  } else if (s.v == 1 && !f64acc && allow_staged && aligned(A, 16) &&
              s.nk <= 8 * 32 * (int64_t)pick_vec(dt, s.nk, A, 4) && s.u >= 8) {
     // Staged short rows: tiles of R = 8*RW whole rows through shared memory.
     p.kind = K_ROWS_TMA;
     p.vec = pick_vec(dt, s.nk, A, 4);
     int G = 1;
-    while (G < 32 && (int64_t)G * p.vec * staged_steps_target() < s.nk) G <<= 1;
+    while (G < 32 && (int64_t)G * p.vec * kStagedSteps < s.nk) G <<= 1;
     p.G = G;
     p.nst = (int)ceil_div(s.nk, (int64_t)G * p.vec);
-    p.dq = (dt == TVC_F64) ? std::min(p.nst - 1, staged_dfma_steps(p.nst)) : 0;
+    p.dq = 0;
     const int gpw = kWarp / G;
     const int64_t row_bytes = s.nk * (int64_t)es;
     int RW = gpw;  // at least one row per group
@@ -1663,7 +1551,7 @@ static Plan make_plan_impl(const Shape& s, tvc_dtype dt, const void* A, bool all
     p.splits = 1;
     p.chunk = s.nk;
     p.grid = dim3((unsigned)std::max<int64_t>(1, blocks), 1);
-  } else if (s.v == 1 && !f64acc && rows_multi_enabled() && pick_vec(dt, s.nk, A) * (int)es == 16) {
+  } else if (s.v == 1 && !f64acc && pick_vec(dt, s.nk, A) * (int)es == 16) {
     // Long rows of the narrow types: RB rows per warp share each x piece.
     p.kind = K_ROWS_MULTI;
     p.vec = pick_vec(dt, s.nk, A);
@@ -1690,7 +1578,7 @@ static Plan make_plan_impl(const Shape& s, tvc_dtype dt, const void* A, bool all
     p.G = G;
     const int64_t group = 4 * (int64_t)G * p.vec;  // one unrolled step of a group
     int64_t rows_per_block = (int64_t)kWarpsPerBlock * (kWarp / G);
-    if (f64acc && (G < 32 || (p.vec == 1 && s.nk <= f64_slots_max_nk()))) {
+    if (f64acc && (G < 32 || (p.vec == 1 && s.nk <= kF64SlotsMaxNk))) {
       p.kind = K_ROWS_F64S;  // 32 rows per warp, results converted in slots
       rows_per_block = (int64_t)kWarpsPerBlock * kWarp;
     }
@@ -1702,8 +1590,8 @@ static Plan make_plan_impl(const Shape& s, tvc_dtype dt, const void* A, bool all
     p.grid = dim3((unsigned)ceil_div(s.u, rows_per_block), (unsigned)p.splits);
   } else if (S > 512 &&
              (dt == TVC_E4M3 || ((dt == TVC_BF16 || dt == TVC_F16) && s.v % 2 == 0) ||
-              (dt == TVC_F32 && s.v % 4 == 0 && slab_async_f32())) &&
-             aligned(A, 16) && slab_async_enabled()) {
+              (dt == TVC_F32 && s.v % 4 == 0)) &&
+             aligned(A, 16)) {
     // Large slabs: staged 16-byte pieces (see the kernel).  Measured on
     // 4096x4096x16 mode 1: BF16 3.5 TB/s, E4M3 2.1, FP32 5.0 (the per-warp
     // slab kernel: 2.2, 0.54 and 4.9; FP32 on 16384x8192x8: 5.5 against
@@ -1730,7 +1618,7 @@ static Plan make_plan_impl(const Shape& s, tvc_dtype dt, const void* A, bool all
     p.chunk = ceil_div(ceil_div(s.nk, splits), p.G) * p.G;
     p.splits = ceil_div(s.nk, p.chunk);
     p.grid = dim3((unsigned)ceil_div(s.u, kWarpsPerBlock), (unsigned)p.splits);
-  } else if (aligned(A, 16) && tile_async_enabled()) {
+  } else if (aligned(A, 16)) {
     // Small slabs, persistent double-buffered tiles (see the kernel).
     p.kind = K_TILE_ASYNC;
     int64_t R = std::min<int64_t>(kThreads / s.v, (int64_t)(48 * 1024) / (int64_t)(S * es));
@@ -1847,10 +1735,9 @@ static void launch_rows_tma(const Plan& p, const TvcArgs<DT>& a, cudaStream_t st
     kern<<<p.grid, kTmaThreads, p.smem, st>>>(a, prm);
   };
   const bool n4 = p.nst <= 4;
-  if constexpr (DT == TVC_F64) {
-    if (p.vec == 2) n4 ? go(tvc_rows_tma_kernel<DT, 2, 4>) : go(tvc_rows_tma_kernel<DT, 2, 8>);
-    else n4 ? go(tvc_rows_tma_kernel<DT, 1, 4>) : go(tvc_rows_tma_kernel<DT, 1, 8>);
-  } else {
+  // The planner sends only FP32 and the narrow types here (FP64 rows are
+  // faster in the register kernels).
+  if constexpr (!kF64Acc<DT>) {
     if (p.vec == 4) n4 ? go(tvc_rows_tma_kernel<DT, 4, 4>) : go(tvc_rows_tma_kernel<DT, 4, 8>);
     else if (p.vec == 2) n4 ? go(tvc_rows_tma_kernel<DT, 2, 4>) : go(tvc_rows_tma_kernel<DT, 2, 8>);
     else n4 ? go(tvc_rows_tma_kernel<DT, 1, 4>) : go(tvc_rows_tma_kernel<DT, 1, 8>);
@@ -1870,37 +1757,23 @@ static void launch_rows_f64s_dq(const Plan& p, const TvcArgs<DT>& a, cudaStream_
 }
 
 // Share (of 4 unrolled steps) of the FP64 short-row products sent to the
-// DFMA pipe (exact FP64 products beside the float-float ones): 2 by default
-// (128-element rows 5.45 -> 5.77 TB/s, 40-element rows unchanged);
-// TVC_F64_ROWS_DFMA (0..2) overrides.
-static int slots_dfma_steps() {
-  static int v = [] {
-    const char* e = std::getenv("TVC_F64_ROWS_DFMA");
-    const int r = e ? std::atoi(e) : 2;
-    return (r >= 0 && r <= 2) ? r : 2;
-  }();
-  return v;
-}
+// DFMA pipe (exact FP64 products beside the float-float ones): 2 (measured:
+// 128-element rows 5.45 -> 5.77 TB/s, 40-element rows unchanged).
+constexpr int kSlotsDfmaSteps = 2;
 
 template <tvc_dtype DT, int VEC>
 static void launch_rows_f64s_vec(const Plan& p, const TvcArgs<DT>& a, cudaStream_t st) {
-  const int dq = (DT == TVC_F64) ? slots_dfma_steps() : 0;
-  if (dq == 0) launch_rows_f64s_dq<DT, VEC, 0>(p, a, st);
-  else if (dq == 1) launch_rows_f64s_dq<DT, VEC, 1>(p, a, st);
-  else launch_rows_f64s_dq<DT, VEC, 2>(p, a, st);
+  if constexpr (DT == TVC_F64) launch_rows_f64s_dq<DT, VEC, kSlotsDfmaSteps>(p, a, st);
+  else launch_rows_f64s_dq<DT, VEC, 0>(p, a, st);
 }
 
 template <tvc_dtype DT>
 static void launch_main(const Plan& p, const TvcArgs<DT>& a, cudaStream_t st) {
   switch (p.kind) {
     case K_COLS: {
-      const int dr = (DT == TVC_F64) ? dfma_rows_option() : 0;
       if constexpr (DT == TVC_F64) {
         if (p.vec == 2) {
-          if (dr == 2) tvc_cols_kernel<DT, 2, 2><<<p.grid, kThreads, 0, st>>>(a);
-          else if (dr == 3) tvc_cols_kernel<DT, 2, 3><<<p.grid, kThreads, 0, st>>>(a);
-          else if (dr == 4) tvc_cols_kernel<DT, 2, 4><<<p.grid, kThreads, 0, st>>>(a);
-          else tvc_cols_kernel<DT, 2, 0><<<p.grid, kThreads, 0, st>>>(a);
+          tvc_cols_kernel<DT, 2, 0><<<p.grid, kThreads, 0, st>>>(a);
         } else {
           tvc_cols_kernel<DT, 1, 0><<<p.grid, kThreads, 0, st>>>(a);
         }
@@ -1941,7 +1814,6 @@ static void launch_main(const Plan& p, const TvcArgs<DT>& a, cudaStream_t st) {
       break;
     case K_SLAB:
       if (slab_unroll(DT) == 16) tvc_slab_kernel<DT, 16><<<p.grid, kThreads, 0, st>>>(a, p.g, p.G);
-      else if (slab_unroll(DT) == 4) tvc_slab_kernel<DT, 4><<<p.grid, kThreads, 0, st>>>(a, p.g, p.G);
       else tvc_slab_kernel<DT, 8><<<p.grid, kThreads, 0, st>>>(a, p.g, p.G);
       break;
     case K_SLAB_ASYNC:
@@ -2072,8 +1944,12 @@ extern "C" tvc_status tvc(const void* A, int order, const int64_t* dims, int mod
   Shape s;
   tvc_status st = validate(A, order, dims, mode, x, y, dtype, &s);
   if (st != TVC_OK) return st;
+  const cudaStream_t cs = (cudaStream_t)stream;
   const size_t need = tvc_ws_bytes(s, dtype, A);
-  void* ws = library_workspace(need, &st);
+  void* ws = nullptr;
+  st = stream_scratch_alloc(need, cs, &ws);
   if (st != TVC_OK) return st;
-  return tvc_launch(A, s, x, y, dtype, nullptr, 1.0, 0.0, ws, need, (cudaStream_t)stream);
+  st = tvc_launch(A, s, x, y, dtype, nullptr, 1.0, 0.0, ws, need, cs);
+  const tvc_status fr = stream_scratch_free(ws, cs);
+  return st != TVC_OK ? st : fr;
 }
