@@ -141,12 +141,17 @@ def dist_setup():
     return world, rank, local
 
 
-# ----------------------------------------------------------- oracle timing
+# ------------------------------------------------ CPU-baseline (oracle) leg
+#
+# The only part of this file that runs the oracle (the FP64 CPU reference
+# under oracle/): its timings on the host cores, and the reference values at
+# sampled outputs of the timed GPU calls, from which the error of the timed
+# results is reported.
 
 class OracleSample:
-    """A bounded sample of the workload for the FP64 CPU oracle: each tensor
-    cut to its first slabs (dims[0] reduced so the cut holds about 2^22
-    elements), in FP64 and FP32 storage, contracted along every mode."""
+    """A bounded sample of the sweep workload for the FP64 CPU oracle: each
+    tensor cut to its first slabs (dims[0] reduced so the cut holds about
+    2^22 elements), in FP64 and FP32 storage, contracted along every mode."""
 
     def __init__(self, elems=1 << 22):
         import oracle
@@ -165,7 +170,7 @@ class OracleSample:
                 xs = [synth.vector("u64", 1, synth.stream_x(k), sd[k]) for k in range(len(sd))]
                 self.items.append((A, sd, xs, es))
         self.desc = ("oracle TVC along every mode of " + ", ".join("x".join(map(str, c)) for c in self.cut) +
-                     " (the first slabs of each workload tensor), FP64 and FP32 storage")
+                     " (the first slabs of each sweep tensor), FP64 and FP32 storage")
 
     def run_once(self):
         nbytes, secs = 0, 0.0
@@ -190,6 +195,110 @@ def oracle_threads():
     return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
 
 
+def _gbs(nbytes, secs):
+    return round(nbytes / secs / 1e9, 2)
+
+
+def oracle_config_timings(dev, threads):
+    """The oracle on each workload at `threads` threads, bounded: the
+    128^3 FP64 contraction along every mode and 20 HOPM sweeps (whole); one
+    sweep of the oracle's three-buffer HOPM (Algorithm 1) on the first 4
+    slabs of the planted 256^4 tensor and on the first 16 slabs of the
+    2048^3 tensor stored BF16 and E4M3 (quantised by the oracle); GB/s of
+    algorithmic bytes.  Inputs of the large workloads come from the device
+    generator (the host generator's bits)."""
+    import numpy as np
+    import torch
+    import oracle
+    import synth
+    import synth.device as sd
+    prev = oracle.set_threads(threads)
+    out = {}
+    try:
+        dims = (128, 128, 128)
+        A = synth.tensor("u64", 0, dims)
+        t0 = time.perf_counter()
+        nb = 0
+        for k in range(3):
+            oracle.tvc(A, k, synth.vector("u64", 1, synth.stream_x(k), 128))
+            nb += tvc_bytes(dims, k, 8, 8)
+        out["c1_tvc_GB/s"] = _gbs(nb, time.perf_counter() - t0)
+        ones = [np.ones(n) / math.sqrt(n) for n in dims]
+        t0 = time.perf_counter()
+        oracle.hopm(A, ones, 20)
+        sec = time.perf_counter() - t0
+        out["c1_hopm20_s"] = round(sec, 3)
+        # planted 4 x 256^3 slab sample, one sweep (FP32 storage)
+        pd = (4, 256, 256, 256)
+        us = [synth.unit_gaussian(0, synth.stream_u(j), 256) for j in range(4)]
+        t = torch.empty(math.prod(pd), dtype=torch.float32, device=dev)
+        sd.fill(t, "planted", 0, 0, dims=(256,) * 4, us=us)
+        Ah = t.cpu().numpy().reshape(pd)
+        del t
+        t0 = time.perf_counter()
+        oracle.hopm3(Ah, [np.ones(n) / math.sqrt(n) for n in pd], 1)
+        out["c3_sweep_GB/s"] = _gbs(hopm_bytes(pd, 4, 4), time.perf_counter() - t0)
+        del Ah
+        # mixed-precision 16 x 2048^2 slab sample, one sweep per format
+        md = (16, 2048, 2048)
+        t = torch.empty(math.prod(md), dtype=torch.float32, device=dev)
+        sd.fill(t, "lognormal", 0, synth.STREAM_A)
+        src = t.cpu().numpy().reshape(md)
+        del t
+        for name, fmt, es in (("bf16", oracle.BF16, 2), ("e4m3", oracle.E4M3, 1)):
+            codes, scales = oracle.quantise(src, fmt)
+            t0 = time.perf_counter()
+            oracle.hopm3(codes, [np.ones(n) / math.sqrt(n) for n in md], 1, scales=scales)
+            out[f"c4_{name}_sweep_GB/s"] = _gbs(hopm_bytes(md, es, 4), time.perf_counter() - t0)
+    finally:
+        oracle.set_threads(prev)
+    return out
+
+
+def cpu_baseline_leg(dev, cores, sampled=None):
+    """Timings of the oracle on the host cores (all of them, and one thread),
+    and, for `sampled` = [(kind, dims, mode, x, picks)] of timed GPU calls,
+    the oracle's values there (plain FP64 sum and the exactly rounded sum)
+    with sum_j |a_j x_j|."""
+    import oracle
+    smp = OracleSample()
+    gbs, secs = smp.timed(10.0)
+    prev = oracle.set_threads(1)
+    try:
+        b1, s1 = smp.run_once()
+    finally:
+        oracle.set_threads(prev)
+    res = {"value": gbs, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": smp.desc,
+           "seconds": round(secs, 2),
+           "one_thread": {"value": _gbs(b1, s1), "cores": 1, "seconds": round(s1, 2)},
+           "configs": {"cores_%d" % cores: oracle_config_timings(dev, cores),
+                       "cores_1": oracle_config_timings(dev, 1)}}
+    refs = None
+    if sampled is not None:
+        refs = [sampled_reference(*item) for item in sampled]
+    return res, refs
+
+
+def sampled_reference(kind, dims, mode, x, picks):
+    """Oracle values (plain and exactly rounded) and sum |a x| at flat output
+    indices `picks` of A x_mode x, from host-generated elements."""
+    import numpy as np
+    import oracle
+    import synth
+    nk = dims[mode]
+    v = math.prod(dims[mode + 1:])
+    j = np.arange(nk, dtype=np.int64)
+    plain, exact, mag = (np.empty(len(picks)) for _ in range(3))
+    gen = synth.uniform_f64 if kind == "u64" else synth.uniform_f32
+    for t, o in enumerate(picks):
+        i, l = divmod(int(o), v)
+        a = gen(0, synth.STREAM_A, ((i * nk + j) * v + l).astype(np.uint64))
+        plain[t] = oracle.tvc(a, 0, x)
+        exact[t] = oracle.tvc_exact(a, 0, x)
+        mag[t] = np.sum(np.abs(a.astype(np.float64) * x))
+    return plain, exact, mag
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return 0
@@ -206,7 +315,7 @@ def run_reference(args, world, rank):
     v = statistics.median(vals)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GB/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * step_s,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "sample": smp.desc},
             "cpu_baseline": {"value": v, "unit": "GB/s", "cores": oracle_threads(), "kind": "oracle",
                              "sample": smp.desc},
@@ -353,8 +462,100 @@ def hopm_bytes(dims, es, vs):
     return b
 
 
+def golden_hopm():
+    """The FP64 oracle's results for the full-size power-method workloads,
+    stored by tests/golden/make_fullsize_hopm.py (oracle only), or None."""
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "hopm_fullsize.json")) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return None
+
+
+def _rel(a, b):
+    return abs(a - b) / abs(b)
+
+
+def hopm_workloads(dev):
+    """The two full-size power-method workloads, timed, with their error
+    against the FP64 oracle's stored results:
+    planted rank-1 + noise 256^4 FP32 (50 sweeps, tol 1e-8, from a start
+    overlapping the planted factors), and 2048^3 N(0,1)exp(U[-3,3]) stored
+    FP32, BF16 and E4M3 with per-slab scales (30 sweeps from all-ones).
+    Returns (summary for the result line, details)."""
+    import numpy as np
+    import torch
+    import synth
+    import synth.device as sd
+    import paper_2501_03121_gb300 as tg
+    gold = golden_hopm()
+    summary, detail = {}, {}
+    # planted rank-1 + noise
+    dims = (256, 256, 256, 256)
+    us = [synth.unit_gaussian(0, synth.stream_u(j), n) for j, n in enumerate(dims)]
+    A = torch.empty(math.prod(dims), dtype=torch.float32, device=dev)
+    sd.fill(A, "planted", 0, 0, dims=dims, us=us)
+    ws = torch.empty(tg.hopm_workspace_size(dims, tg.F32), dtype=torch.uint8, device=dev)
+    pert = []
+    for j, n in enumerate(dims):
+        v = us[j] + synth.unit_gaussian(1, synth.stream_u(j), n)
+        pert.append(torch.from_numpy((v / np.linalg.norm(v)).astype(np.float32)).to(dev))
+    r = tg.hopm(A, pert, 50, 1e-8, shape=dims, workspace=ws)
+    torch.cuda.synchronize()
+    sub = max(math.sqrt(max(0.0, 1 - float(np.dot(x.cpu().numpy().astype(np.float64), u)) ** 2))
+              for x, u in zip(r.x, us))
+    ms = _timed(lambda: tg.hopm(A, pert, 50, 0.0, shape=dims, workspace=ws), 2)
+    c3 = {"lambda": round(r.lam.item(), 6), "sweeps": int(r.sweeps.item()), "subspace_err": round(sub, 5),
+          "sweeps_per_s": round(50 / (ms / 1e3), 1),
+          "GB/s": round(50 * hopm_bytes(dims, 4, 4) / (ms / 1e3) / 1e9, 1)}
+    if gold and "planted" in gold:
+        c3["lambda_rel_err_vs_oracle"] = float("%.3g" % _rel(r.lam.item(), gold["planted"]["lam"]))
+    summary["hopm_c3"] = c3
+    ones = [torch.full((n,), 1 / math.sqrt(n), dtype=torch.float32, device=dev) for n in dims]
+    rr = tg.hopm(A, ones, 50, 1e-8, shape=dims, workspace=ws)
+    torch.cuda.synchronize()
+    detail["hopm_planted_from_ones"] = {"lambda": rr.lam.item(), "sweeps": int(rr.sweeps.item())}
+    del A, ws, r, rr
+    torch.cuda.empty_cache()
+    # 2048^3 stored FP32 / BF16 / E4M3
+    dims = (2048, 2048, 2048)
+    src = torch.empty(math.prod(dims), dtype=torch.float32, device=dev)
+    sd.fill(src, "lognormal", 0, synth.STREAM_A)
+    xs0 = [torch.full((n,), 1 / math.sqrt(n), dtype=torch.float32, device=dev) for n in dims]
+    res = {}
+    gm = gold.get("mixed") if gold else None
+    for name, code in (("f32", tg.F32), ("bf16", tg.BF16), ("e4m3", tg.E4M3)):
+        if code == tg.F32:
+            A, sc = src, None
+        else:
+            A, sc, _ = tg.quantise(src.view(dims), code)
+            A = A.view(-1)
+        ws = torch.empty(tg.hopm_workspace_size(dims, code), dtype=torch.uint8, device=dev)
+        r = tg.hopm(A, xs0, 30, 0.0, scales=sc, shape=dims, workspace=ws)
+        torch.cuda.synchronize()
+        lam = r.lam.item()
+        ms = _timed(lambda: tg.hopm(A, xs0, 30, 0.0, scales=sc, shape=dims, workspace=ws), 2)
+        es = {"f32": 4, "bf16": 2, "e4m3": 1}[name]
+        e = {"sweeps_per_s": round(30 / (ms / 1e3), 1),
+             "GB/s": round(30 * hopm_bytes(dims, es, 4) / (ms / 1e3) / 1e9, 1), "lambda": round(lam, 6)}
+        if gm:
+            # against the oracle on the binary32 source (storage + kernel error)
+            e["lambda_rel_err_vs_oracle"] = float("%.3g" % _rel(lam, gm["f32"]["lam"]))
+            if name != "f32":  # against the oracle on the same stored codes (kernel error)
+                e["kernel_rel_err"] = float("%.3g" % _rel(lam, gm[name]["lam"]))
+        res[name] = e
+        del A, ws, r
+        torch.cuda.empty_cache()
+    res["bf16_over_f32_sweeps"] = round(res["bf16"]["sweeps_per_s"] / res["f32"]["sweeps_per_s"], 3)
+    res["e4m3_over_f32_sweeps"] = round(res["e4m3"]["sweeps_per_s"] / res["f32"]["sweeps_per_s"], 3)
+    summary["hopm_c4"] = res
+    del src
+    torch.cuda.empty_cache()
+    return summary, detail
+
+
 def secondary(dev):
-    """HOPM, batched, TMC and MTTKRP figures (other workloads; not part of `value`)."""
+    """HOPM 128^3, batched, TMC and MTTKRP figures (details, not part of `value`)."""
     import numpy as np
     import torch
     import synth
@@ -370,7 +571,6 @@ def secondary(dev):
     ms = _timed(lambda: tg.hopm(A, xs, 20, shape=dims, workspace=ws), 5)
     # the same 20 sweeps replayed from a CUDA graph (no launch overhead)
     xg = [v.clone() for v in xs]
-    lam = torch.zeros(1, dtype=torch.float64, device=dev)
     hopm_graph = torch.cuda.CUDAGraph()
     gs = torch.cuda.Stream()
     gs.wait_stream(torch.cuda.current_stream())
@@ -385,63 +585,6 @@ def secondary(dev):
                                         "GB/s_effective_L2": 20 * hopm_bytes(dims, 8, 8) / (gms / 1e3) / 1e9,
                                         "note": "16.8 MB tensor: L2-resident"}
     del A, ws
-    # planted rank-1 + noise 256^4 FP32, 50 sweeps, tol 1e-8
-    dims = (256, 256, 256, 256)
-    us = [synth.unit_gaussian(0, synth.stream_u(j), n) for j, n in enumerate(dims)]
-    A = torch.empty(math.prod(dims), dtype=torch.float32, device=dev)
-    sd.fill(A, "planted", 0, 0, dims=dims, us=us)
-    ws = torch.empty(tg.hopm_workspace_size(dims, tg.F32), dtype=torch.uint8, device=dev)
-
-    def planted_run(xs0):
-        r = tg.hopm(A, xs0, 50, 1e-8, shape=dims, workspace=ws)
-        torch.cuda.synchronize()
-        sub = max(math.sqrt(max(0.0, 1 - float(np.dot(x.cpu().numpy().astype(np.float64), u)) ** 2))
-                  for x, u in zip(r.x, us))
-        return {"lambda": r.lam.item(), "sweeps_to_tol_1e-8": int(r.sweeps.item()), "subspace_error": sub}
-
-    ones = [torch.full((n,), 1 / math.sqrt(n), dtype=torch.float32, device=dev) for n in dims]
-    # a start that overlaps the planted factors: u_j plus an independent unit
-    # Gaussian vector, normalised (overlap about 0.7 per mode)
-    pert = []
-    for j, n in enumerate(dims):
-        g = synth.unit_gaussian(1, synth.stream_u(j), n)
-        v = us[j] + g
-        pert.append(torch.from_numpy((v / np.linalg.norm(v)).astype(np.float32)).to(dev))
-    ms = _timed(lambda: tg.hopm(A, ones, 50, 0.0, shape=dims, workspace=ws), 2)
-    bps = hopm_bytes(dims, 4, 4)
-    out["hopm_planted_256^4_f32"] = {"from_ones": planted_run(ones), "from_overlapping_start": planted_run(pert),
-                                    "sweeps_per_s": 50 / (ms / 1e3), "GB/s": 50 * bps / (ms / 1e3) / 1e9}
-    del A, ws
-    torch.cuda.empty_cache()
-    # 2048^3 N(0,1)exp(U[-3,3]): FP32 vs BF16 vs E4M3 storage, 30 sweeps
-    dims = (2048, 2048, 2048)
-    src = torch.empty(math.prod(dims), dtype=torch.float32, device=dev)
-    sd.fill(src, "lognormal", 0, synth.STREAM_A)
-    res = {}
-    xs0 = [torch.full((n,), 1 / math.sqrt(n), dtype=torch.float32, device=dev) for n in dims]
-    lam = {}
-    for name, code in (("f32", tg.F32), ("bf16", tg.BF16), ("e4m3", tg.E4M3)):
-        if code == tg.F32:
-            A, sc = src, None
-        else:
-            A, sc, st = tg.quantise(src.view(dims), code)
-            A = A.view(-1)
-        ws = torch.empty(tg.hopm_workspace_size(dims, code), dtype=torch.uint8, device=dev)
-        r = tg.hopm(A, xs0, 30, 0.0, scales=sc, shape=dims, workspace=ws)
-        torch.cuda.synchronize()
-        lam[name] = r.lam.item()
-        ms = _timed(lambda: tg.hopm(A, xs0, 30, 0.0, scales=sc, shape=dims, workspace=ws), 2)
-        es = {"f32": 4, "bf16": 2, "e4m3": 1}[name]
-        res[name] = {"sweeps_per_s": 30 / (ms / 1e3), "GB/s": 30 * hopm_bytes(dims, es, 4) / (ms / 1e3) / 1e9,
-                     "lambda": lam[name]}
-        del A, ws, r
-        torch.cuda.empty_cache()
-    res["bf16_over_f32_sweeps"] = res["bf16"]["sweeps_per_s"] / res["f32"]["sweeps_per_s"]
-    res["e4m3_over_f32_sweeps"] = res["e4m3"]["sweeps_per_s"] / res["f32"]["sweeps_per_s"]
-    res["lambda_rel_diff_bf16_vs_f32"] = abs(lam["bf16"] - lam["f32"]) / lam["f32"]
-    res["lambda_rel_diff_e4m3_vs_f32"] = abs(lam["e4m3"] - lam["f32"]) / lam["f32"]
-    out["hopm_mixed_2048^3"] = res
-    del src
     torch.cuda.empty_cache()
     # batched: 4096 FP32 tensors (order 3/4, dims U[8,192], <= 2^24 elements)
     spec = batched_spec(4096)
@@ -697,7 +840,7 @@ def main(argv=None):
                 xh = synth.vector(kind, 1, synth.stream_x(k), dims[k])
                 x = torch.from_numpy(xh).to(dev)
                 y = torch.empty(N // dims[k], dtype=dt, device=dev)
-                calls.append(dict(A=A, dims=dims, k=k, x=x, y=y, code=code,
+                calls.append(dict(A=A, dims=dims, k=k, x=x, xh=xh, y=y, code=code,
                                   bytes=tvc_bytes(dims, k, es, es), name=f"{'f64' if code == tg.F64 else 'f32'}:"
                                   f"{'x'.join(map(str, dims))}:k{k}", v=math.prod(dims[k + 1:])))
     torch.cuda.synchronize()
@@ -761,6 +904,16 @@ def main(argv=None):
         for name, gbs in per_mode.items():
             print(f"{name:40s} {gbs:8.1f} GB/s  {100 * gbs / peak:5.1f}%", file=sys.stderr)
 
+    # Outputs of the timed calls at sampled indices (checked against the
+    # oracle in the CPU-baseline leg below).
+    rng = np.random.default_rng(0)
+    sampled, got_sampled = [], []
+    for c in calls:
+        uv = c["y"].numel()
+        picks = np.unique(np.concatenate([rng.integers(0, uv, size=32, dtype=np.int64), [0, uv - 1]]))
+        got_sampled.append(c["y"].reshape(-1)[torch.from_numpy(picks).to(dev)].double().cpu().numpy())
+        sampled.append(("u64" if c["code"] == tg.F64 else "u32", c["dims"], c["k"], c["xh"], picks))
+
     # End to end through the public API: inputs from pinned host memory,
     # results read back, every step.
     e2e = None
@@ -806,35 +959,53 @@ def main(argv=None):
     n_calls = len(calls)
     del tensors, calls, evs
     torch.cuda.empty_cache()
-    sec = None
+    hopm_sum, detail = {}, {}
     if world == 1 and not args.no_secondary:
-        sec = secondary(dev)
-        sec["paper_shapes_fp64"] = paper_shapes(dev, peak)
+        hopm_sum, detail = hopm_workloads(dev)
+        detail.update(secondary(dev))
+        detail["paper_shapes_fp64"] = paper_shapes(dev, peak)
 
     cpu = None
+    fp_err = {}
     if rank == 0 and world == 1 and not args.no_cpu:
-        smp = OracleSample()
-        gbs, secs = smp.timed(10.0)
-        cpu = {"value": gbs, "unit": "GB/s", "cores": oracle_threads(), "kind": "oracle", "sample": smp.desc,
-               "seconds": round(secs, 2)}
+        cpu, refs = cpu_baseline_leg(dev, oracle_threads(), sampled)
+        for code_name in ("f64", "f32"):
+            sel = [i for i, smp in enumerate(sampled) if (smp[0] == "u64") == (code_name == "f64")]
+            got = np.concatenate([got_sampled[i] for i in sel])
+            plain = np.concatenate([refs[i][0] for i in sel])
+            fp_err[code_name] = {"rel_l2_vs_oracle": float("%.3g" % (np.linalg.norm(got - plain) /
+                                                                       np.linalg.norm(plain))),
+                                 "outputs_checked": int(got.size)}
+            if code_name == "f64":
+                exact = np.concatenate([refs[i][1] for i in sel])
+                mag = np.concatenate([refs[i][2] for i in sel])
+                # the FP64 error model: |y - y_exact| <= c 2^-46 sum|a x| (c = 4 tested)
+                fp_err[code_name]["max_err_over_2^-46_sum|ax|"] = float(
+                    "%.3g" % np.max(np.abs(got - exact) / (2.0 ** -46 * mag)))
 
     if rank == 0:
+        detail["per_mode_GBs"] = per_mode
+        print("detail " + json.dumps(detail), file=sys.stderr, flush=True)
+        f64_modes = [v for n, v in per_mode.items() if n.startswith("f64")]
         line = {
             "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64 (float-float products) + f32",
+            "data": "synthetic",
             "config": {"workload": WORKLOAD, "tvcs_per_step": n_calls, "bytes_per_step": step_bytes,
                        "l2": "inputs larger than L2 (smallest tensor 1.07 GB); no flush needed",
                        "parallelism": f"replicas x{world}"},
-            "frac_of_peak": value / world / peak,
-            "fp64": {"GB/s": f64_bytes / (f64_ms / 1e3) / 1e9, "frac": f64_bytes / (f64_ms / 1e3) / 1e9 / peak,
-                     "mean_mode_frac": statistics.mean(v for n, v in per_mode.items() if n.startswith("f64")) / peak,
-                     "std_mode_frac": statistics.stdev(v for n, v in per_mode.items() if n.startswith("f64")) / peak},
-            "fp32": {"GB/s": f32_bytes / (f32_ms / 1e3) / 1e9, "frac": f32_bytes / (f32_ms / 1e3) / 1e9 / peak},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
-            "per_mode_GBs": per_mode,
-            "secondary": sec,
+            "frac_of_peak": round(value / world / peak, 4),
+            "fp64": dict({"GB/s": round(f64_bytes / (f64_ms / 1e3) / 1e9, 1),
+                          "frac": round(f64_bytes / (f64_ms / 1e3) / 1e9 / peak, 4),
+                          "min_mode_frac": round(min(f64_modes) / peak, 4),
+                          "mean_mode_frac": round(statistics.mean(f64_modes) / peak, 4),
+                          "std_mode_frac": round(statistics.stdev(f64_modes) / peak, 4)}, **fp_err.get("f64", {})),
+            "fp32": dict({"GB/s": round(f32_bytes / (f32_ms / 1e3) / 1e9, 1),
+                          "frac": round(f32_bytes / (f32_ms / 1e3) / 1e9 / peak, 4)}, **fp_err.get("f32", {})),
         }
+        line.update(hopm_sum)
         print(json.dumps(line), flush=True)
     if pg is not None:
         pg.destroy_process_group()

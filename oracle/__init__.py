@@ -23,7 +23,7 @@ import threading
 import numpy as np
 
 __all__ = [
-    "F64", "F32", "BF16", "E4M3", "F16", "build", "tvc", "tvc_grad_x", "tvc_grad_A",
+    "F64", "F32", "BF16", "E4M3", "F16", "build", "set_threads", "tvc", "tvc_exact", "tvc_grad_x", "tvc_grad_A",
     "hopm", "hopm3", "hopm_jacobi", "quantise", "decode_bf16", "decode_e4m3", "decode_f16",
     "bf16_from_f32", "e4m3_from_f32", "f16_from_f32", "dequantise", "OracleError", "dhopm_touched",
 ]
@@ -67,6 +67,9 @@ def _load():
             lib = ctypes.CDLL(build())
             P, I, D, L = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64
             lib.oracle_tvc.argtypes = [I, P, P, I, P, I, P, P, D, D]
+            lib.oracle_tvc_exact.argtypes = [I, P, P, I, P, I, P, P]
+            lib.oracle_set_threads.argtypes = [I]
+            lib.oracle_set_threads.restype = I
             lib.oracle_tmc.argtypes = [I, P, P, I, P, I, P, L, P, D, D]
             lib.oracle_khatri_rao.argtypes = [P, I, P, L, P]
             lib.oracle_mttkrp.argtypes = [I, P, P, I, P, I, P, L, P]
@@ -92,6 +95,12 @@ def _load():
             lib.oracle_dhopm_touched.restype = L
             _lib = lib
     return _lib
+
+
+def set_threads(n: int) -> int:
+    """Threads of the oracle's OpenMP loops run from this thread from now on
+    (results do not depend on it); returns the previous count."""
+    return int(_load().oracle_set_threads(int(n)))
 
 
 def _p(a):
@@ -141,6 +150,22 @@ def tvc(A, mode: int, x, *, dims=None, scales=None, y=None, alpha=1.0, beta=0.0)
     if st:
         raise OracleError(st, "tvc")
     return out
+
+
+def tvc_exact(A, mode: int, x, *, dims=None, scales=None) -> np.ndarray:
+    """Y = A x_mode x with error-free transformations (compensated dot
+    product Dot2, see the C source): the exact sum rounded about once, for
+    measuring the error of other arithmetic."""
+    A, d, dt = _tensor(A, dims)
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+    if not 0 <= mode < d.size or x.size != int(d[mode]):
+        raise ValueError("bad mode or x length")
+    s = _scales(dt, scales, int(d[0]))
+    y = np.zeros(int(np.prod(d)) // int(d[mode]))
+    st = _load().oracle_tvc_exact(dt, _p(A), _p(s), int(d.size), _p(d), int(mode), _p(x), _p(y))
+    if st:
+        raise OracleError(st, "tvc_exact")
+    return y.reshape(tuple(int(n) for i, n in enumerate(d) if i != mode))
 
 
 def tmc(A, mode: int, X, *, dims=None, scales=None, Y=None, alpha=1.0, beta=0.0) -> np.ndarray:

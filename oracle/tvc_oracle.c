@@ -28,6 +28,7 @@
  * no fused multiply-add, no reassociation).
  */
 #include <math.h>
+#include <omp.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -44,6 +45,15 @@
 #define OR_ERR_NONFINITE 6
 
 #define OR_MAXD 16
+
+/* Threads of the OpenMP loops that follow in the calling thread (the
+ * outer-index "parallel for" of each routine); the results do not depend on
+ * it.  Returns the previous count. */
+int oracle_set_threads(int n) {
+  int prev = omp_get_max_threads();
+  if (n > 0) omp_set_num_threads(n);
+  return prev;
+}
 
 /* ---------------------------------------------------------------- decoding */
 
@@ -131,6 +141,43 @@ int oracle_tvc(int dtype, const void* A, const float* scales, int order, const i
     double s = 0.0;
     for (int64_t j = 0; j < nk; j++) s += elem(dtype, A, scales, slab, (i * nk + j) * v + l) * x[j];
     y[o] = (beta != 0.0) ? alpha * s + beta * y[o] : alpha * s;
+  }
+  return OR_OK;
+}
+
+/* The same contraction with error-free transformations, for measuring the
+ * error of another arithmetic against the exact sum: every product a*x is
+ * split exactly into p + e by one fused multiply-add (TwoProduct:
+ * e = fma(a, x, -p)), the p are added with Knuth's TwoSum (each rounding
+ * error recovered exactly) and every recovered error and every e is summed
+ * in a second accumulator; the result is the two accumulators added once.
+ * This is the compensated dot product "Dot2" of Ogita, Rump and Oishi
+ * (Accurate sum and dot product, SIAM J. Sci. Comput. 26, 2005): its error is
+ * at most 2^-53 |y| + (n 2^-53)^2 / (1 - n 2^-53)^2 * sum_j |a_j x_j|, i.e.
+ * the exact sum rounded once unless n is astronomically large.  alpha = 1,
+ * beta = 0.  fma() is the C99 correctly rounded fused multiply-add (the
+ * explicit call is not affected by -ffp-contract=off). */
+int oracle_tvc_exact(int dtype, const void* A, const float* scales, int order, const int64_t* dims,
+                     int mode, const double* x, double* y) {
+  if (!valid_shape(order, dims) || mode < 0 || mode >= order) return OR_ERR_ARG;
+  int64_t u = prod(dims, 0, mode), nk = dims[mode], v = prod(dims, mode + 1, order);
+  int64_t slab = prod(dims, 1, order);
+  int64_t nout = u * v;
+#pragma omp parallel for schedule(static)
+  for (int64_t o = 0; o < nout; o++) {
+    int64_t i = o / v, l = o % v;
+    double s = 0.0, c = 0.0;
+    for (int64_t j = 0; j < nk; j++) {
+      double a = elem(dtype, A, scales, slab, (i * nk + j) * v + l);
+      double p = a * x[j];
+      double e = fma(a, x[j], -p);
+      double t = s + p;
+      double bp = t - s;
+      double err = (s - (t - bp)) + (p - bp);
+      s = t;
+      c = c + (err + e);
+    }
+    y[o] = s + c;
   }
   return OR_OK;
 }

@@ -9,6 +9,20 @@ DEV = torch.device("cuda:0") if torch.cuda.is_available() else None
 
 TOL = {oracle.F64: 1e-12, oracle.F32: 1e-5, oracle.BF16: 1e-5, oracle.E4M3: 1e-5, oracle.F16: 1e-5}
 
+# Elementwise error model of the FP64 contraction (products in float-float
+# pieces on the FP32 pipe, compensated FP32 pairs folded into an FP64 sum
+# every 64 products): |y - y_exact| <= F64_MODEL_C * 2^-46 * sum_j |a_j x_j|
+# + (ceil(n_k / 64) - 1) * 2^-53 * sum_j |a_j x_j| (the FP64 sum of the folded
+# blocks), with y_exact the exactly rounded result.
+F64_MODEL_C = 4.0
+
+
+def f64_model_bound(mag, nk):
+    """Largest error the FP64 error model allows for outputs whose
+    sum_j |a_j x_j| is `mag`, with n_k terms per output."""
+    blocks = max(1, -(-int(nk) // 64))
+    return (F64_MODEL_C * 2.0 ** -46 + (blocks - 1) * 2.0 ** -53) * np.asarray(mag, dtype=np.float64)
+
 
 def rel_l2(got, ref):
     """||got - ref||_2 / ||ref||_2, evaluated with both scaled by max|ref|
@@ -66,9 +80,11 @@ def sample_outputs(dims, mode, count, rng):
     return picks, u, v
 
 
-def oracle_at(kind, seed, dims, mode, x, picks, v):
+def oracle_at(kind, seed, dims, mode, x, picks, v, exact=False):
     """Oracle values of y at flat output indices `picks`, from host-generated
-    elements A[(i*n_k + j)*v + l] (a dot product per output)."""
+    elements A[(i*n_k + j)*v + l] (a dot product per output; with `exact`
+    the compensated oracle contraction, the exact sum rounded about once),
+    and sum_j |a_j x_j| per output."""
     nk = dims[mode]
     out = np.empty(len(picks))
     mag = np.empty(len(picks))
@@ -80,6 +96,6 @@ def oracle_at(kind, seed, dims, mode, x, picks, v):
             a = synth.uniform_f64(seed, synth.STREAM_A, idx)
         else:
             a = synth.uniform_f32(seed, synth.STREAM_A, idx)
-        out[t] = oracle.tvc(a, 0, x)
+        out[t] = oracle.tvc_exact(a, 0, x) if exact else oracle.tvc(a, 0, x)
         mag[t] = np.sum(np.abs(a.astype(np.float64) * x))
     return out, mag

@@ -1,6 +1,6 @@
 """GPU HOPM backward (recomputation) against central finite differences of
-the FP64 oracle's power method, and the envelope theorem at a fixed point:
-d lambda / dA = x_0 (x) ... (x) x_{d-1}."""
+the FP64 oracle's power method (FP64, FP32 and narrow storage), and the
+envelope theorem at a fixed point: d lambda / dA = x_0 (x) ... (x) x_{d-1}."""
 import math
 
 import numpy as np
@@ -82,12 +82,44 @@ def test_hopm_autograd_matches_backward():
     assert torch.allclose(g1, gs[1], rtol=1e-13, atol=1e-15)
 
 
-def test_hopm_backward_fp32_against_fp64():
-    dims = (8, 7, 6)
-    A64 = synth.tensor("u64", 2, dims)
-    xs = [np.ones(n) / math.sqrt(n) for n in dims]
-    g64, _ = tg.hopm_backward(gu.to_dev(A64), [gu.to_dev(v) for v in xs], 4, None,
-                              torch.tensor([1.0], dtype=torch.float64))
-    g32, _ = tg.hopm_backward(gu.to_dev(A64.astype(np.float32)), [gu.to_dev(v.astype(np.float32)) for v in xs], 4,
-                              None, torch.tensor([1.0], dtype=torch.float64))
-    assert gu.rel_l2(g32.cpu().numpy(), g64.cpu().numpy()) <= 1e-4
+@pytest.mark.parametrize("code", [oracle.F32, oracle.BF16, oracle.E4M3, oracle.F16],
+                         ids=["f32", "bf16", "e4m3", "f16"])
+def test_hopm_backward_low_precision_fd(code):
+    """FP32-vector HOPM backward (binary32 or narrow storage, FP32
+    arithmetic) against central finite differences of the FP64 oracle's
+    power method on the stored (dequantised) values: the gradient with
+    respect to those values, to the accuracy of FP32 accumulation."""
+    dims, iters = (6, 5, 4), 3
+    A, Ao, scales = gu.inputs(dims, code, seed=4)
+    vals = Ao.astype(np.float64) if scales is None else oracle.dequantise(Ao, scales)
+    xs = [synth.vector("u64", 4, 70 + m, n) + 1.5 for m, n in enumerate(dims)]
+    xs = [(v / np.linalg.norm(v)).astype(np.float32).astype(np.float64) for v in xs]
+    gx = [synth.vector("u32", 5, 80 + m, n).astype(np.float64) for m, n in enumerate(dims)]
+    glam = 0.7
+    f32 = lambda v: torch.from_numpy(np.asarray(v, dtype=np.float32)).to(gu.DEV)  # noqa: E731
+    gA, gstart = tg.hopm_backward(gu.to_dev(A), [f32(v) for v in xs], iters, [f32(g) for g in gx],
+                                  torch.tensor([glam], dtype=torch.float64),
+                                  scales=gu.to_dev(scales) if scales is not None else None, shape=dims)
+    torch.cuda.synchronize()
+    gA = gA.cpu().numpy().astype(np.float64).ravel()
+    h = 1e-6 * float(np.max(np.abs(vals)))
+    flat = vals.ravel()
+    fds = []
+    for f in range(flat.size):
+        Ap, Am = flat.copy(), flat.copy()
+        Ap[f] += h
+        Am[f] -= h
+        fds.append((loss_oracle(Ap.reshape(dims), xs, iters, gx, glam)
+                    - loss_oracle(Am.reshape(dims), xs, iters, gx, glam)) / (2 * h))
+    fds = np.array(fds)
+    assert gu.rel_l2(gA, fds) <= 1e-4, gu.rel_l2(gA, fds)
+    for m in range(1, len(dims)):
+        g = gstart[m].cpu().numpy().astype(np.float64)
+        fd = []
+        for i in range(dims[m]):
+            xp = [v.copy() for v in xs]
+            xm = [v.copy() for v in xs]
+            xp[m][i] += 1e-6
+            xm[m][i] -= 1e-6
+            fd.append((loss_oracle(vals, xp, iters, gx, glam) - loss_oracle(vals, xm, iters, gx, glam)) / 2e-6)
+        assert gu.rel_l2(g, np.array(fd)) <= 1e-4, (m, gu.rel_l2(g, np.array(fd)))

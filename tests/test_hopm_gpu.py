@@ -4,7 +4,9 @@ quantiser, against the FP64 oracle.
 Tolerances: FP64 lambda history 1e-12 relative, x_j within 1e-10; FP32
 storage 1e-5; narrow storage: kernel against the oracle on the same codes
 1e-5 (FP32 accumulation), lambda against the FP64 oracle on the unquantised
-values within 1e-3 for BF16.  Quantiser codes bit-exact.
+values within 1e-3 for BF16 and binary16 (E4M3: see
+LAMBDA_STORAGE_BOUND_256; the full-size workload holds every format to
+1e-3).  Quantiser codes bit-exact.
 """
 import math
 
@@ -30,6 +32,17 @@ def ones_start(dims, code):
 
 def ones_np(dims):
     return [np.ones(n) / math.sqrt(n) for n in dims]
+
+
+def as_stored(xs, code):
+    """Vectors as the GPU holds them: FP64, or rounded to binary32."""
+    if code == oracle.F64:
+        return [np.asarray(v, dtype=np.float64).copy() for v in xs]
+    return [np.asarray(v, dtype=np.float64).astype(np.float32).astype(np.float64) for v in xs]
+
+
+def to_dev_vectors(xs, code):
+    return [torch.from_numpy(np.asarray(v, dtype=np.float64)).to(dtype=VEC[code], device=gu.DEV) for v in xs]
 
 
 def run_gpu(A, dims, code, iters, tol=0.0, scales=None, xs=None):
@@ -174,25 +187,43 @@ def test_quantise_nonfinite_status_and_zero_slab():
     assert np.array_equal(codes.cpu().numpy().view(np.uint16), ref.view(np.uint16))
 
 
+# Storage error of lambda at this reduced size, against the FP64 oracle on
+# the binary32 source.  BF16 and binary16 meet the 1e-3 target of the
+# full-size 2048^3 workload here already (1.6e-4, 1.6e-5).  E4M3 rounds each
+# element with a relative RMS error of 2.6%; its first-order effect on lambda,
+# E(x_0, x_1, x_2) for the rounding error tensor E, shrinks like 1/sqrt(n)
+# with the side n: 1.5e-3 at 256^3 and 3.7e-4 at 2048^3, where
+# test_fullsize_hopm_gpu.py asserts the 1e-3 target.  Here E4M3 is held to
+# 2e-3.
+LAMBDA_STORAGE_BOUND_256 = {oracle.BF16: 1e-3, oracle.E4M3: 2e-3, oracle.F16: 1e-3}
+
+
 @pytest.mark.parametrize("code", [oracle.BF16, oracle.E4M3, oracle.F16], ids=["bf16", "e4m3", "f16"])
 def test_low_precision_hopm_lambda_vs_fp64(code):
     """Mixed-precision recipe at reduced size (256^3): N(0,1)exp(U[-3,3])
-    entries, stored narrow with per-slab scales, 30 sweeps; lambda against
-    the FP64 oracle on the unquantised values."""
+    entries, stored narrow with per-slab scales, 30 sweeps.  The GPU's codes
+    equal the oracle quantiser's; lambda against the oracle on those codes
+    (kernel error, 1e-5) and on the binary32 source (storage error)."""
     dims = (256, 256, 256)
     src = synth.tensor("lognormal", 0, dims).astype(np.float32)
+    codes_o, scales_o = oracle.quantise(src, code)
     codes, scales, status = tg.quantise(gu.to_dev(src), code)
+    assert int(status.item()) == 0
+    got_codes = codes.cpu().numpy()
+    if code == oracle.F16:
+        got_codes, codes_cmp = got_codes.view(np.uint16), codes_o.view(np.uint16)
+    else:
+        codes_cmp = codes_o
+    assert np.array_equal(got_codes.reshape(codes_cmp.shape), codes_cmp)
+    assert np.array_equal(scales.cpu().numpy(), scales_o)
     r = tg.hopm(codes, ones_start(dims, code), 30, scales=scales, shape=dims)
     torch.cuda.synchronize()
     ref = oracle.hopm(src, ones_np(dims), 30)
     err = abs(r.lam.item() - ref["lam"]) / ref["lam"]
     print(f"{ {oracle.BF16: 'bf16', oracle.E4M3: 'e4m3', oracle.F16: 'f16'}[code]} lambda rel err vs FP64 oracle: {err:.3e}")
-    if code in (oracle.BF16, oracle.F16):
-        assert err <= 1e-3
-    else:
-        assert err <= 2e-2
-    # kernel error: the oracle on the same stored codes
-    ref_q = oracle.hopm(codes.cpu().numpy(), ones_np(dims), 30, scales=scales.cpu().numpy())
+    assert err <= LAMBDA_STORAGE_BOUND_256[code]
+    # kernel error: the oracle on the same stored codes (its own quantiser's)
+    ref_q = oracle.hopm(codes_o, ones_np(dims), 30, scales=scales_o)
     assert abs(r.lam.item() - ref_q["lam"]) <= 1e-5 * ref_q["lam"]
 
 
@@ -214,21 +245,24 @@ def test_hopm_single_double(dims):
 @pytest.mark.parametrize("code", [oracle.F64, oracle.F32, oracle.BF16, oracle.E4M3, oracle.F16],
                          ids=["f64", "f32", "bf16", "e4m3", "f16"])
 def test_hopm_jacobi_matches_oracle(dims, code):
-    """Sweep by sweep: from the GPU's own vectors after sweep t-1, one GPU
-    sweep against one oracle sweep (a Jacobi iteration need not contract,
-    so differences of rounding may grow over many sweeps; the map itself
-    is what must agree)."""
+    """Sweep by sweep: the oracle iterates from all-ones on its own vectors;
+    before each sweep both sides start from the oracle's current vectors (as
+    the GPU stores them: binary32 for the FP32-vector types), and one GPU
+    sweep is compared with one oracle sweep.  (A Jacobi iteration need not
+    contract, so differences of rounding may grow over many sweeps; the map
+    itself is what must agree.)"""
     A, Ao, scales = gu.inputs(dims, code)
     st = gu.to_dev(scales) if scales is not None else None
-    xs = ones_start(dims, code)
+    xs_o = ones_np(dims)
     for t in range(5):
-        ref = oracle.hopm_jacobi(Ao, [v.cpu().numpy().astype(np.float64) for v in xs], 1, scales=scales)
+        start = as_stored(xs_o, code)
+        ref = oracle.hopm_jacobi(Ao, start, 1, scales=scales)
         assert ref["status"] == 0
-        r = tg.hopm_jacobi(gu.to_dev(A), xs, 1, scales=st, shape=dims)
+        r = tg.hopm_jacobi(gu.to_dev(A), to_dev_vectors(start, code), 1, scales=st, shape=dims)
         torch.cuda.synchronize()
         assert int(r.status.item()) == 0
         check_against(r, ref, code)
-        xs = r.x
+        xs_o = ref["x"]
 
 
 def test_hopm_jacobi_single_double_and_stopping_rule():
@@ -257,14 +291,15 @@ SINGLE_PASS_SHAPES = [(6, 5, 256), (7, 3, 512), (3, 1024), (2, 3, 2048), (1, 409
 def test_hopm_jacobi_single_pass_kernel(dims, code):
     A, Ao, scales = gu.inputs(dims, code)
     st = gu.to_dev(scales) if scales is not None else None
-    xs = ones_start(dims, code)
+    xs_o = ones_np(dims)
     for t in range(3):
-        ref = oracle.hopm_jacobi(Ao, [v.cpu().numpy().astype(np.float64) for v in xs], 1, scales=scales)
-        r = tg.hopm_jacobi(gu.to_dev(A), xs, 1, scales=st, shape=dims)
+        start = as_stored(xs_o, code)
+        ref = oracle.hopm_jacobi(Ao, start, 1, scales=scales)
+        r = tg.hopm_jacobi(gu.to_dev(A), to_dev_vectors(start, code), 1, scales=st, shape=dims)
         torch.cuda.synchronize()
         assert int(r.status.item()) == 0
         check_against(r, ref, code)
-        xs = r.x
+        xs_o = ref["x"]
 
 
 def test_read_status_after_a_zero_tensor():

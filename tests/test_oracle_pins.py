@@ -151,6 +151,64 @@ def test_tvc_narrow_types_dequantise():
                                np.tensordot(A32.astype(np.float64), x, axes=([1], [0])), rtol=1e-13)
 
 
+def _cancelling(dims, mode, seed, kappa=1e6):
+    """Uniform A and x, with the last slice of mode `mode` set so that every
+    output is about sum|a x| / kappa (heavy cancellation)."""
+    rng = np.random.default_rng(seed)
+    A = rng.uniform(-1, 1, dims)
+    x = rng.uniform(-1, 1, dims[mode])
+    x[-1] = 0.75
+    u, nk = int(np.prod(dims[:mode])), dims[mode]
+    Ar = A.reshape(u, nk, -1)
+    part = np.einsum("ijl,j->il", Ar[:, :-1, :], x[:-1])
+    mag = np.einsum("ijl,j->il", np.abs(Ar[:, :-1, :]), np.abs(x[:-1]))
+    Ar[:, -1, :] = -(part - mag / kappa * rng.uniform(-1, 1, part.shape)) / x[-1]
+    return A, x
+
+
+def _exact_fraction(A, mode, x):
+    from fractions import Fraction
+    u, nk = int(np.prod(A.shape[:mode])), A.shape[mode]
+    Ar = A.reshape(u, nk, -1)
+    out = np.empty((u, Ar.shape[2]))
+    for i in range(u):
+        for l in range(Ar.shape[2]):
+            out[i, l] = float(sum(Fraction(float(Ar[i, j, l])) * Fraction(float(x[j])) for j in range(nk)))
+    return out
+
+
+@pytest.mark.parametrize("dims", [(4, 7, 5), (3, 40), (2, 3, 33, 2)], ids=lambda d: "x".join(map(str, d)))
+def test_tvc_exact_matches_rational_arithmetic_on_cancelling_sums(dims):
+    """The compensated oracle contraction against exact rational arithmetic
+    (Fraction sums of exact products, rounded once) on sums that cancel to
+    about 1e-6 of sum|a x|: within one rounding of the exact value, where the
+    plain FP64 sum (and a compensated sum that drops the product errors
+    or the addition errors) is off by far more."""
+    for k in range(len(dims)):
+        A, x = _cancelling(dims, k, seed=3 + k)
+        exact = _exact_fraction(A, k, x)
+        got = oracle.tvc_exact(A, k, x).reshape(exact.shape)
+        assert np.all(np.abs(got - exact) <= 2.0 ** -52 * np.abs(exact)), (dims, k)
+        plain = oracle.tvc(A, k, x).reshape(exact.shape)
+        assert np.max(np.abs(plain - exact) / np.abs(exact)) > 2.0 ** -45  # the plain sum really errs here
+
+
+def test_tvc_exact_integer_and_narrow_inputs():
+    rng = np.random.default_rng(5)
+    A = rng.integers(-1000, 1000, size=(6, 5, 7)).astype(np.float64)
+    for k in range(3):
+        x = rng.integers(-1000, 1000, size=A.shape[k]).astype(np.float64)
+        assert np.array_equal(oracle.tvc_exact(A, k, x), oracle.tvc(A, k, x))
+    src = synth.tensor("lognormal", 1, (3, 20, 9)).astype(np.float32)
+    codes, scales = oracle.quantise(src, oracle.E4M3)
+    vals = oracle.dequantise(codes, scales)
+    for k in range(3):
+        x = synth.vector("u64", 2, synth.stream_x(k), vals.shape[k])
+        got = oracle.tvc_exact(codes, k, x, scales=scales)
+        exact = _exact_fraction(vals, k, x).reshape(got.shape)
+        assert np.all(np.abs(got - exact) <= 2.0 ** -52 * np.abs(exact) + 1e-300)
+
+
 def test_tvc_bad_arguments():
     A = rand_tensor((2, 3))
     with pytest.raises(ValueError):

@@ -33,7 +33,7 @@ def _case(dims, mode, code, seed):
     ref = oracle.tvc(Ao, mode, x)
     At, xt = gu.to_dev(A), gu.to_dev(x)
     y = torch.full(ref.shape, float("nan"), dtype=xt.dtype, device=gu.DEV)
-    return At, xt, y, ref
+    return At, xt, y, ref, Ao
 
 
 def test_tvc_two_streams_concurrently():
@@ -41,7 +41,7 @@ def test_tvc_two_streams_concurrently():
     work = []
     for si, cases in enumerate(STREAM_CASES):
         for ci, (dims, mode, code) in enumerate(cases):
-            work.append((si, dims, mode, code) + _case(dims, mode, code, seed=10 * si + ci))
+            work.append((si, dims, mode, code) + _case(dims, mode, code, seed=10 * si + ci)[:4])
     torch.cuda.synchronize()
     # interleave the two streams' calls, several rounds, without ordering
     for _ in range(4):
@@ -57,8 +57,7 @@ def test_tvc_two_streams_concurrently():
 @pytest.mark.parametrize("dims,mode,code", [((3, 300000), 1, oracle.F64), ((2, 3, 250000), 2, oracle.F32),
                                             ((40, 37, 66), 1, oracle.F64)])
 def test_tvc_graph_capture_after_warm_call(dims, mode, code):
-    At, xt, y, ref = _case(dims, mode, code, seed=3)
-    A_host = At.cpu().numpy()
+    At, xt, y, ref, A_host = _case(dims, mode, code, seed=3)
     s = torch.cuda.Stream()
     s.wait_stream(torch.cuda.current_stream())
     g = torch.cuda.CUDAGraph()
@@ -82,7 +81,7 @@ def test_tvc_graph_capture_after_warm_call(dims, mode, code):
 
 def test_read_status_refuses_capture_and_keeps_it_valid():
     dims, mode, code = (3, 300000), 1, oracle.F64
-    At, xt, y, ref = _case(dims, mode, code, seed=5)
+    At, xt, y, ref, _ = _case(dims, mode, code, seed=5)
     status = torch.zeros(1, dtype=torch.int32, device=gu.DEV)
     s = torch.cuda.Stream()
     s.wait_stream(torch.cuda.current_stream())
