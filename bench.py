@@ -395,9 +395,10 @@ class LoopedCublas:
         self.lib.cublasDestroy_v2(self.h)
 
 
-def paper_shapes(dev, peak):
+def paper_shapes(dev, peak, index=0):
     """Per-mode GB/s of the native TVC and of the looped cuBLAS TVC on
-    Table 1's FP64 tensors; mean and sample std over all modes."""
+    Table 1's FP64 tensors; mean and sample std over all modes; SM clocks
+    sampled during the whole measurement."""
     import torch
     import synth
     import synth.device as sd
@@ -408,6 +409,8 @@ def paper_shapes(dev, peak):
         looped = None
         why = str(e)
     native, loop, worst = {}, {}, 0.0
+    sampler = ClockSampler(index)
+    sampler.start()
     for dims in PAPER_SHAPES:
         N = math.prod(dims)
         A = torch.empty(N, dtype=torch.float64, device=dev)
@@ -435,7 +438,9 @@ def paper_shapes(dev, peak):
                 "mean_frac": statistics.mean(vals) / peak, "std_frac": statistics.stdev(vals) / peak,
                 "min_frac": min(vals) / peak, "max_frac": max(vals) / peak}
 
+    clocks = sampler.stop()
     out = {"shapes": "Table 1 FP64 tensors 30623^2, 979^3, 175^4, 63^5, 31^6, 19^7, 13^8, 10^9, 8^10; every mode",
+           "clocks": clocks,
            "native": summary(native), "native_per_mode_GBs": {n: round(v, 1) for n, v in native.items()}}
     if looped is not None:
         out["looped_cublas"] = summary(loop)
@@ -963,7 +968,7 @@ def main(argv=None):
     if world == 1 and not args.no_secondary:
         hopm_sum, detail = hopm_workloads(dev)
         detail.update(secondary(dev))
-        detail["paper_shapes_fp64"] = paper_shapes(dev, peak)
+        detail["paper_shapes_fp64"] = paper_shapes(dev, peak, local)
 
     cpu = None
     fp_err = {}

@@ -1485,6 +1485,32 @@ static Plan make_plan_unstaged(const Shape& s, tvc_dtype dt, const void* A) {
 }
 static Plan make_plan(const Shape& s, tvc_dtype dt, const void* A) { return make_plan_impl(s, dt, A, true); }
 
+// Persistent double-buffered tiles of whole slabs, one thread per output
+// (the small-slab kernel): R slabs of S = n_k * v elements per tile.
+static void plan_tile_async(Plan& p, const Shape& s, size_t es, bool f64acc, int sms) {
+  const int64_t S = s.nk * s.v;
+  p.kind = K_TILE_ASYNC;
+  int64_t R = std::min<int64_t>(kThreads / s.v, (int64_t)(48 * 1024) / (int64_t)(S * es));
+  R = std::max<int64_t>(1, std::min<int64_t>(R, s.u));
+  p.R = (int)R;
+  p.ntiles = ceil_div(s.u, R);
+  p.vec16 = (int)(align_up((size_t)R * S * es, 16) + 32);  // tile capacity in bytes
+  const size_t x_bytes = align_up((size_t)s.nk * (f64acc ? sizeof(XSplit) : 4), 16);
+  p.smem = x_bytes + 2 * (size_t)p.vec16;
+  const int bps = (int)std::max<size_t>(1, std::min<size_t>(8, (size_t)(220 * 1024) / p.smem));
+  p.splits = 1;
+  p.chunk = s.nk;
+  p.grid = dim3((unsigned)std::max<int64_t>(1, std::min<int64_t>(p.ntiles, (int64_t)sms * bps)), 1);
+}
+
+// FP64-arithmetic rows (v = 1) that go to the small-slab kernel, one thread
+// per row from shared-memory tiles: 9 .. 27 elements, except 16, 20 and 24,
+// where the grouped-row kernel's 16-byte passes come out even.  Measured on
+// 1 GB tensors (n_k = 2 .. 31): 1.1-2.8x faster in that range (10 elements:
+// 35% -> 65% of the copy peak, 12: 28% -> 66%, 19: 52% -> 64%), slower at
+// 16, 20, 24 (81% -> 33%, 80% -> 65%, 76% -> 49%) and for rows of <= 8.
+static bool f64_rows_by_tiles(int64_t nk) { return nk >= 9 && nk <= 27 && !(nk % 4 == 0 && nk >= 16); }
+
 static Plan make_plan_impl(const Shape& s, tvc_dtype dt, const void* A, bool allow_staged) {
   Plan p;
   const bool f64acc = (dt == TVC_F64 || dt == TVC_F32D);  // FP64 arithmetic (float-float kernels)
@@ -1565,6 +1591,8 @@ static Plan make_plan_impl(const Shape& s, tvc_dtype dt, const void* A, bool all
     p.chunk = ceil_div(ceil_div(s.nk, splits), step) * step;
     p.splits = ceil_div(s.nk, p.chunk);
     p.grid = dim3((unsigned)ceil_div(warps, kWarpsPerBlock), (unsigned)p.splits);
+  } else if (s.v == 1 && f64acc && aligned(A, 16) && f64_rows_by_tiles(s.nk)) {
+    plan_tile_async(p, s, es, f64acc, sms);
   } else if (s.v == 1) {
     p.kind = K_ROWS;
     p.vec = pick_vec(dt, s.nk, A);
@@ -1620,18 +1648,7 @@ static Plan make_plan_impl(const Shape& s, tvc_dtype dt, const void* A, bool all
     p.grid = dim3((unsigned)ceil_div(s.u, kWarpsPerBlock), (unsigned)p.splits);
   } else if (aligned(A, 16)) {
     // Small slabs, persistent double-buffered tiles (see the kernel).
-    p.kind = K_TILE_ASYNC;
-    int64_t R = std::min<int64_t>(kThreads / s.v, (int64_t)(48 * 1024) / (int64_t)(S * es));
-    R = std::max<int64_t>(1, std::min<int64_t>(R, s.u));
-    p.R = (int)R;
-    p.ntiles = ceil_div(s.u, R);
-    p.vec16 = (int)(align_up((size_t)R * S * es, 16) + 32);  // tile capacity in bytes
-    const size_t x_bytes = align_up((size_t)s.nk * (f64acc ? sizeof(XSplit) : 4), 16);
-    p.smem = x_bytes + 2 * (size_t)p.vec16;
-    const int bps = (int)std::max<size_t>(1, std::min<size_t>(8, (size_t)(220 * 1024) / p.smem));
-    p.splits = 1;
-    p.chunk = s.nk;
-    p.grid = dim3((unsigned)std::max<int64_t>(1, std::min<int64_t>(p.ntiles, (int64_t)sms * bps)), 1);
+    plan_tile_async(p, s, es, f64acc, sms);
   } else {
     p.kind = K_TILE;
     int64_t R = std::min<int64_t>(kThreads / s.v, (int64_t)(48 * 1024) / (int64_t)(S * es));

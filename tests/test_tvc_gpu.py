@@ -31,6 +31,10 @@ SHAPES = [
     # types, 4, 2 or 1 columns per thread): v = 16, 12, 7, 31 and 2, ragged
     # n_k, split n_k
     (3, 600, 16), (2, 300, 12), (5, 3000, 7), (3, 700, 31), (6, 4099, 2),
+    # FP64 rows of 9 .. 27 elements through shared-memory tiles of 256 rows
+    # (ragged last tiles, a single partial tile), and the neighbouring
+    # lengths that stay with the grouped-row kernel
+    (1001, 10), (777, 19), (513, 22), (257, 27), (300, 12), (100, 9), (600, 16), (600, 8),
 ]
 CODES = [oracle.F64, oracle.F32, oracle.BF16, oracle.E4M3, oracle.F16]
 
@@ -77,7 +81,7 @@ def test_integer_inputs_bit_exact_f64(dims):
 
 # shapes reaching the column, slab (1 < v < 32, large slabs), small-slab
 # (tile), odd short-row (8-byte loads) and even short-row kernels
-WINDOW_SHAPES = [(40, 37, 66), (500, 19, 19), (40, 600, 12), (3000, 13), (2001, 175), (300, 40)]
+WINDOW_SHAPES = [(40, 37, 66), (500, 19, 19), (40, 600, 12), (3000, 13), (2001, 175), (300, 40), (1001, 10), (777, 22)]
 
 
 @pytest.mark.parametrize("dims", WINDOW_SHAPES, ids=lambda d: "x".join(map(str, d)))
