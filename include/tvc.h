@@ -138,6 +138,12 @@ size_t tvc_workspace_size(int order, const int64_t* dims, int mode, tvc_dtype dt
  * once per pass of up to 16 rows of X (8 for FP64 vectors; R <= 4 and R <= 8
  * use one pass of 4 or 8).  FP32 accumulation for FP32 and the narrow
  * types, FP64 multiply-adds for FP64 and single-double storage.
+ * BF16 storage along the last mode (mode = order - 1 >= 1) with
+ * 8 <= R <= 64, n_mode a multiple of 8, A 16-byte aligned and at least
+ * 128 * (number of SMs) rows runs on the tensor cores: X is split into three
+ * BF16 pieces (exact to binary32 precision), every product of two BF16
+ * values is exact, and the MMAs accumulate in FP32; its workspace holds the
+ * pieces (tmc_workspace_size includes them).
  * slab_scales: as for tvc_ex.  workspace: tmc_workspace_size(...) bytes (0
  * when the output columns fill the GPU without splitting n_mode).
  * Errors: TVC_ERR_INVALID_ARG for a bad shape, mode, dtype, R < 1, a NULL
@@ -460,8 +466,11 @@ size_t dhopm_workspace_size(int parts, const int64_t* starts, int order, const i
 /* Sticky device error of the staged (TMA-fed) kernels: every wait in them
  * is bounded, and a wait that gives up records a nonzero code (1: the copy
  * engine's producer waited for a free buffer, 2: a consumer waited for a
- * tile, 3: draining copies at exit) and lets the kernel finish; its
- * results are then invalid.  Synchronises the device; returns
+ * tile, 3: draining copies at exit; 11-14 the same for the tensor-core
+ * tensor-matrix contraction: 11 producer, 12 MMA issuer, 13 drain, 14 the
+ * epilogue's wait for the last MMAs) and lets the kernel finish (a kernel
+ * of the tensor-core path also releases its tensor memory); its results
+ * are then invalid.  Synchronises the device; returns
  * TVC_ERR_TIMEOUT when a code is set (and clears it when clear != 0). */
 tvc_status tvc_device_error(int* code_out, int clear);
 

@@ -67,6 +67,17 @@ tvc_status combine_parts(const void* const* parts, int nparts, const int64_t* of
                          tvc_dtype vdt, int gather, double alpha, double beta, cudaStream_t st,
                          const int* done);
 
+// Tensor-matrix contraction on the tensor cores (tmc_tc.cu): BF16 storage
+// along the last mode, 8 <= R <= 64, n_k a multiple of 8, A 16-byte aligned,
+// enough rows for the GPU (a16 stands for the alignment of A when A is NULL,
+// for the workspace query).  Workspace: the three BF16 pieces of X.
+bool tmc_tc_supported(const Shape& s, int64_t R, tvc_dtype dt, const void* A, bool a16);
+size_t tmc_tc_ws_bytes(const Shape& s, int64_t R);
+tvc_status tmc_tc_launch(const void* A, const Shape& s, const float* X, int64_t R, float* Y, const float* scales,
+                         double alpha, double beta, void* ws, size_t ws_bytes, cudaStream_t st);
+// Sticky error word of that kernel's bounded waits (cleared when clear != 0).
+tvc_status tmc_tc_device_error(int* code_out, int clear);
+
 // One pass over an R x C row-major matrix M (FP32, BF16, F16 or E4M3
 // storage) for T = M x (scaled per slab: T[r] *= scales[r / upi0] when
 // scales is given) and z = M^T w (dual.cu).  dual_supported says whether

@@ -675,6 +675,7 @@ struct TmcPlan {
   bool loop_rows = false;   // X staged once, the block loops over row groups
   int64_t chunk = 0, blocks_x = 0;
   bool vj = false;
+  bool tc = false;          // the tensor-core kernel (tmc_tc.cu)
   size_t ws = 0;
 };
 
@@ -689,6 +690,13 @@ int tmc_rp(tvc_dtype dt, int64_t R) {
 // query reports the larger workspace of the aligned and unaligned plans.
 TmcPlan tmc_plan(const Shape& s, int64_t R, tvc_dtype dt, const void* A, bool a16 = false) {
   TmcPlan p;
+  if (tmc_tc_supported(s, R, dt, A, a16)) {
+    // BF16 codes along the last mode with R >= 8: a matrix product on the
+    // tensor cores (the CUDA-core kernels are issue-bound there)
+    p.tc = true;
+    p.ws = tmc_tc_ws_bytes(s, R);
+    return p;
+  }
   p.rp = tmc_rp(dt, R);
   p.passes = (int)((R + p.rp - 1) / p.rp);
   const int avec = 16 / p.rp;
@@ -764,8 +772,13 @@ void launch_rp(const TmcArgs<DT>& a, const TmcPlan& p, cudaStream_t st) {
 
 template <tvc_dtype DT>
 tvc_status run(const void* A, const Shape& s, const void* X, int64_t R, void* Y, const float* scales, double alpha,
-               double beta, void* ws, const TmcPlan& p, cudaStream_t st) {
+               double beta, void* ws, size_t ws_size, const TmcPlan& p, cudaStream_t st) {
   using W = TmcW<DT>;
+  if constexpr (DT == TVC_BF16) {
+    if (p.tc)
+      return tmc_tc_launch(A, s, static_cast<const float*>(X), R, static_cast<float*>(Y), scales, alpha, beta, ws,
+                           ws_size, st);
+  }
   TmcArgs<DT> a;
   a.A = static_cast<const typename Elem<DT>::T*>(A);
   a.X = static_cast<const W*>(X);
@@ -831,12 +844,12 @@ extern "C" tvc_status tmc(const void* A, int order, const int64_t* dims, int mod
   if (p.ws > 0 && (!workspace || ws_bytes < p.ws)) return TVC_ERR_WORKSPACE;
   cudaStream_t st = (cudaStream_t)stream;
   switch (dtype) {
-    case TVC_F64: return run<TVC_F64>(A, s, X, R, Y, slab_scales, alpha, beta, workspace, p, st);
-    case TVC_F32: return run<TVC_F32>(A, s, X, R, Y, slab_scales, alpha, beta, workspace, p, st);
-    case TVC_BF16: return run<TVC_BF16>(A, s, X, R, Y, slab_scales, alpha, beta, workspace, p, st);
-    case TVC_E4M3: return run<TVC_E4M3>(A, s, X, R, Y, slab_scales, alpha, beta, workspace, p, st);
-    case TVC_F16: return run<TVC_F16>(A, s, X, R, Y, slab_scales, alpha, beta, workspace, p, st);
-    case TVC_F32D: return run<TVC_F32D>(A, s, X, R, Y, slab_scales, alpha, beta, workspace, p, st);
+    case TVC_F64: return run<TVC_F64>(A, s, X, R, Y, slab_scales, alpha, beta, workspace, ws_bytes, p, st);
+    case TVC_F32: return run<TVC_F32>(A, s, X, R, Y, slab_scales, alpha, beta, workspace, ws_bytes, p, st);
+    case TVC_BF16: return run<TVC_BF16>(A, s, X, R, Y, slab_scales, alpha, beta, workspace, ws_bytes, p, st);
+    case TVC_E4M3: return run<TVC_E4M3>(A, s, X, R, Y, slab_scales, alpha, beta, workspace, ws_bytes, p, st);
+    case TVC_F16: return run<TVC_F16>(A, s, X, R, Y, slab_scales, alpha, beta, workspace, ws_bytes, p, st);
+    case TVC_F32D: return run<TVC_F32D>(A, s, X, R, Y, slab_scales, alpha, beta, workspace, ws_bytes, p, st);
   }
   return TVC_ERR_INVALID_ARG;
 }

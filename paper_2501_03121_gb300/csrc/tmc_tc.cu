@@ -1,0 +1,398 @@
+// Tensor-matrix contraction (TMC, Section 1) on the tensor cores, for BF16
+// storage along the last mode, where the contraction is a matrix product
+// with the contracted index contiguous in memory:
+//     Y[i][r] = alpha * scale[slab(i)] * sum_j A[i][j] X[r][j] + beta * Y[i][r],
+// A the u x n_k row-major BF16 codes, X the R x n_k FP32 matrix.
+//
+// X is split on the device into three BF16 pieces, X = X0 + X1 + X2 to
+// binary32 precision (each piece the BF16 rounding of what the previous ones
+// left).  A product of two BF16 values is exact in FP32, so the tensor cores
+// form A[i][j] X_p[r][j] exactly and accumulate in FP32 in tensor memory:
+// the result carries FP32 accumulation error only, like the CUDA-core path.
+//
+// Dataflow (one CTA per 128 rows of A):
+//   - a producer thread brings, per block of 64 codes along n_k, the 128 x 64
+//     tile of A and the three R_p x 64 tiles of X pieces into one stage of a
+//     shared-memory ring with TMA (2-D tensor maps, 128-byte swizzle; rows
+//     past u and codes past n_k are filled with zeros);
+//   - one thread issues the MMAs (tcgen05.mma kind::f16, M = 128, K = 16 per
+//     instruction; the three piece tiles are read as one tile of N = 3 R_p
+//     rows, R_p = R rounded up to 16, so each K step is one MMA and each
+//     piece accumulates in its own group of R_p columns) into FP32
+//     accumulators in tensor memory, and returns the stage to the producer
+//     with tcgen05.commit on its "empty" barrier;
+//   - after the last block the four warps read the 128 x 3 R_p accumulators
+//     back with tcgen05.ld (warp w owns rows 32w .. 32w + 31), add the three
+//     groups (smallest first) and write Y.
+// Every barrier wait is bounded in time; a wait that gives up records a code
+// in a device word (read by tvc_device_error) and the CTA still releases its
+// tensor memory.
+#include <cuda.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "common.cuh"
+#include "internal.h"
+#include "tma.cuh"
+
+namespace tvcg {
+
+namespace {
+
+__device__ int g_tmc_tc_error = 0;
+
+constexpr int kTcThreads = 128;
+constexpr int kTcRows = 128;      // M: rows of A per CTA (one TMEM lane each)
+constexpr int kTcK = 64;          // codes per stage along n_k: one 128-byte swizzle row
+constexpr int kTileA = kTcRows * kTcK * 2;  // 16 KB
+
+// ------------------------------------------------------------ PTX helpers
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int c0, int c1, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Whole-warp allocation of `ncols` tensor-memory columns (a power of two >= 32);
+// the base address is written to *dst.
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// D (tensor memory) [+]= A (shared, descriptor) * B (shared, descriptor)^T.
+__device__ __forceinline__ void tc_mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// Arrives on `bar` once every MMA this thread issued before has completed.
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+// 16 consecutive FP32 columns of this warp's 32 tensor-memory lanes (one
+// lane per thread), waited for before returning.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int q = 0; q < 16; q++) v[q] = __uint_as_float(r[q]);
+}
+
+// Shared-memory matrix descriptor of a K-major tile whose rows are 128 bytes
+// (64 BF16) laid out by TMA with the 128-byte swizzle: start address, leading
+// byte offset (unused for swizzled K-major tiles, 16), stride byte offset
+// 1024 (8 rows of 128 bytes), descriptor version 1, swizzle mode 128 bytes.
+__device__ __forceinline__ uint64_t sw128_kmajor_desc(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)(16u >> 4) << 16;
+  d |= (uint64_t)(1024u >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N = n columns, M = 128 rows.
+__host__ __device__ constexpr uint32_t bf16_idesc(uint32_t n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((n >> 3) << 17) | ((uint32_t)(kTcRows >> 4) << 24);
+}
+
+// ----------------------------------------------------------------- kernels
+
+// X (R x nk FP32) -> three BF16 pieces, pieces[p][r][j] for r < Rp, j < nkp,
+// zero outside R x nk: X0 = bf16(x), X1 = bf16(x - X0), X2 = bf16(x - X0 - X1)
+// (the differences are exact in FP32).
+__global__ void tmc_tc_split_x_kernel(const float* __restrict__ X, uint16_t* __restrict__ pieces, int64_t R,
+                                      int64_t nk, int64_t Rp, int64_t nkp) {
+  const int64_t n = Rp * nkp;
+  for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = o / nkp, j = o - r * nkp;
+    const float x = (r < R && j < nk) ? X[r * nk + j] : 0.0f;
+    const __nv_bfloat16 h0 = __float2bfloat16_rn(x);
+    const float rem1 = __fsub_rn(x, __bfloat162float(h0));
+    const __nv_bfloat16 h1 = __float2bfloat16_rn(rem1);
+    const float rem2 = __fsub_rn(rem1, __bfloat162float(h1));
+    const __nv_bfloat16 h2 = __float2bfloat16_rn(rem2);
+    pieces[o] = __bfloat16_as_ushort(h0);
+    pieces[n + o] = __bfloat16_as_ushort(h1);
+    pieces[2 * n + o] = __bfloat16_as_ushort(h2);
+  }
+}
+
+struct TcArgs {
+  float* Y;
+  const float* scales;  // per slab, nullable
+  int64_t u, R, upi0;
+  int Rp, nkb, stages, ncols;
+  uint32_t stage_bytes;
+  float alpha, beta;
+};
+
+// One CTA: rows m0 .. m0 + 127 of Y.  Warp 0 lane 0 produces (TMA), warp 1
+// lane 0 issues the MMAs, all four warps run the epilogue.
+__global__ void __launch_bounds__(kTcThreads) tmc_tc_kernel(const __grid_constant__ CUtensorMap mapA,
+                                                           const __grid_constant__ CUtensorMap mapX,
+                                                           const TcArgs a) {
+  extern __shared__ unsigned char smraw[];
+  // stages start at a 1024-byte boundary (the 128-byte swizzle atom)
+  unsigned char* sm = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smraw) + 1023) & ~static_cast<uintptr_t>(1023));
+  const int S = a.stages;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + (size_t)S * a.stage_bytes);
+  uint64_t* empty = full + S;
+  uint64_t* done = empty + S;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t m0 = (int64_t)blockIdx.x * kTcRows;
+  const uint32_t tile_x = (uint32_t)a.Rp * 128u;  // bytes of one piece's R_p x 64 tile
+
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < S; q++) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], 1);
+    }
+    mbar_init(done, 1);
+    mbar_fence_init();
+  }
+  if (warp == 0) tmem_alloc(tmem_slot, (uint32_t)a.ncols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  __shared__ int mma_ok;  // every MMA of the tile was issued
+
+  if (warp == 0 && lane == 0) {
+    // producer
+    const uint32_t bytes = (uint32_t)kTileA + 3u * tile_x;
+    int kb = 0;
+    for (; kb < a.nkb; kb++) {
+      const int st = kb % S;
+      if (kb >= S && !mbar_wait(&empty[st], (uint32_t)((kb / S) - 1) & 1u, &g_tmc_tc_error, 1)) break;
+      unsigned char* base = sm + (size_t)st * a.stage_bytes;
+      mbar_arrive_expect_tx(&full[st], bytes);
+      tma_load_2d(base, &mapA, kb * kTcK, (int)m0, &full[st]);
+      for (int p = 0; p < 3; p++)
+        tma_load_2d(base + kTileA + p * tile_x, &mapX, kb * kTcK, p * a.Rp, &full[st]);
+    }
+    // never leave with copies in flight
+    for (int q = 0; q < S && q < kb; q++) {
+      const int kk = kb - 1 - q;
+      mbar_wait(&full[kk % S], (uint32_t)(kk / S) & 1u, &g_tmc_tc_error, 3, 400000000LL);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    const uint32_t idesc = bf16_idesc(3u * (uint32_t)a.Rp);
+    int kb = 0;
+    for (; kb < a.nkb; kb++) {
+      const int st = kb % S;
+      if (!mbar_wait(&full[st], (uint32_t)(kb / S) & 1u, &g_tmc_tc_error, 2)) break;
+      tc_fence_after();
+      const uint32_t abase = smem_u32(sm + (size_t)st * a.stage_bytes);
+      // the three piece tiles are one K-major tile of 3 R_p rows: one MMA per
+      // K step, the pieces' products in column groups [p R_p, (p + 1) R_p)
+#pragma unroll
+      for (int kk = 0; kk < kTcK / 16; kk++) {
+        const uint64_t ad = sw128_kmajor_desc(abase + kk * 32u);
+        const uint64_t bd = sw128_kmajor_desc(abase + (uint32_t)kTileA + kk * 32u);
+        tc_mma_bf16(tmem, ad, bd, idesc, (kb | kk) != 0 ? 1u : 0u);
+      }
+      tc_commit(&empty[st]);  // the stage is free once these MMAs have read it
+    }
+    mma_ok = (kb == a.nkb) ? 1 : 0;
+    tc_commit(done);
+  }
+  __syncwarp();
+  __syncthreads();  // mma_ok is visible; the producer has drained its copies
+
+  // epilogue: warp w reads tensor-memory lanes 32w .. 32w + 31 (rows of Y)
+  const bool ok = mbar_wait(done, 0u, &g_tmc_tc_error, 4) && mma_ok != 0;
+  tc_fence_after();
+  const int64_t i = m0 + warp * 32 + lane;
+  const float sc = (a.scales != nullptr && i < a.u) ? a.scales[i / a.upi0] : 1.0f;
+  const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+  for (int c0 = 0; c0 < a.Rp; c0 += 16) {
+    float v0[16], v1[16], v2[16];
+    tmem_ld16(trow + (uint32_t)c0, v0);
+    tmem_ld16(trow + (uint32_t)(a.Rp + c0), v1);
+    tmem_ld16(trow + (uint32_t)(2 * a.Rp + c0), v2);
+    if (ok && i < a.u) {
+#pragma unroll
+      for (int q = 0; q < 16; q++) {
+        const int64_t r = c0 + q;
+        if (r < a.R) {
+          const float acc = __fadd_rn(__fadd_rn(v2[q], v1[q]), v0[q]);  // smallest pieces first
+          float out = __fmul_rn(__fmul_rn(acc, sc), a.alpha);
+          if (a.beta != 0.0f) out = __fmaf_rn(a.beta, a.Y[i * a.R + r], out);
+          a.Y[i * a.R + r] = out;
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, (uint32_t)a.ncols);
+  }
+}
+
+}  // namespace
+}  // namespace tvcg
+
+namespace tvcg {
+
+namespace {
+
+// cuTensorMapEncodeTiled, looked up once through the runtime (no link to the
+// driver library).
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+  static std::once_flag once;
+  static EncodeTiledFn fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+// Row-major rows x cols BF16 matrix (row stride `stride` elements) read in
+// boxes of box_rows x 64 with the 128-byte swizzle; zero fill outside.
+bool encode_bf16_rows(CUtensorMap* m, const void* base, int64_t rows, int64_t cols, int64_t stride, int box_rows) {
+  EncodeTiledFn fn = encode_tiled();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)stride * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)kTcK, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int64_t round_up(int64_t x, int64_t q) { return (x + q - 1) / q * q; }
+
+struct TcLayout {
+  int Rp = 0, stages = 0, ncols = 0;
+  int64_t nkp = 0;
+  uint32_t stage_bytes = 0;
+  size_t smem = 0, ws = 0;
+};
+
+TcLayout tc_layout(const Shape& s, int64_t R) {
+  TcLayout L;
+  L.Rp = (int)round_up(R, 16);
+  L.ncols = 32;
+  while (L.ncols < 3 * L.Rp) L.ncols *= 2;  // the three pieces' accumulators
+  L.nkp = round_up(s.nk, kTcK);
+  L.stage_bytes = (uint32_t)(kTileA + 3 * L.Rp * 128);
+  L.stages = (int)std::max<int64_t>(2, std::min<int64_t>(6, (int64_t)(96 * 1024) / L.stage_bytes));
+  L.smem = 1024 + (size_t)L.stages * L.stage_bytes + (2 * (size_t)L.stages + 2) * 8;
+  // at most 512 / ncols CTAs may hold tensor memory on an SM at once: ask for
+  // enough shared memory that no more become resident (a further CTA's
+  // allocation would wait for one of them to finish)
+  const size_t per_sm = 228 * 1024;
+  const size_t most = (size_t)(512 / L.ncols);
+  L.smem = std::max(L.smem, per_sm / (most + 1) + 1024);
+  L.ws = align_up((size_t)3 * L.Rp * L.nkp * 2, 256);
+  return L;
+}
+
+}  // namespace
+
+bool tmc_tc_supported(const Shape& s, int64_t R, tvc_dtype dt, const void* A, bool a16) {
+  if (dt != TVC_BF16 || s.v != 1 || s.mode < 1) return false;
+  if (R < 8 || R > 64) return false;
+  if (s.nk % 8 != 0 || s.nk >= ((int64_t)1 << 31) || s.u >= ((int64_t)1 << 31)) return false;
+  if (!(A == nullptr ? a16 : aligned(A, 16))) return false;
+  // enough 128-row tiles to fill the GPU
+  return (s.u + kTcRows - 1) / kTcRows >= device_sms();
+}
+
+size_t tmc_tc_ws_bytes(const Shape& s, int64_t R) { return tc_layout(s, R).ws; }
+
+tvc_status tmc_tc_launch(const void* A, const Shape& s, const float* X, int64_t R, float* Y, const float* scales,
+                         double alpha, double beta, void* ws, size_t ws_bytes, cudaStream_t st) {
+  const TcLayout L = tc_layout(s, R);
+  if (!ws || ws_bytes < L.ws || !aligned(ws, 256)) return TVC_ERR_WORKSPACE;
+  uint16_t* pieces = static_cast<uint16_t*>(ws);
+  CUtensorMap mapA, mapX;
+  if (!encode_bf16_rows(&mapA, A, s.u, s.nk, s.nk, kTcRows) ||
+      !encode_bf16_rows(&mapX, pieces, 3 * (int64_t)L.Rp, L.nkp, L.nkp, L.Rp))
+    return TVC_ERR_UNSUPPORTED;
+  static std::once_flag attr_once;
+  std::call_once(attr_once, [] {
+    cudaFuncSetAttribute(reinterpret_cast<const void*>(tmc_tc_kernel), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         200 * 1024);
+  });
+  const int64_t n = (int64_t)L.Rp * L.nkp;
+  const int sblocks = (int)std::min<int64_t>((n + 255) / 256, 4LL * device_sms());
+  tmc_tc_split_x_kernel<<<sblocks, 256, 0, st>>>(X, pieces, R, s.nk, L.Rp, L.nkp);
+  TcArgs a;
+  a.Y = Y;
+  a.scales = scales;
+  a.u = s.u;
+  a.R = R;
+  a.upi0 = s.upi0 > 0 ? s.upi0 : 1;
+  a.Rp = L.Rp;
+  a.nkb = (int)(L.nkp / kTcK);
+  a.stages = L.stages;
+  a.ncols = L.ncols;
+  a.stage_bytes = L.stage_bytes;
+  a.alpha = (float)alpha;
+  a.beta = (float)beta;
+  const unsigned grid = (unsigned)((s.u + kTcRows - 1) / kTcRows);
+  tmc_tc_kernel<<<grid, kTcThreads, L.smem, st>>>(mapA, mapX, a);
+  count_launches(2);
+  return cuda_status(cudaGetLastError());
+}
+
+// Sticky error word of the tensor-core kernel's bounded waits.
+tvc_status tmc_tc_device_error(int* code_out, int clear) {
+  int v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_tmc_tc_error, sizeof(int)) != cudaSuccess) return TVC_ERR_CUDA;
+  if (clear && v) {
+    const int z = 0;
+    if (cudaMemcpyToSymbol(g_tmc_tc_error, &z, sizeof(int)) != cudaSuccess) return TVC_ERR_CUDA;
+  }
+  if (code_out) *code_out = v;
+  return TVC_OK;
+}
+
+}  // namespace tvcg

@@ -1926,12 +1926,14 @@ static tvc_status validate(const void* A, int order, const int64_t* dims, int mo
 using namespace tvcg;
 
 extern "C" tvc_status tvc_device_error(int* code_out, int clear) {
-  int v = 0;
+  int v = 0, w = 0;
   if (cudaMemcpyFromSymbol(&v, g_tvc_device_error, sizeof(int)) != cudaSuccess) return TVC_ERR_CUDA;
   if (clear) {
     const int z = 0;
     if (cudaMemcpyToSymbol(g_tvc_device_error, &z, sizeof(int)) != cudaSuccess) return TVC_ERR_CUDA;
   }
+  if (tmc_tc_device_error(&w, clear) != TVC_OK) return TVC_ERR_CUDA;
+  if (v == 0 && w != 0) v = 10 + w;  // the tensor-core TMC kernel's waits
   if (code_out) *code_out = v;
   return v ? TVC_ERR_TIMEOUT : TVC_OK;
 }

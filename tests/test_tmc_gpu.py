@@ -203,3 +203,40 @@ def test_tmc_full_size_1024cube_sampled(code):
         del Y, Yr
     del At
     torch.cuda.empty_cache()
+
+
+# BF16 codes along the last mode with 8 <= R <= 64 and at least 152 tiles of
+# 128 rows go to the tensor-core kernel (TMA tiles, tcgen05 MMAs on the three
+# BF16 pieces of X, FP32 accumulation in tensor memory): ragged n_k (zero
+# filled to blocks of 64), ragged row tiles, one and several slabs with
+# their scales, R not a multiple of 16.
+TC_CASES = [((20480, 64), 8), ((19500, 200), 13), ((4, 5000, 1024), 16), ((2, 9781, 8), 33), ((19457, 520), 64)]
+
+
+@pytest.mark.parametrize("dims,R", TC_CASES, ids=lambda c: "x".join(map(str, c)) if isinstance(c, tuple) else str(c))
+def test_tmc_tensor_core_bf16_last_mode(dims, R):
+    k = len(dims) - 1
+    A, Ao, scales = gu.inputs(dims, oracle.BF16, seed=5)
+    X = mat(oracle.BF16, R, dims[k], synth.stream_x(k), seed=6)
+    ref = oracle.tmc(Ao, k, X, scales=scales)
+    launches0 = tg.kernel_launches()
+    got = gpu_tmc(A, k, X, scales=scales, dims=dims)
+    torch.cuda.synchronize()
+    assert tg.kernel_launches() - launches0 == 2  # split of X + the tensor-core kernel
+    assert gu.rel_l2(got, ref) <= 1e-5, (dims, R, gu.rel_l2(got, ref))
+    lib = tg.load_library()
+    import ctypes
+    code = ctypes.c_int(0)
+    assert lib.tvc_device_error(ctypes.byref(code), 1) == 0, code.value
+
+
+def test_tmc_tensor_core_alpha_beta():
+    dims, R = (20000, 128), 24
+    A, Ao, scales = gu.inputs(dims, oracle.BF16, seed=7)
+    X = mat(oracle.BF16, R, 128, synth.stream_x(1), seed=8)
+    Y0 = synth.tensor("u32", 9, (20000, R)).astype(np.float32)
+    ref = oracle.tmc(Ao, 1, X, scales=scales, Y=Y0.astype(np.float64), alpha=0.5, beta=-2.0)
+    Yt = gu.to_dev(Y0)
+    tg.tmc(gu.to_dev(A), 1, gu.to_dev(X), Y=Yt, scales=gu.to_dev(scales), shape=dims, alpha=0.5, beta=-2.0)
+    torch.cuda.synchronize()
+    assert gu.rel_l2(Yt.cpu().numpy(), ref) <= 1e-5
