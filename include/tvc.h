@@ -138,12 +138,14 @@ size_t tvc_workspace_size(int order, const int64_t* dims, int mode, tvc_dtype dt
  * once per pass of up to 16 rows of X (8 for FP64 vectors; R <= 4 and R <= 8
  * use one pass of 4 or 8).  FP32 accumulation for FP32 and the narrow
  * types, FP64 multiply-adds for FP64 and single-double storage.
- * BF16 storage along the last mode (mode = order - 1 >= 1) with
- * 8 <= R <= 64, n_mode a multiple of 8, A 16-byte aligned and at least
- * 128 * (number of SMs) rows runs on the tensor cores: X is split into three
- * BF16 pieces (exact to binary32 precision), every product of two BF16
- * values is exact, and the MMAs accumulate in FP32; its workspace holds the
- * pieces (tmc_workspace_size includes them).
+ * BF16 storage with 8 <= R <= 64 and A 16-byte aligned runs on the tensor
+ * cores when the contraction is along the last mode (n_mode a multiple of
+ * 8) or along another mode with v a multiple of 8 and v >= 64, and there are
+ * at least as many 128-output tiles as SMs: X is split into three BF16
+ * pieces (exact to binary32 precision; for mode 0 the slab scales are
+ * folded into X first), every product of two BF16 values is exact, and the
+ * MMAs accumulate in FP32.  Its workspace holds the pieces
+ * (tmc_workspace_size includes them).
  * slab_scales: as for tvc_ex.  workspace: tmc_workspace_size(...) bytes (0
  * when the output columns fill the GPU without splitting n_mode).
  * Errors: TVC_ERR_INVALID_ARG for a bad shape, mode, dtype, R < 1, a NULL

@@ -1,8 +1,11 @@
 // Tensor-matrix contraction (TMC, Section 1) on the tensor cores, for BF16
-// storage along the last mode, where the contraction is a matrix product
-// with the contracted index contiguous in memory:
-//     Y[i][r] = alpha * scale[slab(i)] * sum_j A[i][j] X[r][j] + beta * Y[i][r],
-// A the u x n_k row-major BF16 codes, X the R x n_k FP32 matrix.
+// storage.  With A read as u x n_k x v (Section 3), every slab i is a matrix
+// product:
+//     Y[i][r][l] = alpha * scale * sum_j A[i][j][l] X[r][j] + beta * Y[i][r][l],
+// X the R x n_k FP32 matrix.  Along the last mode (v = 1) the rows of A are
+// the M dimension and the contracted index is contiguous (K-major tiles);
+// along any other mode the v columns of a slab are the M dimension and are
+// contiguous (MN-major tiles).
 //
 // X is split on the device into three BF16 pieces, X = X0 + X1 + X2 to
 // binary32 precision (each piece the BF16 rounding of what the previous ones
@@ -10,9 +13,10 @@
 // form A[i][j] X_p[r][j] exactly and accumulate in FP32 in tensor memory:
 // the result carries FP32 accumulation error only, like the CUDA-core path.
 //
-// Dataflow (one CTA per 128 rows of A):
+// Dataflow (one CTA per 128 outputs: rows of A, or columns of one slab):
 //   - a producer thread brings, per block of 64 codes along n_k, the 128 x 64
-//     tile of A and the three R_p x 64 tiles of X pieces into one stage of a
+//     tile of A (one box, or two 64 x 64 boxes along v for MN-major tiles)
+//     and the three R_p x 64 tiles of X pieces into one stage of a
 //     shared-memory ring with TMA (2-D tensor maps, 128-byte swizzle; rows
 //     past u and codes past n_k are filled with zeros);
 //   - one thread issues the MMAs (tcgen05.mma kind::f16, M = 128, K = 16 per
@@ -54,6 +58,15 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
           "r"(smem_u32(dst)),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+          "r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
       : "memory");
 }
 
@@ -118,10 +131,24 @@ __device__ __forceinline__ uint64_t sw128_kmajor_desc(uint32_t saddr) {
   return d;
 }
 
-// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
-// K-major, N = n columns, M = 128 rows.
-__host__ __device__ constexpr uint32_t bf16_idesc(uint32_t n) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((n >> 3) << 17) | ((uint32_t)(kTcRows >> 4) << 24);
+// The same for an MN-major tile (M contiguous): 64-element (128-byte) rows
+// along M, one row per K index, 8-row groups of 1024 bytes along K (stride
+// byte offset), and the next 64 elements of M `atom_bytes` further (leading
+// byte offset).
+__device__ __forceinline__ uint64_t sw128_mnmajor_desc(uint32_t saddr, uint32_t atom_bytes) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((atom_bytes >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)(1024u >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, B
+// K-major, A K-major or (mn_a) MN-major, N = n columns, M = 128 rows.
+__host__ __device__ constexpr uint32_t bf16_idesc(uint32_t n, bool mn_a = false) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((mn_a ? 1u : 0u) << 15) | ((n >> 3) << 17) |
+         ((uint32_t)(kTcRows >> 4) << 24);
 }
 
 // ----------------------------------------------------------------- kernels
@@ -129,12 +156,15 @@ __host__ __device__ constexpr uint32_t bf16_idesc(uint32_t n) {
 // X (R x nk FP32) -> three BF16 pieces, pieces[p][r][j] for r < Rp, j < nkp,
 // zero outside R x nk: X0 = bf16(x), X1 = bf16(x - X0), X2 = bf16(x - X0 - X1)
 // (the differences are exact in FP32).
+// jscale (nullable): per-j factors folded into X first (mode 0 of narrow
+// storage, where the slab scale runs along the contracted index).
 __global__ void tmc_tc_split_x_kernel(const float* __restrict__ X, uint16_t* __restrict__ pieces, int64_t R,
-                                      int64_t nk, int64_t Rp, int64_t nkp) {
+                                      int64_t nk, int64_t Rp, int64_t nkp, const float* __restrict__ jscale) {
   const int64_t n = Rp * nkp;
   for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = o / nkp, j = o - r * nkp;
-    const float x = (r < R && j < nk) ? X[r * nk + j] : 0.0f;
+    float x = (r < R && j < nk) ? X[r * nk + j] : 0.0f;
+    if (jscale != nullptr && j < nk) x = __fmul_rn(x, jscale[j]);
     const __nv_bfloat16 h0 = __float2bfloat16_rn(x);
     const float rem1 = __fsub_rn(x, __bfloat162float(h0));
     const __nv_bfloat16 h1 = __float2bfloat16_rn(rem1);
@@ -148,15 +178,19 @@ __global__ void tmc_tc_split_x_kernel(const float* __restrict__ X, uint16_t* __r
 
 struct TcArgs {
   float* Y;
-  const float* scales;  // per slab, nullable
-  int64_t u, R, upi0;
+  const float* scales;  // per slab (row i of the u x n_k x v view), nullable
+  int64_t u, R, upi0, v, vt;  // vt: tiles of 128 along v (1 when v == 1)
   int Rp, nkb, stages, ncols;
   uint32_t stage_bytes;
   float alpha, beta;
 };
 
-// One CTA: rows m0 .. m0 + 127 of Y.  Warp 0 lane 0 produces (TMA), warp 1
+// One CTA: 128 outputs of Y.  MN == false (v == 1): rows m0 .. m0 + 127 of
+// the u x n_k matrix A (K-major tiles).  MN == true (v > 1): slab i of A, an
+// n_k x v matrix, and columns l0 .. l0 + 127 of it (MN-major tiles: two
+// 64-wide boxes per stage, 8 KB apart).  Warp 0 lane 0 produces (TMA), warp 1
 // lane 0 issues the MMAs, all four warps run the epilogue.
+template <bool MN>
 __global__ void __launch_bounds__(kTcThreads) tmc_tc_kernel(const __grid_constant__ CUtensorMap mapA,
                                                            const __grid_constant__ CUtensorMap mapX,
                                                            const TcArgs a) {
@@ -170,7 +204,8 @@ __global__ void __launch_bounds__(kTcThreads) tmc_tc_kernel(const __grid_constan
   uint64_t* done = empty + S;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t m0 = (int64_t)blockIdx.x * kTcRows;
+  const int64_t tile_i = MN ? (int64_t)blockIdx.x / a.vt : 0;               // slab (MN)
+  const int64_t m0 = MN ? ((int64_t)blockIdx.x % a.vt) * kTcRows : (int64_t)blockIdx.x * kTcRows;
   const uint32_t tile_x = (uint32_t)a.Rp * 128u;  // bytes of one piece's R_p x 64 tile
 
   if (threadIdx.x == 0) {
@@ -197,7 +232,12 @@ __global__ void __launch_bounds__(kTcThreads) tmc_tc_kernel(const __grid_constan
       if (kb >= S && !mbar_wait(&empty[st], (uint32_t)((kb / S) - 1) & 1u, &g_tmc_tc_error, 1)) break;
       unsigned char* base = sm + (size_t)st * a.stage_bytes;
       mbar_arrive_expect_tx(&full[st], bytes);
-      tma_load_2d(base, &mapA, kb * kTcK, (int)m0, &full[st]);
+      if constexpr (MN) {
+        tma_load_3d(base, &mapA, (int)m0, kb * kTcK, (int)tile_i, &full[st]);
+        tma_load_3d(base + kTileA / 2, &mapA, (int)m0 + 64, kb * kTcK, (int)tile_i, &full[st]);
+      } else {
+        tma_load_2d(base, &mapA, kb * kTcK, (int)m0, &full[st]);
+      }
       for (int p = 0; p < 3; p++)
         tma_load_2d(base + kTileA + p * tile_x, &mapX, kb * kTcK, p * a.Rp, &full[st]);
     }
@@ -208,7 +248,7 @@ __global__ void __launch_bounds__(kTcThreads) tmc_tc_kernel(const __grid_constan
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
-    const uint32_t idesc = bf16_idesc(3u * (uint32_t)a.Rp);
+    const uint32_t idesc = bf16_idesc(3u * (uint32_t)a.Rp, MN);
     int kb = 0;
     for (; kb < a.nkb; kb++) {
       const int st = kb % S;
@@ -219,7 +259,10 @@ __global__ void __launch_bounds__(kTcThreads) tmc_tc_kernel(const __grid_constan
       // K step, the pieces' products in column groups [p R_p, (p + 1) R_p)
 #pragma unroll
       for (int kk = 0; kk < kTcK / 16; kk++) {
-        const uint64_t ad = sw128_kmajor_desc(abase + kk * 32u);
+        // K step kk: 32 bytes along a K-major row, or 16 rows (2 groups of
+        // 8 x 128 bytes) of an MN-major tile
+        const uint64_t ad = MN ? sw128_mnmajor_desc(abase + kk * 2048u, (uint32_t)kTileA / 2)
+                               : sw128_kmajor_desc(abase + kk * 32u);
         const uint64_t bd = sw128_kmajor_desc(abase + (uint32_t)kTileA + kk * 32u);
         tc_mma_bf16(tmem, ad, bd, idesc, (kb | kk) != 0 ? 1u : 0u);
       }
@@ -234,23 +277,27 @@ __global__ void __launch_bounds__(kTcThreads) tmc_tc_kernel(const __grid_constan
   // epilogue: warp w reads tensor-memory lanes 32w .. 32w + 31 (rows of Y)
   const bool ok = mbar_wait(done, 0u, &g_tmc_tc_error, 4) && mma_ok != 0;
   tc_fence_after();
-  const int64_t i = m0 + warp * 32 + lane;
-  const float sc = (a.scales != nullptr && i < a.u) ? a.scales[i / a.upi0] : 1.0f;
+  // output row of this thread: i (v == 1) or column l of slab tile_i
+  const int64_t row = m0 + warp * 32 + lane;
+  const int64_t i = MN ? tile_i : row;
+  const bool live = MN ? row < a.v : row < a.u;
+  const float sc = (a.scales != nullptr && live) ? a.scales[i / a.upi0] : 1.0f;
   const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
   for (int c0 = 0; c0 < a.Rp; c0 += 16) {
     float v0[16], v1[16], v2[16];
     tmem_ld16(trow + (uint32_t)c0, v0);
     tmem_ld16(trow + (uint32_t)(a.Rp + c0), v1);
     tmem_ld16(trow + (uint32_t)(2 * a.Rp + c0), v2);
-    if (ok && i < a.u) {
+    if (ok && live) {
 #pragma unroll
       for (int q = 0; q < 16; q++) {
         const int64_t r = c0 + q;
         if (r < a.R) {
           const float acc = __fadd_rn(__fadd_rn(v2[q], v1[q]), v0[q]);  // smallest pieces first
           float out = __fmul_rn(__fmul_rn(acc, sc), a.alpha);
-          if (a.beta != 0.0f) out = __fmaf_rn(a.beta, a.Y[i * a.R + r], out);
-          a.Y[i * a.R + r] = out;
+          const int64_t o = MN ? (i * a.R + r) * a.v + row : i * a.R + r;  // Y[i][r][l] / Y[i][r]
+          if (a.beta != 0.0f) out = __fmaf_rn(a.beta, a.Y[o], out);
+          a.Y[o] = out;
         }
       }
     }
@@ -306,7 +353,23 @@ bool encode_bf16_rows(CUtensorMap* m, const void* base, int64_t rows, int64_t co
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// The slabs of a u x n_k x v BF16 tensor (v contiguous, v > 1) read in
+// boxes of 64 (along v) x 64 (along n_k) x 1 slab, 128-byte swizzle.
+bool encode_bf16_slabs(CUtensorMap* m, const void* base, int64_t u, int64_t nk, int64_t v) {
+  EncodeTiledFn fn = encode_tiled();
+  if (!fn) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)v, (cuuint64_t)nk, (cuuint64_t)u};
+  const cuuint64_t strides[2] = {(cuuint64_t)v * 2, (cuuint64_t)nk * (cuuint64_t)v * 2};
+  const cuuint32_t box[3] = {64, (cuuint32_t)kTcK, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 int64_t round_up(int64_t x, int64_t q) { return (x + q - 1) / q * q; }
+
+int64_t tc_tiles(const Shape& s) { return s.v == 1 ? (s.u + kTcRows - 1) / kTcRows : s.u * ((s.v + kTcRows - 1) / kTcRows); }
 
 struct TcLayout {
   int Rp = 0, stages = 0, ncols = 0;
@@ -337,12 +400,17 @@ TcLayout tc_layout(const Shape& s, int64_t R) {
 }  // namespace
 
 bool tmc_tc_supported(const Shape& s, int64_t R, tvc_dtype dt, const void* A, bool a16) {
-  if (dt != TVC_BF16 || s.v != 1 || s.mode < 1) return false;
-  if (R < 8 || R > 64) return false;
-  if (s.nk % 8 != 0 || s.nk >= ((int64_t)1 << 31) || s.u >= ((int64_t)1 << 31)) return false;
+  if (dt != TVC_BF16 || R < 8 || R > 64) return false;
+  if (s.nk >= ((int64_t)1 << 31) || s.u >= ((int64_t)1 << 31) || s.v >= ((int64_t)1 << 31)) return false;
+  if (s.v == 1) {
+    // rows of the last mode: the contracted index is contiguous (K-major)
+    if (s.mode < 1 || s.nk % 8 != 0) return false;
+  } else {
+    // slabs n_k x v with v contiguous (MN-major): 16-byte rows along v
+    if (s.v % 8 != 0 || s.v < 64) return false;
+  }
   if (!(A == nullptr ? a16 : aligned(A, 16))) return false;
-  // enough 128-row tiles to fill the GPU
-  return (s.u + kTcRows - 1) / kTcRows >= device_sms();
+  return tc_tiles(s) >= device_sms();  // enough 128-output tiles to fill the GPU
 }
 
 size_t tmc_tc_ws_bytes(const Shape& s, int64_t R) { return tc_layout(s, R).ws; }
@@ -352,24 +420,30 @@ tvc_status tmc_tc_launch(const void* A, const Shape& s, const float* X, int64_t 
   const TcLayout L = tc_layout(s, R);
   if (!ws || ws_bytes < L.ws || !aligned(ws, 256)) return TVC_ERR_WORKSPACE;
   uint16_t* pieces = static_cast<uint16_t*>(ws);
+  const bool mn = s.v > 1;
   CUtensorMap mapA, mapX;
-  if (!encode_bf16_rows(&mapA, A, s.u, s.nk, s.nk, kTcRows) ||
-      !encode_bf16_rows(&mapX, pieces, 3 * (int64_t)L.Rp, L.nkp, L.nkp, L.Rp))
-    return TVC_ERR_UNSUPPORTED;
+  const bool okA = mn ? encode_bf16_slabs(&mapA, A, s.u, s.nk, s.v) : encode_bf16_rows(&mapA, A, s.u, s.nk, s.nk, kTcRows);
+  if (!okA || !encode_bf16_rows(&mapX, pieces, 3 * (int64_t)L.Rp, L.nkp, L.nkp, L.Rp)) return TVC_ERR_UNSUPPORTED;
   static std::once_flag attr_once;
   std::call_once(attr_once, [] {
-    cudaFuncSetAttribute(reinterpret_cast<const void*>(tmc_tc_kernel), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         200 * 1024);
+    cudaFuncSetAttribute(reinterpret_cast<const void*>(tmc_tc_kernel<false>),
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(reinterpret_cast<const void*>(tmc_tc_kernel<true>),
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   });
+  // mode 0: the slab scale belongs to the contracted index j; fold it into X
+  const bool fold = s.mode == 0 && scales != nullptr;
   const int64_t n = (int64_t)L.Rp * L.nkp;
   const int sblocks = (int)std::min<int64_t>((n + 255) / 256, 4LL * device_sms());
-  tmc_tc_split_x_kernel<<<sblocks, 256, 0, st>>>(X, pieces, R, s.nk, L.Rp, L.nkp);
+  tmc_tc_split_x_kernel<<<sblocks, 256, 0, st>>>(X, pieces, R, s.nk, L.Rp, L.nkp, fold ? scales : nullptr);
   TcArgs a;
   a.Y = Y;
-  a.scales = scales;
+  a.scales = fold ? nullptr : scales;
   a.u = s.u;
   a.R = R;
   a.upi0 = s.upi0 > 0 ? s.upi0 : 1;
+  a.v = s.v;
+  a.vt = (s.v + kTcRows - 1) / kTcRows;
   a.Rp = L.Rp;
   a.nkb = (int)(L.nkp / kTcK);
   a.stages = L.stages;
@@ -377,8 +451,12 @@ tvc_status tmc_tc_launch(const void* A, const Shape& s, const float* X, int64_t 
   a.stage_bytes = L.stage_bytes;
   a.alpha = (float)alpha;
   a.beta = (float)beta;
-  const unsigned grid = (unsigned)((s.u + kTcRows - 1) / kTcRows);
-  tmc_tc_kernel<<<grid, kTcThreads, L.smem, st>>>(mapA, mapX, a);
+  const int64_t tiles = tc_tiles(s);
+  if (tiles > 0x7FFFFFFF) return TVC_ERR_UNSUPPORTED;
+  if (mn)
+    tmc_tc_kernel<true><<<(unsigned)tiles, kTcThreads, L.smem, st>>>(mapA, mapX, a);
+  else
+    tmc_tc_kernel<false><<<(unsigned)tiles, kTcThreads, L.smem, st>>>(mapA, mapX, a);
   count_launches(2);
   return cuda_status(cudaGetLastError());
 }

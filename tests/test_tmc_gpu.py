@@ -205,17 +205,22 @@ def test_tmc_full_size_1024cube_sampled(code):
     torch.cuda.empty_cache()
 
 
-# BF16 codes along the last mode with 8 <= R <= 64 and at least 152 tiles of
-# 128 rows go to the tensor-core kernel (TMA tiles, tcgen05 MMAs on the three
-# BF16 pieces of X, FP32 accumulation in tensor memory): ragged n_k (zero
-# filled to blocks of 64), ragged row tiles, one and several slabs with
-# their scales, R not a multiple of 16.
-TC_CASES = [((20480, 64), 8), ((19500, 200), 13), ((4, 5000, 1024), 16), ((2, 9781, 8), 33), ((19457, 520), 64)]
+# BF16 storage with 8 <= R <= 64 and at least 152 tiles of 128 outputs goes
+# to the tensor-core kernel (TMA tiles, tcgen05 MMAs on the three BF16 pieces
+# of X, FP32 accumulation in tensor memory).  Last mode (K-major tiles):
+# ragged n_k (zero filled to blocks of 64), ragged row tiles, one and several
+# slabs with their scales, R not a multiple of 16.  Other modes (MN-major
+# tiles, v a multiple of 8): mode 0 (the slab scales folded into X), ragged
+# v tiles (a half-empty second box), ragged n_k, order 4.
+TC_CASES = [((20480, 64), 1, 8), ((19500, 200), 1, 13), ((4, 5000, 1024), 2, 16), ((2, 9781, 8), 2, 33),
+            ((19457, 520), 1, 64),
+            ((300, 20480), 0, 16), ((40, 96, 520), 1, 8), ((160, 33, 64), 1, 21), ((2, 80, 130, 128), 2, 64),
+            ((8, 64, 2432), 0, 24)]
 
 
-@pytest.mark.parametrize("dims,R", TC_CASES, ids=lambda c: "x".join(map(str, c)) if isinstance(c, tuple) else str(c))
-def test_tmc_tensor_core_bf16_last_mode(dims, R):
-    k = len(dims) - 1
+@pytest.mark.parametrize("dims,k,R", TC_CASES,
+                         ids=lambda c: "x".join(map(str, c)) if isinstance(c, tuple) else str(c))
+def test_tmc_tensor_core_bf16(dims, k, R):
     A, Ao, scales = gu.inputs(dims, oracle.BF16, seed=5)
     X = mat(oracle.BF16, R, dims[k], synth.stream_x(k), seed=6)
     ref = oracle.tmc(Ao, k, X, scales=scales)
