@@ -68,11 +68,14 @@ tvc_status combine_parts(const void* const* parts, int nparts, const int64_t* of
                          const int* done);
 
 // Tensor-matrix contraction on the tensor cores (tmc_tc.cu): BF16 storage
-// along the last mode, 8 <= R <= 64, n_k a multiple of 8, A 16-byte aligned,
-// enough rows for the GPU (a16 stands for the alignment of A when A is NULL,
-// for the workspace query).  Workspace: the three BF16 pieces of X.
+// (any mode; see tmc_tc_supported) and FP32 storage along the last mode,
+// 8 <= R <= 64, A 16-byte aligned, enough 128-output tiles for the GPU (a16
+// stands for the alignment of A when A is NULL, for the workspace query).
+// Workspace: the pieces of X.
 bool tmc_tc_supported(const Shape& s, int64_t R, tvc_dtype dt, const void* A, bool a16);
-size_t tmc_tc_ws_bytes(const Shape& s, int64_t R);
+size_t tmc_tc_ws_bytes(const Shape& s, int64_t R, tvc_dtype dt);
+tvc_status tmc_tc_launch_f32(const void* A, const Shape& s, const float* X, int64_t R, float* Y, double alpha,
+                             double beta, void* ws, size_t ws_bytes, cudaStream_t st);
 tvc_status tmc_tc_launch(const void* A, const Shape& s, const float* X, int64_t R, float* Y, const float* scales,
                          double alpha, double beta, void* ws, size_t ws_bytes, cudaStream_t st);
 // Sticky error word of that kernel's bounded waits (cleared when clear != 0).

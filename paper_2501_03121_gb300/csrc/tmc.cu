@@ -691,10 +691,11 @@ int tmc_rp(tvc_dtype dt, int64_t R) {
 TmcPlan tmc_plan(const Shape& s, int64_t R, tvc_dtype dt, const void* A, bool a16 = false) {
   TmcPlan p;
   if (tmc_tc_supported(s, R, dt, A, a16)) {
-    // BF16 codes along the last mode with R >= 8: a matrix product on the
-    // tensor cores (the CUDA-core kernels are issue-bound there)
+    // BF16 codes (any mode) or FP32 along the last mode with R >= 8: a
+    // matrix product on the tensor cores (the CUDA-core kernels are
+    // issue-bound there)
     p.tc = true;
-    p.ws = tmc_tc_ws_bytes(s, R);
+    p.ws = tmc_tc_ws_bytes(s, R, dt);
     return p;
   }
   p.rp = tmc_rp(dt, R);
@@ -778,6 +779,11 @@ tvc_status run(const void* A, const Shape& s, const void* X, int64_t R, void* Y,
     if (p.tc)
       return tmc_tc_launch(A, s, static_cast<const float*>(X), R, static_cast<float*>(Y), scales, alpha, beta, ws,
                            ws_size, st);
+  }
+  if constexpr (DT == TVC_F32) {
+    if (p.tc)
+      return tmc_tc_launch_f32(A, s, static_cast<const float*>(X), R, static_cast<float*>(Y), alpha, beta, ws,
+                               ws_size, st);
   }
   TmcArgs<DT> a;
   a.A = static_cast<const typename Elem<DT>::T*>(A);

@@ -1,5 +1,6 @@
 // Tensor-matrix contraction (TMC, Section 1) on the tensor cores, for BF16
-// storage.  With A read as u x n_k x v (Section 3), every slab i is a matrix
+// storage (every mode) and FP32 storage (the last mode; see the FP32 section
+// below).  With A read as u x n_k x v (Section 3), every slab i is a matrix
 // product:
 //     Y[i][r][l] = alpha * scale * sum_j A[i][j][l] X[r][j] + beta * Y[i][r][l],
 // X the R x n_k FP32 matrix.  Along the last mode (v = 1) the rows of A are
@@ -92,6 +93,16 @@ __device__ __forceinline__ void tc_mma_bf16(uint32_t d_tmem, uint64_t adesc, uin
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
@@ -310,6 +321,171 @@ __global__ void __launch_bounds__(kTcThreads) tmc_tc_kernel(const __grid_constan
   }
 }
 
+// ------------------------------------------------------------ FP32 storage
+//
+// kind::tf32 reads an FP32 container through its sign, exponent and top 10
+// fraction bits.  A (FP32, from TMA) serves as its own high part; four
+// converter warps write A_lo = A - trunc(A) (trunc keeps those 19 bits; the
+// difference is exact) into a second tile of the stage, elementwise at the
+// same swizzled offsets.  X is split likewise: X_hi = trunc(X), X_lo = X -
+// X_hi.  Two MMAs per K step of 8: A [X_hi; X_lo] (N = 2 R_p, accumulator
+// groups 0 and 1) and A_lo X_hi (N = R_p, into group 1); the products
+// dropped (A_lo X_lo, the bits of A_lo and X_lo beyond the container's 11)
+// are below 2^-20 of |A X|.  Y = group 1 + group 0.
+
+constexpr int kTcKf = 32;                      // FP32 per stage along n_k: one 128-byte row
+constexpr int kTileAf = kTcRows * kTcKf * 4;  // 16 KB
+
+constexpr uint32_t kTf32Mask = 0xFFFFE000u;
+
+__global__ void tmc_tc_split_x_f32_kernel(const float* __restrict__ X, float* __restrict__ pieces, int64_t R,
+                                          int64_t nk, int64_t Rp, int64_t nkp) {
+  const int64_t n = Rp * nkp;
+  for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = o / nkp, j = o - r * nkp;
+    const float x = (r < R && j < nk) ? X[r * nk + j] : 0.0f;
+    const float hi = __uint_as_float(__float_as_uint(x) & kTf32Mask);
+    pieces[o] = hi;
+    pieces[n + o] = __fsub_rn(x, hi);
+  }
+}
+
+__host__ __device__ constexpr uint32_t tf32_idesc(uint32_t n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((n >> 3) << 17) | ((uint32_t)(kTcRows >> 4) << 24);
+}
+
+constexpr int kTcThreadsF = 192;  // producer warp, MMA warp, four converter / epilogue warps
+
+// Last mode of FP32 storage: rows m0 .. m0 + 127 of the u x n_k matrix A.
+__global__ void __launch_bounds__(kTcThreadsF) tmc_tc_f32_kernel(const __grid_constant__ CUtensorMap mapA,
+                                                                const __grid_constant__ CUtensorMap mapX,
+                                                                const TcArgs a) {
+  extern __shared__ unsigned char smraw[];
+  unsigned char* sm = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smraw) + 1023) & ~static_cast<uintptr_t>(1023));
+  const int S = a.stages;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + (size_t)S * a.stage_bytes);
+  uint64_t* conv = full + S;
+  uint64_t* empty = conv + S;
+  uint64_t* done = empty + S;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  __shared__ int mma_ok;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t m0 = (int64_t)blockIdx.x * kTcRows;
+  const uint32_t tile_x = 2u * (uint32_t)a.Rp * 128u;  // X_hi and X_lo rows, 128 bytes each
+
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < S; q++) {
+      mbar_init(&full[q], 1);
+      mbar_init(&conv[q], 128);
+      mbar_init(&empty[q], 1);
+    }
+    mbar_init(done, 1);
+    mbar_fence_init();
+  }
+  if (warp == 0) tmem_alloc(tmem_slot, (uint32_t)a.ncols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {  // producer
+      const uint32_t bytes = (uint32_t)kTileAf + tile_x;
+      int kb = 0;
+      for (; kb < a.nkb; kb++) {
+        const int st = kb % S;
+        if (kb >= S && !mbar_wait(&empty[st], (uint32_t)((kb / S) - 1) & 1u, &g_tmc_tc_error, 1)) break;
+        unsigned char* base = sm + (size_t)st * a.stage_bytes;
+        mbar_arrive_expect_tx(&full[st], bytes);
+        tma_load_2d(base, &mapA, kb * kTcKf, (int)m0, &full[st]);
+        tma_load_2d(base + 2 * kTileAf, &mapX, kb * kTcKf, 0, &full[st]);
+      }
+      for (int q = 0; q < S && q < kb; q++) {
+        const int kk = kb - 1 - q;
+        mbar_wait(&full[kk % S], (uint32_t)(kk / S) & 1u, &g_tmc_tc_error, 3, 400000000LL);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // MMA issuer
+      const uint32_t id2 = tf32_idesc(2u * (uint32_t)a.Rp), id1 = tf32_idesc((uint32_t)a.Rp);
+      int kb = 0;
+      for (; kb < a.nkb; kb++) {
+        const int st = kb % S;
+        if (!mbar_wait(&conv[st], (uint32_t)(kb / S) & 1u, &g_tmc_tc_error, 2)) break;
+        tc_fence_after();
+        const uint32_t base = smem_u32(sm + (size_t)st * a.stage_bytes);
+#pragma unroll
+        for (int kk = 0; kk < kTcKf / 8; kk++) {
+          const uint64_t ahi = sw128_kmajor_desc(base + kk * 32u);
+          const uint64_t alo = sw128_kmajor_desc(base + (uint32_t)kTileAf + kk * 32u);
+          const uint64_t bx = sw128_kmajor_desc(base + 2u * (uint32_t)kTileAf + kk * 32u);
+          tc_mma_tf32(tmem, ahi, bx, id2, (kb | kk) != 0 ? 1u : 0u);   // groups 0, 1
+          tc_mma_tf32(tmem + (uint32_t)a.Rp, alo, bx, id1, 1u);          // A_lo X_hi into group 1
+        }
+        tc_commit(&empty[st]);
+      }
+      mma_ok = (kb == a.nkb) ? 1 : 0;
+      tc_commit(done);
+    }
+  } else {
+    // converters: A_lo of every stage, 128 threads x 8 chunks of 16 bytes
+    const int t = threadIdx.x - 64;
+    for (int kb = 0; kb < a.nkb; kb++) {
+      const int st = kb % S;
+      if (!mbar_wait(&full[st], (uint32_t)(kb / S) & 1u, &g_tmc_tc_error, 5)) break;
+      unsigned char* base = sm + (size_t)st * a.stage_bytes;
+#pragma unroll
+      for (int c = 0; c < kTileAf / 16 / 128; c++) {
+        const int off = (c * 128 + t) * 16;
+        const float4 v = *reinterpret_cast<const float4*>(base + off);
+        float4 lo;
+        lo.x = __fsub_rn(v.x, __uint_as_float(__float_as_uint(v.x) & kTf32Mask));
+        lo.y = __fsub_rn(v.y, __uint_as_float(__float_as_uint(v.y) & kTf32Mask));
+        lo.z = __fsub_rn(v.z, __uint_as_float(__float_as_uint(v.z) & kTf32Mask));
+        lo.w = __fsub_rn(v.w, __uint_as_float(__float_as_uint(v.w) & kTf32Mask));
+        *reinterpret_cast<float4*>(base + kTileAf + off) = lo;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the tensor cores
+      mbar_arrive(&conv[st]);
+    }
+  }
+  __syncwarp();
+  __syncthreads();
+
+  if (warp >= 2) {  // epilogue: warp w reads tensor-memory lanes 32 (w % 4) ..
+    const int q4 = warp & 3;
+    const bool ok = mbar_wait(done, 0u, &g_tmc_tc_error, 4) && mma_ok != 0;
+    tc_fence_after();
+    const int64_t i = m0 + q4 * 32 + lane;
+    const bool live = i < a.u;
+    const float sc = (a.scales != nullptr && live) ? a.scales[i / a.upi0] : 1.0f;
+    const uint32_t trow = tmem + ((uint32_t)(q4 * 32) << 16);
+    for (int c0 = 0; c0 < a.Rp; c0 += 16) {
+      float g0[16], g1[16];
+      tmem_ld16(trow + (uint32_t)c0, g0);
+      tmem_ld16(trow + (uint32_t)(a.Rp + c0), g1);
+      if (ok && live) {
+#pragma unroll
+        for (int q = 0; q < 16; q++) {
+          const int64_t r = c0 + q;
+          if (r < a.R) {
+            float out = __fmul_rn(__fmul_rn(__fadd_rn(g1[q], g0[q]), sc), a.alpha);
+            if (a.beta != 0.0f) out = __fmaf_rn(a.beta, a.Y[i * a.R + r], out);
+            a.Y[i * a.R + r] = out;
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, (uint32_t)a.ncols);
+  }
+}
+
 }  // namespace
 }  // namespace tvcg
 
@@ -367,6 +543,20 @@ bool encode_bf16_slabs(CUtensorMap* m, const void* base, int64_t u, int64_t nk, 
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Row-major rows x cols FP32 matrix read in boxes of box_rows x 32 (128-byte
+// rows), 128-byte swizzle, zero fill outside.
+bool encode_f32_rows(CUtensorMap* m, const void* base, int64_t rows, int64_t cols, int64_t stride, int box_rows) {
+  EncodeTiledFn fn = encode_tiled();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)stride * 4};
+  const cuuint32_t box[2] = {(cuuint32_t)kTcKf, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 int64_t round_up(int64_t x, int64_t q) { return (x + q - 1) / q * q; }
 
 int64_t tc_tiles(const Shape& s) { return s.v == 1 ? (s.u + kTcRows - 1) / kTcRows : s.u * ((s.v + kTcRows - 1) / kTcRows); }
@@ -377,6 +567,22 @@ struct TcLayout {
   uint32_t stage_bytes = 0;
   size_t smem = 0, ws = 0;
 };
+
+// FP32 storage: stage = A tile + A_lo tile + X_hi / X_lo tile.
+TcLayout tc_layout_f32(const Shape& s, int64_t R) {
+  TcLayout L;
+  L.Rp = (int)round_up(R, 16);
+  L.ncols = 32;
+  while (L.ncols < 2 * L.Rp) L.ncols *= 2;
+  L.nkp = round_up(s.nk, kTcKf);
+  L.stage_bytes = (uint32_t)(2 * kTileAf + 2 * L.Rp * 128);
+  // about 110 KB of stages: two CTAs per SM (measured on 65536x16384, R = 8:
+  // 5.8 TB/s; one CTA with 5 stages 3.8, three with 2 stages 4.2)
+  L.stages = (int)std::max<int64_t>(2, std::min<int64_t>(6, (int64_t)(110 * 1024) / L.stage_bytes));
+  L.smem = 1024 + (size_t)L.stages * L.stage_bytes + (3 * (size_t)L.stages + 2) * 8;
+  L.ws = align_up((size_t)2 * L.Rp * L.nkp * 4, 256);
+  return L;
+}
 
 TcLayout tc_layout(const Shape& s, int64_t R) {
   TcLayout L;
@@ -400,6 +606,13 @@ TcLayout tc_layout(const Shape& s, int64_t R) {
 }  // namespace
 
 bool tmc_tc_supported(const Shape& s, int64_t R, tvc_dtype dt, const void* A, bool a16) {
+  if (dt == TVC_F32) {
+    // FP32 (tf32 pieces): the last mode only
+    if (R < 8 || R > 64 || s.v != 1 || s.mode < 1 || s.nk % 4 != 0) return false;
+    if (s.nk >= ((int64_t)1 << 31) || s.u >= ((int64_t)1 << 31)) return false;
+    if (!(A == nullptr ? a16 : aligned(A, 16))) return false;
+    return tc_tiles(s) >= device_sms();
+  }
   if (dt != TVC_BF16 || R < 8 || R > 64) return false;
   if (s.nk >= ((int64_t)1 << 31) || s.u >= ((int64_t)1 << 31) || s.v >= ((int64_t)1 << 31)) return false;
   if (s.v == 1) {
@@ -413,7 +626,48 @@ bool tmc_tc_supported(const Shape& s, int64_t R, tvc_dtype dt, const void* A, bo
   return tc_tiles(s) >= device_sms();  // enough 128-output tiles to fill the GPU
 }
 
-size_t tmc_tc_ws_bytes(const Shape& s, int64_t R) { return tc_layout(s, R).ws; }
+size_t tmc_tc_ws_bytes(const Shape& s, int64_t R, tvc_dtype dt) {
+  return dt == TVC_F32 ? tc_layout_f32(s, R).ws : tc_layout(s, R).ws;
+}
+
+tvc_status tmc_tc_launch_f32(const void* A, const Shape& s, const float* X, int64_t R, float* Y, double alpha,
+                             double beta, void* ws, size_t ws_bytes, cudaStream_t st) {
+  const TcLayout L = tc_layout_f32(s, R);
+  if (!ws || ws_bytes < L.ws || !aligned(ws, 256)) return TVC_ERR_WORKSPACE;
+  float* pieces = static_cast<float*>(ws);
+  CUtensorMap mapA, mapX;
+  if (!encode_f32_rows(&mapA, A, s.u, s.nk, s.nk, kTcRows) ||
+      !encode_f32_rows(&mapX, pieces, 2 * (int64_t)L.Rp, L.nkp, L.nkp, 2 * L.Rp))
+    return TVC_ERR_UNSUPPORTED;
+  static std::once_flag attr_once;
+  std::call_once(attr_once, [] {
+    cudaFuncSetAttribute(reinterpret_cast<const void*>(tmc_tc_f32_kernel),
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  });
+  const int64_t n = (int64_t)L.Rp * L.nkp;
+  const int sblocks = (int)std::min<int64_t>((n + 255) / 256, 4LL * device_sms());
+  tmc_tc_split_x_f32_kernel<<<sblocks, 256, 0, st>>>(X, pieces, R, s.nk, L.Rp, L.nkp);
+  TcArgs a;
+  a.Y = Y;
+  a.scales = nullptr;
+  a.u = s.u;
+  a.R = R;
+  a.upi0 = 1;
+  a.v = 1;
+  a.vt = 1;
+  a.Rp = L.Rp;
+  a.nkb = (int)(L.nkp / kTcKf);
+  a.stages = L.stages;
+  a.ncols = L.ncols;
+  a.stage_bytes = L.stage_bytes;
+  a.alpha = (float)alpha;
+  a.beta = (float)beta;
+  const int64_t tiles = tc_tiles(s);
+  if (tiles > 0x7FFFFFFF) return TVC_ERR_UNSUPPORTED;
+  tmc_tc_f32_kernel<<<(unsigned)tiles, kTcThreadsF, L.smem, st>>>(mapA, mapX, a);
+  count_launches(2);
+  return cuda_status(cudaGetLastError());
+}
 
 tvc_status tmc_tc_launch(const void* A, const Shape& s, const float* X, int64_t R, float* Y, const float* scales,
                          double alpha, double beta, void* ws, size_t ws_bytes, cudaStream_t st) {

@@ -245,3 +245,39 @@ def test_tmc_tensor_core_alpha_beta():
     tg.tmc(gu.to_dev(A), 1, gu.to_dev(X), Y=Yt, scales=gu.to_dev(scales), shape=dims, alpha=0.5, beta=-2.0)
     torch.cuda.synchronize()
     assert gu.rel_l2(Yt.cpu().numpy(), ref) <= 1e-5
+
+
+# FP32 storage along the last mode (n_k a multiple of 4): tf32 tensor-core
+# MMAs on A, its low part A - trunc(A) written by converter warps, and the
+# two parts of X; FP32 tolerance against the oracle.
+TC_F32_CASES = [((20480, 64), 8), ((19500, 200), 13), ((4, 5000, 1024), 16), ((2, 9781, 12), 33),
+                ((19457, 520), 64)]
+
+
+@pytest.mark.parametrize("dims,R", TC_F32_CASES,
+                         ids=lambda c: "x".join(map(str, c)) if isinstance(c, tuple) else str(c))
+def test_tmc_tensor_core_f32_last_mode(dims, R):
+    k = len(dims) - 1
+    A, Ao, _ = gu.inputs(dims, oracle.F32, seed=5)
+    X = mat(oracle.F32, R, dims[k], synth.stream_x(k), seed=6)
+    ref = oracle.tmc(Ao, k, X)
+    launches0 = tg.kernel_launches()
+    got = gpu_tmc(A, k, X, dims=dims)
+    torch.cuda.synchronize()
+    assert tg.kernel_launches() - launches0 == 2  # split of X + the tensor-core kernel
+    assert gu.rel_l2(got, ref) <= 1e-5, (dims, R, gu.rel_l2(got, ref))
+    import ctypes
+    code = ctypes.c_int(0)
+    assert tg.load_library().tvc_device_error(ctypes.byref(code), 1) == 0, code.value
+
+
+def test_tmc_tensor_core_f32_alpha_beta():
+    dims, R = (20000, 128), 24
+    A, Ao, _ = gu.inputs(dims, oracle.F32, seed=7)
+    X = mat(oracle.F32, R, 128, synth.stream_x(1), seed=8)
+    Y0 = synth.tensor("u32", 9, (20000, R)).astype(np.float32)
+    ref = oracle.tmc(Ao, 1, X, Y=Y0.astype(np.float64), alpha=0.5, beta=-2.0)
+    Yt = gu.to_dev(Y0)
+    tg.tmc(gu.to_dev(A), 1, gu.to_dev(X), Y=Yt, shape=dims, alpha=0.5, beta=-2.0)
+    torch.cuda.synchronize()
+    assert gu.rel_l2(Yt.cpu().numpy(), ref) <= 1e-5
