@@ -144,10 +144,12 @@ size_t tvc_workspace_size(int order, const int64_t* dims, int mode, tvc_dtype dt
  * at least as many 128-output tiles as SMs: X is split into three BF16
  * pieces (exact to binary32 precision; for mode 0 the slab scales are
  * folded into X first), every product of two BF16 values is exact, and the
- * MMAs accumulate in FP32.  FP32 storage along the last mode (n_mode a
- * multiple of 4, the same R and tile conditions) runs on the tensor cores
- * as well: tf32 MMAs on A and its low part A - trunc(A) against the two
- * parts of X, with products dropped below 2^-20 of |A X|.  The workspace
+ * MMAs accumulate in FP32.  FP32 storage with A 16-byte aligned runs on the
+ * tensor cores as well, along the last mode (n_mode a multiple of 4,
+ * 8 <= R <= 64) or along another mode (v a multiple of 4, v >= 32,
+ * 8 < R <= 64), with the same tile condition: tf32 MMAs on A and its low
+ * part A - trunc(A) against the two parts of X, with products dropped below
+ * 2^-20 of |A X|.  The workspace
  * holds the pieces of X (tmc_workspace_size includes them).
  * slab_scales: as for tvc_ex.  workspace: tmc_workspace_size(...) bytes (0
  * when the output columns fill the GPU without splitting n_mode).

@@ -191,6 +191,8 @@ struct TcArgs {
   float* Y;
   const float* scales;  // per slab (row i of the u x n_k x v view), nullable
   int64_t u, R, upi0, v, vt;  // vt: tiles of 128 along v (1 when v == 1)
+  const float* A;             // FP32 slabs (v > 1), read by the converter warps
+  int64_t nk;
   int Rp, nkb, stages, ncols;
   uint32_t stage_bytes;
   float alpha, beta;
@@ -337,6 +339,12 @@ constexpr int kTcKf = 32;                      // FP32 per stage along n_k: one 
 constexpr int kTileAf = kTcRows * kTcKf * 4;  // 16 KB
 
 constexpr uint32_t kTf32Mask = 0xFFFFE000u;
+// Slab (MN) kernel: shared-memory stages, and stages of each converter
+// thread's column in flight (1024^3 FP32 mode 1, R = 16, TB/s: 3 in flight /
+// 2 stages 4.89, 4 / 2 4.84, 3 / 3 4.45, 2 / 3 4.29, 1 / 2 3.70; R = 32 needs
+// the 2 stages to keep two CTAs per SM)
+constexpr int kStagesMN = 2;
+constexpr int kAheadMN = 3;
 
 __global__ void tmc_tc_split_x_f32_kernel(const float* __restrict__ X, float* __restrict__ pieces, int64_t R,
                                           int64_t nk, int64_t Rp, int64_t nkp) {
@@ -354,9 +362,38 @@ __host__ __device__ constexpr uint32_t tf32_idesc(uint32_t n) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((n >> 3) << 17) | ((uint32_t)(kTcRows >> 4) << 24);
 }
 
+// Component q (a compile-time constant after unrolling) of a float4.
+__device__ __forceinline__ float f4_at(const float4& f, int q) {
+  return q == 0 ? f.x : q == 1 ? f.y : q == 2 ? f.z : f.w;
+}
+
+// Two 4 x 4 blocks of a slab for one stage starting at row k0: rows
+// k0 + 4 c_r + i (i = 0..3) of four adjacent columns, row stride v; zero past
+// n_k or outside the slab.  Streamed: each value is read once.
+__device__ __forceinline__ void tc_load_blocks(float4 (&d)[2][4], const float* src, int64_t k0, int c0, int c1,
+                                               int64_t nk, int64_t v, bool cin) {
+#pragma unroll
+  for (int r = 0; r < 2; r++) {
+    const int64_t k = k0 + 4 * (r ? c1 : c0);
+    const float* p = src + k * v;
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+      d[r][i] = (cin && k + i < nk) ? __ldcs(reinterpret_cast<const float4*>(p)) : make_float4(0.f, 0.f, 0.f, 0.f);
+      p += v;
+    }
+  }
+}
+
 constexpr int kTcThreadsF = 192;  // producer warp, MMA warp, four converter / epilogue warps
 
-// Last mode of FP32 storage: rows m0 .. m0 + 127 of the u x n_k matrix A.
+// FP32 storage.  MN == false: rows m0 .. m0 + 127 of the u x n_k matrix A
+// (the last mode, K-major tiles; the TMA tile serves as the high part).
+// MN == true: columns l0 .. l0 + 127 of slab i.  The tf32 MMAs take K-major
+// operands, so the converter warps read the slab themselves, one column per
+// thread (each k a coalesced 128-byte load of the warp, one stage ahead in
+// registers), and write the high and low parts as K-major tiles: shared
+// memory sees no copy of A that is only read back to be transposed.
+template <bool MN>
 __global__ void __launch_bounds__(kTcThreadsF) tmc_tc_f32_kernel(const __grid_constant__ CUtensorMap mapA,
                                                                 const __grid_constant__ CUtensorMap mapX,
                                                                 const TcArgs a) {
@@ -371,7 +408,8 @@ __global__ void __launch_bounds__(kTcThreadsF) tmc_tc_f32_kernel(const __grid_co
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
   __shared__ int mma_ok;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t m0 = (int64_t)blockIdx.x * kTcRows;
+  const int64_t tile_i = MN ? (int64_t)blockIdx.x / a.vt : 0;
+  const int64_t m0 = MN ? ((int64_t)blockIdx.x % a.vt) * kTcRows : (int64_t)blockIdx.x * kTcRows;
   const uint32_t tile_x = 2u * (uint32_t)a.Rp * 128u;  // X_hi and X_lo rows, 128 bytes each
 
   if (threadIdx.x == 0) {
@@ -391,14 +429,14 @@ __global__ void __launch_bounds__(kTcThreadsF) tmc_tc_f32_kernel(const __grid_co
 
   if (warp == 0) {
     if (lane == 0) {  // producer
-      const uint32_t bytes = (uint32_t)kTileAf + tile_x;
+      const uint32_t bytes = (MN ? 0u : (uint32_t)kTileAf) + tile_x;
       int kb = 0;
       for (; kb < a.nkb; kb++) {
         const int st = kb % S;
         if (kb >= S && !mbar_wait(&empty[st], (uint32_t)((kb / S) - 1) & 1u, &g_tmc_tc_error, 1)) break;
         unsigned char* base = sm + (size_t)st * a.stage_bytes;
         mbar_arrive_expect_tx(&full[st], bytes);
-        tma_load_2d(base, &mapA, kb * kTcKf, (int)m0, &full[st]);
+        if constexpr (!MN) tma_load_2d(base, &mapA, kb * kTcKf, (int)m0, &full[st]);
         tma_load_2d(base + 2 * kTileAf, &mapX, kb * kTcKf, 0, &full[st]);
       }
       for (int q = 0; q < S && q < kb; q++) {
@@ -417,6 +455,8 @@ __global__ void __launch_bounds__(kTcThreadsF) tmc_tc_f32_kernel(const __grid_co
         const uint32_t base = smem_u32(sm + (size_t)st * a.stage_bytes);
 #pragma unroll
         for (int kk = 0; kk < kTcKf / 8; kk++) {
+          // K-major tiles: high part, low part, X; K step kk is 32 bytes
+          // along the rows
           const uint64_t ahi = sw128_kmajor_desc(base + kk * 32u);
           const uint64_t alo = sw128_kmajor_desc(base + (uint32_t)kTileAf + kk * 32u);
           const uint64_t bx = sw128_kmajor_desc(base + 2u * (uint32_t)kTileAf + kk * 32u);
@@ -429,25 +469,86 @@ __global__ void __launch_bounds__(kTcThreadsF) tmc_tc_f32_kernel(const __grid_co
       tc_commit(done);
     }
   } else {
-    // converters: A_lo of every stage, 128 threads x 8 chunks of 16 bytes
     const int t = threadIdx.x - 64;
-    for (int kb = 0; kb < a.nkb; kb++) {
-      const int st = kb % S;
-      if (!mbar_wait(&full[st], (uint32_t)(kb / S) & 1u, &g_tmc_tc_error, 5)) break;
-      unsigned char* base = sm + (size_t)st * a.stage_bytes;
+    if constexpr (MN) {
+      // thread t = 32 w + l: columns l0 + 4 l .. + 3 of slab i (rows 4 l ..
+      // 4 l + 3 of the K-major tiles) and, per stage, the 4-row blocks
+      // c_r = (2 w + r + l / 2) mod 8, r = 0, 1 (rows 4 c_r .. 4 c_r + 3 of the
+      // stage): 16-byte loads, a 4 x 4 transpose in registers, and 16-byte
+      // stores whose swizzled chunks c_r ^ (row % 8) differ across each 8 lanes.
+      // A ring of kAheadMN stages in registers keeps that many in flight.
+      const int w = t >> 5, l = t & 31;
+      const int64_t col = m0 + 4 * l;
+      const bool cin = col < a.v;  // v % 4 == 0: all four columns or none
+      const float* src = a.A + tile_i * a.nk * a.v + (cin ? col : 0);
+      const int c0 = (2 * w + (l >> 1)) & 7, c1 = (c0 + 1) & 7;
+      float4 buf[kAheadMN][2][4];
 #pragma unroll
-      for (int c = 0; c < kTileAf / 16 / 128; c++) {
-        const int off = (c * 128 + t) * 16;
-        const float4 v = *reinterpret_cast<const float4*>(base + off);
-        float4 lo;
-        lo.x = __fsub_rn(v.x, __uint_as_float(__float_as_uint(v.x) & kTf32Mask));
-        lo.y = __fsub_rn(v.y, __uint_as_float(__float_as_uint(v.y) & kTf32Mask));
-        lo.z = __fsub_rn(v.z, __uint_as_float(__float_as_uint(v.z) & kTf32Mask));
-        lo.w = __fsub_rn(v.w, __uint_as_float(__float_as_uint(v.w) & kTf32Mask));
-        *reinterpret_cast<float4*>(base + kTileAf + off) = lo;
+      for (int j = 0; j < kAheadMN; j++)
+        if (j < a.nkb) tc_load_blocks(buf[j], src, (int64_t)j * kTcKf, c0, c1, a.nk, a.v, cin);
+      bool ok = true;
+      for (int kb0 = 0; ok && kb0 < a.nkb; kb0 += kAheadMN) {
+#pragma unroll
+        for (int j = 0; j < kAheadMN; j++) {
+          const int kb = kb0 + j, st = kb % S;
+          if (!ok || kb >= a.nkb) break;
+          if (kb >= S && !mbar_wait(&empty[st], (uint32_t)((kb / S) - 1) & 1u, &g_tmc_tc_error, 5)) {
+            ok = false;
+            break;
+          }
+          unsigned char* base = sm + (size_t)st * a.stage_bytes;
+#pragma unroll
+          for (int r = 0; r < 2; r++) {
+            const int c = r ? c1 : c0;
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+              const float e0 = f4_at(buf[j][r][0], q), e1 = f4_at(buf[j][r][1], q);
+              const float e2 = f4_at(buf[j][r][2], q), e3 = f4_at(buf[j][r][3], q);
+              float4 hi, lo;
+              hi.x = __uint_as_float(__float_as_uint(e0) & kTf32Mask);
+              hi.y = __uint_as_float(__float_as_uint(e1) & kTf32Mask);
+              hi.z = __uint_as_float(__float_as_uint(e2) & kTf32Mask);
+              hi.w = __uint_as_float(__float_as_uint(e3) & kTf32Mask);
+              lo.x = __fsub_rn(e0, hi.x);
+              lo.y = __fsub_rn(e1, hi.y);
+              lo.z = __fsub_rn(e2, hi.z);
+              lo.w = __fsub_rn(e3, hi.w);
+              const int m = 4 * l + q;
+              const int dst = m * 128 + ((c ^ (m & 7)) << 4);  // 128-byte swizzle
+              *reinterpret_cast<float4*>(base + dst) = hi;
+              *reinterpret_cast<float4*>(base + kTileAf + dst) = lo;
+            }
+          }
+          if (kb + kAheadMN < a.nkb)
+            tc_load_blocks(buf[j], src, (int64_t)(kb + kAheadMN) * kTcKf, c0, c1, a.nk, a.v, cin);
+          if (!mbar_wait(&full[st], (uint32_t)(kb / S) & 1u, &g_tmc_tc_error, 5)) {  // X of the stage
+            ok = false;
+            break;
+          }
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the tensor cores
+          mbar_arrive(&conv[st]);
+        }
       }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the tensor cores
-      mbar_arrive(&conv[st]);
+    } else {
+      // A_lo of every stage, 128 threads x 8 chunks of 16 bytes
+      for (int kb = 0; kb < a.nkb; kb++) {
+        const int st = kb % S;
+        if (!mbar_wait(&full[st], (uint32_t)(kb / S) & 1u, &g_tmc_tc_error, 5)) break;
+        unsigned char* base = sm + (size_t)st * a.stage_bytes;
+#pragma unroll
+        for (int c = 0; c < kTileAf / 16 / 128; c++) {
+          const int off = (c * 128 + t) * 16;
+          const float4 v = *reinterpret_cast<const float4*>(base + off);
+          float4 lo;
+          lo.x = __fsub_rn(v.x, __uint_as_float(__float_as_uint(v.x) & kTf32Mask));
+          lo.y = __fsub_rn(v.y, __uint_as_float(__float_as_uint(v.y) & kTf32Mask));
+          lo.z = __fsub_rn(v.z, __uint_as_float(__float_as_uint(v.z) & kTf32Mask));
+          lo.w = __fsub_rn(v.w, __uint_as_float(__float_as_uint(v.w) & kTf32Mask));
+          *reinterpret_cast<float4*>(base + kTileAf + off) = lo;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the tensor cores
+        mbar_arrive(&conv[st]);
+      }
     }
   }
   __syncwarp();
@@ -457,9 +558,9 @@ __global__ void __launch_bounds__(kTcThreadsF) tmc_tc_f32_kernel(const __grid_co
     const int q4 = warp & 3;
     const bool ok = mbar_wait(done, 0u, &g_tmc_tc_error, 4) && mma_ok != 0;
     tc_fence_after();
-    const int64_t i = m0 + q4 * 32 + lane;
-    const bool live = i < a.u;
-    const float sc = (a.scales != nullptr && live) ? a.scales[i / a.upi0] : 1.0f;
+    const int64_t row = m0 + q4 * 32 + lane;
+    const int64_t i = MN ? tile_i : row;
+    const bool live = MN ? row < a.v : row < a.u;
     const uint32_t trow = tmem + ((uint32_t)(q4 * 32) << 16);
     for (int c0 = 0; c0 < a.Rp; c0 += 16) {
       float g0[16], g1[16];
@@ -470,9 +571,10 @@ __global__ void __launch_bounds__(kTcThreadsF) tmc_tc_f32_kernel(const __grid_co
         for (int q = 0; q < 16; q++) {
           const int64_t r = c0 + q;
           if (r < a.R) {
-            float out = __fmul_rn(__fmul_rn(__fadd_rn(g1[q], g0[q]), sc), a.alpha);
-            if (a.beta != 0.0f) out = __fmaf_rn(a.beta, a.Y[i * a.R + r], out);
-            a.Y[i * a.R + r] = out;
+            float out = __fmul_rn(__fadd_rn(g1[q], g0[q]), a.alpha);
+            const int64_t o = MN ? (i * a.R + r) * a.v + row : i * a.R + r;
+            if (a.beta != 0.0f) out = __fmaf_rn(a.beta, a.Y[o], out);
+            a.Y[o] = out;
           }
         }
       }
@@ -568,7 +670,7 @@ struct TcLayout {
   size_t smem = 0, ws = 0;
 };
 
-// FP32 storage: stage = A tile + A_lo tile + X_hi / X_lo tile.
+// FP32 storage: stage = A (high part) tile + A_lo tile + X_hi / X_lo tile.
 TcLayout tc_layout_f32(const Shape& s, int64_t R) {
   TcLayout L;
   L.Rp = (int)round_up(R, 16);
@@ -576,9 +678,11 @@ TcLayout tc_layout_f32(const Shape& s, int64_t R) {
   while (L.ncols < 2 * L.Rp) L.ncols *= 2;
   L.nkp = round_up(s.nk, kTcKf);
   L.stage_bytes = (uint32_t)(2 * kTileAf + 2 * L.Rp * 128);
-  // about 110 KB of stages: two CTAs per SM (measured on 65536x16384, R = 8:
-  // 5.8 TB/s; one CTA with 5 stages 3.8, three with 2 stages 4.2)
-  L.stages = (int)std::max<int64_t>(2, std::min<int64_t>(6, (int64_t)(110 * 1024) / L.stage_bytes));
+  // rows (TMA tiles of A): about 110 KB of stages, two CTAs per SM (measured
+  // on 65536x16384, R = 8: 5.8 TB/s; one CTA with 5 stages 3.8, three with 2
+  // stages 4.2).  Slabs (A in registers one stage ahead): kStagesMN stages.
+  L.stages = s.v > 1 ? kStagesMN
+                     : (int)std::max<int64_t>(2, std::min<int64_t>(6, (int64_t)(110 * 1024) / L.stage_bytes));
   L.smem = 1024 + (size_t)L.stages * L.stage_bytes + (3 * (size_t)L.stages + 2) * 8;
   L.ws = align_up((size_t)2 * L.Rp * L.nkp * 4, 256);
   return L;
@@ -607,9 +711,13 @@ TcLayout tc_layout(const Shape& s, int64_t R) {
 
 bool tmc_tc_supported(const Shape& s, int64_t R, tvc_dtype dt, const void* A, bool a16) {
   if (dt == TVC_F32) {
-    // FP32 (tf32 pieces): the last mode only
-    if (R < 8 || R > 64 || s.v != 1 || s.mode < 1 || s.nk % 4 != 0) return false;
-    if (s.nk >= ((int64_t)1 << 31) || s.u >= ((int64_t)1 << 31)) return false;
+    // FP32 (tf32 parts): rows of the last mode (TMA tiles, n_k % 4 == 0), or
+    // slabs at least 32 wide with v % 4 == 0 (16-byte loads by the converter
+    // warps) for R > 8 (at R = 8 the CUDA-core column kernel is faster there);
+    // A 16-byte aligned
+    if (R < 8 || R > 64) return false;
+    if (s.v == 1 ? (s.mode < 1 || s.nk % 4 != 0) : (s.v < 32 || s.v % 4 != 0 || R == 8)) return false;
+    if (s.nk >= ((int64_t)1 << 31) || s.u >= ((int64_t)1 << 31) || s.v >= ((int64_t)1 << 31)) return false;
     if (!(A == nullptr ? a16 : aligned(A, 16))) return false;
     return tc_tiles(s) >= device_sms();
   }
@@ -635,13 +743,18 @@ tvc_status tmc_tc_launch_f32(const void* A, const Shape& s, const float* X, int6
   const TcLayout L = tc_layout_f32(s, R);
   if (!ws || ws_bytes < L.ws || !aligned(ws, 256)) return TVC_ERR_WORKSPACE;
   float* pieces = static_cast<float*>(ws);
+  const bool mn = s.v > 1;
   CUtensorMap mapA, mapX;
-  if (!encode_f32_rows(&mapA, A, s.u, s.nk, s.nk, kTcRows) ||
-      !encode_f32_rows(&mapX, pieces, 2 * (int64_t)L.Rp, L.nkp, L.nkp, 2 * L.Rp))
+  if (!encode_f32_rows(&mapX, pieces, 2 * (int64_t)L.Rp, L.nkp, L.nkp, 2 * L.Rp)) return TVC_ERR_UNSUPPORTED;
+  if (mn)
+    mapA = mapX;  // unused: the converter warps read the slabs
+  else if (!encode_f32_rows(&mapA, A, s.u, s.nk, s.nk, kTcRows))
     return TVC_ERR_UNSUPPORTED;
   static std::once_flag attr_once;
   std::call_once(attr_once, [] {
-    cudaFuncSetAttribute(reinterpret_cast<const void*>(tmc_tc_f32_kernel),
+    cudaFuncSetAttribute(reinterpret_cast<const void*>(tmc_tc_f32_kernel<false>),
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    cudaFuncSetAttribute(reinterpret_cast<const void*>(tmc_tc_f32_kernel<true>),
                          cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
   });
   const int64_t n = (int64_t)L.Rp * L.nkp;
@@ -653,8 +766,10 @@ tvc_status tmc_tc_launch_f32(const void* A, const Shape& s, const float* X, int6
   a.u = s.u;
   a.R = R;
   a.upi0 = 1;
-  a.v = 1;
-  a.vt = 1;
+  a.v = s.v;
+  a.vt = (s.v + kTcRows - 1) / kTcRows;
+  a.A = static_cast<const float*>(A);
+  a.nk = s.nk;
   a.Rp = L.Rp;
   a.nkb = (int)(L.nkp / kTcKf);
   a.stages = L.stages;
@@ -664,7 +779,10 @@ tvc_status tmc_tc_launch_f32(const void* A, const Shape& s, const float* X, int6
   a.beta = (float)beta;
   const int64_t tiles = tc_tiles(s);
   if (tiles > 0x7FFFFFFF) return TVC_ERR_UNSUPPORTED;
-  tmc_tc_f32_kernel<<<(unsigned)tiles, kTcThreadsF, L.smem, st>>>(mapA, mapX, a);
+  if (mn)
+    tmc_tc_f32_kernel<true><<<(unsigned)tiles, kTcThreadsF, L.smem, st>>>(mapA, mapX, a);
+  else
+    tmc_tc_f32_kernel<false><<<(unsigned)tiles, kTcThreadsF, L.smem, st>>>(mapA, mapX, a);
   count_launches(2);
   return cuda_status(cudaGetLastError());
 }

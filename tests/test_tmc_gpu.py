@@ -8,6 +8,8 @@ FP64 values outside the float-float window are covered too.
 
 Tolerances (relative l2 over the output): FP64 and single-double 1e-12,
 FP32 and the narrow types (against the oracle on the same codes) 1e-5."""
+import ctypes
+
 import numpy as np
 import pytest
 import torch
@@ -247,17 +249,22 @@ def test_tmc_tensor_core_alpha_beta():
     assert gu.rel_l2(Yt.cpu().numpy(), ref) <= 1e-5
 
 
-# FP32 storage along the last mode (n_k a multiple of 4): tf32 tensor-core
-# MMAs on A, its low part A - trunc(A) written by converter warps, and the
-# two parts of X; FP32 tolerance against the oracle.
-TC_F32_CASES = [((20480, 64), 8), ((19500, 200), 13), ((4, 5000, 1024), 16), ((2, 9781, 12), 33),
-                ((19457, 520), 64)]
+# FP32 storage: tf32 tensor-core MMAs on A, its low part A - trunc(A)
+# written by converter warps, and the two parts of X; FP32 tolerance against
+# the oracle.  Last mode (n_k a multiple of 4, K-major tiles) and the other
+# modes (v a multiple of 4, MN-major tiles of four 32-wide boxes).
+# FP32: rows of the last mode (TMA tiles, n_k % 4 == 0, R >= 8) as for BF16;
+# other modes (R > 8, v >= 32 and v % 4 == 0, the slabs read by the converter
+# warps): a part-filled last tile, ragged n_k, order 4.
+TC_F32_CASES = [((20480, 64), 1, 8), ((19500, 200), 1, 13), ((4, 5000, 1024), 2, 16), ((2, 9781, 12), 2, 33),
+                ((19457, 520), 1, 64),
+                ((300, 20480), 0, 16), ((40, 96, 520), 1, 9), ((160, 33, 64), 1, 21), ((2, 80, 130, 128), 2, 64),
+                ((8, 64, 2432), 0, 24), ((160, 37, 52), 1, 12), ((8, 200, 70, 34), 1, 40), ((97, 300, 132), 1, 17)]
 
 
-@pytest.mark.parametrize("dims,R", TC_F32_CASES,
+@pytest.mark.parametrize("dims,k,R", TC_F32_CASES,
                          ids=lambda c: "x".join(map(str, c)) if isinstance(c, tuple) else str(c))
-def test_tmc_tensor_core_f32_last_mode(dims, R):
-    k = len(dims) - 1
+def test_tmc_tensor_core_f32(dims, k, R):
     A, Ao, _ = gu.inputs(dims, oracle.F32, seed=5)
     X = mat(oracle.F32, R, dims[k], synth.stream_x(k), seed=6)
     ref = oracle.tmc(Ao, k, X)
@@ -265,10 +272,10 @@ def test_tmc_tensor_core_f32_last_mode(dims, R):
     got = gpu_tmc(A, k, X, dims=dims)
     torch.cuda.synchronize()
     assert tg.kernel_launches() - launches0 == 2  # split of X + the tensor-core kernel
-    assert gu.rel_l2(got, ref) <= 1e-5, (dims, R, gu.rel_l2(got, ref))
-    import ctypes
     code = ctypes.c_int(0)
     assert tg.load_library().tvc_device_error(ctypes.byref(code), 1) == 0, code.value
+    assert code.value == 0, code.value  # no bounded wait ran out
+    assert gu.rel_l2(got, ref) <= 1e-5, (dims, R, gu.rel_l2(got, ref))
 
 
 def test_tmc_tensor_core_f32_alpha_beta():
