@@ -1,6 +1,7 @@
 // Host-side declarations shared by the translation units of the library.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -38,6 +39,13 @@ inline bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
 // becomes the graph's own allocation and free nodes.  bytes == 0 gives NULL.
 tvc_status stream_scratch_alloc(size_t bytes, cudaStream_t st, void** out);
 tvc_status stream_scratch_free(void* p, cudaStream_t st);
+
+// cuTensorMapEncodeTiled, looked up once through the runtime (no link to the
+// driver library); NULL when the driver does not offer it.
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled();
 
 // Number of SMs of the current device (cached per device).
 int device_sms();

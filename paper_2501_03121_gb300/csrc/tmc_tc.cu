@@ -593,14 +593,6 @@ __global__ void __launch_bounds__(kTcThreadsF) tmc_tc_f32_kernel(const __grid_co
 
 namespace tvcg {
 
-namespace {
-
-// cuTensorMapEncodeTiled, looked up once through the runtime (no link to the
-// driver library).
-using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
 EncodeTiledFn encode_tiled() {
   static std::once_flag once;
   static EncodeTiledFn fn = nullptr;
@@ -616,6 +608,8 @@ EncodeTiledFn encode_tiled() {
   });
   return fn;
 }
+
+namespace {
 
 // Row-major rows x cols BF16 matrix (row stride `stride` elements) read in
 // boxes of box_rows x 64 with the 128-byte swizzle; zero fill outside.

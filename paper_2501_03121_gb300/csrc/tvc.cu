@@ -26,6 +26,7 @@
 #include "common.cuh"
 #include "internal.h"
 #include "tma.cuh"
+#include "tvc_args.cuh"
 
 namespace tvcg {
 
@@ -37,31 +38,6 @@ __device__ int g_tvc_device_error = 0;
 constexpr int kThreads = 256;
 constexpr int kWarpsPerBlock = kThreads / kWarp;
 constexpr int kRB = 64;  // additions per accumulator between folds
-
-template <tvc_dtype DT>
-struct TvcArgs {
-  const typename Elem<DT>::T* A;
-  const void* x;        // FP64 for F64, FP32 otherwise
-  const XSplit* xs;     // F64: split x (workspace)
-  const float* scales;  // narrow types, nullable
-  void* y;
-  void* partial;
-  int64_t u, nk, v, uv, upi0, chunk, splits;
-  int mode0;
-  int plain;  // splits == 1, alpha == 1, beta == 0: y[o] = value
-  double alpha, beta;
-  const int* done;  // nullable: when *done != 0 the kernel returns at once
-};
-
-// Early exit of work queued behind a converged (or failed) power method.
-__device__ __forceinline__ bool skip(const int* done) {
-  return done != nullptr && *reinterpret_cast<const volatile int*>(done) != 0;
-}
-
-__device__ __forceinline__ XSplit ldxs(const XSplit* p) {
-  float2 f = __ldg(reinterpret_cast<const float2*>(p));
-  return XSplit{f.x, f.y};
-}
 
 // x entry of row j for the FP32 accumulators (slab scale folded in for k = 0).
 template <tvc_dtype DT>
@@ -103,22 +79,6 @@ __device__ __forceinline__ float out_scale(const TvcArgs<DT>& a, int64_t i) {
     if (!a.mode0 && a.scales) return __ldg(a.scales + i / a.upi0);
   }
   return 1.0f;
-}
-
-template <tvc_dtype DT>
-__device__ __forceinline__ void emit(const TvcArgs<DT>& a, int64_t s, int64_t o,
-                                     typename Elem<DT>::V val) {
-  using V = typename Elem<DT>::V;
-  if (a.plain) {
-    static_cast<V*>(a.y)[o] = val;
-  } else if (a.splits == 1) {
-    V* y = static_cast<V*>(a.y);
-    V r = (V)a.alpha * val;
-    if (a.beta != 0.0) r += (V)a.beta * y[o];
-    y[o] = r;
-  } else {
-    static_cast<V*>(a.partial)[s * a.uv + o] = val;
-  }
 }
 
 // ------------------------------------------------------------------ COLS --
@@ -1413,7 +1373,8 @@ enum Kind {
   K_ROWS_F64S = 6,
   K_ROWS_MULTI = 7,
   K_TILE_ASYNC = 8,
-  K_SLAB_ASYNC = 9
+  K_SLAB_ASYNC = 9,
+  K_F64_TILE = 10
 };
 
 struct Plan {
@@ -1425,6 +1386,7 @@ struct Plan {
   uint32_t tile_bytes = 0;
   size_t smem = 0;
   dim3 grid;
+  F64TileParams ft{};
   size_t ws_xs = 0, ws_partial = 0, ws_total = 0;
 };
 
@@ -1511,6 +1473,89 @@ static void plan_tile_async(Plan& p, const Shape& s, size_t es, bool f64acc, int
 // 16, 20, 24 (81% -> 33%, 80% -> 65%, 76% -> 49%) and for rows of <= 8.
 static bool f64_rows_by_tiles(int64_t nk) { return nk >= 9 && nk <= 27 && !(nk % 4 == 0 && nk >= 16); }
 
+// FP64 small slabs and short rows through the copy-engine tile kernel
+// (tvc_f64tile.cu).  G, the lanes per output, is the smallest power of two
+// that keeps a lane at <= 32 steps per output (the error model allows 64
+// products per compensated sum) and fits two stages of at least one pass of
+// outputs into a block's share of shared memory (two blocks per SM): with
+// fewer than ~16 steps per lane the per-output work (group reduction,
+// slots) measured 10-20% slower.  Tiles are up to 54 KB of whole passes
+// (v = 1) or whole slabs (v > 1: the count that leaves the fewest idle
+// lanes, and G raised while that leaves more than 15% of them idle).  Rows whose length is a multiple of 4 (8 or more) are copied as
+// 2-D boxes with a padded row of n_k + 2 elements (their plain starts fall
+// on 8 or fewer of the 16 shared-memory bank pairs); they need
+// G | n_k / 2 (no step reads the zero columns) and n_k + 2 <= 256 (the box
+// limit).  Rows of 4 measured faster in the grouped-row kernel.
+constexpr int64_t kFtTileMax = 54 * 1024;     // bytes of one tile
+constexpr int64_t kFtBlockSmem = 111 * 1024;  // shared memory of one block: two blocks per SM
+constexpr int kFtQMax = 32;                   // steps per lane and output
+
+static bool plan_f64_tile_g(Plan& p, const Shape& s, int sms, double min_util);
+static bool plan_f64_tile(Plan& p, const Shape& s, int sms) {
+  // slabs: the smallest G whose tiles keep >= 85% of the lanes busy, else
+  // the smallest G at all
+  return plan_f64_tile_g(p, s, sms, s.v > 1 ? 0.85 : 0.0) || (s.v > 1 && plan_f64_tile_g(p, s, sms, 0.0));
+}
+
+static bool plan_f64_tile_g(Plan& p, const Shape& s, int sms, double min_util) {
+  if (s.v >= 32 || s.nk < 2 || s.nk > 32 * kFtQMax) return false;
+  const bool pad = s.v == 1 && s.nk % 4 == 0;
+  if (pad && (s.nk < 8 || s.nk + 2 > 256 || s.u >= ((int64_t)1 << 30) || encode_tiled() == nullptr)) return false;
+  const int64_t S = s.nk * s.v;
+  const int64_t srow = pad ? s.nk + 2 : S;
+  for (int G = 1; G <= 32; G *= 2) {
+    if (pad && s.nk % (2 * G) != 0) break;
+    const int64_t Q = ceil_div(s.nk, G);
+    if (Q > kFtQMax) continue;
+    const int64_t OPP = 256 / G;
+    int64_t R = 0;
+    if (s.v == 1) {
+      if (OPP * srow * 8 > kFtTileMax) continue;
+      R = OPP * (kFtTileMax / (OPP * srow * 8));
+      if (pad && R > 256) R = R / 256 * 256;  // whole boxes of 256 rows
+    } else {
+      const int64_t rmax = kFtTileMax / (S * 8);
+      double best = -1.0;
+      for (int64_t r = 1; r <= rmax; r++) {
+        if ((r * S) % 2 != 0) continue;
+        const int64_t outs = r * s.v, passes = ceil_div(outs, OPP);
+        const double util = (double)outs / (double)(passes * OPP);
+        if (util >= best) {
+          best = util;
+          R = r;
+        }
+      }
+      if (R == 0) return false;  // slabs too large for a tile
+      if (best < min_util) continue;
+    }
+    // one tile (then the last) when u is smaller; padded rows keep whole
+    // boxes (rows past u arrive as zeros)
+    if (!pad) R = std::min<int64_t>(R, s.u);
+    const int npairs = (int)ceil_div(Q, 2);
+    const int64_t over = pad ? 0 : (2 * (int64_t)npairs * G - s.nk) * s.v;  // padded steps past a tile's end
+    const int64_t stride = (int64_t)align_up((size_t)(R * srow * 8 + over * 8), 128) + 128;
+    const int64_t fixed = (int64_t)G * npairs * 16 + 16 * 8;  // x pieces and barriers
+    const int NS = (int)std::min<int64_t>(8, (kFtBlockSmem - fixed) / stride);
+    if (NS < 2) continue;
+    p.kind = K_F64_TILE;
+    p.ft.R = (int)R;
+    p.ft.G = G;
+    p.ft.NS = NS;
+    p.ft.npairs = npairs;
+    p.ft.ntiles = ceil_div(s.u, R);
+    p.ft.stage_bytes = (uint32_t)stride;
+    p.ft.srow = (int)srow;
+    p.ft.box_rows = pad ? (int)std::min<int64_t>(R, 256) : 0;
+    p.ft.w16 = (G == 1 && s.v == 1 && srow % 2 == 0) ? 1 : 0;
+    p.smem = f64tile_smem_bytes(p.ft);
+    p.splits = 1;
+    p.chunk = s.nk;
+    p.grid = dim3((unsigned)std::max<int64_t>(1, std::min<int64_t>(p.ft.ntiles, (int64_t)sms * 2)), 1);
+    return true;
+  }
+  return false;
+}
+
 static Plan make_plan_impl(const Shape& s, tvc_dtype dt, const void* A, bool allow_staged) {
   Plan p;
   const bool f64acc = (dt == TVC_F64 || dt == TVC_F32D);  // FP64 arithmetic (float-float kernels)
@@ -1527,6 +1572,8 @@ static Plan make_plan_impl(const Shape& s, tvc_dtype dt, const void* A, bool all
     p.chunk = ceil_div(ceil_div(s.nk, splits), 8) * 8;
     p.splits = ceil_div(s.nk, p.chunk);
     p.grid = dim3((unsigned)ceil_div(threads, kThreads), (unsigned)p.splits);
+  } else if (dt == TVC_F64 && aligned(A, 16) && s.v < 32 && plan_f64_tile(p, s, sms)) {
+    // FP64 small slabs and short rows: the copy-engine tile kernel.
   } else if (s.v == 1 && !f64acc && allow_staged && aligned(A, 16) &&
              s.nk <= 8 * 32 * (int64_t)pick_vec(dt, s.nk, A, 4) && s.u >= 8) {
     // Staged short rows: tiles of R = 8*RW whole rows through shared memory.
@@ -1785,7 +1832,7 @@ static void launch_rows_f64s_vec(const Plan& p, const TvcArgs<DT>& a, cudaStream
 }
 
 template <tvc_dtype DT>
-static void launch_main(const Plan& p, const TvcArgs<DT>& a, cudaStream_t st) {
+static bool launch_main(const Plan& p, const TvcArgs<DT>& a, cudaStream_t st) {
   switch (p.kind) {
     case K_COLS: {
       if constexpr (DT == TVC_F64) {
@@ -1847,12 +1894,16 @@ static void launch_main(const Plan& p, const TvcArgs<DT>& a, cudaStream_t st) {
       tvc_tile_async_kernel<DT><<<p.grid, kThreads, p.smem, st>>>(a, p.R, p.ntiles, p.vec16);
       break;
     }
+    case K_F64_TILE:
+      if constexpr (DT == TVC_F64) return f64tile_launch(a, p.ft, p.grid, st);
+      break;
     case K_TILE: {
       opt_in_smem(reinterpret_cast<const void*>(tvc_tile_kernel<DT>), 64 * 1024);
       tvc_tile_kernel<DT><<<p.grid, kThreads, p.smem, st>>>(a, p.R, p.vec16);
       break;
     }
   }
+  return true;
 }
 
 template <tvc_dtype DT>
@@ -1884,7 +1935,7 @@ static tvc_status run(const void* A, const Shape& s, const void* x, void* y, con
     tvc_split_x_kernel<<<blocks, 256, 0, st>>>(static_cast<const double*>(x), reinterpret_cast<XSplit*>(w), s.nk, done);
   }
   if (p.splits > 1) a.partial = w + p.ws_xs;
-  launch_main<DT>(p, a, st);
+  if (!launch_main<DT>(p, a, st)) return TVC_ERR_UNSUPPORTED;
   count_launches((kF64Acc<DT> ? 1 : 0) + 1 + (p.splits > 1 ? 1 : 0));
   if (p.splits > 1) {
     using V = typename Elem<DT>::V;
@@ -1934,6 +1985,8 @@ extern "C" tvc_status tvc_device_error(int* code_out, int clear) {
   }
   if (tmc_tc_device_error(&w, clear) != TVC_OK) return TVC_ERR_CUDA;
   if (v == 0 && w != 0) v = 10 + w;  // the tensor-core TMC kernel's waits
+  if (f64tile_device_error(&w, clear) != TVC_OK) return TVC_ERR_CUDA;
+  if (v == 0 && w != 0) v = 20 + w;  // the FP64 tile kernel's waits
   if (code_out) *code_out = v;
   return v ? TVC_ERR_TIMEOUT : TVC_OK;
 }

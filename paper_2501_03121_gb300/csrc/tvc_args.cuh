@@ -1,0 +1,73 @@
+// Arguments of the TVC kernels and the store of one result, shared by the
+// translation units that hold TVC kernels (tvc.cu, tvc_f64tile.cu).
+#pragma once
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace tvcg {
+
+template <tvc_dtype DT>
+struct TvcArgs {
+  const typename Elem<DT>::T* A;
+  const void* x;        // FP64 for F64, FP32 otherwise
+  const XSplit* xs;     // F64: split x (workspace)
+  const float* scales;  // narrow types, nullable
+  void* y;
+  void* partial;
+  int64_t u, nk, v, uv, upi0, chunk, splits;
+  int mode0;
+  int plain;  // splits == 1, alpha == 1, beta == 0: y[o] = value
+  double alpha, beta;
+  const int* done;  // nullable: when *done != 0 the kernel returns at once
+};
+
+// Early exit of work queued behind a converged (or failed) power method.
+__device__ __forceinline__ bool skip(const int* done) {
+  return done != nullptr && *reinterpret_cast<const volatile int*>(done) != 0;
+}
+
+__device__ __forceinline__ XSplit ldxs(const XSplit* p) {
+  float2 f = __ldg(reinterpret_cast<const float2*>(p));
+  return XSplit{f.x, f.y};
+}
+
+template <tvc_dtype DT>
+__device__ __forceinline__ void emit(const TvcArgs<DT>& a, int64_t s, int64_t o,
+                                     typename Elem<DT>::V val) {
+  using V = typename Elem<DT>::V;
+  if (a.plain) {
+    static_cast<V*>(a.y)[o] = val;
+  } else if (a.splits == 1) {
+    V* y = static_cast<V*>(a.y);
+    V r = (V)a.alpha * val;
+    if (a.beta != 0.0) r += (V)a.beta * y[o];
+    y[o] = r;
+  } else {
+    static_cast<V*>(a.partial)[s * a.uv + o] = val;
+  }
+}
+
+// FP64 small slabs and short rows through the copy engine (tvc_f64tile.cu).
+// A tile is R whole slabs (R*S elements, S = n_k*v, R*S even so that every
+// tile starts on a 16-byte boundary; or R padded rows); G lanes share one output, each taking
+// the products j = p, p + G, ... (2*npairs of them, zero x pieces past n_k).
+struct F64TileParams {
+  int R;                // slabs per tile
+  int G;                // lanes per output (1, 2, 4, 8, 16 or 32)
+  int NS;               // stages of the shared-memory ring
+  int npairs;           // ceil(ceil(n_k / G) / 2)
+  int64_t ntiles;       // ceil(u / R)
+  uint32_t stage_bytes; // stride between stages: R*srow*8 plus slack for the padded reads
+  int srow;             // elements between consecutive slabs of a tile in shared memory
+  int box_rows;         // > 0: rows (v = 1) copied as 2-D boxes of box_rows x srow (srow > n_k)
+  int w16;              // G == 1, v == 1, rows on 16-byte boundaries: paired 16-byte loads
+};
+// Shared memory of one block of that kernel for the given parameters.
+size_t f64tile_smem_bytes(const F64TileParams& prm);
+// Returns false (nothing launched) when the 2-D copy view cannot be made.
+bool f64tile_launch(const TvcArgs<TVC_F64>& a, const F64TileParams& prm, dim3 grid, cudaStream_t st);
+// Sticky error word of its bounded waits (cleared when clear != 0).
+tvc_status f64tile_device_error(int* code_out, int clear);
+
+}  // namespace tvcg

@@ -52,6 +52,37 @@ def test_tvc_every_mode(dims, code):
         assert err <= gu.TOL[code], (dims, k, err)
 
 
+# FP64 small slabs and short rows through the copy-engine tile kernel: rows
+# of odd length or of length 2 mod 4 for every lanes-per-output count
+# (G = 1 .. 32), rows of length 0 mod 4 (padded 2-D boxes, zero rows past
+# the tensor), slabs with 1 < v < 32, tensors of fewer slabs than one tile,
+# ragged last tiles and odd element counts (the last element copied by hand)
+F64_TILE_SHAPES = [(1001, 3), (4001, 2), (2003, 31), (999, 63), (2001, 175), (301, 333), (257, 767), (5, 10),
+                   (3, 7), (1, 9), (1003, 6), (777, 3, 5), (2001, 9, 2), (101, 31, 31), (37, 40, 20),
+                   (1999, 4, 3), (3, 5, 17), (1001, 8), (257, 16), (999, 24), (1001, 4), (77, 128), (3, 8),
+                   (5, 20), (2049, 40), (301, 2, 12)]
+
+
+@pytest.mark.parametrize("dims", F64_TILE_SHAPES, ids=lambda d: "x".join(map(str, d)))
+def test_fp64_tile_kernel_shapes(dims):
+    import ctypes
+    lib = tg.load_library()
+    code = ctypes.c_int(-1)
+    lib.tvc_device_error(ctypes.byref(code), 1)
+    A = synth.tensor("u64", 9, dims)
+    mode = len(dims) - 1 if len(dims) == 2 else 1
+    for k in sorted({mode, 0, len(dims) - 1}):
+        x = synth.vector("u64", 9, synth.stream_x(k), dims[k])
+        got = gu.gpu_tvc(tg, A, k, x)
+        assert gu.rel_l2(got, oracle.tvc(A, k, x)) <= 1e-12, (dims, k)
+    rng = np.random.default_rng(sum(dims))
+    Ai = rng.integers(-1000, 1000, size=dims).astype(np.float64)
+    xi = rng.integers(-1000, 1000, size=dims[mode]).astype(np.float64)
+    assert np.array_equal(gu.gpu_tvc(tg, Ai, mode, xi), oracle.tvc(Ai, mode, xi)), dims
+    torch.cuda.synchronize()
+    assert lib.tvc_device_error(ctypes.byref(code), 0) == 0 and code.value == 0
+
+
 @pytest.mark.parametrize("dims", [(3, 50, 64), (5, 1000), (4, 100, 7), (300, 40)])
 def test_narrow_storage_error_vs_source(dims):
     src = synth.tensor("lognormal", 0, dims).astype(np.float32)
@@ -339,7 +370,8 @@ def cancelling(dims, mode, seed, kappa=1e6, lanes=1):
 # 1 < v < 32, small slabs (persistent tiles), unaligned small slabs
 CANCEL_CASES = [((40, 37, 66), 1), ((3, 2000, 64), 1), ((300, 4096), 1), ((3, 300000), 1), ((3000, 40), 1),
                 ((3000, 13), 1), ((2001, 175), 1), ((40, 600, 12), 1), ((500, 19, 19), 1), ((5, 3000, 7), 1),
-                ((9, 33, 130), 0), ((6, 5, 4, 3), 2)]
+                ((9, 33, 130), 0), ((6, 5, 4, 3), 2), ((999, 63), 1), ((101, 31, 31), 1), ((301, 333), 1),
+                ((2049, 8), 1), ((301, 128), 1)]
 
 
 @pytest.mark.parametrize("dims,mode", CANCEL_CASES, ids=lambda c: "x".join(map(str, c)) if isinstance(c, tuple) else str(c))
