@@ -12,6 +12,7 @@ struct TvcArgs {
   const typename Elem<DT>::T* A;
   const void* x;        // FP64 for F64, FP32 otherwise
   const XSplit* xs;     // F64: split x (workspace)
+  const XSplit* xs1;    // F64 rows of odd length: xs shifted by one entry (xs1[j + 1] = xs[j], zeros at both ends)
   const float* scales;  // narrow types, nullable
   void* y;
   void* partial;

@@ -60,7 +60,10 @@ def test_tvc_every_mode(dims, code):
 F64_TILE_SHAPES = [(1001, 3), (4001, 2), (2003, 31), (999, 63), (2001, 175), (301, 333), (257, 767), (5, 10),
                    (3, 7), (1, 9), (1003, 6), (777, 3, 5), (2001, 9, 2), (101, 31, 31), (37, 40, 20),
                    (1999, 4, 3), (3, 5, 17), (1001, 8), (257, 16), (999, 24), (1001, 4), (77, 128), (3, 8),
-                   (5, 20), (2049, 40), (301, 2, 12)]
+                   (5, 20), (2049, 40), (301, 2, 12),
+                   # FP64 rows of odd length beyond the tile kernel: 16-byte
+                   # pairs from each row's first 16-byte boundary (split n_k too)
+                   (7, 1001), (4, 4097), (3, 100001), (9, 2049), (2, 30623)]
 
 
 @pytest.mark.parametrize("dims", F64_TILE_SHAPES, ids=lambda d: "x".join(map(str, d)))
@@ -371,7 +374,7 @@ def cancelling(dims, mode, seed, kappa=1e6, lanes=1):
 CANCEL_CASES = [((40, 37, 66), 1), ((3, 2000, 64), 1), ((300, 4096), 1), ((3, 300000), 1), ((3000, 40), 1),
                 ((3000, 13), 1), ((2001, 175), 1), ((40, 600, 12), 1), ((500, 19, 19), 1), ((5, 3000, 7), 1),
                 ((9, 33, 130), 0), ((6, 5, 4, 3), 2), ((999, 63), 1), ((101, 31, 31), 1), ((301, 333), 1),
-                ((2049, 8), 1), ((301, 128), 1)]
+                ((2049, 8), 1), ((301, 128), 1), ((7, 4097), 1), ((3, 100001), 1)]
 
 
 @pytest.mark.parametrize("dims,mode", CANCEL_CASES, ids=lambda c: "x".join(map(str, c)) if isinstance(c, tuple) else str(c))
