@@ -475,9 +475,10 @@ size_t dhopm_workspace_size(int parts, const int64_t* starts, int order, const i
  * engine's producer waited for a free buffer, 2: a consumer waited for a
  * tile, 3: draining copies at exit; 11-14 the same for the tensor-core
  * tensor-matrix contraction: 11 producer, 12 MMA issuer, 13 drain, 14 the
- * epilogue's wait for the last MMAs) and lets the kernel finish (a kernel
- * of the tensor-core path also releases its tensor memory); its results
- * are then invalid.  Synchronises the device; returns
+ * epilogue's wait for the last MMAs; 21-23 the same three for the FP64
+ * small-slab / short-row kernel, 31-33 for the narrow-storage slab kernel)
+ * and lets the kernel finish (a kernel of the tensor-core path also
+ * releases its tensor memory); its results are then invalid.  Synchronises the device; returns
  * TVC_ERR_TIMEOUT when a code is set (and clears it when clear != 0). */
 tvc_status tvc_device_error(int* code_out, int clear);
 

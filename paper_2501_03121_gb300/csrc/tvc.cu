@@ -39,16 +39,6 @@ constexpr int kThreads = 256;
 constexpr int kWarpsPerBlock = kThreads / kWarp;
 constexpr int kRB = 64;  // additions per accumulator between folds
 
-// x entry of row j for the FP32 accumulators (slab scale folded in for k = 0).
-template <tvc_dtype DT>
-__device__ __forceinline__ float xval(const TvcArgs<DT>& a, int64_t j) {
-  float xv = __ldg(static_cast<const float*>(a.x) + j);
-  if constexpr (kNarrow<DT>) {
-    if (a.mode0 && a.scales) xv = __fmul_rn(xv, __ldg(a.scales + j));
-  }
-  return xv;
-}
-
 // x entries j .. j+VEC-1 (j a multiple of VEC): 16-byte loads when x is
 // 16-byte aligned and no per-row slab scale applies (k > 0), else one by one.
 template <tvc_dtype DT, int VEC>
@@ -70,15 +60,6 @@ __device__ __forceinline__ void xvec(const TvcArgs<DT>& a, int64_t j, float (&xq
   }
 #pragma unroll
   for (int e = 0; e < VEC; e++) xq[e] = xval(a, j + e);
-}
-
-// Scale of output row i (k > 0): all elements of an output share slab i / upi0.
-template <tvc_dtype DT>
-__device__ __forceinline__ float out_scale(const TvcArgs<DT>& a, int64_t i) {
-  if constexpr (kNarrow<DT>) {
-    if (!a.mode0 && a.scales) return __ldg(a.scales + i / a.upi0);
-  }
-  return 1.0f;
 }
 
 // ------------------------------------------------------------------ COLS --
@@ -1403,7 +1384,8 @@ enum Kind {
   K_ROWS_MULTI = 7,
   K_TILE_ASYNC = 8,
   K_SLAB_ASYNC = 9,
-  K_F64_TILE = 10
+  K_F64_TILE = 10,
+  K_SLAB_TILE = 11
 };
 
 struct Plan {
@@ -1416,6 +1398,7 @@ struct Plan {
   size_t smem = 0;
   dim3 grid;
   F64TileParams ft{};
+  SlabTileParams st{};
   int xs_shift = 0;  // FP64 rows of odd length with 16-byte pairs: the shifted split x too
   size_t ws_xs = 0, ws_partial = 0, ws_total = 0;
 };
@@ -1586,6 +1569,45 @@ static bool plan_f64_tile_g(Plan& p, const Shape& s, int sms, double min_util) {
   return false;
 }
 
+// Large slabs whose rows are whole 16-byte pieces (v * element size = 16,
+// 32, 64 or 128 bytes: BF16 / F16 v = 8, 16; E4M3 v = 16; FP32 v = 4, 8,
+// 16), FP32 accumulators: the copy-engine slab kernel (tvc_slabtile.cu).
+// Tiles of up to 32 KB of rows (at most 64 rows per thread), the rows of a
+// slab split when the slabs alone give fewer than 8 work items per SM.
+constexpr int64_t kStTileMax = 32 * 1024;
+constexpr int64_t kStBlockSmem = 111 * 1024;
+
+static bool plan_slab_tile(Plan& p, const Shape& s, tvc_dtype dt, int sms) {
+  const int64_t rb = s.v * (int64_t)elem_size(dt);
+  if (s.v < 2 || s.v >= 32 || rb % 16 != 0 || s.nk < 256) return false;
+  const int CPR = (int)(rb / 16);
+  if (CPR != 1 && CPR != 2 && CPR != 4 && CPR != 8) return false;
+  const int64_t P = 256 / CPR;
+  int64_t TR = std::min<int64_t>(kStTileMax / rb, 64 * P);
+  const int64_t target = (int64_t)sms * 8;
+  int64_t splits = 1;
+  if (s.u < target) splits = std::min(ceil_div(target, s.u), std::max<int64_t>(1, s.nk / TR));
+  p.chunk = ceil_div(s.nk, splits);
+  p.splits = ceil_div(s.nk, p.chunk);
+  TR = std::min<int64_t>(TR, p.chunk);
+  const int64_t stride = (int64_t)align_up((size_t)(TR * rb), 128);
+  const int64_t part = (int64_t)align_up((size_t)8 * s.v * 4, 16);
+  const int NS = (int)std::min<int64_t>(8, (kStBlockSmem - part - 128) / stride);
+  if (NS < 2) return false;
+  p.kind = K_SLAB_TILE;
+  p.st.TR = (int)TR;
+  p.st.NS = NS;
+  p.st.CPR = CPR;
+  p.st.splits = p.splits;
+  p.st.chunk = p.chunk;
+  p.st.nitems = s.u * p.splits;
+  p.st.stage_bytes = (uint32_t)stride;
+  p.st.part_bytes = (uint32_t)part;
+  p.smem = slabtile_smem_bytes(p.st);
+  p.grid = dim3((unsigned)std::max<int64_t>(1, std::min<int64_t>(p.st.nitems, (int64_t)sms * 2)), 1);
+  return true;
+}
+
 static Plan make_plan_impl(const Shape& s, tvc_dtype dt, const void* A, bool allow_staged) {
   Plan p;
   const bool f64acc = (dt == TVC_F64 || dt == TVC_F32D);  // FP64 arithmetic (float-float kernels)
@@ -1707,6 +1729,8 @@ static Plan make_plan_impl(const Shape& s, tvc_dtype dt, const void* A, bool all
     p.chunk = ceil_div(ceil_div(s.nk, splits), group) * group;
     p.splits = ceil_div(s.nk, p.chunk);
     p.grid = dim3((unsigned)ceil_div(s.u, rows_per_block), (unsigned)p.splits);
+  } else if (!f64acc && aligned(A, 16) && plan_slab_tile(p, s, dt, sms)) {
+    // large slabs of whole 16-byte rows: the copy-engine slab kernel
   } else if (S > 512 &&
              (dt == TVC_E4M3 || ((dt == TVC_BF16 || dt == TVC_F16) && s.v % 2 == 0) ||
               (dt == TVC_F32 && s.v % 4 == 0)) &&
@@ -1943,6 +1967,10 @@ static bool launch_main(const Plan& p, const TvcArgs<DT>& a, cudaStream_t st) {
     case K_F64_TILE:
       if constexpr (DT == TVC_F64) return f64tile_launch(a, p.ft, p.grid, st);
       break;
+    case K_SLAB_TILE:
+      if constexpr (DT == TVC_F32 || DT == TVC_BF16 || DT == TVC_F16 || DT == TVC_E4M3)
+        slabtile_launch(a, p.st, p.grid, st);
+      break;
     case K_TILE: {
       opt_in_smem(reinterpret_cast<const void*>(tvc_tile_kernel<DT>), 64 * 1024);
       tvc_tile_kernel<DT><<<p.grid, kThreads, p.smem, st>>>(a, p.R, p.vec16);
@@ -2037,6 +2065,8 @@ extern "C" tvc_status tvc_device_error(int* code_out, int clear) {
   if (v == 0 && w != 0) v = 10 + w;  // the tensor-core TMC kernel's waits
   if (f64tile_device_error(&w, clear) != TVC_OK) return TVC_ERR_CUDA;
   if (v == 0 && w != 0) v = 20 + w;  // the FP64 tile kernel's waits
+  if (slabtile_device_error(&w, clear) != TVC_OK) return TVC_ERR_CUDA;
+  if (v == 0 && w != 0) v = 30 + w;  // the slab tile kernel's waits
   if (code_out) *code_out = v;
   return v ? TVC_ERR_TIMEOUT : TVC_OK;
 }

@@ -1,5 +1,6 @@
 // Arguments of the TVC kernels and the store of one result, shared by the
-// translation units that hold TVC kernels (tvc.cu, tvc_f64tile.cu).
+// translation units that hold TVC kernels (tvc.cu, tvc_f64tile.cu,
+// tvc_slabtile.cu).
 #pragma once
 
 #include "common.cuh"
@@ -31,6 +32,25 @@ __device__ __forceinline__ bool skip(const int* done) {
 __device__ __forceinline__ XSplit ldxs(const XSplit* p) {
   float2 f = __ldg(reinterpret_cast<const float2*>(p));
   return XSplit{f.x, f.y};
+}
+
+// x entry of row j for the FP32 accumulators (slab scale folded in for k = 0).
+template <tvc_dtype DT>
+__device__ __forceinline__ float xval(const TvcArgs<DT>& a, int64_t j) {
+  float xv = __ldg(static_cast<const float*>(a.x) + j);
+  if constexpr (kNarrow<DT>) {
+    if (a.mode0 && a.scales) xv = __fmul_rn(xv, __ldg(a.scales + j));
+  }
+  return xv;
+}
+
+// Scale of output row i (k > 0): all elements of an output share slab i / upi0.
+template <tvc_dtype DT>
+__device__ __forceinline__ float out_scale(const TvcArgs<DT>& a, int64_t i) {
+  if constexpr (kNarrow<DT>) {
+    if (!a.mode0 && a.scales) return __ldg(a.scales + i / a.upi0);
+  }
+  return 1.0f;
 }
 
 template <tvc_dtype DT>
@@ -70,5 +90,24 @@ size_t f64tile_smem_bytes(const F64TileParams& prm);
 bool f64tile_launch(const TvcArgs<TVC_F64>& a, const F64TileParams& prm, dim3 grid, cudaStream_t st);
 // Sticky error word of its bounded waits (cleared when clear != 0).
 tvc_status f64tile_device_error(int* code_out, int clear);
+
+// Large slabs whose rows are whole 16-byte pieces, FP32 accumulators
+// (tvc_slabtile.cu): work items are (slab, split of its rows), tiles of TR
+// rows; CPR = v * sizeof(element) / 16 pieces per row (1, 2, 4 or 8).
+struct SlabTileParams {
+  int TR;                // rows per tile
+  int NS;                // stages of the shared-memory ring
+  int CPR;               // 16-byte pieces per row
+  int64_t nitems;        // u * splits
+  int64_t splits, chunk; // splits of n_k and rows per split
+  uint32_t stage_bytes;  // stride between stages
+  uint32_t part_bytes;   // per-warp column sums (8 * v floats, rounded to 16 bytes)
+};
+size_t slabtile_smem_bytes(const SlabTileParams& prm);
+void slabtile_launch(const TvcArgs<TVC_F32>& a, const SlabTileParams& prm, dim3 grid, cudaStream_t st);
+void slabtile_launch(const TvcArgs<TVC_BF16>& a, const SlabTileParams& prm, dim3 grid, cudaStream_t st);
+void slabtile_launch(const TvcArgs<TVC_F16>& a, const SlabTileParams& prm, dim3 grid, cudaStream_t st);
+void slabtile_launch(const TvcArgs<TVC_E4M3>& a, const SlabTileParams& prm, dim3 grid, cudaStream_t st);
+tvc_status slabtile_device_error(int* code_out, int clear);
 
 }  // namespace tvcg

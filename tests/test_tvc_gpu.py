@@ -35,6 +35,10 @@ SHAPES = [
     # (ragged last tiles, a single partial tile), and the neighbouring
     # lengths that stay with the grouped-row kernel
     (1001, 10), (777, 19), (513, 22), (257, 27), (300, 12), (100, 9), (600, 16), (600, 8),
+    # large slabs whose rows are whole 16-byte pieces (the copy-engine slab
+    # kernel for FP32 and the narrow types): ragged tiles, one slab split
+    # over its rows, mode 0 of a matrix (slab scales folded into x)
+    (7, 1000, 8), (1, 4096, 16), (33, 300, 16), (4096, 16), (5, 4099, 4),
 ]
 CODES = [oracle.F64, oracle.F32, oracle.BF16, oracle.E4M3, oracle.F16]
 
@@ -213,6 +217,22 @@ def test_e4m3_columns_with_large_and_nonfinite_x(dims):
         assert np.array_equal(np.isfinite(got), np.isfinite(ref)), (dims, k)
 
 
+@pytest.mark.parametrize("dims", [(3, 600, 16), (7, 1000, 16)], ids=lambda d: "x".join(map(str, d)))
+def test_e4m3_nan_codes_in_slabs(dims):
+    """E4M3 slabs (decoded with integer operations): a NaN code (S.1111.111)
+    makes exactly the outputs it feeds NaN, as in the oracle's decode."""
+    src = synth.tensor("lognormal", 5, dims).astype(np.float32)
+    codes, scales = oracle.quantise(src, oracle.E4M3)
+    flat = codes.reshape(-1)
+    flat[[5, 16 * 37 + 3, 16 * 600 + 15]] = [0x7F, 0xFF, 0x7F]
+    x = gu.vec(oracle.E4M3, dims[1], synth.stream_x(1))
+    ref = oracle.tvc(codes, 1, x, scales=scales)
+    got = gu.gpu_tvc(tg, codes, 1, x, scales)
+    assert np.array_equal(np.isnan(got), np.isnan(ref))
+    fin = ~np.isnan(ref)
+    assert gu.rel_l2(got[fin], ref[fin]) <= 1e-5
+
+
 def test_bad_arguments_raise():
     A = gu.to_dev(np.zeros((3, 4)))
     with pytest.raises(ValueError):
@@ -288,13 +308,15 @@ def test_full_size_sweep_sampled(dims, code):
 
 
 def test_staged_kernel_waits_never_time_out():
-    """The TMA-staged row kernel bounds every wait and records a timeout in a
-    sticky device word; after a run over many tiles the word must be 0."""
+    """The copy-engine kernels (staged rows, FP64 tiles, slab tiles) bound
+    every wait and record a timeout in a sticky device word; after runs over
+    many tiles the word must be 0."""
     import ctypes
     lib = tg.load_library()
     code = ctypes.c_int(-1)
     lib.tvc_device_error(ctypes.byref(code), 1)  # clear
-    for dims, dt in (((200000, 40), "u32"), ((4096, 128), "u32"), ((30001, 8), "u32")):
+    for dims, dt in (((200000, 40), "u32"), ((4096, 128), "u32"), ((30001, 8), "u32"), ((64, 4096, 8), "u32"),
+                     ((999, 63), "u64"), ((3000, 8), "u64")):
         A = synth.tensor(dt, 3, dims)
         x = synth.vector(dt, 4, 2, dims[1])
         got = gu.gpu_tvc(tg, A, 1, x)
