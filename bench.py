@@ -794,6 +794,15 @@ def run_case(argv):
 
 def main(argv=None):
     argv = sys.argv[1:] if argv is None else list(argv)
+    # Tensors through torch's expandable segments (physical memory mapped in
+    # 2 MB granules): after the workloads' earlier allocations and frees, a
+    # fresh multi-GB tensor could otherwise be backed by small pages, and a
+    # contraction that walks every row of the whole tensor at once (mode 0
+    # of 979^3: 979 rows 7.6 MB apart in flight) lost 30% of its bandwidth
+    # to address-translation misses (4410 against 6290 GB/s).  Takes effect
+    # only when set before torch's first CUDA allocation; a setting of the
+    # caller's own is kept.
+    os.environ.setdefault("PYTORCH_CUDA_ALLOC_CONF", "expandable_segments:True")
     if argv and argv[0] == "--case":
         return run_case(argv[1:])
     ap = argparse.ArgumentParser()
