@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(kThreads) tvc_cols_kernel(const TvcArgs<DT> a)
   using T = typename E::T;
   const int64_t o = ((int64_t)blockIdx.x * kThreads + threadIdx.x) * VEC;
   if (o >= a.uv) return;
-  const int64_t i = o / a.v;
+  const int64_t i = div_v(a, o);
   const int64_t l = o - i * a.v;
   const int64_t j0 = (int64_t)blockIdx.y * a.chunk;
   const int64_t j1 = min(a.nk, j0 + a.chunk);
@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(kThreads) tvc_cols_async_kernel(const TvcArgs<
   const int64_t o = ((int64_t)blockIdx.x * kThreads + threadIdx.x) * VEC;
   const bool active = o < a.uv;
   const int64_t oo = active ? o : 0;
-  const int64_t i = oo / a.v;
+  const int64_t i = div_v(a, oo);
   const int64_t l = oo - i * a.v;
   const int64_t j0 = (int64_t)blockIdx.y * a.chunk;
   const int64_t j1 = min(a.nk, j0 + a.chunk);
@@ -2003,6 +2003,9 @@ static tvc_status run(const void* A, const Shape& s, const void* x, void* y, con
   a.alpha = alpha;
   a.beta = beta;
   a.done = done;
+  a.vmag = 0;
+  a.vsh = -1;
+  if (s.uv < ((int64_t)1 << 32) && s.v < ((int64_t)1 << 32)) div_magic((uint32_t)s.v, &a.vmag, &a.vsh);
   char* w = static_cast<char*>(ws);
   if (kF64Acc<DT>) {
     a.xs = reinterpret_cast<const XSplit*>(w);

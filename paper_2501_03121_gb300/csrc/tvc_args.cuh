@@ -22,7 +22,30 @@ struct TvcArgs {
   int plain;  // splits == 1, alpha == 1, beta == 0: y[o] = value
   double alpha, beta;
   const int* done;  // nullable: when *done != 0 the kernel returns at once
+  uint32_t vmag;    // u*v < 2^32: o / v = (umulhi(o, vmag) + o) >> vsh (vsh < 0: divide)
+  int vsh;
 };
+
+// Magic multiplier and shift of a 32-bit divisor d >= 1 (Granlund and
+// Montgomery, division by invariant integers): for every 32-bit n,
+// n / d = (umulhi(n, m) + n) >> s with s = ceil(log2 d) and
+// m = floor(2^32 (2^s - d) / d) + 1, the sum taken in 64 bits.
+inline void div_magic(uint32_t d, uint32_t* m, int* s) {
+  int k = 0;
+  while (k < 32 && (uint64_t(1) << k) < d) k++;
+  *s = k;
+  *m = (uint32_t)((((uint64_t)1 << 32) * ((uint64_t(1) << k) - d)) / d + 1);
+}
+
+// o / v for an output index o of the contraction (v the trailing size).
+template <tvc_dtype DT>
+__device__ __forceinline__ int64_t div_v(const TvcArgs<DT>& a, int64_t o) {
+  if (a.vsh >= 0) {
+    const uint32_t n = (uint32_t)o;
+    return (int64_t)(((uint64_t)__umulhi(n, a.vmag) + n) >> a.vsh);
+  }
+  return o / a.v;
+}
 
 // Early exit of work queued behind a converged (or failed) power method.
 __device__ __forceinline__ bool skip(const int* done) {

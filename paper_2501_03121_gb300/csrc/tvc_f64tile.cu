@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(kFtThreads, 2) tvc_f64tile_kernel(const TvcArg
         r = oc;
         l = 0;
       } else {
-        r = oc / v;
+        r = (int)div_v(a, oc);
         l = oc - r * v;
       }
       const double* const ob_base = tile + r * SR + l;  // element (r, 0, l)
