@@ -39,6 +39,9 @@ SHAPES = [
     # kernel for FP32 and the narrow types): ragged tiles, one slab split
     # over its rows, mode 0 of a matrix (slab scales folded into x)
     (7, 1000, 8), (1, 4096, 16), (33, 300, 16), (4096, 16), (5, 4099, 4),
+    # columns with short contractions (n_k <= 32, v >= 32): odd and even v,
+    # ragged thread tails, n_k of 1 .. 32
+    (13, 13, 13, 13), (10, 10, 10, 10), (3, 32, 67), (5, 1, 99), (31, 97), (2, 7, 1000),
 ]
 CODES = [oracle.F64, oracle.F32, oracle.BF16, oracle.E4M3, oracle.F16]
 
@@ -119,7 +122,8 @@ def test_integer_inputs_bit_exact_f64(dims):
 
 # shapes reaching the column, slab (1 < v < 32, large slabs), small-slab
 # (tile), odd short-row (8-byte loads) and even short-row kernels
-WINDOW_SHAPES = [(40, 37, 66), (500, 19, 19), (40, 600, 12), (3000, 13), (2001, 175), (300, 40), (1001, 10), (777, 22)]
+WINDOW_SHAPES = [(40, 37, 66), (500, 19, 19), (40, 600, 12), (3000, 13), (2001, 175), (300, 40), (1001, 10), (777, 22),
+                 (13, 13, 13, 13), (10, 10, 10, 10)]
 
 
 @pytest.mark.parametrize("dims", WINDOW_SHAPES, ids=lambda d: "x".join(map(str, d)))
@@ -393,7 +397,7 @@ def cancelling(dims, mode, seed, kappa=1e6, lanes=1):
 # split n_k, long rows and their split, short rows with 16-byte (even n_k)
 # and 8-byte loads (odd n_k, slots kernel with G = 32), large slabs with
 # 1 < v < 32, small slabs (persistent tiles), unaligned small slabs
-CANCEL_CASES = [((40, 37, 66), 1), ((3, 2000, 64), 1), ((300, 4096), 1), ((3, 300000), 1), ((3000, 40), 1),
+CANCEL_CASES = [((13, 13, 13, 13), 1), ((10, 10, 10, 10), 0), ((40, 37, 66), 1), ((3, 2000, 64), 1), ((300, 4096), 1), ((3, 300000), 1), ((3000, 40), 1),
                 ((3000, 13), 1), ((2001, 175), 1), ((40, 600, 12), 1), ((500, 19, 19), 1), ((5, 3000, 7), 1),
                 ((9, 33, 130), 0), ((6, 5, 4, 3), 2), ((999, 63), 1), ((101, 31, 31), 1), ((301, 333), 1),
                 ((2049, 8), 1), ((301, 128), 1), ((7, 4097), 1), ((3, 100001), 1)]
