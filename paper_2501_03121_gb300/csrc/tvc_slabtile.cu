@@ -8,7 +8,7 @@
 // the products (every thread issuing 16-byte copies of 8 KB tiles, two block
 // barriers per tile, an x entry from global memory per row, and a serial sum
 // over 64-128 row phases per slab).  Here:
-//   * one producer lane copies tiles of up to 32 KB of consecutive rows of a
+//   * one producer lane copies tiles of up to 48 KB of consecutive rows of a
 //     slab with cp.async.bulk into an NS-stage shared-memory ring (full /
 //     empty mbarriers; every wait is bounded, and a block that saw a wait
 //     give up records it and finishes with single-try waits, so it cannot
