@@ -801,8 +801,9 @@ def main(argv=None):
     # of 979^3: 979 rows 7.6 MB apart in flight) lost 30% of its bandwidth
     # to address-translation misses (4410 against 6290 GB/s).  Takes effect
     # only when set before torch's first CUDA allocation; a setting of the
-    # caller's own is kept.
-    os.environ.setdefault("PYTORCH_CUDA_ALLOC_CONF", "expandable_segments:True")
+    # caller's own (under either name) is kept.
+    if "PYTORCH_ALLOC_CONF" not in os.environ and "PYTORCH_CUDA_ALLOC_CONF" not in os.environ:
+        os.environ["PYTORCH_ALLOC_CONF"] = "expandable_segments:True"
     if argv and argv[0] == "--case":
         return run_case(argv[1:])
     ap = argparse.ArgumentParser()
