@@ -145,6 +145,55 @@ __device__ void blk_tvc(const float* __restrict__ A, int64_t u, int64_t nk, int6
   }
 }
 
+// The power method's two passes over A (v >= 2): where v is even and A is
+// 8-byte aligned each thread takes two adjacent outputs and loads pairs,
+// twice the bytes in flight per thread for the same sixteen rows (a block
+// of the register-held contraction streams at the rate its bytes in flight
+// allow); otherwise blk_tvc.
+__device__ void blk_tvc_pass(const float* __restrict__ A, int64_t u, int64_t nk, int64_t v,
+                             const float* __restrict__ x, float* __restrict__ y, int G) {
+  if (v % 2 != 0 || (reinterpret_cast<uintptr_t>(A) & 7) != 0) {
+    blk_tvc(A, u, nk, v, x, y, G);
+    return;
+  }
+  const int64_t uv2 = u * v / 2;  // output pairs
+  int64_t q2 = threadIdx.x;
+  if (q2 >= uv2) return;
+  const int64_t v2 = v / 2;
+  int64_t i = q2 / v2, l = 2 * (q2 - i * v2);
+  const int64_t di = kBBT / v2, dl = 2 * (kBBT - di * v2);
+  for (; q2 < uv2; q2 += kBBT) {
+    const float* p = A + i * nk * v + l;
+    float a0 = 0.0f, a1 = 0.0f;
+    int64_t jj = 0;
+    for (; jj + 16 <= nk; jj += 16, p += 16 * v) {
+      float2 av[16];
+#pragma unroll
+      for (int q = 0; q < 16; q++) av[q] = __ldcs(reinterpret_cast<const float2*>(p + q * v));
+#pragma unroll
+      for (int q = 0; q < 16; q++) {
+        const float xv = __ldg(x + jj + q);
+        a0 = __fmaf_rn(av[q].x, xv, a0);
+        a1 = __fmaf_rn(av[q].y, xv, a1);
+      }
+    }
+    for (; jj < nk; jj++, p += v) {
+      const float2 av = __ldcs(reinterpret_cast<const float2*>(p));
+      const float xv = __ldg(x + jj);
+      a0 = __fmaf_rn(av.x, xv, a0);
+      a1 = __fmaf_rn(av.y, xv, a1);
+    }
+    y[i * v + l] = a0;
+    y[i * v + l + 1] = a1;
+    i += di;
+    l += dl;
+    if (l >= v) {
+      l -= v;
+      i++;
+    }
+  }
+}
+
 // gA[(i*nk + j)*v + l] = gy[i*v + l] * x[j] over slabs i in [i0, i1) and
 // rows j in [j0, j1), with coalesced stores: threads own columns l (v >= 32)
 // or positions q = j*v + l of the slab (v < 32, whole slabs).
@@ -419,9 +468,9 @@ __global__ void __launch_bounds__(kBBT) hopm_batched_kernel(const HItem* __restr
           int64_t rest2 = 1;
           for (int m = 2; m < d; m++) rest2 *= n[m];
           if (j == 0)
-            blk_tvc(it.A, n[0], n[1], rest2, it.x[1], S1, it.gsel[1]);  // T = A x_1 x_1
+            blk_tvc_pass(it.A, n[0], n[1], rest2, it.x[1], S1, it.gsel[1]);  // T = A x_1 x_1
           else
-            blk_tvc(it.A, 1, n[0], N / n[0], it.x[0], S1, it.gsel[0]);  // W_1 = A x_0 x_0
+            blk_tvc_pass(it.A, 1, n[0], N / n[0], it.x[0], S1, it.gsel[0]);  // W_1 = A x_0 x_0
           __syncthreads();
           const float* wvec = it.x[2];
           if (d > 3) {
