@@ -1727,8 +1727,11 @@ static Plan make_plan_impl(const Shape& s, tvc_dtype dt, const void* A, bool all
     // FP64 rows whose split x (8 bytes an entry) outgrows L1, enough rows to
     // fill the GPU: segments of about 4096 entries, so that the blocks
     // working on one segment (the grid runs rows fastest) share its pieces
-    // of x in L1 (30623-element rows: 77% -> 82% of the copy peak).
-    if (f64acc && splits == 1 && s.nk * (int64_t)sizeof(XSplit) > 160 * 1024) splits = ceil_div(s.nk, 4096);
+    // of x in L1 (30623-element rows: 77% -> 82% of the copy peak); not when
+    // the segments' partial sums would pass 16 MB of workspace.
+    if (f64acc && splits == 1 && s.nk * (int64_t)sizeof(XSplit) > 160 * 1024 &&
+        s.u * ceil_div(s.nk, 4096) * (int64_t)sizeof(double) <= 16 * 1024 * 1024)
+      splits = ceil_div(s.nk, 4096);
     p.chunk = ceil_div(ceil_div(s.nk, splits), group) * group;
     p.splits = ceil_div(s.nk, p.chunk);
     p.grid = dim3((unsigned)ceil_div(s.u, rows_per_block), (unsigned)p.splits);
