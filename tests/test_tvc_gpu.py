@@ -31,9 +31,9 @@ SHAPES = [
     # types, 4, 2 or 1 columns per thread): v = 16, 12, 7, 31 and 2, ragged
     # n_k, split n_k
     (3, 600, 16), (2, 300, 12), (5, 3000, 7), (3, 700, 31), (6, 4099, 2),
-    # FP64 rows of 9 .. 27 elements through shared-memory tiles of 256 rows
-    # (ragged last tiles, a single partial tile), and the neighbouring
-    # lengths that stay with the grouped-row kernel
+    # short rows of 8 .. 27 elements (FP64: the copy-engine tile kernel,
+    # padded 2-D boxes for lengths 0 mod 4; single-double: shared-memory
+    # tiles or the grouped-row kernel), ragged last tiles, one partial tile
     (1001, 10), (777, 19), (513, 22), (257, 27), (300, 12), (100, 9), (600, 16), (600, 8),
     # large slabs whose rows are whole 16-byte pieces (the copy-engine slab
     # kernel for FP32 and the narrow types): ragged tiles, one slab split
@@ -393,10 +393,12 @@ def cancelling(dims, mode, seed, kappa=1e6, lanes=1):
     return A, (X[0] if lanes == 1 else X)
 
 
-# one shape per FP64 kernel (mode in brackets): columns (v >= 32) and their
-# split n_k, long rows and their split, short rows with 16-byte (even n_k)
-# and 8-byte loads (odd n_k, slots kernel with G = 32), large slabs with
-# 1 < v < 32, small slabs (persistent tiles), unaligned small slabs
+# one shape per FP64 kernel (mode in brackets): columns (v >= 32, short and
+# long n_k) and their split n_k, long rows and their split, odd long rows
+# (16-byte pairs from each row's boundary, L1-sized segments), short rows
+# and small slabs through the copy-engine tile kernel (G = 1 .. 16, padded
+# rows of 8 and 128), large slabs with 1 < v < 32, unaligned tensors (the
+# f64_unaligned store: the kernels that need no 16-byte alignment)
 CANCEL_CASES = [((13, 13, 13, 13), 1), ((10, 10, 10, 10), 0), ((40, 37, 66), 1), ((3, 2000, 64), 1), ((300, 4096), 1), ((3, 300000), 1), ((3000, 40), 1),
                 ((3000, 13), 1), ((2001, 175), 1), ((40, 600, 12), 1), ((500, 19, 19), 1), ((5, 3000, 7), 1),
                 ((9, 33, 130), 0), ((6, 5, 4, 3), 2), ((999, 63), 1), ((101, 31, 31), 1), ((301, 333), 1),
