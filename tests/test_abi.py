@@ -81,6 +81,34 @@ def test_workspace_size_query(lib):
     assert lib.tvc_workspace_size(2, bad, 0, 0) == 0
 
 
+def _align256(n):
+    return (n + 255) // 256 * 256
+
+
+def test_workspace_of_fp64_row_plans(lib):
+    """Host planning of FP64 rows, through the workspace query (no GPU):
+    rows of odd length >= 1024 read 16-byte pairs against a second, shifted
+    copy of the split x (n_k + 2 entries); rows whose split x outgrows L1
+    (n_k * 8 > 160 KB) run in segments of about 4096 entries with their
+    partial sums in the workspace, unless those would pass 16 MB."""
+    lib.tvc_workspace_size.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
+    lib.tvc_workspace_size.restype = ctypes.c_size_t
+    F64 = 0
+    xs = lambda nk: _align256(nk * 8)  # noqa: E731  the split x (two floats per entry)
+    # odd rows of 4097 elements, 100000 rows (no split of n_k): split x and its shifted copy
+    odd = (ctypes.c_int64 * 2)(100000, 4097)
+    assert lib.tvc_workspace_size(2, odd, 1, F64) == xs(4097) + _align256(4099 * 8)
+    even = (ctypes.c_int64 * 2)(100000, 4096)
+    assert lib.tvc_workspace_size(2, even, 1, F64) == xs(4096)
+    # 30623 x 30623 mode 1: 8 segments of the rows, partials 8 x 30623 doubles
+    t1 = (ctypes.c_int64 * 2)(30623, 30623)
+    got = lib.tvc_workspace_size(2, t1, 1, F64)
+    assert got == xs(30623) + _align256((30623 + 2) * 8) + _align256(8 * 30623 * 8)
+    # a million such rows: 8 segments would need 64 MB of partials, so no segments
+    big = (ctypes.c_int64 * 2)(1000000, 30623)
+    assert lib.tvc_workspace_size(2, big, 1, F64) == xs(30623) + _align256((30623 + 2) * 8)
+
+
 def test_tmc_validation_without_gpu(lib):
     P, I, D, Z, L = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t, ctypes.c_int64
     lib.tmc.argtypes = [P, I, P, I, P, L, P, I, P, D, D, P, Z, P]
